@@ -1,0 +1,312 @@
+"""Plain FP64 CPU oracle for ACCORD-FBS (HP-ACCORD, Sec 3).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct
+reference that the CUDA library is graded against.  Only the test-suite, the
+package smoke check and the benchmark's CPU-baseline leg may import it; the
+library never calls it and has no CPU fallback.
+
+Notation follows the paper: X is n x p (rows are samples), S = X^T X / n,
+Omega is p x p and asymmetric, g(Omega) = 1/2 tr(Omega^T Omega S) (Eq. 3.4),
+h(Omega) = -log det Omega_D + lambda ||Omega||_1 (Eq. 3.4), f = g + h (Eq. 3.2).
+
+Every array here is float64; numpy's matmul and symmetric eigensolver serve as
+library primitives.  Nothing is blocked, fused or reordered beyond what the
+definitions and Algorithm 1 state.
+
+Readings of the paper taken here (each listed in the design notes):
+  * lambda penalises every entry, the diagonal included (Eq. 3.2; the diagonal
+    prox of Eq. 3.5 carries tau*lambda).  `penalize_diag=False` drops it from
+    the diagonal only.
+  * The line-search inner product is <Delta, grad g(Omega^t)> (the proof of
+    Thm 3.3 writes the gradient; Algorithm 1's printed "g" is a typo).
+  * Since g is quadratic, g(Omega+) - g(Omega) - <Delta, grad g> equals
+    ||Delta X^T||_F^2 / (2n) exactly, so the sufficient-decrease test is
+    evaluated as ||Y+ - Y||^2 / n <= ||Delta||^2 / tau.  The printed form is
+    computed alongside and returned in the log for comparison.
+  * grad g does not depend on tau, so it is formed once per outer iteration.
+  * tau_0 = 1, beta = 1/2, restart at tau_0 every outer iteration unless
+    `tau_warm` (then min(tau_0, tau_{t-1}/beta)); beta == 1 is the fixed-step
+    variant (every trial accepted).
+  * Omega^0 = I.  Stopping: the KKT residual r(Omega^t) <= tol, checked before
+    step t is taken; r is the max-abs entry of the minimum-norm element of the
+    subdifferential of Eq. 3.3.
+  * Diagonal root of Eq. 3.5 written in the cancellation-free form when
+    b = y - tau*lambda < 0 (algebraically identical).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+OK, NOT_CONVERGED, EBACKTRACK, ENONFINITE = 0, 1, -4, -3
+
+
+# ----------------------------------------------------------------- basics ---
+
+def sample_covariance(X: np.ndarray) -> np.ndarray:
+    """S = X^T X / n (Sec 2, sample covariance of the centred data matrix)."""
+    X = np.asarray(X, dtype=np.float64)
+    return X.T @ X / X.shape[0]
+
+
+def smooth_g(Omega: np.ndarray, X: np.ndarray) -> float:
+    """g(Omega) = 1/2 tr(Omega^T Omega S) = ||Omega X^T||_F^2 / (2n) (Eq. 3.4)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = Omega @ X.T
+    return float(np.sum(Y * Y)) / (2.0 * X.shape[0])
+
+
+def grad_g(Omega: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """grad g(Omega) = Omega S, formed in the two steps Y = Omega X^T and
+    (1/n) Y X (Remark after Thm 3.3; Sec 3.3)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = Omega @ X.T
+    return Y @ X / X.shape[0]
+
+
+def diag_entries(Omega: np.ndarray, row0: int = 0) -> np.ndarray:
+    """Entries omega_ii of a block of rows [row0, row0 + m) of Omega."""
+    m = Omega.shape[0]
+    idx = np.arange(m)
+    return Omega[idx, row0 + idx]
+
+
+def objective(Omega: np.ndarray, X: np.ndarray, lam: float, penalize_diag: bool = True) -> float:
+    """f(Omega) = -sum log omega_ii + 1/2 tr(Omega^T Omega S) + lambda ||Omega||_1
+    (Eq. 3.2).  +inf outside dom f (some omega_ii <= 0)."""
+    d = np.diag(Omega)
+    if np.any(d <= 0):
+        return math.inf
+    lam_d = lam if penalize_diag else 0.0
+    off = np.abs(Omega).sum() - np.abs(d).sum()
+    return smooth_g(Omega, X) - float(np.sum(np.log(d))) + lam * off + lam_d * float(d.sum())
+
+
+def soft_threshold(x: np.ndarray, a: float) -> np.ndarray:
+    """S_a(x) = (|x| - a)_+ sign(x) (Eq. 3.5)."""
+    return np.sign(x) * np.maximum(np.abs(x) - a, 0.0)
+
+
+def diag_prox(y: np.ndarray, tau: float, lam_d: float) -> np.ndarray:
+    """Diagonal update of Eq. 3.5: the positive root of w^2 - b w - tau = 0 with
+    b = y - tau*lambda, i.e. w = (b + sqrt(b^2 + 4 tau)) / 2; for b < 0 the
+    equal value 2 tau / (sqrt(b^2 + 4 tau) - b) is used."""
+    b = y - tau * lam_d
+    root = np.sqrt(b * b + 4.0 * tau)
+    return np.where(b >= 0, 0.5 * (b + root), 2.0 * tau / (root - b))
+
+
+def prox(A: np.ndarray, tau: float, lam: float, lam_d: float, row0: int = 0) -> np.ndarray:
+    """Backward step of Eq. 3.5 applied to A = Omega - tau * grad g(Omega):
+    soft-threshold off the diagonal, log-barrier root on it.  `row0` places a
+    block of rows [row0, row0 + m) inside the full matrix."""
+    out = soft_threshold(A, tau * lam)
+    m = A.shape[0]
+    idx = np.arange(m)
+    out[idx, row0 + idx] = diag_prox(A[idx, row0 + idx], tau, lam_d)
+    return out
+
+
+def kkt_residual(Omega: np.ndarray, G: np.ndarray, lam: float, lam_d: float, row0: int = 0) -> float:
+    """max_ij of the minimum-norm element of the subdifferential of f (Eq. 3.3,
+    with z_ii = 1 and z_ij in [-1, 1] at zero entries):
+      diagonal            |G_ii - 1/omega_ii + lambda_d|
+      omega_ij != 0       |G_ij + lambda sign(omega_ij)|
+      omega_ij == 0       max(|G_ij| - lambda, 0)."""
+    R = np.where(Omega != 0, np.abs(G + lam * np.sign(Omega)), np.maximum(np.abs(G) - lam, 0.0))
+    m = Omega.shape[0]
+    idx = np.arange(m)
+    d = Omega[idx, row0 + idx]
+    R[idx, row0 + idx] = np.abs(G[idx, row0 + idx] - 1.0 / d + lam_d)
+    return float(R.max()) if R.size else 0.0
+
+
+def lipschitz(X: np.ndarray) -> float:
+    """L = sigma_max(S) = lambda_max(X X^T) / n (Sec 3.2); the n x n Gram has
+    the same nonzero spectrum as S."""
+    X = np.asarray(X, dtype=np.float64)
+    K = X @ X.T / X.shape[0]
+    return float(np.linalg.eigvalsh(K)[-1])
+
+
+# ------------------------------------------------------------ Algorithm 1 ---
+
+@dataclasses.dataclass
+class FitResult:
+    Omega: np.ndarray
+    status: int
+    iters: int                 # accepted steps taken
+    trials: int                # prox evaluations (accepted + rejected)
+    L: float
+    f: list                    # f(Omega^t), t = 0..iters
+    kkt: list                  # r(Omega^t), t = 0..iters
+    tau: list                  # accepted tau_t, t = 0..iters-1
+    ntrials: list              # trials spent on step t
+    nnz: list                  # off-diagonal nonzeros of Omega^t
+    delta_fro: list            # ||Omega^{t+1} - Omega^t||_F
+    margin: list               # accepted test: ||Delta||^2/tau - ||Y+ - Y||^2/n
+    printed_form_agrees: list  # per trial: printed Alg. 1 test gives the same verdict
+
+
+def fit(X: np.ndarray, lam: float, *, tau0: float = 1.0, beta: float = 0.5, tau_warm: bool = False,
+        max_iter: int = 500, max_backtracks: int = 60, kkt_tol: float = 1e-8,
+        penalize_diag: bool = True, Omega0: np.ndarray | None = None, L: float | None = None) -> FitResult:
+    """ACCORD-FBS with backtracking (Algorithm 1, update Eq. 3.5)."""
+    X = np.asarray(X, dtype=np.float64)
+    n, p = X.shape
+    lam_d = lam if penalize_diag else 0.0
+    if L is None:
+        L = lipschitz(X)
+    if tau0 <= 0:
+        tau0 = 1.0 / L
+    Omega = np.eye(p) if Omega0 is None else np.array(Omega0, dtype=np.float64)
+    Y = Omega @ X.T
+    G = Y @ X / n
+    g = float(np.sum(Y * Y)) / (2.0 * n)
+
+    res = FitResult(Omega, NOT_CONVERGED, 0, 0, L, [], [], [], [], [], [], [], [])
+    t = 0
+    tau_prev = tau0
+    while True:
+        d = np.diag(Omega)
+        f = g - float(np.sum(np.log(d))) + lam * (np.abs(Omega).sum() - d.sum()) + lam_d * float(d.sum())
+        r = kkt_residual(Omega, G, lam, lam_d)
+        res.f.append(f)
+        res.kkt.append(r)
+        res.nnz.append(int(np.count_nonzero(Omega)) - int(np.count_nonzero(d)))
+        if not (math.isfinite(f) and math.isfinite(r)):
+            res.status = ENONFINITE
+            break
+        if r <= kkt_tol:
+            res.status = OK
+            break
+        if t >= max_iter:
+            res.status = NOT_CONVERGED
+            break
+        tau = min(tau0, tau_prev / beta) if (tau_warm and t > 0) else tau0
+        accepted = False
+        for k in range(max_backtracks + 1):
+            res.trials += 1
+            A = Omega - tau * G                      # forward step
+            Op = prox(A, tau, lam, lam_d)            # backward step, Eq. 3.5
+            Delta = Op - Omega
+            Yp = Op @ X.T
+            d2 = float(np.sum(Delta * Delta))
+            dy2 = float(np.sum((Yp - Y) ** 2))
+            gp = float(np.sum(Yp * Yp)) / (2.0 * n)
+            ok_diff = dy2 / n <= d2 / tau
+            ok_printed = gp <= g + float(np.sum(Delta * G)) + d2 / (2.0 * tau)
+            res.printed_form_agrees.append(ok_diff == ok_printed)
+            if ok_diff or tau <= 1.0 / L or beta == 1.0:
+                accepted = True
+                res.margin.append(d2 / tau - dy2 / n)
+                break
+            tau *= beta
+        if not accepted:
+            res.status = EBACKTRACK
+            break
+        res.tau.append(tau)
+        res.ntrials.append(k + 1)
+        res.delta_fro.append(math.sqrt(d2))
+        Omega, Y, g = Op, Yp, gp
+        G = Y @ X / n
+        tau_prev = tau
+        t += 1
+    res.Omega = Omega
+    res.iters = t
+    return res
+
+
+# --------------------------------------------------------- exact row solve ---
+
+def row_solution(S: np.ndarray, i: int, active: np.ndarray, signs: np.ndarray,
+                 lam: float, lam_d: float) -> np.ndarray | None:
+    """Row i of the minimiser on a given support.  f separates over the rows of
+    Omega (proof of Thm 3.2, vectorised objective); restricted to an active set
+    A (containing i) with fixed signs s, the stationarity condition of Eq. 3.3 is
+    S_AA w_A = (1/w_i) e_i - v with v_j = lambda s_j (j != i), v_i = lambda_d.
+    With c = S_AA^-1 e_i and d = S_AA^-1 v this gives w_i^2 + d_i w_i - c_i = 0,
+    w_i = (-d_i + sqrt(d_i^2 + 4 c_i)) / 2 and w_A = c / w_i - d.
+    Returns the dense row (zeros off A), or None if S_AA is singular."""
+    p = S.shape[0]
+    A = np.asarray(active, dtype=np.int64)
+    pos = int(np.nonzero(A == i)[0][0])
+    SAA = S[np.ix_(A, A)]
+    v = lam * np.asarray(signs, dtype=np.float64).copy()
+    v[pos] = lam_d
+    e = np.zeros(A.size)
+    e[pos] = 1.0
+    try:
+        c = np.linalg.solve(SAA, e)
+        d = np.linalg.solve(SAA, v)
+    except np.linalg.LinAlgError:
+        return None
+    if c[pos] <= 0:
+        return None
+    wi = 0.5 * (-d[pos] + math.sqrt(d[pos] ** 2 + 4.0 * c[pos]))
+    w = c / wi - d
+    w[pos] = wi
+    row = np.zeros(p)
+    row[A] = w
+    return row
+
+
+def polish(Omega: np.ndarray, S: np.ndarray, lam: float, lam_d: float, rows=None) -> np.ndarray:
+    """Re-solve each requested row exactly on the support and signs of Omega
+    (row_solution); a converged Omega becomes the minimiser to rounding."""
+    out = np.array(Omega, dtype=np.float64)
+    p = Omega.shape[0]
+    for i in (range(p) if rows is None else rows):
+        A = np.nonzero(Omega[i] != 0)[0]
+        if i not in A:
+            A = np.sort(np.append(A, i))
+        s = np.sign(Omega[i, A])
+        r = row_solution(S, i, A, s, lam, lam_d)
+        if r is not None:
+            out[i] = r
+    return out
+
+
+def brute_force(S: np.ndarray, lam: float, lam_d: float) -> np.ndarray:
+    """Exact minimiser for tiny p (p <= 3): for each row enumerate all 3^(p-1)
+    sign patterns of the off-diagonal entries, solve each with row_solution,
+    keep the patterns that satisfy Eq. 3.3 (signs consistent, |(S w)_j| <= lambda
+    off the support) and return the one with the smallest row objective."""
+    p = S.shape[0]
+    if p > 3:
+        raise ValueError("brute force is meant for p <= 3")
+    Om = np.zeros((p, p))
+    for i in range(p):
+        others = [j for j in range(p) if j != i]
+        best, best_val = None, math.inf
+        for code in range(3 ** len(others)):
+            pat, c = [], code
+            for _ in others:
+                pat.append(c % 3 - 1)
+                c //= 3
+            act = sorted([i] + [j for j, s in zip(others, pat) if s != 0])
+            sg = np.array([1.0 if j == i else float(pat[others.index(j)]) for j in act])
+            w = row_solution(S, i, np.array(act), sg, lam, lam_d)
+            if w is None:
+                continue
+            ok = all(np.sign(w[j]) == pat[others.index(j)] for j in act if j != i)
+            Sw = S @ w
+            ok = ok and all(abs(Sw[j]) <= lam * (1 + 1e-12) + 1e-14 for j in others if w[j] == 0)
+            if not ok:
+                continue
+            val = row_objective(S, i, w, lam, lam_d)
+            if val < best_val:
+                best, best_val = w, val
+        Om[i] = best
+    return Om
+
+
+def row_objective(S: np.ndarray, i: int, w: np.ndarray, lam: float, lam_d: float) -> float:
+    """Row i's share of f: -log w_i + 1/2 w^T S w + lambda sum_{j != i} |w_j| + lambda_d w_i."""
+    if w[i] <= 0:
+        return math.inf
+    off = np.abs(w).sum() - abs(w[i])
+    return -math.log(w[i]) + 0.5 * float(w @ S @ w) + lam * off + lam_d * w[i]

@@ -1,0 +1,248 @@
+"""Pins for the FP64 oracle: closed forms, invariants and brute force that the
+paper and the mathematics fix independently of the oracle's own code.
+
+Each `pin_*` function returns True when the oracle satisfies it; the tests
+assert them, and the planted-mistake tests at the bottom swap one oracle
+function for a plausible mistake and check that some pin then fails.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+from oracle import accord_ref as R
+from synth import orthogonal_design, workload
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _gauss(n, p, seed):
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal((n, p))
+
+
+# ------------------------------------------------------------------ pins ---
+
+def pin_prox_root():
+    """Eq. 3.5 diagonal: the root solves w^2 - b w - tau = 0 and minimises
+    -tau log w + tau lambda w + (w - y)^2 / 2 (scalar brute minimisation)."""
+    ok = True
+    for y, tau, lam in [(0.3, 1.0, 0.2), (-2.0, 0.5, 0.1), (5.0, 0.01, 0.0), (-40.0, 2.0, 0.3)]:
+        w = float(R.diag_prox(np.array([y]), tau, lam)[0])
+        b = y - tau * lam
+        ok &= abs(w * w - b * w - tau) <= 1e-12 * max(1.0, w * w, abs(b * w))
+        res = so.minimize_scalar(lambda v: -tau * math.log(v) + tau * lam * v + 0.5 * (v - y) ** 2,
+                                 bounds=(1e-12, 100.0), method="bounded", options={"xatol": 1e-12})
+        ok &= abs(res.x - w) <= 1e-6 * max(1.0, w)
+    return bool(ok)
+
+
+def pin_soft_threshold():
+    """S_a(x) minimises a|w| + (w - x)^2 / 2 (checked on a fine grid)."""
+    grid = np.linspace(-3, 3, 600001)
+    ok = True
+    for x, a in [(1.3, 0.4), (-0.2, 0.5), (-2.0, 0.25), (0.5, 0.5)]:
+        w = float(R.soft_threshold(np.array([x]), a)[0])
+        v = a * np.abs(grid) + 0.5 * (grid - x) ** 2
+        ok &= abs(grid[np.argmin(v)] - w) <= 2e-5
+    return bool(ok)
+
+
+def pin_gradient():
+    """grad g = Omega S with S = X^T X / n formed explicitly, and equal to the
+    central finite difference of g."""
+    X = _gauss(7, 5, 11)
+    Om = _gauss(5, 5, 12)
+    S = X.T @ X / 7
+    G = R.grad_g(Om, X)
+    ok = np.allclose(G, Om @ S, rtol=1e-13, atol=1e-13)
+    ok &= abs(R.smooth_g(Om, X) - 0.5 * np.trace(Om.T @ Om @ S)) <= 1e-12
+    h = 1e-6
+    for (i, j) in [(0, 0), (1, 3), (4, 2)]:
+        E = np.zeros_like(Om)
+        E[i, j] = h
+        fd = (R.smooth_g(Om + E, X) - R.smooth_g(Om - E, X)) / (2 * h)
+        ok &= abs(fd - G[i, j]) <= 1e-7
+    return bool(ok)
+
+
+def pin_lipschitz():
+    """L = sigma_max(S): largest singular value of the explicitly formed S."""
+    X = _gauss(9, 14, 13)
+    S = X.T @ X / 9
+    return abs(R.lipschitz(X) - np.linalg.norm(S, 2)) <= 1e-12 * np.linalg.norm(S, 2)
+
+
+def pin_f_identity():
+    """f(I) = tr(S)/2 + lambda p (condition of Thm 3.3)."""
+    X = _gauss(6, 8, 14)
+    S = X.T @ X / 6
+    lam = 0.37
+    return abs(R.objective(np.eye(8), X, lam) - (np.trace(S) / 2 + lam * 8)) <= 1e-12
+
+
+def pin_diagonal_S():
+    """Diagonal S: omega_ii = (-lambda + sqrt(lambda^2 + 4 s_i)) / (2 s_i) and
+    omega_ij = 0 (Eq. 3.3 with z_ii = 1); without the diagonal penalty
+    omega_ii = 1 / sqrt(s_i)."""
+    s = np.random.Generator(np.random.PCG64(15)).uniform(0.4, 2.5, size=9)
+    X = orthogonal_design(40, s, 16)
+    ok = True
+    for pen in (True, False):
+        lam = 0.3
+        r = R.fit(X, lam, kkt_tol=1e-13, max_iter=2000, penalize_diag=pen)
+        ld = lam if pen else 0.0
+        want = (-ld + np.sqrt(ld * ld + 4 * s)) / (2 * s)
+        ok &= r.status == R.OK
+        ok &= np.max(np.abs(np.diag(r.Omega) - want)) <= 1e-11
+        ok &= np.max(np.abs(r.Omega - np.diag(np.diag(r.Omega)))) <= 1e-12
+    return bool(ok)
+
+
+def pin_identity_S():
+    """S = I and lambda = 0 give Omega-hat = I (reached from a perturbed start)."""
+    X = orthogonal_design(30, np.ones(6), 17)
+    Om0 = np.eye(6) + 0.05 * _gauss(6, 6, 18)
+    r = R.fit(X, 0.0, kkt_tol=1e-13, max_iter=3000, Omega0=Om0)
+    return r.status == R.OK and np.max(np.abs(r.Omega - np.eye(6))) <= 1e-11
+
+
+def pin_low_dim_closed_form():
+    """lambda = 0, n > p: Omega-hat = diag(S^-1)^(-1/2) S^-1 (Sec 3.1)."""
+    X = _gauss(80, 12, 19)
+    S = X.T @ X / 80
+    Th = np.linalg.inv(S)
+    want = np.diag(1 / np.sqrt(np.diag(Th))) @ Th
+    r = R.fit(X, 0.0, kkt_tol=1e-12, max_iter=20000)
+    return r.status == R.OK and np.max(np.abs(r.Omega - want)) <= 1e-9 * np.max(np.abs(want))
+
+
+def pin_brute_force():
+    """p <= 3: the solver's limit equals the sign-pattern enumeration, and the
+    enumeration's rows match a derivative-free minimisation of the row objective."""
+    ok = True
+    for seed, (n, p, lam) in [(20, (10, 3, 0.3)), (21, (4, 3, 0.05)), (22, (6, 2, 0.2)), (23, (5, 3, 0.8))]:
+        X = _gauss(n, p, seed)
+        S = X.T @ X / n
+        for pen in (True, False):
+            ld = lam if pen else 0.0
+            bf = R.brute_force(S, lam, ld)
+            r = R.fit(X, lam, kkt_tol=1e-13, max_iter=20000, penalize_diag=pen)
+            ok &= r.status == R.OK
+            ok &= np.max(np.abs(r.Omega - bf)) <= 1e-9
+            for i in range(p):
+                obj = lambda w: R.row_objective(S, i, w, lam, ld)  # noqa: E731
+                best = min((so.minimize(obj, x0, method="Nelder-Mead",
+                                        options={"xatol": 1e-10, "fatol": 1e-14, "maxiter": 40000})
+                            for x0 in (np.eye(p)[i], bf[i] + 0.1)), key=lambda q: q.fun)
+                ok &= best.fun >= obj(bf[i]) - 1e-10
+                ok &= np.max(np.abs(best.x - bf[i])) <= 1e-4
+    return bool(ok)
+
+
+def pin_kkt_descent_path():
+    """On a chain workload: f decreases on every accepted step (Thm 3.3),
+    f(Omega^0 = I) = tr(S)/2 + lambda p, the returned iterate satisfies the
+    KKT tolerance, and the exact row solve on its support moves it by less
+    than the tolerance allows."""
+    w = workload("ar1", p=60, n=40)
+    X = w.X.astype(np.float64)
+    S = X.T @ X / X.shape[0]
+    r = R.fit(X, w.lam, kkt_tol=1e-10, max_iter=5000)
+    f = np.array(r.f)
+    ok = r.status == R.OK
+    ok &= bool(np.all(np.diff(f) <= 1e-12 * np.abs(f[:-1])))
+    ok &= abs(f[0] - (np.trace(S) / 2 + w.lam * X.shape[1])) <= 1e-10
+    G = R.grad_g(r.Omega, X)
+    ok &= R.kkt_residual(r.Omega, G, w.lam, w.lam) <= 1e-10
+    P = R.polish(r.Omega, S, w.lam, w.lam)
+    ok &= R.kkt_residual(P, R.grad_g(P, X), w.lam, w.lam) <= 1e-12
+    ok &= np.max(np.abs(P - r.Omega)) <= 1e-8
+    return bool(ok)
+
+
+def pin_line_search_identity():
+    """g(O+) - g(O) - <Delta, grad g(O)> = ||Delta X^T||^2 / (2n) (g is quadratic),
+    so the printed and difference forms of the test agree away from rounding."""
+    X = _gauss(11, 9, 24)
+    O = _gauss(9, 9, 25)
+    D = 0.1 * _gauss(9, 9, 26)
+    lhs = R.smooth_g(O + D, X) - R.smooth_g(O, X) - float(np.sum(D * R.grad_g(O, X)))
+    rhs = float(np.sum((D @ X.T) ** 2)) / (2 * 11)
+    return abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
+
+
+PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
+        pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
+        pin_kkt_descent_path, pin_line_search_identity]
+
+
+@pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
+def test_pin(pin):
+    assert pin()
+
+
+def test_printed_and_difference_tests_agree_on_chain():
+    """Away from rounding (early trials), the printed Alg. 1 test and the
+    difference form give the same verdicts on the chain workload."""
+    w = workload("ar1")
+    r = R.fit(w.X, w.lam, kkt_tol=1e-6)
+    assert r.status == R.OK
+    assert all(r.printed_form_agrees[:100])
+
+
+def test_kkt_residual_definition_small():
+    """r = 0 exactly at a brute-force minimiser's KKT point up to rounding, and
+    positive when one entry is perturbed."""
+    X = _gauss(10, 3, 27)
+    S = X.T @ X / 10
+    bf = R.brute_force(S, 0.3, 0.3)
+    G = bf @ S
+    assert R.kkt_residual(bf, G, 0.3, 0.3) <= 1e-12
+    bad = bf.copy()
+    bad[0, 1] += 1e-3
+    assert R.kkt_residual(bad, bad @ S, 0.3, 0.3) > 1e-5
+
+
+def test_row_offset_consistency():
+    """Row-block helpers with row0 agree with the full-matrix versions (the
+    objective separates over rows of Omega)."""
+    w = workload("ar1", p=40, n=30)
+    X = w.X.astype(np.float64)
+    r = R.fit(X, w.lam, kkt_tol=1e-6)
+    G = R.grad_g(r.Omega, X)
+    A = r.Omega - 0.3 * G
+    full = R.prox(A, 0.3, w.lam, w.lam)
+    blk = R.prox(A[10:25], 0.3, w.lam, w.lam, row0=10)
+    assert np.array_equal(full[10:25], blk)
+    k_full = R.kkt_residual(r.Omega, G, w.lam, w.lam)
+    k_blocks = max(R.kkt_residual(r.Omega[a:b], G[a:b], w.lam, w.lam, row0=a) for a, b in [(0, 13), (13, 40)])
+    assert k_full == k_blocks
+
+
+# ------------------------------------------------------ planted mistakes ---
+
+MUTANTS = {
+    "soft_threshold_sign": ("soft_threshold", lambda x, a: -np.sign(x) * np.maximum(np.abs(x) - a, 0.0)),
+    "soft_threshold_shift": ("soft_threshold", lambda x, a: np.sign(x) * np.maximum(np.abs(x) - 2 * a, 0.0)),
+    "diag_prox_drops_lambda": ("diag_prox", lambda y, tau, ld: 0.5 * (y + np.sqrt(y * y + 4 * tau))),
+    "diag_prox_wrong_root": ("diag_prox", lambda y, tau, ld: 0.5 * ((y - tau * ld) + np.sqrt((y - tau * ld) ** 2 + 2 * tau))),
+    "grad_transposed": ("grad_g", lambda Om, X: (np.asarray(X, float).T @ np.asarray(X, float) @ Om.T) / X.shape[0]),
+    "grad_missing_1_over_n": ("grad_g", lambda Om, X: (Om @ np.asarray(X, float).T) @ np.asarray(X, float)),
+    "g_missing_half": ("smooth_g", lambda Om, X: float(np.sum((Om @ np.asarray(X, float).T) ** 2)) / X.shape[0]),
+    "lipschitz_trace": ("lipschitz", lambda X: float(np.trace(np.asarray(X, float) @ np.asarray(X, float).T)) / X.shape[0] / 3),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_planted_mistake_is_caught(monkeypatch, mutant):
+    attr, fn = MUTANTS[mutant]
+    monkeypatch.setattr(R, attr, fn)
+    results = []
+    for pin in PINS:
+        try:
+            results.append(bool(pin()))
+        except Exception:
+            results.append(False)
+    assert not all(results), f"mutant {mutant} passed every pin"
