@@ -1,0 +1,171 @@
+/*
+ * accord.h -- C ABI of the GB300 ACCORD-FBS solver (HP-ACCORD, arXiv 2412.11554).
+ *
+ * The library fits the ACCORD estimator (Eq. 3.2)
+ *
+ *     Omega-hat = argmin_Omega  -sum_i log omega_ii + 1/2 tr(Omega^T Omega S) + lambda ||Omega||_1,
+ *     S = X^T X / n,
+ *
+ * with the forward-backward splitting of Eq. 3.4, the elementwise update of
+ * Eq. 3.5 and the backtracking line search of Algorithm 1.  The gradient
+ * Omega S is formed in two steps, Y = Omega X^T and (1/n) Y X (Sec 3.3), on the
+ * GPU; nothing runs on the CPU except argument checks and launch control.
+ *
+ * Conventions shared by every entry point
+ *   - X is n x p, row-major (rows are samples, as in Sec 2), never centred or
+ *     scaled by the library, divisor n in S.
+ *   - Omega is p x p, row-major, dense, asymmetric.  Its element type follows
+ *     opts->precision: double for ACCORD_FP64, float for the mixed modes.
+ *   - All array pointers are DEVICE pointers owned by the caller; the library
+ *     never frees them and never keeps them after the call returns.
+ *   - Work is queued on opts->stream (a cudaStream_t; NULL = legacy default
+ *     stream).  Every call returns after synchronising that stream, so
+ *     outputs are ready when it returns.
+ *   - Return value: ACCORD_OK (0), a positive soft status, or a negative error.
+ *     No call aborts, throws or traps the GPU; device loops are bounded.
+ *   - Only compute capability 10.3 (GB300, sm_103a) is supported; any other
+ *     device gives ACCORD_EUNSUPPORTED.  There is no CPU fallback.
+ */
+#ifndef ACCORD_H_
+#define ACCORD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ACCORD_OK             0   /* converged: KKT residual <= kkt_tol                */
+#define ACCORD_NOT_CONVERGED  1   /* max_iter accepted steps; Omega = last iterate      */
+#define ACCORD_EINVAL        -1   /* NULL pointer, n < 1, p < 1, lambda < 0, bad opts   */
+#define ACCORD_EDOMAIN       -2   /* warm start with omega_ii <= 0 or non-finite entry  */
+#define ACCORD_ENONFINITE    -3   /* NaN/Inf appeared in an iterate or a reduction      */
+#define ACCORD_EBACKTRACK    -4   /* max_backtracks step reductions without acceptance  */
+#define ACCORD_ENOMEM        -5   /* workspace too small, or allocation failed          */
+#define ACCORD_ECUDA         -6   /* CUDA runtime/driver error, or a device wait gave up */
+#define ACCORD_EUNSUPPORTED  -7   /* device is not sm_103, or option not supported      */
+
+/* ---- precision modes --------------------------------------------------- */
+#define ACCORD_FP64          0    /* FP64 GEMMs, FP64 iterate                           */
+#define ACCORD_MIXED_BF16X3  1    /* tcgen05 BF16 hi+lo split GEMMs (3 products),
+                                     FP32 accumulation, FP32 iterate, FP64 reductions   */
+
+/* Columns of one trace row (one row per iterate Omega^t, t = 0..iters). */
+#define ACCORD_TRACE_FIELDS  8
+#define ACCORD_TRACE_F       0    /* f(Omega^t)                                         */
+#define ACCORD_TRACE_KKT     1    /* KKT residual r(Omega^t)                             */
+#define ACCORD_TRACE_TAU     2    /* accepted step tau_t (Omega^t -> Omega^t+1)          */
+#define ACCORD_TRACE_NTRIALS 3    /* prox evaluations spent on step t                    */
+#define ACCORD_TRACE_NNZ     4    /* off-diagonal nonzeros of Omega^t                    */
+#define ACCORD_TRACE_DELTA   5    /* ||Omega^t+1 - Omega^t||_F                           */
+#define ACCORD_TRACE_G       6    /* g(Omega^t) = ||Omega^t X^T||_F^2 / (2n)             */
+
+typedef struct accord_opts {
+    int32_t precision;       /* ACCORD_FP64 or ACCORD_MIXED_BF16X3 (default MIXED)          */
+    int32_t tau_warm;        /* 0: every outer step starts at tau0 (Algorithm 1 as printed);
+                                1: starts at min(tau0, tau_{t-1}/beta)                         */
+    int32_t max_iter;        /* accepted steps allowed (default 500)                           */
+    int32_t max_backtracks;  /* step reductions allowed per outer step (default 60)            */
+    int32_t penalize_diag;   /* 1: lambda on the diagonal too (Eq. 3.2, default); 0: off only  */
+    int32_t init_from_omega; /* 1: Omega holds the starting iterate on entry; 0: Omega^0 = I   */
+    int32_t lipschitz_max_iter; /* Lanczos steps allowed for L, at most 128 (default 128)    */
+    int32_t profile;         /* 1: time every GEMM launch with CUDA events (stats t_*_gemm_ms)  */
+    double  tau0;            /* initial step (default 1); <= 0 means 1/L                        */
+    double  beta;            /* backtracking factor in (0, 1]; 1 = fixed step (default 0.5)     */
+    double  kkt_tol;         /* stop when r(Omega^t) <= kkt_tol (default 1e-8)                  */
+    double  lipschitz;       /* > 0: use this L = sigma_max(S); 0: estimate it by Lanczos on
+                                X X^T / n (default 0)                                            */
+    double  lipschitz_tol;   /* relative change of the Ritz value that ends Lanczos (1e-14)    */
+    void*   stream;          /* cudaStream_t for all work (default NULL)                        */
+    double* trace;           /* optional HOST array, trace_cap x ACCORD_TRACE_FIELDS doubles    */
+    int64_t trace_cap;       /* rows available in trace (rows beyond are dropped)               */
+} accord_opts;
+
+typedef struct accord_stats {
+    int32_t iters;           /* accepted steps taken                                            */
+    int32_t trials;          /* prox evaluations (accepted + rejected)                           */
+    int32_t status;          /* same value as the call's return                                  */
+    int32_t reserved0;
+    double  f;               /* objective of the returned Omega (Eq. 3.2)                        */
+    double  g;               /* its smooth part g = 1/2 tr(Omega^T Omega S)                      */
+    double  kkt;             /* its KKT residual                                                 */
+    double  tau_last;        /* last accepted step                                               */
+    double  L;               /* Lipschitz constant used (estimated or given)                     */
+    int64_t nnz_offdiag;     /* off-diagonal nonzeros of the returned Omega                     */
+    double  t_setup_ms;      /* device time: conversions, L estimate, Omega^0, Y^0              */
+    double  t_solve_ms;      /* device time: the iteration loop and the copy-out                 */
+    int32_t n_prox_gemm;     /* prox GEMM launches that did work (trials + final KKT check)     */
+    int32_t n_y_gemm;        /* Y GEMM launches that did work (one per trial)                    */
+    double  t_prox_gemm_ms;  /* their summed device time when opts->profile, else 0              */
+    double  t_y_gemm_ms;
+    int64_t n_launches;      /* kernels this call launched (setup + every queued trial)          */
+} accord_stats;
+
+/* Fills *opts with the defaults listed above. */
+void accord_default_opts(accord_opts* opts);
+
+/* Device workspace, in bytes, that accord_fit needs for an n x p problem under
+ * opts (precision and max_iter matter).  Returns 0 for invalid sizes. */
+size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* opts);
+
+/* ACCORD-FBS fit (Algorithm 1 with Eq. 3.5; stopping rule r(Omega^t) <= kkt_tol
+ * with r the max-abs minimum-norm subgradient of Eq. 3.3).
+ *   X          device, n x p float, row-major.
+ *   lambda     >= 0, penalty weight of Eq. 3.2.
+ *   opts       may be NULL (defaults).
+ *   Omega      device, p x p, double (FP64) or float (mixed).  Read on entry
+ *              only when opts->init_from_omega; always overwritten with the
+ *              returned iterate (also on NOT_CONVERGED / EBACKTRACK /
+ *              ENONFINITE, where it is the last accepted iterate).
+ *   workspace  device buffer of at least accord_workspace_bytes(n, p, opts)
+ *              bytes, 256-byte aligned; NULL makes the call allocate and free
+ *              its own on the stream.
+ *   out        optional host stats.
+ * Errors: EINVAL (arguments), ENOMEM (ws_bytes too small), EDOMAIN (bad warm
+ * start or non-finite X), ENONFINITE, EBACKTRACK, ECUDA, EUNSUPPORTED. */
+int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts,
+               void* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
+
+/* Same as accord_fit for FP64 data; requires opts->precision == ACCORD_FP64
+ * (else EUNSUPPORTED).  Omega is double. */
+int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const accord_opts* opts,
+                   double* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
+
+/* Objective of Eq. 3.2 at Omega (device, p x p, element type per precision):
+ *   *g_out = 1/2 tr(Omega^T Omega S) = ||Omega X^T||_F^2 / (2n)   (Eq. 3.4)
+ *   *f_out = *g_out - sum_i log omega_ii + lambda sum_{i!=j} |omega_ij|
+ *            + lambda_d sum_i omega_ii, lambda_d = lambda or 0 per penalize_diag;
+ *            +Inf when some omega_ii <= 0.
+ * f_out, g_out are HOST doubles (either may be NULL).  Allocates its scratch
+ * on opts->stream (stream-ordered) and frees it before returning. */
+int accord_loss(const float* X, int64_t n, int64_t p, const void* Omega, double lambda,
+                const accord_opts* opts, double* f_out, double* g_out);
+
+/* Gradient of the smooth part (Sec 3.2):
+ *   smooth = 0:  G_out = Omega S = (1/n)(Omega X^T) X                 (grad g, Eq. 3.4)
+ *   smooth = 1:  G_out = -Omega_D^{-1} + Omega S  (gradient of Eq. 3.1's sample loss;
+ *                the first two terms of the KKT condition Eq. 3.3)
+ * G_out: device p x p, same element type as Omega, row-major, may not alias Omega.
+ * Allocates its scratch on opts->stream and frees it before returning. */
+int accord_grad(const float* X, int64_t n, int64_t p, const void* Omega, int smooth,
+                const accord_opts* opts, void* G_out);
+
+/* Static description of a status code. */
+const char* accord_status_string(int status);
+
+/* ACCORD_OK when the current device is sm_103 and the kernels load, else
+ * ACCORD_EUNSUPPORTED / ACCORD_ECUDA. */
+int accord_device_check(void);
+
+/* Description of the first failure of the calling thread's most recent
+ * accord_fit / accord_loss / accord_grad call ("" when it succeeded): the
+ * source location and the CUDA error string or the device error bits.  The
+ * pointer stays valid until the thread's next call. */
+const char* accord_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACCORD_H_ */

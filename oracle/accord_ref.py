@@ -134,6 +134,26 @@ def lipschitz(X: np.ndarray) -> float:
 
 # ------------------------------------------------------------ Algorithm 1 ---
 
+def fbs_trial(Omega: np.ndarray, Y: np.ndarray, G: np.ndarray, X: np.ndarray, tau: float, lam: float,
+              lam_d: float, row0: int = 0):
+    """One trial of Algorithm 1's inner loop: forward step A = Omega - tau G,
+    backward step of Eq. 3.5, Delta = Omega+ - Omega and Y+ = Omega+ X^T.
+    Returns (Omega+, Y+, ||Delta||^2, ||Y+ - Y||^2, g(Omega+), <Delta, G>).
+    Works on a block of rows [row0, row0 + m) as well (the objective separates
+    over the rows of Omega)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    A = Omega - tau * G                      # forward step
+    Op = prox(A, tau, lam, lam_d, row0)      # backward step, Eq. 3.5
+    Delta = Op - Omega
+    Yp = Op @ X.T
+    d2 = float(np.sum(Delta * Delta))
+    dy2 = float(np.sum((Yp - Y) ** 2))
+    gp = float(np.sum(Yp * Yp)) / (2.0 * n)
+    dG = float(np.sum(Delta * G))
+    return Op, Yp, d2, dy2, gp, dG
+
+
 @dataclasses.dataclass
 class FitResult:
     Omega: np.ndarray
@@ -190,15 +210,9 @@ def fit(X: np.ndarray, lam: float, *, tau0: float = 1.0, beta: float = 0.5, tau_
         accepted = False
         for k in range(max_backtracks + 1):
             res.trials += 1
-            A = Omega - tau * G                      # forward step
-            Op = prox(A, tau, lam, lam_d)            # backward step, Eq. 3.5
-            Delta = Op - Omega
-            Yp = Op @ X.T
-            d2 = float(np.sum(Delta * Delta))
-            dy2 = float(np.sum((Yp - Y) ** 2))
-            gp = float(np.sum(Yp * Yp)) / (2.0 * n)
+            Op, Yp, d2, dy2, gp, dG = fbs_trial(Omega, Y, G, X, tau, lam, lam_d)
             ok_diff = dy2 / n <= d2 / tau
-            ok_printed = gp <= g + float(np.sum(Delta * G)) + d2 / (2.0 * tau)
+            ok_printed = gp <= g + dG + d2 / (2.0 * tau)
             res.printed_form_agrees.append(ok_diff == ok_printed)
             if ok_diff or tau <= 1.0 / L or beta == 1.0:
                 accepted = True

@@ -1,0 +1,18 @@
+"""GB300-native ACCORD-FBS (HP-ACCORD, arXiv 2412.11554).
+
+The solver lives in the CUDA library libaccord.so (C ABI in include/accord.h);
+this package holds its sources (csrc/), the build step and the ctypes binding.
+"""
+from .accord import (  # noqa: F401
+    AccordError,
+    FitStats,
+    accord_default_opts,
+    accord_device_check,
+    accord_fit,
+    accord_grad,
+    accord_last_error,
+    accord_loss,
+    accord_status_string,
+    accord_workspace_bytes,
+    load_library,
+)

@@ -1,0 +1,239 @@
+"""Thin Python binding of libaccord (include/accord.h).
+
+Argument marshalling only: tensors supply device pointers and the stream,
+every step of the computation runs in the library's CUDA kernels.  There is
+no CPU fallback; calls fail loudly if the library is missing or the device is
+not a GB300 (sm_103).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libaccord.so")
+
+OK, NOT_CONVERGED = 0, 1
+EINVAL, EDOMAIN, ENONFINITE, EBACKTRACK, ENOMEM, ECUDA, EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+FP64, MIXED_BF16X3 = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED_BF16X3, "bf16x3": MIXED_BF16X3}
+TRACE_FIELDS = 8
+TRACE_COLUMNS = ("f", "kkt", "tau", "ntrials", "nnz", "delta", "g", "reserved")
+
+
+class AccordOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32), ("tau_warm", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+        ("max_backtracks", ctypes.c_int32), ("penalize_diag", ctypes.c_int32),
+        ("init_from_omega", ctypes.c_int32), ("lipschitz_max_iter", ctypes.c_int32), ("profile", ctypes.c_int32),
+        ("tau0", ctypes.c_double), ("beta", ctypes.c_double), ("kkt_tol", ctypes.c_double),
+        ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
+        ("trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int64),
+    ]
+
+
+class AccordStats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32), ("trials", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("f", ctypes.c_double), ("g", ctypes.c_double), ("kkt", ctypes.c_double),
+        ("tau_last", ctypes.c_double), ("L", ctypes.c_double), ("nnz_offdiag", ctypes.c_int64),
+        ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
+        ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
+        ("n_launches", ctypes.c_int64),
+    ]
+
+
+EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_loss",
+           "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error")
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libaccord.so (built by paper_2412_11554_gb300.build) and declare
+    every exported signature."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libaccord.so not found at {path}: run paper_2412_11554_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    opts_p, stats_p = ctypes.POINTER(AccordOpts), ctypes.POINTER(AccordStats)
+    lib.accord_default_opts.argtypes = [opts_p]
+    lib.accord_default_opts.restype = None
+    lib.accord_workspace_bytes.argtypes = [i64, i64, opts_p]
+    lib.accord_workspace_bytes.restype = ctypes.c_size_t
+    lib.accord_fit.argtypes = [P, i64, i64, dbl, opts_p, P, P, ctypes.c_size_t, stats_p]
+    lib.accord_fit.restype = i32
+    lib.accord_fit_f64.argtypes = [P, i64, i64, dbl, opts_p, P, P, ctypes.c_size_t, stats_p]
+    lib.accord_fit_f64.restype = i32
+    lib.accord_loss.argtypes = [P, i64, i64, P, dbl, opts_p, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.accord_loss.restype = i32
+    lib.accord_grad.argtypes = [P, i64, i64, P, i32, opts_p, P]
+    lib.accord_grad.restype = i32
+    lib.accord_status_string.argtypes = [i32]
+    lib.accord_status_string.restype = ctypes.c_char_p
+    lib.accord_device_check.argtypes = []
+    lib.accord_device_check.restype = i32
+    lib.accord_last_error.argtypes = []
+    lib.accord_last_error.restype = ctypes.c_char_p
+    if path == _LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class AccordError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load_library()
+        msg = lib.accord_status_string(status).decode()
+        detail = lib.accord_last_error().decode()
+        super().__init__(f"{where}: status {status} ({msg})" + (f" [{detail}]" if detail else ""))
+        self.status = status
+
+
+@dataclasses.dataclass
+class FitStats:
+    iters: int
+    trials: int
+    status: int
+    f: float
+    g: float
+    kkt: float
+    tau_last: float
+    L: float
+    nnz_offdiag: int
+    t_setup_ms: float
+    t_solve_ms: float
+    n_prox_gemm: int = 0
+    n_y_gemm: int = 0
+    t_prox_gemm_ms: float = 0.0
+    t_y_gemm_ms: float = 0.0
+    n_launches: int = 0
+    trace: np.ndarray | None = None
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def accord_default_opts(**kw) -> AccordOpts:
+    """AccordOpts with the library defaults, overridden by keyword fields
+    (precision may be given as 'fp64' / 'mixed')."""
+    o = AccordOpts()
+    load_library().accord_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if isinstance(v, bool):
+            v = int(v)
+        setattr(o, k, v)
+    return o
+
+
+def accord_workspace_bytes(n: int, p: int, **kw) -> int:
+    return int(load_library().accord_workspace_bytes(n, p, ctypes.byref(accord_default_opts(**kw))))
+
+
+def _check_x(X: torch.Tensor, dtype=torch.float32) -> None:
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == dtype and X.dim() == 2 and X.is_contiguous()):
+        raise ValueError(f"X must be a contiguous 2-D CUDA {dtype} tensor")
+
+
+def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: torch.Tensor | None = None,
+               init_from_omega: bool = False, workspace: torch.Tensor | None = None, trace: bool = False,
+               stream=None, check: bool = True, **opts) -> tuple[torch.Tensor, FitStats]:
+    """Fit Omega-hat (Eq. 3.2) with ACCORD-FBS.  X: CUDA float32 (or float64
+    with precision='fp64'), n x p.  Remaining keyword arguments set
+    accord_opts fields (tau0, beta, tau_warm, max_iter, max_backtracks,
+    kkt_tol, penalize_diag, lipschitz, lipschitz_max_iter, lipschitz_tol, profile)."""
+    lib = load_library()
+    prec = PRECISIONS[precision]
+    x64 = X.dtype == torch.float64
+    _check_x(X, torch.float64 if x64 else torch.float32)
+    if x64 and prec != FP64:
+        raise ValueError("float64 X requires precision='fp64'")
+    n, p = X.shape
+    odt = torch.float64 if prec == FP64 else torch.float32
+    if Omega is None:
+        if init_from_omega:
+            raise ValueError("init_from_omega needs Omega")
+        Omega = torch.empty((p, p), dtype=odt, device=X.device)
+    elif not (Omega.is_cuda and Omega.dtype == odt and Omega.shape == (p, p) and Omega.is_contiguous()):
+        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA {odt} tensor")
+    o = accord_default_opts(precision=prec, init_from_omega=int(init_from_omega), **opts)
+    o.stream = _stream_handle(stream)
+    tr = None
+    if trace:
+        tr = np.full((o.max_iter + 2, TRACE_FIELDS), np.nan)
+        o.trace = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.trace_cap = tr.shape[0]
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = AccordStats()
+    fn = lib.accord_fit_f64 if x64 else lib.accord_fit
+    status = fn(X.data_ptr(), n, p, float(lam), ctypes.byref(o), Omega.data_ptr(), ws_ptr, ws_bytes,
+                ctypes.byref(st))
+    stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
+                     st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms,
+                     st.t_y_gemm_ms, st.n_launches, None)
+    if tr is not None:
+        stats.trace = tr[: st.iters + 1].copy()
+    if check and status < 0:
+        raise AccordError(status, "accord_fit")
+    return Omega, stats
+
+
+def accord_loss(X: torch.Tensor, Omega: torch.Tensor, lam: float, *, precision: str | None = None,
+                penalize_diag: bool = True, stream=None) -> tuple[float, float]:
+    """(f, g) of Eq. 3.2 / Eq. 3.4 at Omega; precision follows Omega's dtype."""
+    lib = load_library()
+    _check_x(X)
+    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
+    o = accord_default_opts(precision=prec, penalize_diag=int(penalize_diag))
+    o.stream = _stream_handle(stream)
+    f, g = ctypes.c_double(), ctypes.c_double()
+    n, p = X.shape
+    status = lib.accord_loss(X.data_ptr(), n, p, Omega.data_ptr(), float(lam), ctypes.byref(o), ctypes.byref(f),
+                             ctypes.byref(g))
+    if status != OK:
+        raise AccordError(status, "accord_loss")
+    return f.value, g.value
+
+
+def accord_grad(X: torch.Tensor, Omega: torch.Tensor, smooth: bool = False, *, precision: str | None = None,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Omega S (smooth=False) or -Omega_D^-1 + Omega S (smooth=True)."""
+    lib = load_library()
+    _check_x(X)
+    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
+    o = accord_default_opts(precision=prec)
+    o.stream = _stream_handle(stream)
+    n, p = X.shape
+    if out is None:
+        out = torch.empty_like(Omega)
+    status = lib.accord_grad(X.data_ptr(), n, p, Omega.data_ptr(), int(bool(smooth)), ctypes.byref(o),
+                             out.data_ptr())
+    if status != OK:
+        raise AccordError(status, "accord_grad")
+    return out
+
+
+def accord_status_string(status: int) -> str:
+    return load_library().accord_status_string(status).decode()
+
+
+def accord_device_check() -> int:
+    return int(load_library().accord_device_check())
+
+
+def accord_last_error() -> str:
+    return load_library().accord_last_error().decode()

@@ -1,0 +1,649 @@
+// C ABI of libaccord (include/accord.h): argument checks, workspace layout,
+// setup (conversions, Omega^0, Y^0 = Omega^0 X^T, L = sigma_max(S)) and the
+// launch loop of Algorithm 1.  All arithmetic happens in the kernels; the host
+// only queues launches and reads the device control block to learn when the
+// fit has finished.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/accord.h"
+#include "internal.h"
+#include "tc_gemm.h"
+
+namespace accord {
+
+static thread_local char g_last_error[256] = "";
+
+void set_last_error(const char* where, int line, const char* what) {
+  if (g_last_error[0] != 0) return;  // keep the first failure
+  const char* base = where;
+  for (const char* c = where; *c; ++c)
+    if (*c == '/') base = c + 1;
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s", base, line, what);
+}
+
+void clear_last_error() { g_last_error[0] = 0; }
+
+namespace {
+
+constexpr size_t kAlign = 1024;
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Byte offsets of every sub-buffer of the fit workspace.
+struct Layout {
+  bool f64 = true;
+  int64_t n = 0, p = 0;
+  int64_t ldo = 0;   // Omega (elements)
+  int64_t ldy = 0;   // Y (elements)
+  int64_t ldk = 0;   // BF16 planes whose columns run over p
+  int64_t ldyk = 0;  // BF16 planes whose columns run over n
+  int64_t tiles_prox = 0, tiles_y = 0, trace_rows = 0;
+  size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0;
+  size_t om[2] = {0, 0}, y[2] = {0, 0};
+  size_t x64 = 0, xt64 = 0;                        // FP64 mode
+  size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
+  size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed mode
+  size_t gram = 0, lz_v = 0, lz_w = 0, lz_a = 0, lz_b = 0;
+  int lz_k = 0;
+  size_t total = 0;
+};
+
+size_t take(size_t& cursor, size_t bytes) {
+  const size_t at = cursor;
+  cursor += (bytes + kAlign - 1) / kAlign * kAlign;
+  return at;
+}
+
+Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max) {
+  Layout L;
+  L.f64 = f64;
+  L.n = n;
+  L.p = p;
+  L.ldo = round_up(p, 8);
+  L.ldy = round_up(n, 8);
+  L.ldk = round_up(p, 8);
+  L.ldyk = round_up(n, 8);
+  L.tiles_prox = f64 ? gemm_f64_tiles(p, p) : tc_tiles(p, p);
+  const int64_t ty = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
+  const int64_t tg = f64 ? gemm_f64_tiles(n, n) : tc_tiles(n, n);
+  L.tiles_y = ty > tg ? ty : tg;
+  L.trace_rows = (int64_t)max_iter + 2;
+  const size_t es = f64 ? 8 : 4;
+  size_t c = 0;
+  L.ctrl = take(c, sizeof(Ctrl));
+  L.bad = take(c, 64);
+  L.trace = take(c, (size_t)L.trace_rows * kTraceFields * 8);
+  L.part_prox = take(c, (size_t)L.tiles_prox * kProxSlots * 8);
+  L.part_y = take(c, (size_t)L.tiles_y * kProxSlots * 8);
+  L.part_om = take(c, (size_t)p * kProxSlots * 8);
+  for (int b = 0; b < 2; ++b) L.om[b] = take(c, (size_t)p * L.ldo * es);
+  if (f64) {
+    for (int b = 0; b < 2; ++b) L.y[b] = take(c, (size_t)p * L.ldy * 8);
+    L.x64 = take(c, (size_t)n * L.ldo * 8);
+    L.xt64 = take(c, (size_t)p * L.ldy * 8);
+  } else {
+    for (int b = 0; b < 2; ++b) L.y[b] = take(c, (size_t)p * L.ldy * 4);
+    L.om_hi = take(c, (size_t)p * L.ldk * 2);
+    L.om_lo = take(c, (size_t)p * L.ldk * 2);
+    for (int b = 0; b < 2; ++b) {
+      L.y_hi[b] = take(c, (size_t)p * L.ldyk * 2);
+      L.y_lo[b] = take(c, (size_t)p * L.ldyk * 2);
+    }
+    L.x_hi = take(c, (size_t)n * L.ldk * 2);
+    L.x_lo = take(c, (size_t)n * L.ldk * 2);
+    L.xt_hi = take(c, (size_t)p * L.ldyk * 2);
+    L.xt_lo = take(c, (size_t)p * L.ldyk * 2);
+  }
+  L.gram = take(c, (size_t)n * n * 8);
+  int64_t k = lanczos_max < kLanczosMax ? lanczos_max : kLanczosMax;
+  if (k > n) k = n;
+  if (k < 1) k = 1;
+  L.lz_k = (int)k;
+  L.lz_v = take(c, (size_t)(k + 1) * n * 8);
+  L.lz_w = take(c, (size_t)n * 8);
+  L.lz_a = take(c, (size_t)k * 8);
+  L.lz_b = take(c, (size_t)k * 8);
+  L.total = c;
+  return L;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+struct Guard {  // frees an internally allocated workspace on every exit path
+  void* ptr = nullptr;
+  cudaStream_t st = nullptr;
+  ~Guard() {
+    if (ptr) cudaFreeAsync(ptr, st);
+  }
+};
+
+#define ACCORD_CK(call)                                            \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      set_last_error(__FILE__, __LINE__, cudaGetErrorString(e_));  \
+      return kEcuda;                                               \
+    }                                                              \
+  } while (0)
+
+int check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return kEcuda;
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return kEcuda;
+  if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return kEcuda;
+  if (major != 10 || minor != 3) return kEunsupported;
+  return kOk;
+}
+
+int check_opts(const accord_opts& o) {
+  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
+  if (!(o.beta > 0.0 && o.beta <= 1.0)) return kEinval;
+  if (!std::isfinite(o.tau0)) return kEinval;
+  if (!(o.kkt_tol >= 0.0)) return kEinval;
+  if (o.max_iter < 0 || o.max_backtracks < 0) return kEinval;
+  if (!(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz)) return kEinval;
+  if (o.lipschitz_max_iter < 1) return kEinval;
+  if (!(o.lipschitz_tol >= 0.0)) return kEinval;
+  if (o.trace_cap < 0) return kEinval;
+  return kOk;
+}
+
+// Device GEMM wrappers that pick the precision's kernel family.
+struct Plan {
+  Layout L;
+  void* ws;
+  cudaStream_t st;
+  Ctrl* ctrl;
+  int* err;
+};
+
+// Y^(b) = Omega^(src) X^T for setup (no control block).  Partials -> part_y.
+int setup_y(const Plan& P, int src, int dst) {
+  const Layout& L = P.L;
+  void* ws = P.ws;
+  if (L.f64) {
+    GemmF64Params g{};
+    g.ctrl = nullptr;
+    g.A[0] = g.A[1] = at<double>(ws, L.om[src]);
+    g.lda = L.ldo;
+    g.B = at<double>(ws, L.x64);
+    g.ldb = L.ldo;
+    g.M = L.p; g.N = L.n; g.K = L.p;
+    g.out[0] = g.out[1] = at<double>(ws, L.y[dst]);
+    g.ldout = L.ldy;
+    g.aux[0] = g.aux[1] = nullptr;
+    g.part = at<double>(ws, L.part_y);
+    g.scale = 1.0;
+    ACCORD_CK(launch_gemm_f64(kModeY, g, P.st));
+    return kOk;
+  }
+  ACCORD_CK(launch_split_planes(at<float>(ws, L.om[src]), L.p, L.p, L.ldo, at<__nv_bfloat16>(ws, L.om_hi),
+                                at<__nv_bfloat16>(ws, L.om_lo), L.ldk, P.st));
+  TcParams t{};
+  if (!encode_plane_map(&t.a_hi[0], at<__nv_bfloat16>(ws, L.om_hi), L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.a_lo[0], at<__nv_bfloat16>(ws, L.om_lo), L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+    return kEcuda;
+  t.a_hi[1] = t.a_hi[0];
+  t.a_lo[1] = t.a_lo[0];
+  t.ctrl = nullptr;
+  t.err = P.err;
+  tc_shape(t, L.p, L.n, L.p);
+  t.out[0] = t.out[1] = at<float>(ws, L.y[dst]);
+  t.ldout = L.ldy;
+  t.out_hi[0] = t.out_hi[1] = at<__nv_bfloat16>(ws, L.y_hi[dst]);
+  t.out_lo[0] = t.out_lo[1] = at<__nv_bfloat16>(ws, L.y_lo[dst]);
+  t.ldplane = L.ldyk;
+  t.aux[0] = t.aux[1] = nullptr;
+  t.part = at<double>(ws, L.part_y);
+  t.scale = 1.f;
+  ACCORD_CK(launch_tc_gemm(kModeY, t, P.st));
+  return kOk;
+}
+
+// K = X X^T / n into the FP64 Gram buffer.
+int setup_gram(const Plan& P) {
+  const Layout& L = P.L;
+  void* ws = P.ws;
+  if (L.f64) {
+    GemmF64Params g{};
+    g.A[0] = g.A[1] = at<double>(ws, L.x64);
+    g.lda = L.ldo;
+    g.B = at<double>(ws, L.x64);
+    g.ldb = L.ldo;
+    g.M = L.n; g.N = L.n; g.K = L.p;
+    g.out[0] = g.out[1] = at<double>(ws, L.gram);
+    g.ldout = L.n;
+    g.scale = 1.0 / (double)L.n;
+    ACCORD_CK(launch_gemm_f64(kModeGram, g, P.st));
+    return kOk;
+  }
+  TcParams t{};
+  if (!encode_plane_map(&t.a_hi[0], at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.a_lo[0], at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+    return kEcuda;
+  t.a_hi[1] = t.a_hi[0];
+  t.a_lo[1] = t.a_lo[0];
+  t.err = P.err;
+  tc_shape(t, L.n, L.n, L.p);
+  t.out64 = at<double>(ws, L.gram);
+  t.ldout64 = L.n;
+  t.scale = 1.f / (float)L.n;
+  ACCORD_CK(launch_tc_gemm(kModeGram, t, P.st));
+  return kOk;
+}
+
+// Per-trial launch parameters, fixed for the whole fit (buffer choice is made
+// on the device from ctrl->cur).
+struct TrialPlan {
+  GemmF64Params g2{}, g1{};
+  TcParams t2{}, t1{};
+  SolveParams sp{};
+};
+
+int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
+  const Layout& L = P.L;
+  void* ws = P.ws;
+  if (L.f64) {
+    // prox GEMM: G = Y[cur] XT^T / n, Omega[cur] -> Omega[nxt]
+    GemmF64Params& g2 = T.g2;
+    g2.ctrl = P.ctrl;
+    g2.A[0] = at<double>(ws, L.y[0]);
+    g2.A[1] = at<double>(ws, L.y[1]);
+    g2.a_nxt = 0;
+    g2.lda = L.ldy;
+    g2.B = at<double>(ws, L.xt64);
+    g2.ldb = L.ldy;
+    g2.M = L.p; g2.N = L.p; g2.K = L.n;
+    g2.out[0] = at<double>(ws, L.om[0]);
+    g2.out[1] = at<double>(ws, L.om[1]);
+    g2.ldout = L.ldo;
+    g2.aux[0] = at<double>(ws, L.om[0]);
+    g2.aux[1] = at<double>(ws, L.om[1]);
+    g2.ldaux = L.ldo;
+    g2.part = at<double>(ws, L.part_prox);
+    g2.lam = lam; g2.lam_d = lam_d;
+    g2.scale = 1.0 / (double)L.n;
+    // GEMM1: Y[nxt] = Omega[nxt] X^T, old Y[cur] for the difference
+    GemmF64Params& g1 = T.g1;
+    g1.ctrl = P.ctrl;
+    g1.A[0] = at<double>(ws, L.om[0]);
+    g1.A[1] = at<double>(ws, L.om[1]);
+    g1.a_nxt = 1;
+    g1.lda = L.ldo;
+    g1.B = at<double>(ws, L.x64);
+    g1.ldb = L.ldo;
+    g1.M = L.p; g1.N = L.n; g1.K = L.p;
+    g1.out[0] = at<double>(ws, L.y[0]);
+    g1.out[1] = at<double>(ws, L.y[1]);
+    g1.ldout = L.ldy;
+    g1.aux[0] = at<double>(ws, L.y[0]);
+    g1.aux[1] = at<double>(ws, L.y[1]);
+    g1.ldaux = L.ldy;
+    g1.part = at<double>(ws, L.part_y);
+    g1.scale = 1.0;
+    return kOk;
+  }
+  TcParams& t2 = T.t2;
+  for (int b = 0; b < 2; ++b) {
+    if (!encode_plane_map(&t2.a_hi[b], at<__nv_bfloat16>(ws, L.y_hi[b]), L.p, L.n, L.ldyk, 128) ||
+        !encode_plane_map(&t2.a_lo[b], at<__nv_bfloat16>(ws, L.y_lo[b]), L.p, L.n, L.ldyk, 128))
+      return kEcuda;
+  }
+  if (!encode_plane_map(&t2.b_hi, at<__nv_bfloat16>(ws, L.xt_hi), L.p, L.n, L.ldyk, tc_box_n()) ||
+      !encode_plane_map(&t2.b_lo, at<__nv_bfloat16>(ws, L.xt_lo), L.p, L.n, L.ldyk, tc_box_n()))
+    return kEcuda;
+  t2.ctrl = P.ctrl;
+  t2.err = P.err;
+  t2.a_nxt = 0;
+  tc_shape(t2, L.p, L.p, L.n);
+  t2.out[0] = at<float>(ws, L.om[0]);
+  t2.out[1] = at<float>(ws, L.om[1]);
+  t2.ldout = L.ldo;
+  t2.out_hi[0] = t2.out_hi[1] = at<__nv_bfloat16>(ws, L.om_hi);
+  t2.out_lo[0] = t2.out_lo[1] = at<__nv_bfloat16>(ws, L.om_lo);
+  t2.ldplane = L.ldk;
+  t2.aux[0] = at<float>(ws, L.om[0]);
+  t2.aux[1] = at<float>(ws, L.om[1]);
+  t2.ldaux = L.ldo;
+  t2.part = at<double>(ws, L.part_prox);
+  t2.lam = (float)lam;
+  t2.lam_d = (float)lam_d;
+  t2.scale = (float)(1.0 / (double)L.n);
+
+  TcParams& t1 = T.t1;
+  if (!encode_plane_map(&t1.a_hi[0], at<__nv_bfloat16>(ws, L.om_hi), L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t1.a_lo[0], at<__nv_bfloat16>(ws, L.om_lo), L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t1.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t1.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+    return kEcuda;
+  t1.a_hi[1] = t1.a_hi[0];
+  t1.a_lo[1] = t1.a_lo[0];
+  t1.ctrl = P.ctrl;
+  t1.err = P.err;
+  t1.a_nxt = 1;
+  tc_shape(t1, L.p, L.n, L.p);
+  t1.out[0] = at<float>(ws, L.y[0]);
+  t1.out[1] = at<float>(ws, L.y[1]);
+  t1.ldout = L.ldy;
+  for (int b = 0; b < 2; ++b) {
+    t1.out_hi[b] = at<__nv_bfloat16>(ws, L.y_hi[b]);
+    t1.out_lo[b] = at<__nv_bfloat16>(ws, L.y_lo[b]);
+  }
+  t1.ldplane = L.ldyk;
+  t1.aux[0] = at<float>(ws, L.y[0]);
+  t1.aux[1] = at<float>(ws, L.y[1]);
+  t1.ldaux = L.ldy;
+  t1.part = at<double>(ws, L.part_y);
+  t1.scale = 1.f;
+  return kOk;
+}
+
+// Optional per-launch CUDA events around the two GEMMs of every trial.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> prox, y;  // start/stop pairs in launch order
+  ~Profiler() {
+    for (auto e : prox) cudaEventDestroy(e);
+    for (auto e : y) cudaEventDestroy(e);
+  }
+  cudaError_t mark(std::vector<cudaEvent_t>& v, cudaStream_t st) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    v.push_back(e);
+    return cudaEventRecord(e, st);
+  }
+  // summed duration of the first `count` launches
+  double total_ms(const std::vector<cudaEvent_t>& v, int64_t count) const {
+    double t = 0.0;
+    for (int64_t i = 0; i < count && 2 * i + 1 < (int64_t)v.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, v[2 * i], v[2 * i + 1]) == cudaSuccess) t += ms;
+    }
+    return t;
+  }
+};
+
+int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nlaunch) {
+  const Layout& L = P.L;
+  double* trace = at<double>(P.ws, L.trace);
+  if (prof.on) ACCORD_CK(prof.mark(prof.prox, P.st));
+  if (L.f64) ACCORD_CK(launch_gemm_f64(kModeProx, T.g2, P.st));
+  else ACCORD_CK(launch_tc_gemm(kModeProx, T.t2, P.st));
+  if (prof.on) ACCORD_CK(prof.mark(prof.prox, P.st));
+  ACCORD_CK(launch_post_prox(P.ctrl, at<double>(P.ws, L.part_prox), L.tiles_prox, T.sp, trace, P.st));
+  const int64_t ty = L.f64 ? gemm_f64_tiles(L.p, L.n) : tc_tiles(L.p, L.n);
+  if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
+  if (L.f64) ACCORD_CK(launch_gemm_f64(kModeY, T.g1, P.st));
+  else ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
+  if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
+  ACCORD_CK(launch_decide(P.ctrl, at<double>(P.ws, L.part_y), ty, T.sp, trace, P.st));
+  nlaunch += 4;
+  return kOk;
+}
+
+int read_ctrl(const Plan& P, Ctrl* host) {
+  ACCORD_CK(cudaMemcpyAsync(host, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, P.st));
+  ACCORD_CK(cudaStreamSynchronize(P.st));
+  return kOk;
+}
+
+int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double lam, const accord_opts* optp,
+             void* Omega, void* workspace, size_t ws_bytes, accord_stats* out) {
+  clear_last_error();
+  accord_opts o;
+  accord_default_opts(&o);
+  if (optp) o = *optp;
+  if (out) std::memset(out, 0, sizeof(*out));
+  if ((X32 == nullptr && X64in == nullptr) || Omega == nullptr || n < 1 || p < 1 || !(lam >= 0.0) ||
+      !std::isfinite(lam))
+    return kEinval;
+  if (int e = check_opts(o)) return e;
+  if (X64in && o.precision != ACCORD_FP64) return kEunsupported;
+  if (int e = check_device()) return e;
+  const bool f64 = o.precision == ACCORD_FP64;
+  if (!f64 && (n > 2147483647LL / 2 || p > 2147483647LL / 2)) return kEinval;
+
+  Plan P;
+  P.L = make_layout(n, p, f64, o.max_iter, o.lipschitz_max_iter);
+  P.st = static_cast<cudaStream_t>(o.stream);
+  Guard guard;
+  if (workspace == nullptr) {
+    if (cudaMallocAsync(&guard.ptr, P.L.total, P.st) != cudaSuccess) return kEnomem;
+    guard.st = P.st;
+    workspace = guard.ptr;
+  } else if (ws_bytes < P.L.total || ((uintptr_t)workspace & 255u) != 0) {
+    return ws_bytes < P.L.total ? kEnomem : kEinval;
+  }
+  P.ws = workspace;
+  P.ctrl = at<Ctrl>(workspace, P.L.ctrl);
+  P.err = &P.ctrl->dev_error;
+  const Layout& L = P.L;
+  void* ws = workspace;
+  const double lam_d = o.penalize_diag ? lam : 0.0;
+
+  cudaEvent_t ev[3];
+  for (auto& e : ev) ACCORD_CK(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]); }
+  } evg{ev};
+  ACCORD_CK(cudaEventRecord(ev[0], P.st));
+
+  // ---------------------------------------------------------------- setup --
+  int64_t nlaunch = 0;
+  ACCORD_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), P.st));
+  ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bad), 0, 64, P.st));
+  ACCORD_CK(cudaMemsetAsync(at<double>(ws, L.trace), 0xff, (size_t)L.trace_rows * kTraceFields * 8, P.st));
+  if (f64) {
+    ACCORD_CK(launch_convert_x_f64(X32, X64in, n, p, at<double>(ws, L.x64), L.ldo, at<double>(ws, L.xt64), L.ldy,
+                                   at<int>(ws, L.bad), P.st));
+  } else {
+    ACCORD_CK(launch_convert_x_bf16(X32, n, p, at<__nv_bfloat16>(ws, L.x_hi), at<__nv_bfloat16>(ws, L.x_lo), L.ldk,
+                                    at<__nv_bfloat16>(ws, L.xt_hi), at<__nv_bfloat16>(ws, L.xt_lo), L.ldyk,
+                                    at<int>(ws, L.bad), P.st));
+  }
+  if (o.init_from_omega) {
+    ACCORD_CK(launch_copy_omega(Omega, p, at<void>(ws, L.om[0]), L.ldo, f64, p, P.st));
+  } else {
+    ACCORD_CK(launch_set_identity(at<void>(ws, L.om[0]), f64, p, L.ldo, P.st));
+  }
+  int64_t nomp = 0;
+  ACCORD_CK(launch_omega_stats(at<void>(ws, L.om[0]), f64, p, L.ldo, at<double>(ws, L.part_om), &nomp, P.st));
+  if (int e = setup_y(P, 0, 0)) return e;
+  nlaunch += f64 ? 4 : 5;
+  const int64_t ty = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
+
+  Ctrl hc;
+  double L_given = o.lipschitz;
+  if (!(L_given > 0.0)) {
+    if (int e = setup_gram(P)) return e;
+    ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st));
+    nlaunch += 2;
+    const int chunk = 8;
+    for (int steps = 0; steps < L.lz_k + chunk; steps += chunk) {
+      ACCORD_CK(launch_lanczos_steps(P.ctrl, at<double>(ws, L.gram), n, at<double>(ws, L.lz_v),
+                                     at<double>(ws, L.lz_w), at<double>(ws, L.lz_a), at<double>(ws, L.lz_b), n,
+                                     L.lz_k, chunk, o.lipschitz_tol, P.st));
+      nlaunch += 2 * chunk;
+      if (int e = read_ctrl(P, &hc)) return e;
+      if (hc.power_done) break;
+    }
+  }
+  int hbad = 0;
+  ACCORD_CK(cudaMemcpyAsync(&hbad, at<int>(ws, L.bad), sizeof(int), cudaMemcpyDeviceToHost, P.st));
+  ACCORD_CK(cudaStreamSynchronize(P.st));
+  if (hbad != 0) return kEdomain;
+
+  TrialPlan T;
+  if (int e = make_trial_plan(P, T, lam, lam_d)) return e;
+  SolveParams& sp = T.sp;
+  sp.lam = lam;
+  sp.lam_d = lam_d;
+  sp.tau0 = o.tau0;
+  sp.beta = o.beta;
+  sp.kkt_tol = o.kkt_tol;
+  sp.inv_n = 1.0 / (double)n;
+  sp.max_iter = o.max_iter;
+  sp.max_backtracks = o.max_backtracks;
+  sp.tau_warm = o.tau_warm;
+  sp.fixed_step = o.beta >= 1.0 ? 1 : 0;
+  sp.trace_cap = L.trace_rows;
+  ACCORD_CK(launch_ctrl_init(P.ctrl, at<double>(ws, L.part_om), nomp, at<double>(ws, L.part_y), ty, sp, L_given,
+                             at<double>(ws, L.trace), P.st));
+  nlaunch += 1;
+  ACCORD_CK(cudaEventRecord(ev[1], P.st));
+  Profiler prof;
+  prof.on = o.profile != 0;
+
+  // ---------------------------------------------------------- iterations --
+  const int64_t max_trials = ((int64_t)o.max_iter + 1) * ((int64_t)o.max_backtracks + 1) + 2;
+  int64_t queued = 0;
+  int chunk = 2;
+  int32_t last_trials = -1;
+  bool stalled = false;
+  for (;;) {
+    if (int e = read_ctrl(P, &hc)) return e;
+    if (hc.done || queued >= max_trials || hc.dev_error != 0) break;
+    // every live trial advances ctrl->trials; a chunk without progress means
+    // the kernels are not doing their work, so stop queueing more
+    if (hc.trials == last_trials) {
+      stalled = true;
+      break;
+    }
+    last_trials = hc.trials;
+    for (int c = 0; c < chunk; ++c)
+      if (int e = launch_trial(P, T, prof, nlaunch)) return e;
+    queued += chunk;
+    if (chunk < 16) chunk *= 2;
+  }
+  if (!hc.done) hc.status = kNotConverged;
+  if (hc.dev_error != 0) {
+    char msg[96];
+    std::snprintf(msg, sizeof(msg), "device error bits 0x%x (1: an mbarrier wait timed out)", hc.dev_error);
+    set_last_error(__FILE__, __LINE__, msg);
+    hc.status = kEcuda;
+  } else if (stalled) {
+    set_last_error(__FILE__, __LINE__, "trial kernels made no progress");
+    hc.status = kEcuda;
+  }
+
+  // copy the returned iterate to the caller
+  ACCORD_CK(launch_copy_omega(at<void>(ws, L.om[hc.cur]), L.ldo, Omega, p, f64, p, P.st));
+  nlaunch += 1;
+  ACCORD_CK(cudaEventRecord(ev[2], P.st));
+  if (o.trace && o.trace_cap > 0) {
+    const int64_t rows = o.trace_cap < L.trace_rows ? o.trace_cap : L.trace_rows;
+    ACCORD_CK(cudaMemcpyAsync(o.trace, at<double>(ws, L.trace), (size_t)rows * kTraceFields * 8,
+                              cudaMemcpyDeviceToHost, P.st));
+  }
+  ACCORD_CK(cudaStreamSynchronize(P.st));
+  if (out) {
+    out->iters = hc.t;
+    out->trials = hc.trials;
+    out->status = hc.status;
+    out->f = hc.f;
+    out->g = hc.g;
+    out->kkt = hc.kkt;
+    out->tau_last = hc.tau_prev;
+    out->L = hc.L;
+    out->nnz_offdiag = (int64_t)hc.nnz;
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    out->t_setup_ms = a;
+    out->t_solve_ms = b;
+    // prox GEMMs that did work: one per trial, plus the launch whose KKT
+    // check ended the fit (OK, or NOT_CONVERGED at max_iter)
+    const int64_t live_prox = hc.trials + ((hc.status == kOk || hc.status == kNotConverged) ? 1 : 0);
+    out->n_prox_gemm = (int32_t)live_prox;
+    out->n_y_gemm = hc.trials;
+    out->t_prox_gemm_ms = prof.on ? prof.total_ms(prof.prox, live_prox) : 0.0;
+    out->t_y_gemm_ms = prof.on ? prof.total_ms(prof.y, hc.trials) : 0.0;
+    out->n_launches = nlaunch;
+  }
+  return hc.status;
+}
+
+}  // namespace
+}  // namespace accord
+
+using namespace accord;
+
+extern "C" {
+
+void accord_default_opts(accord_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = ACCORD_MIXED_BF16X3;
+  o->tau_warm = 0;
+  o->max_iter = 500;
+  o->max_backtracks = 60;
+  o->penalize_diag = 1;
+  o->init_from_omega = 0;
+  o->lipschitz_max_iter = 128;
+  o->profile = 0;
+  o->tau0 = 1.0;
+  o->beta = 0.5;
+  o->kkt_tol = 1e-8;
+  o->lipschitz = 0.0;
+  o->lipschitz_tol = 1e-14;
+  o->stream = nullptr;
+  o->trace = nullptr;
+  o->trace_cap = 0;
+}
+
+size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* optp) {
+  accord_opts o;
+  accord_default_opts(&o);
+  if (optp) o = *optp;
+  if (n < 1 || p < 1 || check_opts(o) != kOk) return 0;
+  return make_layout(n, p, o.precision == ACCORD_FP64, o.max_iter, o.lipschitz_max_iter).total;
+}
+
+int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, void* Omega,
+               void* workspace, size_t ws_bytes, accord_stats* out) {
+  const int s = fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
+  if (out) out->status = s;
+  return s;
+}
+
+int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, double* Omega,
+                   void* workspace, size_t ws_bytes, accord_stats* out) {
+  if (X == nullptr) return kEinval;
+  const int s = fit_impl(nullptr, X, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
+  if (out) out->status = s;
+  return s;
+}
+
+const char* accord_status_string(int s) {
+  switch (s) {
+    case ACCORD_OK: return "converged (KKT residual <= tolerance)";
+    case ACCORD_NOT_CONVERGED: return "not converged within max_iter";
+    case ACCORD_EINVAL: return "invalid argument";
+    case ACCORD_EDOMAIN: return "input outside the domain (omega_ii <= 0 or non-finite data)";
+    case ACCORD_ENONFINITE: return "non-finite value during the iteration";
+    case ACCORD_EBACKTRACK: return "line search exhausted max_backtracks";
+    case ACCORD_ENOMEM: return "workspace too small or allocation failed";
+    case ACCORD_ECUDA: return "CUDA error or a device wait timed out";
+    case ACCORD_EUNSUPPORTED: return "unsupported device or option";
+    default: return "unknown status";
+  }
+}
+
+int accord_device_check(void) { return check_device(); }
+
+const char* accord_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal declarations shared by the CUDA translation units of libaccord.
+// Elementwise update of Eq. 3.5, KKT residual entries of Eq. 3.3, the device
+// control block of the Algorithm 1 line search and the per-tile partial-sum
+// layouts.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace accord {
+
+// ---------------------------------------------------------------- status ---
+enum : int {
+  kOk = 0, kNotConverged = 1, kEinval = -1, kEdomain = -2, kEnonfinite = -3,
+  kEbacktrack = -4, kEnomem = -5, kEcuda = -6, kEunsupported = -7,
+};
+
+// Device error bits (ctrl->dev_error): a bounded wait gave up, or a kernel
+// found an impossible configuration and skipped its work.
+enum : int { kErrWaitTimeout = 1, kErrBadConfig = 2 };
+
+// ------------------------------------------------ partial-sum slot layout ---
+// Prox epilogue (GEMM2), one row of kProxSlots doubles per output tile.
+enum : int {
+  kPDelta2 = 0,   // ||Omega+ - Omega||_F^2
+  kPLogDiag = 1,  // sum log omega+_ii
+  kPDiagSum = 2,  // sum omega+_ii
+  kPL1Off = 3,    // sum_{i != j} |omega+_ij|
+  kPNnz = 4,      // off-diagonal nonzeros of Omega+
+  kPKkt = 5,      // max KKT residual entry of Omega (input iterate)  [max]
+  kPBad = 6,      // non-finite values seen / non-positive diagonal
+  kProxSlots = 8,
+};
+// Y epilogue (GEMM1), one row of kYSlots doubles per output tile.
+enum : int { kYDiff2 = 0, kYNorm2 = 1, kYBad = 2, kYSlots = 4 };
+
+// ----------------------------------------------------- control block ------
+// Lives in device memory; every per-trial kernel reads it first and returns
+// immediately once `done` is set, so a fixed launch sequence can run past
+// convergence harmlessly.
+struct Ctrl {
+  int32_t t;          // accepted steps so far (index of the current iterate)
+  int32_t k;          // trial index within the current outer step
+  int32_t trials;     // total prox evaluations
+  int32_t done;       // 1 once the fit has finished
+  int32_t status;     // final status when done
+  int32_t cur;        // which of the two iterate buffers holds Omega^t
+  int32_t dev_error;  // kErr* bits
+  int32_t power_done; // power iteration converged
+  double tau;         // step of the pending trial
+  double tau_prev;    // last accepted step
+  double tau0;        // restart step (opts tau0, or 1/L when that is <= 0)
+  double L, inv_L;
+  // current iterate Omega^t
+  double g, logdiag, diagsum, l1off, f, nnz, kkt;
+  // pending trial Omega+ (filled after the prox kernel)
+  double t_d2, t_logdiag, t_diagsum, t_l1off, t_nnz;
+  // pending trial Y+ (filled after GEMM1)
+  double t_dy2, t_y2;
+  // power iteration state
+  double pw_est, pw_prev;
+  int32_t pw_iter, pad0;
+};
+
+struct SolveParams {
+  double lam, lam_d, tau0, beta, kkt_tol;
+  double inv_n;
+  int32_t max_iter, max_backtracks, tau_warm, fixed_step;
+  int64_t trace_cap;
+};
+
+constexpr int kTraceFields = 8;
+
+// --------------------------------------------------------- Eq. 3.5 math ---
+template <class T>
+__device__ __forceinline__ T soft_threshold(T x, T a) {
+  // S_a(x) = (|x| - a)_+ sign(x); |x| == a and x == 0 both give exactly 0.
+  T m = fabs(x) - a;
+  return m > T(0) ? copysign(m, x) : T(0);
+}
+
+template <class T>
+__device__ __forceinline__ T diag_prox(T y, T tau, T lam_d) {
+  // positive root of w^2 - b w - tau = 0, b = y - tau lambda_d; the b < 0
+  // branch uses 2 tau / (sqrt(b^2 + 4 tau) - b), the same value without
+  // cancellation.
+  T b = y - tau * lam_d;
+  T root = sqrt(b * b + T(4) * tau);
+  return b >= T(0) ? T(0.5) * (b + root) : (T(2) * tau) / (root - b);
+}
+
+// One entry of the minimum-norm subgradient of Eq. 3.3 (absolute value).
+template <class T>
+__device__ __forceinline__ T kkt_entry(T omega, T G, bool diag, T lam, T lam_d) {
+  if (diag) {
+    if (!(omega > T(0))) return T(INFINITY);
+    return fabs(G - T(1) / omega + lam_d);
+  }
+  if (omega != T(0)) return fabs(G + copysign(lam, omega));
+  T m = fabs(G) - lam;
+  return m > T(0) ? m : T(0);
+}
+
+// ----------------------------------------------------- warp reductions ----
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// BF16 hi/lo split: x ~= hi + lo with hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+}  // namespace accord

@@ -1,0 +1,91 @@
+// Host-side launchers exported by each CUDA translation unit of libaccord.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace accord {
+
+// Records the first failure of the current call (thread-local): where it
+// happened and the CUDA error or device error bits.  Read through
+// accord_last_error().
+void set_last_error(const char* where, int line, const char* what);
+void clear_last_error();
+
+// Epilogue roles of the fused GEMMs C = A * B^T (A: M x K, B: N x K, both
+// row-major with K contiguous).
+enum GemmMode : int {
+  kModeY = 0,     // Y+ = Omega+ X^T: store Y+, reduce ||Y+ - Y||^2, ||Y+||^2
+  kModeProx = 1,  // G = Y X / n -> Eq. 3.5 prox -> Omega+, reductions, KKT(Omega)
+  kModeGrad = 2,  // G = Omega S (minus diag(1/omega) when smooth)
+  kModeGram = 3,  // K = X X^T / n (for the Lipschitz constant)
+};
+
+// Operand and epilogue pointers.  Arrays of two are the double-buffered
+// iterates: the kernel reads ctrl->cur (0 when ctrl is null) and uses
+// A[a_nxt ? nxt : cur], aux[cur], out[nxt] with nxt = cur ^ 1.
+struct GemmF64Params {
+  const Ctrl* ctrl;
+  const double* A[2];
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  int64_t M, N, K;
+  double* out[2];
+  int64_t ldout;
+  const double* aux[2];
+  int64_t ldaux;
+  double* part;
+  double lam, lam_d, scale;
+  int32_t a_nxt;
+  int32_t smooth;
+};
+
+int64_t gemm_f64_tiles(int64_t M, int64_t N);
+cudaError_t launch_gemm_f64(int mode, const GemmF64Params& prm, cudaStream_t st);
+
+// ---------------------------------------------------------- misc kernels ---
+cudaError_t launch_convert_x_f64(const float* X32, const double* X64in, int64_t n, int64_t p,
+                                 double* X64, int64_t ldx, double* XT64, int64_t ldxt,
+                                 int* bad_flag, cudaStream_t st);
+cudaError_t launch_convert_x_bf16(const float* X32, int64_t n, int64_t p,
+                                  __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t ldx,
+                                  __nv_bfloat16* XThi, __nv_bfloat16* XTlo, int64_t ldxt,
+                                  int* bad_flag, cudaStream_t st);
+// Omega^0 = I in an internal buffer with leading dimension ld (elements).
+cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st);
+// Copy between a dense p x p user array (ld = p) and an internal buffer.
+cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
+                              int64_t p, cudaStream_t st);
+// Per-row-block statistics of Omega into kProxSlots partials (log-diag,
+// diag sum, off-diagonal l1, nnz, bad count); returns the number of rows of
+// partials written through *nparts.
+cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld, double* part,
+                               int64_t* nparts, cudaStream_t st);
+// BF16 hi/lo planes of an FP32 matrix (rows x cols, lds) into ldd planes.
+cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds,
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldd, cudaStream_t st);
+
+// Lanczos estimate of lambda_max of the symmetric n x n matrix K (FP64).
+// V holds (kmax + 1) x n doubles, alpha / beta kmax doubles each, w n.
+constexpr int kLanczosMax = 128;
+cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st);
+cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
+                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st);
+
+// Control kernels of the Algorithm 1 loop.
+cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
+                             int64_t nyp, const SolveParams& sp, double L_given, double* trace,
+                             cudaStream_t st);
+cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
+                             double* trace, cudaStream_t st);
+cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
+                          double* trace, cudaStream_t st);
+// Loss helper: reduce Omega stats and Y partials into out[0] = f, out[1] = g.
+cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
+                               double lam, double lam_d, double inv_n, double* out, cudaStream_t st);
+
+// -------------------------------------------------------- tcgen05 GEMMs ---
+struct TcOperands;  // defined in the tcgen05 translation unit's header
+}  // namespace accord

@@ -1,0 +1,571 @@
+// Setup, statistics and control kernels of the ACCORD-FBS solver: data
+// conversion, Omega^0, Omega statistics, a Lanczos estimate of
+// L = sigma_max(S) (Sec 3.2) and the device-side accept / backtrack logic of
+// Algorithm 1.  All reductions of partial sums run in one block in a fixed
+// order, so every result is reproducible run to run.
+#include <cmath>
+
+#include "internal.h"
+
+namespace accord {
+namespace {
+
+constexpr int kRedThreads = 512;
+
+// Deterministic single-block fold of `rows` partial rows of width W.  Slots
+// whose bit is set in max_mask are folded with max, the others with +.
+template <int W>
+__device__ void fold_partials(const double* __restrict__ part, int64_t rows, unsigned max_mask,
+                              double (&out)[W]) {
+  __shared__ double sh[kRedThreads / 32][W];
+  double acc[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) acc[q] = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const double v = part[r * W + q];
+      acc[q] = ((max_mask >> q) & 1u) ? fmax(acc[q], v) : acc[q] + v;
+    }
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    const double t = ((max_mask >> q) & 1u) ? warp_max(acc[q]) : warp_sum(acc[q]);
+    if (lane == 0) sh[warp][q] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    double t = sh[0][q];
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+      t = ((max_mask >> q) & 1u) ? fmax(t, sh[w][q]) : t + sh[w][q];
+    out[q] = t;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void trace_put(double* trace, int64_t cap, int t, int field, double v) {
+  if (trace && t >= 0 && t < cap) trace[(int64_t)t * kTraceFields + field] = v;
+}
+
+// ------------------------------------------------------------ conversion --
+template <class Tin>
+__global__ void convert_x_f64_kernel(const Tin* __restrict__ X, int64_t n, int64_t p,
+                                     double* __restrict__ X64, int64_t ldx,
+                                     double* __restrict__ XT64, int64_t ldxt, int* bad) {
+  __shared__ double tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  int nbad = 0;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    double v = 0.0;
+    if (r < n && c < p) {
+      v = (double)X[r * p + c];
+      if (!isfinite(v)) ++nbad;
+      X64[r * ldx + c] = v;
+    }
+    tile[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;  // XT[c][r] = X[r][c]
+    if (c < p && r < n) XT64[c * ldxt + r] = tile[threadIdx.x][i];
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void convert_x_bf16_kernel(const float* __restrict__ X, int64_t n, int64_t p,
+                                      __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo,
+                                      int64_t ldx, __nv_bfloat16* __restrict__ XThi,
+                                      __nv_bfloat16* __restrict__ XTlo, int64_t ldxt, int* bad) {
+  __shared__ float tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  int nbad = 0;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (r < n && c < p) {
+      v = X[r * p + c];
+      if (!isfinite(v)) ++nbad;
+      __nv_bfloat16 h, l;
+      split_bf16(v, h, l);
+      Xhi[r * ldx + c] = h;
+      Xlo[r * ldx + c] = l;
+    }
+    tile[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < p && r < n) {
+      __nv_bfloat16 h, l;
+      split_bf16(tile[threadIdx.x][i], h, l);
+      XThi[c * ldxt + r] = h;
+      XTlo[c * ldxt + r] = l;
+    }
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+template <class T>
+__global__ void set_identity_kernel(T* __restrict__ Om, int64_t p, int64_t ld) {
+  const int64_t total = p * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ld, c = i % ld;
+    Om[i] = (r == c) ? T(1) : T(0);
+  }
+}
+
+template <class T>
+__global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
+                                  int64_t ldd, int64_t p) {
+  const int64_t total = p * p;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / p, c = i % p;
+    dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+// One block per row: log-diag, diag sum, off-diagonal l1, nnz, and a bad
+// count (non-finite entry, or omega_ii <= 0).
+template <class T>
+__global__ void omega_stats_kernel(const T* __restrict__ Om, int64_t p, int64_t ld,
+                                   double* __restrict__ part) {
+  const int64_t r = blockIdx.x;
+  double l1 = 0.0, nnz = 0.0, bad = 0.0;
+  for (int64_t c = threadIdx.x; c < p; c += blockDim.x) {
+    const double v = (double)Om[r * ld + c];
+    if (!isfinite(v)) bad += 1.0;
+    if (c != r) {
+      l1 += fabs(v);
+      nnz += (v != 0.0) ? 1.0 : 0.0;
+    }
+  }
+  __shared__ double sh[3][8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  l1 = warp_sum(l1);
+  nnz = warp_sum(nnz);
+  bad = warp_sum(bad);
+  if (lane == 0) { sh[0][warp] = l1; sh[1][warp] = nnz; sh[2][warp] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
+    const double d = (double)Om[r * ld + r];
+    if (!(d > 0.0)) c += 1.0;
+    double* o = part + r * kProxSlots;
+    o[kPDelta2] = 0.0;
+    o[kPLogDiag] = d > 0.0 ? log(d) : 0.0;
+    o[kPDiagSum] = d;
+    o[kPL1Off] = a;
+    o[kPNnz] = b;
+    o[kPKkt] = 0.0;
+    o[kPBad] = c;
+    o[7] = 0.0;
+  }
+}
+
+__global__ void split_planes_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
+                                    int64_t lds, __nv_bfloat16* __restrict__ hi,
+                                    __nv_bfloat16* __restrict__ lo, int64_t ldd) {
+  const int64_t total = rows * ldd;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ldd, c = i % ldd;
+    const float v = c < cols ? src[r * lds + c] : 0.f;
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
+// ------------------------------------------------- Lanczos for sigma_max --
+// L = sigma_max(S) = lambda_max(K), K = X X^T / n (n x n, symmetric PSD).
+// Lanczos with full (two-pass classical Gram-Schmidt) reorthogonalisation;
+// after step j the largest eigenvalue of the tridiagonal T_{j+1} is found by
+// Sturm-count multisection.  Ritz values increase to lambda_max from below.
+
+__global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n) {
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = 1.0 / sqrt((double)n);
+  if (threadIdx.x == 0) {
+    ctrl->power_done = 0;
+    ctrl->pw_iter = 0;
+    ctrl->pw_est = 0.0;
+    ctrl->pw_prev = 0.0;
+  }
+}
+
+// w = K V[j], one warp per row.
+__global__ void lanczos_matvec_kernel(const Ctrl* ctrl, const double* __restrict__ K, int64_t ldk,
+                                      const double* __restrict__ V, double* __restrict__ w, int64_t n) {
+  if (ctrl->power_done) return;
+  const double* v = V + (int64_t)ctrl->pw_iter * n;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t c = lane; c < n; c += 32) s = fma(K[row * ldk + c], v[c], s);
+  s = warp_sum(s);
+  if (lane == 0) w[row] = s;
+}
+
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += sh[q];
+  return t;
+}
+
+// number of eigenvalues of the m x m tridiagonal (a, b) below x
+__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+  int c = 0;
+  double d = a[0] - x;
+  if (d < 0.0) ++c;
+  for (int i = 1; i < m; ++i) {
+    const double dd = (d == 0.0) ? 1e-300 : d;
+    d = a[i] - x - b[i - 1] * b[i - 1] / dd;
+    if (d < 0.0) ++c;
+  }
+  return c;
+}
+
+// One Lanczos step on w = K v_j (block of kLanczosThreads threads).
+constexpr int kLanczosThreads = 1024;
+__global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctrl, double* V, double* w,
+                                                                       double* alpha, double* beta, int64_t n,
+                                                                       int kmax, double tol) {
+  if (ctrl->power_done) return;
+  __shared__ double sh[kLanczosThreads / 32];
+  __shared__ double h[256];
+  __shared__ double lohi[2];
+  const int j = ctrl->pw_iter;
+  const double* vj = V + (int64_t)j * n;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a = fma(vj[i], w[i], a);
+  a = block_sum(a, sh);
+  const double bprev = j > 0 ? beta[j - 1] : 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    w[i] -= a * vj[i] + (j > 0 ? bprev * V[(int64_t)(j - 1) * n + i] : 0.0);
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int pass = 0; pass < 2; ++pass) {  // w -= V_{0..j} (V_{0..j}^T w), twice
+    for (int q = warp; q <= j; q += nw) {
+      const double* vq = V + (int64_t)q * n;
+      double s = 0.0;
+      for (int64_t i = lane; i < n; i += 32) s = fma(vq[i], w[i], s);
+      s = warp_sum(s);
+      if (lane == 0) h[q] = s;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q <= j; ++q) s = fma(h[q], V[(int64_t)q * n + i], s);
+      w[i] -= s;
+    }
+    if (threadIdx.x == 0) a += h[j];
+    __syncthreads();
+  }
+  double bb = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) bb = fma(w[i], w[i], bb);
+  const double b = sqrt(block_sum(bb, sh));
+  if (threadIdx.x == 0) {
+    alpha[j] = a;
+    beta[j] = b;
+  }
+  __syncthreads();
+  // largest eigenvalue of T_{j+1} by multisection (warp 0: 32 probes a round)
+  const int m = j + 1;
+  if (warp == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = lane; i < m; i += 32) {
+      const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(beta[i]) : 0.0);
+      lo = fmin(lo, alpha[i] - r);
+      hi = fmax(hi, alpha[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    for (int round = 0; round < 16 && hi - lo > 4e-16 * fmax(fabs(hi), 1e-300); ++round) {
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const bool above = sturm_count(alpha, beta, m, x) == m;  // lambda_max < x
+      const unsigned mask = __ballot_sync(0xffffffffu, above);
+      const int first = mask ? __ffs(mask) - 1 : 32;  // lowest probe above lambda_max
+      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / 33.0;
+      const double nhi = first == 32 ? hi : lo + (hi - lo) * (double)(first + 1) / 33.0;
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) {
+      lohi[0] = lo;
+      lohi[1] = hi;
+    }
+  }
+  __syncthreads();
+  const double theta = 0.5 * (lohi[0] + lohi[1]);
+  const bool stop = (b <= 1e-13 * fmax(fabs(theta), 1e-300)) || (m >= kmax) || (m >= n) ||
+                    (j >= 3 && fabs(theta - ctrl->pw_est) <= tol * theta);
+  if (!stop)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)(j + 1) * n + i] = w[i] / b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctrl->pw_prev = ctrl->pw_est;
+    ctrl->pw_est = theta;
+    ctrl->pw_iter = j + 1;
+    if (stop) ctrl->power_done = 1;
+  }
+}
+
+// ------------------------------------------------------ Algorithm 1 loop --
+__global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
+                                 int64_t nyp, SolveParams sp, double L_given, double* trace) {
+  double om[kProxSlots], y[kYSlots];
+  fold_partials<kProxSlots>(ompart, nomp, 0u, om);
+  fold_partials<kYSlots>(ypart, nyp, 0u, y);
+  if (threadIdx.x != 0) return;
+  Ctrl& c = *ctrl;
+  c.t = 0;
+  c.k = 0;
+  c.trials = 0;
+  c.cur = 0;
+  c.done = 0;
+  c.status = kNotConverged;
+  c.L = L_given > 0.0 ? L_given : c.pw_est;
+  c.inv_L = c.L > 0.0 ? 1.0 / c.L : INFINITY;
+  c.tau0 = sp.tau0 > 0.0 ? sp.tau0 : c.inv_L;
+  c.tau = c.tau0;
+  c.tau_prev = c.tau0;
+  c.g = 0.5 * y[kYNorm2] * sp.inv_n;
+  c.logdiag = om[kPLogDiag];
+  c.diagsum = om[kPDiagSum];
+  c.l1off = om[kPL1Off];
+  c.nnz = om[kPNnz];
+  c.f = c.g - c.logdiag + sp.lam * c.l1off + sp.lam_d * c.diagsum;
+  c.kkt = INFINITY;
+  if (om[kPBad] > 0.0) {
+    c.done = 1;
+    c.status = kEdomain;
+  } else if (y[kYBad] > 0.0 || !isfinite(c.f) || !(c.L > 0.0) || !isfinite(c.tau0)) {
+    c.done = 1;
+    c.status = kEnonfinite;
+  }
+  trace_put(trace, sp.trace_cap, 0, 0, c.f);
+  trace_put(trace, sp.trace_cap, 0, 4, c.nnz);
+  trace_put(trace, sp.trace_cap, 0, 6, c.g);
+}
+
+// After the prox GEMM: fold its partials; on the first trial of a step the
+// KKT residual of Omega^t decides convergence (it needs G(Omega^t), which this
+// GEMM has just formed).
+__global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
+                                 double* trace) {
+  if (ctrl->done) return;
+  double s[kProxSlots];
+  fold_partials<kProxSlots>(part, ntiles, 1u << kPKkt, s);
+  if (threadIdx.x != 0) return;
+  Ctrl& c = *ctrl;
+  if (c.k == 0) {
+    c.kkt = s[kPKkt];
+    trace_put(trace, sp.trace_cap, c.t, 1, c.kkt);
+    if (c.kkt <= sp.kkt_tol) {
+      c.done = 1;
+      c.status = kOk;
+      return;
+    }
+    if (!isfinite(c.kkt)) {
+      c.done = 1;
+      c.status = kEnonfinite;
+      return;
+    }
+    if (c.t >= sp.max_iter) {
+      c.done = 1;
+      c.status = kNotConverged;
+      return;
+    }
+  }
+  if (s[kPBad] > 0.0) {
+    c.done = 1;
+    c.status = kEnonfinite;
+    return;
+  }
+  c.t_d2 = s[kPDelta2];
+  c.t_logdiag = s[kPLogDiag];
+  c.t_diagsum = s[kPDiagSum];
+  c.t_l1off = s[kPL1Off];
+  c.t_nnz = s[kPNnz];
+}
+
+// After GEMM1 on the trial: sufficient-decrease test of Algorithm 1 in the
+// form ||Y+ - Y||^2 / n <= ||Delta||^2 / tau (identical to the printed test
+// because g is quadratic), or the tau <= 1/L floor; accept or backtrack.
+__global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
+                              double* trace) {
+  if (ctrl->done) return;
+  double s[kYSlots];
+  fold_partials<kYSlots>(part, ntiles, 0u, s);
+  if (threadIdx.x != 0) return;
+  Ctrl& c = *ctrl;
+  c.trials += 1;
+  if (s[kYBad] > 0.0) {
+    c.done = 1;
+    c.status = kEnonfinite;
+    return;
+  }
+  c.t_dy2 = s[kYDiff2];
+  c.t_y2 = s[kYNorm2];
+  const double lhs = c.t_dy2 * sp.inv_n;
+  const double rhs = c.t_d2 / c.tau;
+  const bool accept = (lhs <= rhs) || (c.tau <= c.inv_L) || sp.fixed_step;
+  if (accept) {
+    trace_put(trace, sp.trace_cap, c.t, 2, c.tau);
+    trace_put(trace, sp.trace_cap, c.t, 3, (double)(c.k + 1));
+    trace_put(trace, sp.trace_cap, c.t, 5, sqrt(c.t_d2));
+    c.t += 1;
+    c.cur ^= 1;
+    c.g = 0.5 * c.t_y2 * sp.inv_n;
+    c.logdiag = c.t_logdiag;
+    c.diagsum = c.t_diagsum;
+    c.l1off = c.t_l1off;
+    c.nnz = c.t_nnz;
+    c.f = c.g - c.logdiag + sp.lam * c.l1off + sp.lam_d * c.diagsum;
+    trace_put(trace, sp.trace_cap, c.t, 0, c.f);
+    trace_put(trace, sp.trace_cap, c.t, 4, c.nnz);
+    trace_put(trace, sp.trace_cap, c.t, 6, c.g);
+    c.tau_prev = c.tau;
+    c.k = 0;
+    c.tau = sp.tau_warm ? fmin(c.tau0, c.tau / sp.beta) : c.tau0;
+  } else {
+    c.k += 1;
+    if (c.k > sp.max_backtracks) {
+      c.done = 1;
+      c.status = kEbacktrack;
+      return;
+    }
+    c.tau *= sp.beta;
+  }
+}
+
+__global__ void loss_finish_kernel(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
+                                   double lam, double lam_d, double inv_n, double* out) {
+  double om[kProxSlots], y[kYSlots];
+  fold_partials<kProxSlots>(ompart, nomp, 0u, om);
+  fold_partials<kYSlots>(ypart, nyp, 0u, y);
+  if (threadIdx.x != 0) return;
+  const double g = 0.5 * y[kYNorm2] * inv_n;
+  double f = g - om[kPLogDiag] + lam * om[kPL1Off] + lam_d * om[kPDiagSum];
+  if (om[kPBad] > 0.0) f = INFINITY;
+  out[0] = f;
+  out[1] = g;
+}
+
+unsigned grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_convert_x_f64(const float* X32, const double* X64in, int64_t n, int64_t p,
+                                 double* X64, int64_t ldx, double* XT64, int64_t ldxt, int* bad,
+                                 cudaStream_t st) {
+  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  if (X64in)
+    convert_x_f64_kernel<double><<<grid, block, 0, st>>>(X64in, n, p, X64, ldx, XT64, ldxt, bad);
+  else
+    convert_x_f64_kernel<float><<<grid, block, 0, st>>>(X32, n, p, X64, ldx, XT64, ldxt, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_x_bf16(const float* X32, int64_t n, int64_t p, __nv_bfloat16* Xhi,
+                                  __nv_bfloat16* Xlo, int64_t ldx, __nv_bfloat16* XThi,
+                                  __nv_bfloat16* XTlo, int64_t ldxt, int* bad, cudaStream_t st) {
+  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  convert_x_bf16_kernel<<<grid, block, 0, st>>>(X32, n, p, Xhi, Xlo, ldx, XThi, XTlo, ldxt, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st) {
+  const unsigned g = grid_for(p * ld, 256);
+  if (is_f64) set_identity_kernel<double><<<g, 256, 0, st>>>((double*)Om, p, ld);
+  else set_identity_kernel<float><<<g, 256, 0, st>>>((float*)Om, p, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
+                              int64_t p, cudaStream_t st) {
+  const unsigned g = grid_for(p * p, 256);
+  if (is_f64) copy_omega_kernel<double><<<g, 256, 0, st>>>((const double*)src, lds, (double*)dst, ldd, p);
+  else copy_omega_kernel<float><<<g, 256, 0, st>>>((const float*)src, lds, (float*)dst, ldd, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld, double* part,
+                               int64_t* nparts, cudaStream_t st) {
+  if (p > 2147483647LL) return cudaErrorInvalidValue;
+  if (is_f64) omega_stats_kernel<double><<<(unsigned)p, 256, 0, st>>>((const double*)Om, p, ld, part);
+  else omega_stats_kernel<float><<<(unsigned)p, 256, 0, st>>>((const float*)Om, p, ld, part);
+  *nparts = p;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds,
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldd, cudaStream_t st) {
+  split_planes_kernel<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, hi, lo, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st) {
+  lanczos_init_kernel<<<1, 256, 0, st>>>(ctrl, V, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
+                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st) {
+  if (kmax > 256) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)((n + 7) / 8);
+  for (int s = 0; s < nsteps; ++s) {
+    lanczos_matvec_kernel<<<g, 256, 0, st>>>(ctrl, K, ldk, V, w, n);
+    lanczos_step_kernel<<<1, kLanczosThreads, 0, st>>>(ctrl, V, w, alpha, beta, n, kmax, tol);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
+                             int64_t nyp, const SolveParams& sp, double L_given, double* trace,
+                             cudaStream_t st) {
+  ctrl_init_kernel<<<1, kRedThreads, 0, st>>>(ctrl, ompart, nomp, ypart, nyp, sp, L_given, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
+                             double* trace, cudaStream_t st) {
+  post_prox_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
+                          double* trace, cudaStream_t st) {
+  decide_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
+                               double lam, double lam_d, double inv_n, double* out, cudaStream_t st) {
+  loss_finish_kernel<<<1, kRedThreads, 0, st>>>(ompart, nomp, ypart, nyp, lam, lam_d, inv_n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace accord

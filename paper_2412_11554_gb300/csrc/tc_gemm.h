@@ -1,0 +1,49 @@
+// Parameters of the tcgen05 split-BF16 GEMM C = A * B^T (A: M x K, B: N x K,
+// BF16 hi/lo planes, K contiguous) and its host launcher.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace accord {
+
+struct TcParams {
+  CUtensorMap a_hi[2];  // A planes, index (a_nxt ? nxt : cur)
+  CUtensorMap a_lo[2];
+  CUtensorMap b_hi;     // B planes
+  CUtensorMap b_lo;
+  const Ctrl* ctrl;     // null: cur = 0, no early exit
+  int* err;             // device error word (kErr* bits), never null
+  int64_t M, N, K;
+  int32_t num_kb, tiles_m, tiles_n, ntiles;
+  int32_t a_nxt, smooth, group_m, bn;
+  float* out[2];        // FP32 output (Y+, Omega+ or G), index nxt
+  int64_t ldout;
+  __nv_bfloat16* out_hi[2];  // BF16 planes of the output, index nxt
+  __nv_bfloat16* out_lo[2];
+  int64_t ldplane;
+  const float* aux[2];  // old Y (Y mode) or Omega (prox / grad), index cur
+  int64_t ldaux;
+  double* out64;        // FP64 output (Gram)
+  int64_t ldout64;
+  double* part;         // per-tile partial sums or null
+  float lam, lam_d, scale, pad;
+};
+
+// Encodes a 2-D BF16 tensor map over a rows x cols matrix with leading
+// dimension ld (elements), box 64 x box_rows, 128-byte swizzle.  Returns false
+// when the driver rejects the arguments.
+bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld,
+                      int box_rows);
+
+// Fills the shape fields (num_kb, tiles, bn) for an M x N x K problem.
+void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K);
+int64_t tc_tiles(int64_t M, int64_t N);
+int tc_box_n();  // rows of the B box (= BN)
+cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
+
+}  // namespace accord

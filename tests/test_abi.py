@@ -1,0 +1,102 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/accord.h declares; the ctypes structs match the C layout; host-side
+argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "accord.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_11554_gb300 import build
+    build.build()
+    from paper_2412_11554_gb300 import accord
+    return accord.load_library()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(accord_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for want in ("accord_fit", "accord_loss", "accord_grad", "accord_workspace_bytes", "accord_default_opts"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (accord_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_covers_every_export():
+    from paper_2412_11554_gb300 import accord
+    assert set(accord.EXPORTS) == set(declared_functions())
+
+
+def test_struct_layout_matches_c():
+    """Compile a probe against the header with gcc and compare sizeof/offsetof
+    with the ctypes mirrors."""
+    from paper_2412_11554_gb300.accord import AccordOpts, AccordStats
+    fields = {"accord_opts": AccordOpts, "accord_stats": AccordStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for cname, cls in fields.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "probe.c"), os.path.join(d, "probe")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c11", "-o", exe, src], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, cls in fields.items():
+        assert int(got[cname]) == ctypes.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, f
+
+
+def test_defaults_and_workspace_sizing(lib):
+    from paper_2412_11554_gb300 import accord
+    o = accord.accord_default_opts()
+    assert (o.precision, o.max_iter, o.max_backtracks, o.penalize_diag) == (accord.MIXED_BF16X3, 500, 60, 1)
+    assert (o.tau0, o.beta, o.kkt_tol, o.lipschitz) == (1.0, 0.5, 1e-8, 0.0)
+    small = accord.accord_workspace_bytes(100, 200, precision="fp64")
+    big = accord.accord_workspace_bytes(1000, 40000)
+    assert 0 < small < big
+    # dense Omega and Omega+ alone need 2 * 4 * p^2 bytes in mixed mode
+    assert big >= 2 * 4 * 40000 ** 2
+    assert accord.accord_workspace_bytes(0, 10) == 0
+    assert accord.accord_workspace_bytes(10, 10, beta=1.5) == 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    """Argument checks happen before any device call, so they work here."""
+    from paper_2412_11554_gb300 import accord
+    o = accord.accord_default_opts()
+    st = accord.AccordStats()
+    dummy = ctypes.c_void_p(16)
+    assert lib.accord_fit(None, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    assert lib.accord_fit(dummy, 0, 10, 0.1, ctypes.byref(o), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    assert lib.accord_fit(dummy, 10, 10, -1.0, ctypes.byref(o), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    bad = accord.accord_default_opts(beta=0.0)
+    assert lib.accord_fit(dummy, 10, 10, 0.1, ctypes.byref(bad), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    bad = accord.accord_default_opts(precision=7)
+    assert lib.accord_fit(dummy, 10, 10, 0.1, ctypes.byref(bad), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    assert st.status == accord.EINVAL
+    assert lib.accord_fit_f64(dummy, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, None) == accord.EUNSUPPORTED
+    for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert accord.accord_status_string(s)

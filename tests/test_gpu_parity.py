@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances
+  FP64 mode: the iterate sequence matches the oracle's (same accepted steps,
+  same trial counts and step sizes) and the returned Omega is within 1e-9
+  relative Frobenius of the oracle's (the bar the method's FP64 target states).
+  Mixed BF16x3 mode: 1e-4 relative Frobenius to the FP64 result, support equal
+  except entries within the rounding band of the soft-threshold.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import accord_ref as R
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_11554_gb300 import build
+    build.build()
+    import paper_2412_11554_gb300 as pkg
+    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
+    return pkg
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def support_mismatch(Om, ref, G_ref, lam, band):
+    """Entries whose zero pattern differs, excluding those inside the band
+    around the soft-threshold (|omega| <= band or |lam - |G|| <= band)."""
+    p = ref.shape[0]
+    off = ~np.eye(p, dtype=bool)
+    diff = ((Om != 0) != (ref != 0)) & off
+    border = (np.abs(ref) <= band) | (np.abs(lam - np.abs(G_ref)) <= band)
+    return int(np.sum(diff & ~border))
+
+
+# ------------------------------------------------------------- FP64 path ---
+
+def test_fp64_chain_iterate_sequence_matches_oracle(A):
+    """AR(1) chain p=200, n=100, lambda=0.2, KKT 1e-8: the oracle trajectory."""
+    w = workload("ar1")
+    ref = R.fit(w.X, w.lam, kkt_tol=1e-8, max_iter=500)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-8, max_iter=500, trace=True)
+    assert st.status == R.OK == ref.status
+    assert st.iters == ref.iters and st.trials == ref.trials
+    tr = st.trace
+    assert np.array_equal(tr[:-1, 2], np.array(ref.tau))
+    assert np.array_equal(tr[:-1, 3].astype(int), np.array(ref.ntrials))
+    np.testing.assert_allclose(tr[:, 0], ref.f, rtol=1e-11)
+    np.testing.assert_allclose(tr[:, 1], ref.kkt, rtol=1e-6, atol=1e-12)
+    assert abs(st.L - ref.L) <= 1e-10 * ref.L
+    O = Om.cpu().numpy()
+    assert rel_fro(O, ref.Omega) <= 1e-9
+    gold = json.load(open(os.path.join(GOLD, "chain_p200_n100.json")))
+    assert st.iters == gold["iters"]
+
+
+def test_fp64_matches_exact_row_solution(A):
+    """At a tight tolerance the FP64 result equals the row-wise exact solution
+    on its own support (independent of the iteration) to 1e-9."""
+    w = workload("ar1", p=120, n=90)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-11, max_iter=5000)
+    assert st.status == 0
+    O = Om.cpu().numpy()
+    X = w.X.astype(np.float64)
+    S = X.T @ X / X.shape[0]
+    P = R.polish(O, S, w.lam, w.lam)
+    assert rel_fro(O, P) <= 1e-9
+    assert R.kkt_residual(O, R.grad_g(O, X), w.lam, w.lam) <= 2e-11
+
+
+@pytest.mark.parametrize("n,p", [(61, 137), (1, 5), (7, 3), (3, 1), (50, 64), (33, 65)])
+def test_fp64_ragged_and_tiny(A, n, p):
+    rng = np.random.Generator(np.random.PCG64(100 + p))
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    lam = 0.25
+    ref = R.fit(X, lam, kkt_tol=1e-9, max_iter=3000)
+    Om, st = A.accord_fit(dev(X), lam, precision="fp64", kkt_tol=1e-9, max_iter=3000)
+    assert st.status == ref.status
+    assert st.iters == ref.iters and st.trials == ref.trials
+    assert rel_fro(Om.cpu().numpy(), ref.Omega) <= 1e-9
+
+
+def test_fp64_penalize_diag_off_and_options(A):
+    w = workload("er", p=90, n=60)
+    for kw in (dict(penalize_diag=False), dict(tau_warm=True), dict(beta=1.0, tau0=0.0), dict(tau0=0.3, beta=0.7)):
+        okw = dict(kw)
+        if okw.get("tau0") == 0.0:
+            okw["tau0"] = -1.0  # oracle: <= 0 means 1/L
+        ref = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=4000, **okw)
+        Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-9, max_iter=4000, **kw)
+        assert st.status == ref.status, kw
+        assert st.iters == ref.iters and st.trials == ref.trials, kw
+        assert rel_fro(Om.cpu().numpy(), ref.Omega) <= 1e-9, kw
+
+
+def test_fp64_warm_start_and_max_iter(A):
+    w = workload("ar1", p=80, n=50)
+    ref = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=5)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-9, max_iter=5)
+    assert st.status == R.NOT_CONVERGED == ref.status and st.iters == 5
+    assert rel_fro(Om.cpu().numpy(), ref.Omega) <= 1e-11
+    # resuming from the returned iterate continues the same trajectory shape
+    full = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=3000, Omega0=ref.Omega)
+    Om2, st2 = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-9, max_iter=3000,
+                            Omega=Om.clone(), init_from_omega=True)
+    assert st2.status == 0 and st2.iters == full.iters
+    assert rel_fro(Om2.cpu().numpy(), full.Omega) <= 1e-9
+
+
+def test_fp64_loss_and_grad(A):
+    rng = np.random.Generator(np.random.PCG64(7))
+    n, p = 70, 150
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    Om = np.eye(p) + 0.05 * rng.standard_normal((p, p)) * (rng.random((p, p)) < 0.1)
+    np.fill_diagonal(Om, 1.0 + rng.random(p))
+    Xd = X.astype(np.float64)
+    f, g = A.accord_loss(dev(X), dev(Om, torch.float64), 0.3)
+    assert abs(g - R.smooth_g(Om, Xd)) <= 1e-12 * abs(g)
+    assert abs(f - R.objective(Om, Xd, 0.3)) <= 1e-12 * abs(f)
+    f2, _ = A.accord_loss(dev(X), dev(Om, torch.float64), 0.3, penalize_diag=False)
+    assert abs(f2 - R.objective(Om, Xd, 0.3, penalize_diag=False)) <= 1e-12 * abs(f2)
+    G = A.accord_grad(dev(X), dev(Om, torch.float64)).cpu().numpy()
+    Gref = R.grad_g(Om, Xd)
+    assert np.max(np.abs(G - Gref)) <= 1e-12 * np.max(np.abs(Gref))
+    Gs = A.accord_grad(dev(X), dev(Om, torch.float64), smooth=True).cpu().numpy()
+    np.testing.assert_allclose(Gs, Gref - np.diag(1.0 / np.diag(Om)), rtol=0, atol=1e-12 * np.max(np.abs(Gref)))
+
+
+# ------------------------------------------------------ tcgen05 BF16x3 ----
+
+@pytest.mark.parametrize("n,p", [(64, 128), (100, 333), (257, 520), (1000, 1000), (5, 17)])
+def test_mixed_grad_against_fp64_reference(A, n, p):
+    """accord_grad through the tcgen05 split-BF16 GEMMs vs a float64
+    reference of the same contraction (both GEMMs, ragged tiles)."""
+    g = torch.Generator().manual_seed(n * 1000 + p)
+    X = torch.randn(n, p, generator=g, dtype=torch.float64)
+    Om = torch.randn(p, p, generator=g, dtype=torch.float64) * 0.1
+    Om.diagonal().copy_(1.0 + torch.rand(p, generator=g, dtype=torch.float64))
+    X32, Om32 = X.float(), Om.float()
+    ref = (Om32.double() @ X32.double().T) @ X32.double() / n
+    G = A.accord_grad(X32.cuda().contiguous(), Om32.cuda().contiguous()).double().cpu()
+    scale = (Om32.double().abs() @ (X32.double().T.abs() @ X32.double().abs())).max() / n
+    err = (G - ref).abs().max() / scale
+    assert err <= 2e-5, float(err)
+    Gs = A.accord_grad(X32.cuda().contiguous(), Om32.cuda().contiguous(), smooth=True).double().cpu()
+    refs = ref - torch.diag(1.0 / Om32.double().diagonal())
+    assert ((Gs - refs).abs().max() / scale) <= 2e-5
+
+
+def test_mixed_loss(A):
+    rng = np.random.Generator(np.random.PCG64(8))
+    n, p = 300, 700
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    Om = (0.05 * rng.standard_normal((p, p)) * (rng.random((p, p)) < 0.05)).astype(np.float32)
+    np.fill_diagonal(Om, (1.0 + rng.random(p)).astype(np.float32))
+    f, g = A.accord_loss(dev(X), dev(Om), 0.2)
+    Xd, Od = X.astype(np.float64), Om.astype(np.float64)
+    assert abs(g - R.smooth_g(Od, Xd)) <= 3e-5 * abs(g)
+    assert abs(f - R.objective(Od, Xd, 0.2)) <= 3e-5 * abs(f)
+
+
+def test_mixed_fit_matches_oracle(A):
+    """Scale-free tree p=600, n=400, lambda=0.15: mixed result vs the FP64
+    oracle, rel. Frobenius <= 1e-4 and support equal outside the band."""
+    w = workload("scalefree", p=600, n=400)
+    ref = R.fit(w.X, w.lam, kkt_tol=1e-7, max_iter=3000)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="mixed", kkt_tol=2e-5, max_iter=3000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    assert rel_fro(O, ref.Omega) <= 1e-4
+    G_ref = R.grad_g(ref.Omega, w.X.astype(np.float64))
+    assert support_mismatch(O, ref.Omega, G_ref, w.lam, band=1e-4) == 0
+    Xd = w.X.astype(np.float64)
+    assert R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam) <= 1e-4
+
+
+def test_mixed_fit_ragged_sizes(A):
+    for kind, p, n in (("hubblock", 400, 130), ("er", 77, 45)):
+        w = workload(kind, p=p, n=n)
+        ref = R.fit(w.X, w.lam, kkt_tol=1e-7, max_iter=5000)
+        Om, st = A.accord_fit(dev(w.X), w.lam, precision="mixed", kkt_tol=2e-5, max_iter=5000)
+        assert st.status in (0, 1), st
+        O = Om.double().cpu().numpy()
+        assert rel_fro(O, ref.Omega) <= 1e-4, (kind, rel_fro(O, ref.Omega))
+
+
+# ------------------------------------------------------------ error paths ---
+
+def test_error_statuses(A):
+    w = workload("ar1", p=40, n=30)
+    X = dev(w.X)
+    bad = np.eye(40)
+    bad[3, 3] = -1.0
+    _, st = A.accord_fit(X, w.lam, precision="fp64", Omega=dev(bad, torch.float64), init_from_omega=True,
+                         check=False)
+    assert st.status == -2  # EDOMAIN
+    Xn = w.X.copy()
+    Xn[2, 5] = np.nan
+    _, st = A.accord_fit(dev(Xn), w.lam, precision="fp64", check=False)
+    assert st.status == -2
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    _, st = A.accord_fit(X, w.lam, precision="fp64", workspace=ws, check=False)
+    assert st.status == -5  # ENOMEM
+    _, st = A.accord_fit(X, w.lam, precision="mixed", max_iter=1, kkt_tol=0.0, check=False)
+    assert st.status == 1 and st.iters == 1
+    # a caller-provided workspace gives the same answer as an internal one
+    nbytes = A.accord_workspace_bytes(30, 40, precision="fp64")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    O1, _ = A.accord_fit(X, w.lam, precision="fp64", workspace=ws, kkt_tol=1e-9)
+    O2, _ = A.accord_fit(X, w.lam, precision="fp64", kkt_tol=1e-9)
+    assert torch.equal(O1, O2)
+
+
+@pytest.mark.parametrize("n,p", [(1, 7), (2, 40), (3, 3), (100, 200), (300, 2000), (1000, 1200)])
+def test_lipschitz_matches_eigensolver(A, n, p):
+    """L = sigma_max(S) from the device Lanczos process equals the largest
+    eigenvalue from a dense symmetric eigensolver (FP64 Gram: 1e-10; split
+    BF16 Gram: 1e-4)."""
+    rng = np.random.Generator(np.random.PCG64(500 + n))
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    L_ref = R.lipschitz(X)
+    _, st = A.accord_fit(dev(X), 0.3, precision="fp64", max_iter=0, check=False)
+    assert abs(st.L - L_ref) <= 1e-10 * L_ref, (st.L, L_ref)
+    _, st = A.accord_fit(dev(X), 0.3, precision="mixed", max_iter=0, check=False)
+    assert abs(st.L - L_ref) <= 1e-4 * L_ref, (st.L, L_ref)
