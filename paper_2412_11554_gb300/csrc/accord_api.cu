@@ -8,7 +8,7 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/accord.h"
+#include "accord.h"
 #include "internal.h"
 #include "tc_gemm.h"
 

@@ -5,7 +5,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "../../include/accord.h"
+#include "accord.h"
 #include "internal.h"
 #include "tc_gemm.h"
 

@@ -7,8 +7,9 @@
 // FP32 resolution of the sum), which recovers ~16 significant bits per operand.
 //
 // Warp roles (one CTA per SM, persistent over output tiles):
-//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo tiles into a STAGES-deep
-//               shared-memory ring (128-byte swizzle), one mbarrier per stage.
+//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo tiles (32 BF16 of K a row)
+//               into a 4-deep shared-memory ring (64-byte swizzle), one
+//               mbarrier per stage.
 //   warp 1      TMEM allocator and single-thread MMA issuer (tcgen05.mma).
 //   warps 2..9  epilogue: tcgen05.ld from a double-buffered TMEM accumulator,
 //               so the epilogue of tile i overlaps the main loop of tile i+1.
@@ -25,12 +26,17 @@ namespace accord {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;               // BF16 elements per 128-byte swizzle row
+constexpr int BK = 32;               // BF16 elements per 64-byte swizzle row
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kBN = 256;
-constexpr int kStages = 2;
+constexpr int kStages = 4;
+// CTAs of a cluster take consecutive M blocks of one N block; each loads
+// 1/kClusterM of the shared B tile and multicasts it to all of them.
+constexpr int kClusterM = 2;
+constexpr int kBBox = kBN / kClusterM;                 // B rows one CTA loads
+constexpr uint32_t kBSliceBytes = kBBox * BK * 2;
 constexpr uint32_t kABytes = BM * BK * 2;
 constexpr uint32_t kBBytes = kBN * BK * 2;
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
@@ -46,6 +52,13 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   const int r = t - g * per_group;
   mb = first_m + r % gm;
   nb = r / gm;
+}
+
+// Cluster tile T (scheduled per cluster) -> this CTA's M / N block.
+__device__ __forceinline__ void cta_tile(int T, const TcParams& prm, int rank, int& mb, int& nb) {
+  int mg;
+  tile_coords(T, prm.tiles_mc, prm.tiles_n, prm.group_m, mg, nb);
+  mb = mg * kClusterM + rank;
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
@@ -81,6 +94,32 @@ __device__ __forceinline__ void transpose32(float* buf, const uint32_t (&rr)[32]
   __syncwarp();
 }
 
+// Asynchronous copy of the 32 x 32 FP32 block src[row_base .. +31][col0 .. +31]
+// (row-major, 16-byte aligned rows) into buf, row-major: 8 x 16 bytes a thread,
+// four full 128-byte rows per warp instruction.
+__device__ __forceinline__ void prefetch_block(float* buf, const float* __restrict__ src, int64_t ld,
+                                               int64_t row_base, int64_t col0, int lane) {
+  const uint32_t sbase = ptx::smem_u32(buf);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int idx = k * 32 + lane, r = idx >> 3, seg = idx & 7;
+    const float* g = src + (row_base + r) * ld + col0 + 4 * seg;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + (uint32_t)(r * 128 + seg * 16)),
+                 "l"(g)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Column `lane` of a block written by prefetch_block (conflict-free reads).
+__device__ __forceinline__ void read_block_column(const float* buf, int lane, float (&pre)[32]) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) pre[r] = buf[r * 32 + lane];
+  __syncwarp();
+}
+
 // pre[r] = src[row_base + r][colt] (zero outside the matrix).
 __device__ __forceinline__ void load_column(const float* __restrict__ src, int64_t ld, int64_t row_base,
                                             int64_t colt, bool full, const EpiArgs& ea, float (&pre)[32]) {
@@ -95,30 +134,31 @@ __device__ __forceinline__ void load_column(const float* __restrict__ src, int64
   }
 }
 
-__device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo, float x) {
-  __nv_bfloat16 h, l;
-  split_bf16(x, h, l);
-  *hi = h;
-  *lo = l;
-}
-
 // Y+ = Y + Delta X^T (aux = Y) or Y = Omega X^T (aux = null) for column colt.
 template <bool CHECK>
 __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base, int64_t colt,
                                         const float (&v)[32], const float (&pre)[32], Sums& sm) {
   float sd = 0.f, sn = 0.f, chk = 0.f;
   const bool cok = !CHECK || colt < ea.N;
+  const bool has_aux = ea.aux != nullptr;
+  float* po = ea.out ? ea.out + row_base * prm.ldout + colt : nullptr;
+  __nv_bfloat16* ph = ea.out_hi ? ea.out_hi + row_base * prm.ldplane + colt : nullptr;
+  __nv_bfloat16* pl = ea.out_lo ? ea.out_lo + row_base * prm.ldplane + colt : nullptr;
+  const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
-    const int64_t row = row_base + r;
-    if (CHECK && !(cok && row < ea.M)) continue;
+    if (CHECK && !(cok && row_base + r < ea.M)) continue;
     const float dv = v[r] * ea.scale;
-    const float yn = (ea.aux ? pre[r] : 0.f) + dv;
+    const float yn = (has_aux ? pre[r] : 0.f) + dv;
     sd = fmaf(dv, dv, sd);
     sn = fmaf(yn, yn, sn);
     chk = fmaf(yn, 0.f, chk);
-    if (ea.out) ea.out[row * prm.ldout + colt] = yn;
-    if (ea.out_hi) store_split(ea.out_hi + row * prm.ldplane + colt, ea.out_lo + row * prm.ldplane + colt, yn);
+    if (po) po[r * ldo] = yn;
+    if (ph) {
+      const __nv_bfloat16 hb = __float2bfloat16_rn(yn);
+      ph[r * ldp] = hb;
+      pl[r * ldp] = __float2bfloat16_rn(yn - __bfloat162float(hb));
+    }
   }
   sm.r0 += (double)sd;
   sm.r1 += (double)sn;
@@ -127,38 +167,45 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
-// and the diagonal (row == colt).
+// and the diagonal (row == colt); the unchecked form is the hot path.
 template <bool CHECK>
 __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
                                            int64_t colt, const float (&v)[32], const float (&pre)[32], Sums& sm) {
-  float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f;
-  int nnz = 0;
-  const float tau = ea.tau, tlam = ea.tau * ea.lam;
+  float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
+  const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
+  float* po = ea.out + row_base * prm.ldout + colt;
+  __nv_bfloat16* ph = ea.out_hi + row_base * prm.ldplane + colt;
+  __nv_bfloat16* pl = ea.out_lo + row_base * prm.ldplane + colt;
+  const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
-    const int64_t row = row_base + r;
-    if (CHECK && !(cok && row < ea.M)) continue;
-    const float g = v[r] * ea.scale;
+    if (CHECK && !(cok && row_base + r < ea.M)) continue;
+    const float g = v[r] * scale;
     const float om = pre[r];
     const float a = fmaf(-tau, g, om);
     float w;
-    if (CHECK && row == colt) {
+    if (CHECK && row_base + r == colt) {
       w = diag_prox(a, tau, ea.lam_d);
       sm.r2 += log((double)w);
       sm.r3 += (double)w;
-      kk = fmaxf(kk, kkt_entry(om, g, true, ea.lam, ea.lam_d));
+      kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
     } else {
-      w = soft_threshold(a, tlam);
+      const float m = fabsf(a) - tlam;
+      w = m > 0.f ? copysignf(m, a) : 0.f;
       sl1 += fabsf(w);
-      nnz += (w != 0.f) ? 1 : 0;
-      kk = fmaxf(kk, kkt_entry(om, g, false, ea.lam, ea.lam_d));
+      nnz += (w != 0.f) ? 1.f : 0.f;
+      const float kz = fabsf(g) - lam;                 // omega == 0: max(|G| - lambda, 0)
+      const float knz = fabsf(g + copysignf(lam, om));  // omega != 0: |G + lambda sign(omega)|
+      kk = fmaxf(kk, om != 0.f ? knz : kz);
     }
     chk = fmaf(g, 0.f, chk);
     const float d = w - om;
     sd = fmaf(d, d, sd);
-    ea.out[row * prm.ldout + colt] = w;
-    store_split(ea.out_hi + row * prm.ldplane + colt, ea.out_lo + row * prm.ldplane + colt, d);
+    po[r * ldo] = w;
+    const __nv_bfloat16 hb = __float2bfloat16_rn(d);
+    ph[r * ldp] = hb;
+    pl[r * ldp] = __float2bfloat16_rn(d - __bfloat162float(hb));
   }
   sm.r0 += (double)sd;
   sm.r1 += (double)sl1;
@@ -217,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
+      ptx::mbar_init(&empty[s], kClusterM);  // one release from every CTA's MMA
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
@@ -236,6 +283,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // peers multicast into this CTA's shared memory: their barriers must be live
+  ptx::cluster_sync();
+  const int rank = (int)ptx::cluster_ctarank();
+  const int cluster_id = blockIdx.x / kClusterM;
+  const int nclusters = gridDim.x / kClusterM;
+  constexpr uint16_t kMask = (uint16_t)((1u << kClusterM) - 1u);
 
   const int asel = prm.a_nxt ? nxt : cur;
   const CUtensorMap* mA_hi = &prm.a_hi[asel];
@@ -256,21 +309,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       bool filled[kStages];
       for (int q = 0; q < kStages; ++q) { filled[q] = false; fill_ph[q] = 0; }
       bool ok = true;
-      for (int t = blockIdx.x; t < prm.ntiles && ok; t += gridDim.x) {
+      for (int T = cluster_id; T < prm.ntiles_c && ok; T += nclusters) {
         int mb, nb;
-        tile_coords(t, prm.tiles_m, prm.tiles_n, prm.group_m, mb, nb);
+        cta_tile(T, prm, rank, mb, nb);
         for (int kb = 0; kb < prm.num_kb; ++kb) {
+          // the slot is free only when every CTA of the cluster released it
           if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
           ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
           const uint32_t st = smem_base + s * kStageBytes;
           ptx::tma_load_2d(st, mA_hi, &full[s], kb * BK, mb * BM);
           ptx::tma_load_2d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM);
-          ptx::tma_load_2d(st + 2 * kABytes, mB_hi, &full[s], kb * BK, nb * kBN);
-          ptx::tma_load_2d(st + 2 * kABytes + kBBytes, mB_lo, &full[s], kb * BK, nb * kBN);
+          const int32_t by = nb * kBN + rank * kBBox;
+          ptx::tma_load_2d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, kMask);
+          ptx::tma_load_2d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by,
+                              kMask);
           filled[s] = true;
           fill_ph[s] = ph;
           if (++s == kStages) { s = 0; ph ^= 1u; }
         }
+      }
+      if (ok) {
+        // wait for the last releases of every slot, so that no peer signal
+        // can still be on its way to this CTA when it leaves
+        for (int q = 0; q < kStages; ++q)
+          if (filled[q] && !ptx::mbar_wait(&empty[q], fill_ph[q], abort_flag)) ok = false;
       }
       if (!ok) {
         *abort_flag = 1;
@@ -287,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       uint32_t s = 0, ph = 0;
       bool ok = true;
       int i = 0;
-      for (int t = blockIdx.x; t < prm.ntiles && ok; t += gridDim.x, ++i) {
+      for (int T = cluster_id; T < prm.ntiles_c && ok; T += nclusters, ++i) {
         const uint32_t acc = i & 1, aph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { ok = false; break; }
         ptx::tc_fence_after();
@@ -296,10 +358,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (!ptx::mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t st = smem_base + s * kStageBytes;
-          const uint64_t a_hi = ptx::sdesc_k128(st);
-          const uint64_t a_lo = ptx::sdesc_k128(st + kABytes);
-          const uint64_t b_hi = ptx::sdesc_k128(st + 2 * kABytes);
-          const uint64_t b_lo = ptx::sdesc_k128(st + 2 * kABytes + kBBytes);
+          const uint64_t a_hi = ptx::sdesc_k64(st);
+          const uint64_t a_lo = ptx::sdesc_k64(st + kABytes);
+          const uint64_t b_hi = ptx::sdesc_k64(st + 2 * kABytes);
+          const uint64_t b_lo = ptx::sdesc_k64(st + 2 * kABytes + kBBytes);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
@@ -307,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             ptx::mma_f16(d, a_hi + off, b_lo + off, idesc, 1u);
             ptx::mma_f16(d, a_hi + off, b_hi + off, idesc, 1u);
           }
-          ptx::mma_commit(&empty[s]);
+          ptx::mma_commit_mc(&empty[s], kMask);  // release the slot in every CTA
           if (++s == kStages) { s = 0; ph ^= 1u; }
         }
         if (!ok) break;
@@ -344,19 +406,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.M = prm.M;
     ea.N = prm.N;
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
+    // cp.async needs 16-byte aligned rows
+    const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
     int i = 0;
-    for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x, ++i) {
+    for (int T = cluster_id; T < prm.ntiles_c; T += nclusters, ++i) {
       int mb, nb;
-      tile_coords(t, prm.tiles_m, prm.tiles_n, prm.group_m, mb, nb);
+      cta_tile(T, prm, rank, mb, nb);
       const uint32_t acc = i & 1, aph = (i >> 1) & 1;
       const int64_t row_base = (int64_t)mb * BM + 32 * q;
       const int64_t col_base = (int64_t)nb * kBN + h * kColsPerWarp;
       const bool rows_full = row_base + 32 <= prm.M;
       Sums sm;
       float pre[32];
-      // the first chunk's operand does not depend on the MMA: fetch it before waiting
-      if (kNeedAux && ea.aux != nullptr)
-        load_column(ea.aux, prm.ldaux, row_base, col_base + lane, rows_full && col_base + 32 <= prm.N, ea, pre);
+      // the first chunk's operand does not depend on the MMA: start fetching it
+      // before waiting for the accumulator
+      bool pending = false;
+      if (kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
+        prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane);
+        pending = true;
+      }
       const bool ok = ptx::mbar_wait(&tfull[acc], aph, abort_flag);
       if (!ok) {
         *abort_flag = 1;
@@ -369,13 +437,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int64_t col0 = col_base + c;
           const int64_t colt = col0 + lane;
           const bool full = rows_full && col0 + 32 <= prm.N;
-          if (kNeedAux && ea.aux != nullptr && c > 0)
-            load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
+          if (kNeedAux && ea.aux != nullptr) {
+            if (pending) read_block_column(tbuf, lane, pre);
+            else load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
+          }
+          pending = false;
           uint32_t rr[32];
           ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * kBN + h * kColsPerWarp + c, rr);
           ptx::tmem_ld_wait();
           float v[32];
           transpose32(tbuf, rr, lane, v);
+          // the buffer is free again: fetch the next chunk's operand while this one computes
+          if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
+              col0 + 64 <= prm.N) {
+            prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, lane);
+            pending = true;
+          }
           if (row_base >= prm.M || col0 >= prm.N) continue;  // warp-uniform
           const bool diag = (row_base == col0);
           if (MODE == kModeY) {
@@ -391,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
         }
       }
+      if (pending) asm volatile("cp.async.wait_group 0;" ::: "memory");
       const double r0 = sm.r0, r1 = sm.r1, r2 = sm.r2, r3 = sm.r3, r4 = sm.r4, rbad = sm.bad;
       const float rkkt = sm.kkt;
       ptx::tc_fence_before();
@@ -415,13 +493,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       epi_bar();
       if (e == 0) {
-        if ((MODE == kModeY || MODE == kModeProx) && prm.part != nullptr && lane < W) {
+        if ((MODE == kModeY || MODE == kModeProx) && prm.part != nullptr && lane < W && mb < prm.tiles_m) {
           double x = red[lane];
           for (int w = 1; w < kEpiWarps; ++w)
             x = (MODE == kModeProx && lane == kPKkt) ? fmax(x, red[w * 8 + lane]) : x + red[w * 8 + lane];
           const int bad_slot = (MODE == kModeProx) ? (int)kPBad : (int)kYBad;
           if (*abort_flag && lane == bad_slot) x += 1.0;
-          prm.part[(int64_t)t * W + lane] = x;
+          prm.part[((int64_t)mb * prm.tiles_n + nb) * W + lane] = x;
         }
         if (lane == 0) *stop_flag = *abort_flag;
       }
@@ -433,6 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncwarp();
   ptx::tc_fence_before();
   __syncthreads();
+  ptx::cluster_sync();  // no CTA leaves while a peer may still signal it
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, kTmemCols);
@@ -442,24 +521,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 template <int MODE>
 cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   static int configured = -1;
+  static int max_clusters = 0;
   int dev = 0;
   cudaGetDevice(&dev);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterM;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (configured != dev) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
+    // persistent grid: as many clusters as can be resident at once
+    cfg.gridDim = dim3(kClusterM, 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE>, &cfg) != cudaSuccess || n < 1) {
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      n = sms / kClusterM > 0 ? sms / kClusterM : 1;
+    }
+    max_clusters = n;
     configured = dev;
   }
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(prm.ntiles, sms > 0 ? sms : 1);
-  tc_gemm_kernel<MODE><<<grid, kThreads, kSmemBytes, st>>>(prm);
-  return cudaGetLastError();
+  const int clusters = (int)std::min<int64_t>(prm.ntiles_c, max_clusters);
+  cfg.gridDim = dim3((unsigned)(clusters * kClusterM), 1, 1);
+  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, prm);
 }
 
 }  // namespace
 
-int tc_box_n() { return kBN; }
+int tc_box_n() { return kBBox; }
 
 int64_t tc_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + kBN - 1) / kBN); }
 
@@ -471,12 +569,17 @@ void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K) {
   prm.tiles_m = (int32_t)((M + BM - 1) / BM);
   prm.tiles_n = (int32_t)((N + kBN - 1) / kBN);
   prm.ntiles = prm.tiles_m * prm.tiles_n;
-  prm.group_m = 8;
+  prm.tiles_mc = (prm.tiles_m + kClusterM - 1) / kClusterM;
+  prm.ntiles_c = prm.tiles_mc * prm.tiles_n;
+  // raster: groups of cluster rows, N block by N block; wide groups when there
+  // are many N blocks (the B tiles then stream, A tiles stay in L2)
+  prm.group_m = prm.tiles_n > 16 ? 32 : 4;
   prm.bn = kBN;
 }
 
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st) {
   if (prm.ntiles <= 0) return cudaSuccess;
+  if (prm.ntiles_c <= 0) return cudaErrorInvalidValue;
   switch (mode) {
     case kModeY: return launch_mode<kModeY>(prm, st);
     case kModeProx: return launch_mode<kModeProx>(prm, st);
@@ -505,7 +608,7 @@ bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
   const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides,
-                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }

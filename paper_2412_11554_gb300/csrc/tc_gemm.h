@@ -20,6 +20,7 @@ struct TcParams {
   int* err;             // device error word (kErr* bits), never null
   int64_t M, N, K;
   int32_t num_kb, tiles_m, tiles_n, ntiles;
+  int32_t tiles_mc, ntiles_c;  // cluster rows of M blocks, cluster tiles
   int32_t a_nxt, smooth, group_m, bn;
   float* out[2];        // FP32 output (Y+, Omega+ or G), index nxt
   int64_t ldout;
@@ -43,7 +44,7 @@ bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
 // Fills the shape fields (num_kb, tiles, bn) for an M x N x K problem.
 void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K);
 int64_t tc_tiles(int64_t M, int64_t N);
-int tc_box_n();  // rows of the B box (= BN)
+int tc_box_n();  // rows of the B box one CTA loads (its share of the N tile)
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
 
 }  // namespace accord
