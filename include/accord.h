@@ -159,6 +159,31 @@ const char* accord_status_string(int status);
  * ACCORD_EUNSUPPORTED / ACCORD_ECUDA. */
 int accord_device_check(void);
 
+/* Size of the static device scratch array used by accord_loss_f64_noalloc. */
+#define ACCORD_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* accord_loss without any device allocation, for callers that must not
+ * allocate: code inside a custom allocator's callback, latency-bound loops
+ * that cannot afford the allocator's implicit synchronisation, or processes
+ * whose device memory another caching allocator has already reserved.  The
+ * paper has no counterpart; it is an interface convenience.
+ *   X        device, n x p double, row-major (FP64 data: no conversion buffer).
+ *   Omega    device, p x p double, row-major.
+ *   fg_out   device, 2 doubles: fg_out[0] = f, fg_out[1] = g, as accord_loss.
+ *   stream   cudaStream_t (NULL = legacy default stream); the call does not
+ *            synchronise it -- read fg_out after the stream's work completes.
+ * Scratch: a file-scope __device__ array of ACCORD_NOALLOC_SCRATCH_BYTES bytes
+ * per GPU, held until the process exits; the call needs
+ * 32 * ceil(p/64) * ceil(n/64) + 64 * p bytes of it (each part rounded up to
+ * 256) and returns ACCORD_ENOMEM when that exceeds the array (for n = 1000 this
+ * allows p up to about 116000).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make
+ * that first call before any stream capture.  All calls share the array, so
+ * calls whose work overlaps on the GPU (other streams, unordered host threads)
+ * race on it; the array's previous contents are never read. */
+int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double* Omega, double lambda,
+                            int penalize_diag, void* stream, double* fg_out);
+
 /* Description of the first failure of the calling thread's most recent
  * accord_fit / accord_loss / accord_grad call ("" when it succeeded): the
  * source location and the CUDA error string or the device error bits.  The

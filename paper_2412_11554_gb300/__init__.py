@@ -12,6 +12,7 @@ from .accord import (  # noqa: F401
     accord_grad,
     accord_last_error,
     accord_loss,
+    accord_loss_f64_noalloc,
     accord_status_string,
     accord_workspace_bytes,
     load_library,

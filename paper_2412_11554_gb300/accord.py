@@ -48,7 +48,8 @@ class AccordStats(ctypes.Structure):
 
 
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_loss",
-           "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error")
+           "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
+           "accord_loss_f64_noalloc")
 
 _lib = None
 
@@ -83,6 +84,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_device_check.restype = i32
     lib.accord_last_error.argtypes = []
     lib.accord_last_error.restype = ctypes.c_char_p
+    lib.accord_loss_f64_noalloc.argtypes = [P, i64, i64, P, dbl, i32, P, P]
+    lib.accord_loss_f64_noalloc.restype = i32
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -225,6 +228,24 @@ def accord_grad(X: torch.Tensor, Omega: torch.Tensor, smooth: bool = False, *, p
     if status != OK:
         raise AccordError(status, "accord_grad")
     return out
+
+
+def accord_loss_f64_noalloc(X: torch.Tensor, Omega: torch.Tensor, lam: float, fg_out: torch.Tensor, *,
+                            penalize_diag: bool = True, stream=None) -> None:
+    """(f, g) of Eq. 3.2 / Eq. 3.4 into the device tensor fg_out (2 doubles)
+    without any device allocation by the library (its scratch is a static
+    device array; see include/accord.h).  X and Omega are CUDA float64."""
+    lib = load_library()
+    _check_x(X, torch.float64)
+    n, p = X.shape
+    if not (Omega.is_cuda and Omega.dtype == torch.float64 and Omega.shape == (p, p) and Omega.is_contiguous()):
+        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA float64 tensor")
+    if not (fg_out.is_cuda and fg_out.dtype == torch.float64 and fg_out.numel() >= 2):
+        raise ValueError("fg_out must be a CUDA float64 tensor with at least 2 elements")
+    status = lib.accord_loss_f64_noalloc(X.data_ptr(), n, p, Omega.data_ptr(), float(lam), int(bool(penalize_diag)),
+                                         _stream_handle(stream), fg_out.data_ptr())
+    if status != OK:
+        raise AccordError(status, "accord_loss_f64_noalloc")
 
 
 def accord_status_string(status: int) -> str:
