@@ -70,11 +70,16 @@ struct EpiArgs {
   __nv_bfloat16* out_lo;
   const float* aux;
   int64_t M, N;
+  uint64_t pol_stream;  // L2 evict-first policy for the iterate stream
 };
 
-struct Sums {  // per-thread tile partials (FP64 across chunks, FP32 within)
-  double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0, bad = 0.0;
-  float kkt = 0.f;
+// Per-thread tile partials.  The dense sums run in FP32 over the thread's
+// share of one tile (at most 128 terms) and are folded across warps and tiles
+// in FP64: FP64 is a slow pipe on this part, so it is kept out of the
+// per-element path.  The diagonal terms (one per row) are FP64 throughout.
+struct Sums {
+  float r0 = 0.f, r1 = 0.f, r4 = 0.f, bad = 0.f, kkt = 0.f;
+  double r2 = 0.0, r3 = 0.0;
 };
 
 // Transpose a 32x32 accumulator block: on entry thread `lane` holds TMEM row
@@ -98,15 +103,13 @@ __device__ __forceinline__ void transpose32(float* buf, const uint32_t (&rr)[32]
 // (row-major, 16-byte aligned rows) into buf, row-major: 8 x 16 bytes a thread,
 // four full 128-byte rows per warp instruction.
 __device__ __forceinline__ void prefetch_block(float* buf, const float* __restrict__ src, int64_t ld,
-                                               int64_t row_base, int64_t col0, int lane) {
+                                               int64_t row_base, int64_t col0, int lane, uint64_t pol) {
   const uint32_t sbase = ptx::smem_u32(buf);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int idx = k * 32 + lane, r = idx >> 3, seg = idx & 7;
     const float* g = src + (row_base + r) * ld + col0 + 4 * seg;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + (uint32_t)(r * 128 + seg * 16)),
-                 "l"(g)
-                 : "memory");
+    ptx::cp_async16_hint(sbase + (uint32_t)(r * 128 + seg * 16), g, pol);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -153,16 +156,17 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
     sd = fmaf(dv, dv, sd);
     sn = fmaf(yn, yn, sn);
     chk = fmaf(yn, 0.f, chk);
-    if (po) po[r * ldo] = yn;
+    if (po) ptx::st_f32_hint(po + r * ldo, yn, ea.pol_stream);
     if (ph) {
       const __nv_bfloat16 hb = __float2bfloat16_rn(yn);
-      ph[r * ldp] = hb;
-      pl[r * ldp] = __float2bfloat16_rn(yn - __bfloat162float(hb));
+      ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
+      ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(yn - __bfloat162float(hb))),
+                       ea.pol_stream);
     }
   }
-  sm.r0 += (double)sd;
-  sm.r1 += (double)sn;
-  if (chk != 0.f) sm.bad += 1.0;
+  sm.r0 += sd;
+  sm.r1 += sn;
+  if (chk != 0.f) sm.bad += 1.f;
 }
 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
@@ -202,16 +206,17 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
     chk = fmaf(g, 0.f, chk);
     const float d = w - om;
     sd = fmaf(d, d, sd);
-    po[r * ldo] = w;
+    ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
     const __nv_bfloat16 hb = __float2bfloat16_rn(d);
-    ph[r * ldp] = hb;
-    pl[r * ldp] = __float2bfloat16_rn(d - __bfloat162float(hb));
+    ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
+    ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(d - __bfloat162float(hb))),
+                     ea.pol_stream);
   }
-  sm.r0 += (double)sd;
-  sm.r1 += (double)sl1;
-  sm.r4 += (double)nnz;
+  sm.r0 += sd;
+  sm.r1 += sl1;
+  sm.r4 += nnz;
   sm.kkt = fmaxf(sm.kkt, kk);
-  if (chk != 0.f || !(sd == sd)) sm.bad += 1.0;
+  if (chk != 0.f || !(sd == sd)) sm.bad += 1.f;
 }
 
 __device__ __forceinline__ void grad_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base, int64_t colt,
@@ -304,6 +309,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       ptx::tma_prefetch_desc(mA_lo);
       ptx::tma_prefetch_desc(mB_hi);
       ptx::tma_prefetch_desc(mB_lo);
+      // operand tiles are shared by many CTAs: keep them in L2 (the A operand
+      // of the Y GEMM is the Delta stream, read once: let it leave first)
+      const uint64_t pol_a = (MODE == kModeY && prm.ctrl != nullptr) ? ptx::policy_evict_first()
+                                                                       : ptx::policy_evict_last();
+      const uint64_t pol_keep = ptx::policy_evict_last();
       uint32_t s = 0, ph = 0;
       uint32_t fill_ph[kStages];
       bool filled[kStages];
@@ -317,12 +327,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
           ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
           const uint32_t st = smem_base + s * kStageBytes;
-          ptx::tma_load_2d(st, mA_hi, &full[s], kb * BK, mb * BM);
-          ptx::tma_load_2d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM);
+          ptx::tma_load_2d(st, mA_hi, &full[s], kb * BK, mb * BM, pol_a);
+          ptx::tma_load_2d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM, pol_a);
           const int32_t by = nb * kBN + rank * kBBox;
-          ptx::tma_load_2d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, kMask);
-          ptx::tma_load_2d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by,
-                              kMask);
+          ptx::tma_load_2d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, kMask, pol_keep);
+          ptx::tma_load_2d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by, kMask,
+                              pol_keep);
           filled[s] = true;
           fill_ph[s] = ph;
           if (++s == kStages) { s = 0; ph ^= 1u; }
@@ -405,6 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.aux = prm.aux[cur];
     ea.M = prm.M;
     ea.N = prm.N;
+    ea.pol_stream = ptx::policy_evict_first();
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
     // cp.async needs 16-byte aligned rows
     const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
@@ -422,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       // before waiting for the accumulator
       bool pending = false;
       if (kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
-        prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane);
+        prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane, ea.pol_stream);
         pending = true;
       }
       const bool ok = ptx::mbar_wait(&tfull[acc], aph, abort_flag);
@@ -450,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           // the buffer is free again: fetch the next chunk's operand while this one computes
           if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
               col0 + 64 <= prm.N) {
-            prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, lane);
+            prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, lane, ea.pol_stream);
             pending = true;
           }
           if (row_base >= prm.M || col0 >= prm.N) continue;  // warp-uniform
@@ -469,26 +480,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
       }
       if (pending) asm volatile("cp.async.wait_group 0;" ::: "memory");
-      const double r0 = sm.r0, r1 = sm.r1, r2 = sm.r2, r3 = sm.r3, r4 = sm.r4, rbad = sm.bad;
-      const float rkkt = sm.kkt;
       ptx::tc_fence_before();
       ptx::mbar_arrive(&tempty[acc]);
-      // Partial sums of this tile, folded in a fixed order.  Both named
-      // barriers run on every tile so that all epilogue warps leave the loop
-      // together (the stop decision is taken by one thread between them).
+      // Partial sums of this tile: FP32 warp trees, then FP64 across the warps
+      // (fixed order).  Both named barriers run on every tile so that all
+      // epilogue warps leave the loop together (the stop decision is taken by
+      // one thread between them).
       constexpr int W = (MODE == kModeY) ? kYSlots : kProxSlots;
       if (MODE == kModeY || MODE == kModeProx) {
-        double vals[8];
-        if (MODE == kModeY) {
-          vals[kYDiff2] = r0; vals[kYNorm2] = r1; vals[kYBad] = rbad; vals[3] = 0.0;
-        } else {
-          vals[kPDelta2] = r0; vals[kPLogDiag] = r2; vals[kPDiagSum] = r3; vals[kPL1Off] = r1;
-          vals[kPNnz] = r4; vals[kPKkt] = (double)rkkt; vals[kPBad] = rbad; vals[7] = 0.0;
-        }
+        float f0 = sm.r0, f1 = sm.r1, f4 = sm.r4, fb = sm.bad, fk = sm.kkt;
 #pragma unroll
-        for (int s = 0; s < W; ++s) {
-          const double x = (MODE == kModeProx && s == kPKkt) ? warp_max(vals[s]) : warp_sum(vals[s]);
-          if (lane == 0) red[e * 8 + s] = x;
+        for (int o = 16; o > 0; o >>= 1) {
+          f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+          f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+          f4 += __shfl_xor_sync(0xffffffffu, f4, o);
+          fb += __shfl_xor_sync(0xffffffffu, fb, o);
+          fk = fmaxf(fk, __shfl_xor_sync(0xffffffffu, fk, o));
+        }
+        double d2 = sm.r2, d3 = sm.r3;
+        // diagonal entries exist only where the tile's row and column ranges meet
+        const int64_t r_lo = (int64_t)mb * BM, c_lo = (int64_t)nb * kBN;
+        if (MODE == kModeProx && r_lo < c_lo + kBN && c_lo < r_lo + BM) {
+          d2 = warp_sum(d2);
+          d3 = warp_sum(d3);
+        }
+        if (lane == 0) {
+          double* rw = red + e * 8;
+          if (MODE == kModeY) {
+            rw[kYDiff2] = (double)f0; rw[kYNorm2] = (double)f1; rw[kYBad] = (double)fb; rw[3] = 0.0;
+          } else {
+            rw[kPDelta2] = (double)f0; rw[kPLogDiag] = d2; rw[kPDiagSum] = d3; rw[kPL1Off] = (double)f1;
+            rw[kPNnz] = (double)f4; rw[kPKkt] = (double)fk; rw[kPBad] = (double)fb; rw[7] = 0.0;
+          }
         }
       }
       epi_bar();
