@@ -72,6 +72,10 @@ typedef struct accord_opts {
     int32_t init_from_omega; /* 1: Omega holds the starting iterate on entry; 0: Omega^0 = I   */
     int32_t lipschitz_max_iter; /* Lanczos steps allowed for L, at most 128 (default 128)    */
     int32_t profile;         /* 1: time every GEMM launch with CUDA events (stats t_*_gemm_ms)  */
+    int32_t sparse_update;   /* mixed mode: 1 (default) forms Y+ = Y + Delta X^T from the nonzero
+                                entries of Delta (the iterate is sparse); 0: dense tensor-core
+                                product every trial.  Ignored in FP64 mode (always dense).    */
+    int32_t reserved1;
     double  tau0;            /* initial step (default 1); <= 0 means 1/L                        */
     double  beta;            /* backtracking factor in (0, 1]; 1 = fixed step (default 0.5)     */
     double  kkt_tol;         /* stop when r(Omega^t) <= kkt_tol (default 1e-8)                  */

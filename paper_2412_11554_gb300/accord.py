@@ -30,6 +30,7 @@ class AccordOpts(ctypes.Structure):
         ("precision", ctypes.c_int32), ("tau_warm", ctypes.c_int32), ("max_iter", ctypes.c_int32),
         ("max_backtracks", ctypes.c_int32), ("penalize_diag", ctypes.c_int32),
         ("init_from_omega", ctypes.c_int32), ("lipschitz_max_iter", ctypes.c_int32), ("profile", ctypes.c_int32),
+        ("sparse_update", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("tau0", ctypes.c_double), ("beta", ctypes.c_double), ("kkt_tol", ctypes.c_double),
         ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
         ("trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int64),

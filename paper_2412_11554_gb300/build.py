@@ -24,7 +24,8 @@ BUILD = os.path.join(ROOT, "_build", "libaccord")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "misc.cu", "accord_api.cu", "accord_eval.cu", "accord_noalloc.cu"]
+SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "misc.cu", "sparse_y.cu", "accord_api.cu", "accord_eval.cu",
+           "accord_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -48,6 +48,10 @@ struct Layout {
   size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed mode
   size_t gram = 0, lz_v = 0, lz_w = 0, lz_a = 0, lz_b = 0;
   int lz_k = 0;
+  // sparse Delta update (mixed mode)
+  bool sparse = false;
+  int64_t nbuckets = 0;
+  size_t xt32 = 0, bkt_keys = 0, bkt_vals = 0, bkt_cnt = 0, part_sy = 0;
   size_t total = 0;
 };
 
@@ -57,7 +61,9 @@ size_t take(size_t& cursor, size_t bytes) {
   return at;
 }
 
-Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max) {
+constexpr int kBucketCap = 4096;  // Delta entries a 32-row group can hold
+
+Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max, bool sparse) {
   Layout L;
   L.f64 = f64;
   L.n = n;
@@ -96,6 +102,15 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
     L.x_lo = take(c, (size_t)n * L.ldk * 2);
     L.xt_hi = take(c, (size_t)p * L.ldyk * 2);
     L.xt_lo = take(c, (size_t)p * L.ldyk * 2);
+    L.sparse = sparse;
+    if (sparse) {
+      L.nbuckets = (p + kBucketRows - 1) / kBucketRows;
+      L.xt32 = take(c, (size_t)p * L.ldy * 4);
+      L.bkt_keys = take(c, (size_t)L.nbuckets * kBucketCap * 4);
+      L.bkt_vals = take(c, (size_t)L.nbuckets * kBucketCap * 4);
+      L.bkt_cnt = take(c, (size_t)L.nbuckets * 4);
+      L.part_sy = take(c, (size_t)L.nbuckets * kYSlots * 8);
+    }
   }
   L.gram = take(c, (size_t)n * n * 8);
   int64_t k = lanczos_max < kLanczosMax ? lanczos_max : kLanczosMax;
@@ -140,6 +155,12 @@ int check_device() {
   if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return kEcuda;
   if (major != 10 || minor != 3) return kEunsupported;
   return kOk;
+}
+
+// The sparse Delta update runs in mixed mode; bucket keys hold a column index
+// in 25 bits.
+bool use_sparse(const accord_opts& o, int64_t p) {
+  return o.precision == ACCORD_MIXED_BF16X3 && o.sparse_update != 0 && p < (1 << 25) - 1;
 }
 
 int check_opts(const accord_opts& o) {
@@ -248,6 +269,7 @@ int setup_gram(const Plan& P) {
 struct TrialPlan {
   GemmF64Params g2{}, g1{};
   TcParams t2{}, t1{};
+  SparseYParams sy{};
   SolveParams sp{};
 };
 
@@ -346,6 +368,36 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
   t1.ldaux = L.ldy;
   t1.part = at<double>(ws, L.part_y);
   t1.scale = 1.f;
+  if (L.sparse) {
+    // prox epilogue fills the Delta buckets; the dense Y GEMM only runs when
+    // one of them overflowed (its Delta planes then come from delta_planes)
+    t2.keys = at<uint32_t>(ws, L.bkt_keys);
+    t2.vals = at<float>(ws, L.bkt_vals);
+    t2.counts = at<int>(ws, L.bkt_cnt);
+    t2.dense_flag = &P.ctrl->dense;
+    t2.cap = kBucketCap;
+    t1.gate_dense = 1;
+    SparseYParams& sy = T.sy;
+    sy.ctrl = P.ctrl;
+    for (int b = 0; b < 2; ++b) {
+      sy.y[b] = at<float>(ws, L.y[b]);
+      sy.yw[b] = at<float>(ws, L.y[b]);
+      sy.y_hi[b] = at<__nv_bfloat16>(ws, L.y_hi[b]);
+      sy.y_lo[b] = at<__nv_bfloat16>(ws, L.y_lo[b]);
+    }
+    sy.xt = at<float>(ws, L.xt32);
+    sy.keys = at<uint32_t>(ws, L.bkt_keys);
+    sy.vals = at<float>(ws, L.bkt_vals);
+    sy.counts = at<int>(ws, L.bkt_cnt);
+    sy.cap = kBucketCap;
+    sy.tiles_m = (int32_t)L.nbuckets;
+    sy.tiles_n = t1.tiles_n;
+    sy.p = L.p;
+    sy.n = L.n;
+    sy.ldy = L.ldy;
+    sy.ldyk = L.ldyk;
+    sy.part = at<double>(ws, L.part_sy);
+  }
   return kOk;
 }
 
@@ -385,10 +437,23 @@ int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nla
   ACCORD_CK(launch_post_prox(P.ctrl, at<double>(P.ws, L.part_prox), L.tiles_prox, T.sp, trace, P.st));
   const int64_t ty = L.f64 ? gemm_f64_tiles(L.p, L.n) : tc_tiles(L.p, L.n);
   if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
-  if (L.f64) ACCORD_CK(launch_gemm_f64(kModeY, T.g1, P.st));
-  else ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
+  if (L.f64) {
+    ACCORD_CK(launch_gemm_f64(kModeY, T.g1, P.st));
+  } else if (L.sparse) {
+    // Y+ = Y + Delta X^T: sparse update, or the dense fallback when a bucket
+    // overflowed (each kernel checks ctrl->dense and exits when not its turn)
+    ACCORD_CK(launch_delta_planes(P.ctrl, at<float>(P.ws, L.om[0]), at<float>(P.ws, L.om[1]), L.p, L.ldo,
+                                  at<__nv_bfloat16>(P.ws, L.om_hi), at<__nv_bfloat16>(P.ws, L.om_lo), L.ldk, P.st));
+    ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
+    ACCORD_CK(launch_sparse_y(T.sy, P.st));
+    nlaunch += 2;
+  } else {
+    ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
+  }
   if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
-  ACCORD_CK(launch_decide(P.ctrl, at<double>(P.ws, L.part_y), ty, T.sp, trace, P.st));
+  ACCORD_CK(launch_decide(P.ctrl, at<double>(P.ws, L.part_y), ty, T.sp, trace,
+                          L.sparse ? at<int>(P.ws, L.bkt_cnt) : nullptr, (int)L.nbuckets,
+                          L.sparse ? at<double>(P.ws, L.part_sy) : nullptr, P.st));
   nlaunch += 4;
   return kOk;
 }
@@ -416,7 +481,7 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   if (!f64 && (n > 2147483647LL / 2 || p > 2147483647LL / 2)) return kEinval;
 
   Plan P;
-  P.L = make_layout(n, p, f64, o.max_iter, o.lipschitz_max_iter);
+  P.L = make_layout(n, p, f64, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p));
   P.st = static_cast<cudaStream_t>(o.stream);
   Guard guard;
   if (workspace == nullptr) {
@@ -453,6 +518,11 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     ACCORD_CK(launch_convert_x_bf16(X32, n, p, at<__nv_bfloat16>(ws, L.x_hi), at<__nv_bfloat16>(ws, L.x_lo), L.ldk,
                                     at<__nv_bfloat16>(ws, L.xt_hi), at<__nv_bfloat16>(ws, L.xt_lo), L.ldyk,
                                     at<int>(ws, L.bad), P.st));
+    if (L.sparse) {
+      ACCORD_CK(launch_transpose_x_f32(X32, n, p, at<float>(ws, L.xt32), L.ldy, P.st));
+      ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bkt_cnt), 0, (size_t)L.nbuckets * 4, P.st));
+      nlaunch += 1;
+    }
   }
   if (o.init_from_omega) {
     ACCORD_CK(launch_copy_omega(Omega, p, at<void>(ws, L.om[0]), L.ldo, f64, p, P.st));
@@ -594,6 +664,7 @@ void accord_default_opts(accord_opts* o) {
   o->init_from_omega = 0;
   o->lipschitz_max_iter = 128;
   o->profile = 0;
+  o->sparse_update = 1;
   o->tau0 = 1.0;
   o->beta = 0.5;
   o->kkt_tol = 1e-8;
@@ -609,7 +680,7 @@ size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* optp) {
   accord_default_opts(&o);
   if (optp) o = *optp;
   if (n < 1 || p < 1 || check_opts(o) != kOk) return 0;
-  return make_layout(n, p, o.precision == ACCORD_FP64, o.max_iter, o.lipschitz_max_iter).total;
+  return make_layout(n, p, o.precision == ACCORD_FP64, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p)).total;
 }
 
 int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, void* Omega,

@@ -60,7 +60,8 @@ struct Ctrl {
   double t_dy2, t_y2;
   // power iteration state
   double pw_est, pw_prev;
-  int32_t pw_iter, pad0;
+  int32_t pw_iter;
+  int32_t dense;      // a Delta bucket overflowed: this trial takes the dense Y GEMM
 };
 
 struct SolveParams {

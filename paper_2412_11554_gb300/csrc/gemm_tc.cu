@@ -71,7 +71,25 @@ struct EpiArgs {
   const float* aux;
   int64_t M, N;
   uint64_t pol_stream;  // L2 evict-first policy for the iterate stream
+  // sparse Delta bucket of the current 32-row group (null: dense planes)
+  uint32_t* bkey;
+  float* bval;
+  int* bcnt;
+  int* dense_flag;
+  int cap;
+  int64_t row0;         // first row of the group
 };
+
+// Append one nonzero Delta entry to the bucket of its 32-row group.
+__device__ __forceinline__ void bucket_push(const EpiArgs& ea, int r, int64_t colt, float d) {
+  const int pos = atomicAdd(ea.bcnt, 1);
+  if (pos < ea.cap) {
+    ea.bkey[pos] = ((uint32_t)r << 25) | (uint32_t)colt;
+    ea.bval[pos] = d;
+  } else {
+    atomicOr(ea.dense_flag, 1);
+  }
+}
 
 // Per-thread tile partials.  The dense sums run in FP32 over the thread's
 // share of one tile (at most 128 terms) and are folded across warps and tiles
@@ -174,43 +192,66 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // and the diagonal (row == colt); the unchecked form is the hot path.
 template <bool CHECK>
 __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
-                                           int64_t colt, const float (&v)[32], const float (&pre)[32], Sums& sm) {
+                                           int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
+                                           int lane) {
   float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
+  const bool sparse = ea.bkey != nullptr;
   float* po = ea.out + row_base * prm.ldout + colt;
-  __nv_bfloat16* ph = ea.out_hi + row_base * prm.ldplane + colt;
-  __nv_bfloat16* pl = ea.out_lo + row_base * prm.ldplane + colt;
+  __nv_bfloat16* ph = sparse ? nullptr : ea.out_hi + row_base * prm.ldplane + colt;
+  __nv_bfloat16* pl = sparse ? nullptr : ea.out_lo + row_base * prm.ldplane + colt;
   const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
+  uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
-    if (CHECK && !(cok && row_base + r < ea.M)) continue;
-    const float g = v[r] * scale;
-    const float om = pre[r];
-    const float a = fmaf(-tau, g, om);
-    float w;
-    if (CHECK && row_base + r == colt) {
-      w = diag_prox(a, tau, ea.lam_d);
-      sm.r2 += log((double)w);
-      sm.r3 += (double)w;
-      kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
-    } else {
-      const float m = fabsf(a) - tlam;
-      w = m > 0.f ? copysignf(m, a) : 0.f;
-      sl1 += fabsf(w);
-      nnz += (w != 0.f) ? 1.f : 0.f;
-      const float kz = fabsf(g) - lam;                 // omega == 0: max(|G| - lambda, 0)
-      const float knz = fabsf(g + copysignf(lam, om));  // omega != 0: |G + lambda sign(omega)|
-      kk = fmaxf(kk, om != 0.f ? knz : kz);
+    if (CHECK && row_base + r >= ea.M) continue;  // warp-uniform
+    float d = 0.f;
+    if (cok) {
+      const float g = v[r] * scale;
+      const float om = pre[r];
+      const float a = fmaf(-tau, g, om);
+      float w;
+      if (CHECK && row_base + r == colt) {
+        w = diag_prox(a, tau, ea.lam_d);
+        sm.r2 += log((double)w);
+        sm.r3 += (double)w;
+        kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
+      } else {
+        const float m = fabsf(a) - tlam;
+        w = m > 0.f ? copysignf(m, a) : 0.f;
+        sl1 += fabsf(w);
+        nnz += (w != 0.f) ? 1.f : 0.f;
+        const float kz = fabsf(g) - lam;                 // omega == 0: max(|G| - lambda, 0)
+        const float knz = fabsf(g + copysignf(lam, om));  // omega != 0: |G + lambda sign(omega)|
+        kk = fmaxf(kk, om != 0.f ? knz : kz);
+      }
+      chk = fmaf(g, 0.f, chk);
+      d = w - om;
+      sd = fmaf(d, d, sd);
+      ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
+      if (!sparse) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(d);
+        ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
+        ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(d - __bfloat162float(hb))),
+                         ea.pol_stream);
+      }
     }
-    chk = fmaf(g, 0.f, chk);
-    const float d = w - om;
-    sd = fmaf(d, d, sd);
-    ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
-    const __nv_bfloat16 hb = __float2bfloat16_rn(d);
-    ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
-    ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(d - __bfloat162float(hb))),
-                     ea.pol_stream);
+    v[r] = d;
+    nzmask |= (d != 0.f) ? (1u << r) : 0u;
+  }
+  // Delta is mostly zero: each lane appends only its own nonzero entries
+  if (sparse && nzmask != 0u) {
+    uint32_t m = nzmask;
+    while (m != 0u) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1u;
+      float dr = 0.f;
+#pragma unroll
+      for (int u = 0; u < 32; ++u)
+        if (u == r) dr = v[u];
+      bucket_push(ea, r, colt, dr);
+    }
   }
   sm.r0 += sd;
   sm.r1 += sl1;
@@ -248,7 +289,7 @@ __device__ __forceinline__ void gram_chunk(const TcParams& prm, int64_t row_base
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams prm) {
   const Ctrl* ctrl = prm.ctrl;
-  if (ctrl != nullptr && ctrl->done) return;
+  if (ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
   const int cur = ctrl ? ctrl->cur : 0;
   const int nxt = cur ^ 1;
 
@@ -416,6 +457,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.M = prm.M;
     ea.N = prm.N;
     ea.pol_stream = ptx::policy_evict_first();
+    ea.bkey = nullptr;
+    ea.bval = nullptr;
+    ea.bcnt = nullptr;
+    ea.dense_flag = prm.dense_flag;
+    ea.cap = prm.cap;
+    ea.row0 = 0;
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
     // cp.async needs 16-byte aligned rows
     const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
@@ -427,6 +474,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int64_t row_base = (int64_t)mb * BM + 32 * q;
       const int64_t col_base = (int64_t)nb * kBN + h * kColsPerWarp;
       const bool rows_full = row_base + 32 <= prm.M;
+      if (MODE == kModeProx && prm.keys != nullptr) {
+        const int64_t bkt = row_base / 32;  // one bucket per warp row quarter
+        ea.bkey = prm.keys + bkt * prm.cap;
+        ea.bval = prm.vals + bkt * prm.cap;
+        ea.bcnt = prm.counts + bkt;
+        ea.row0 = row_base;
+      }
       Sums sm;
       float pre[32];
       // the first chunk's operand does not depend on the MMA: start fetching it
@@ -470,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (full) y_chunk<false>(ea, prm, row_base, colt, v, pre, sm);
             else y_chunk<true>(ea, prm, row_base, colt, v, pre, sm);
           } else if (MODE == kModeProx) {
-            if (full && !diag) prox_chunk<false>(ea, prm, row_base, colt, v, pre, sm);
-            else prox_chunk<true>(ea, prm, row_base, colt, v, pre, sm);
+            if (full && !diag) prox_chunk<false>(ea, prm, row_base, colt, v, pre, sm, lane);
+            else prox_chunk<true>(ea, prm, row_base, colt, v, pre, sm, lane);
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
           } else {

@@ -81,10 +81,37 @@ cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, con
 cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                              double* trace, cudaStream_t st);
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
-                          double* trace, cudaStream_t st);
+                          double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
+                          cudaStream_t st);
 // Loss helper: reduce Omega stats and Y partials into out[0] = f, out[1] = g.
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st);
+
+// ------------------------------------------------------ sparse Y update ---
+// Rows of 32 share one bucket of Delta entries: key = (row - 32 b) << 25 | col,
+// value = Delta_ij (FP32), count in counts[b] (may exceed cap: overflow).
+constexpr int kBucketRows = 32;
+struct SparseYParams {
+  const Ctrl* ctrl;
+  const float* y[2];          // Y (p x ldy FP32), index cur / nxt
+  float* yw[2];
+  __nv_bfloat16* y_hi[2];     // planes of Y+ (p x ldyk), index nxt
+  __nv_bfloat16* y_lo[2];
+  const float* xt;            // X^T, p x ldy FP32
+  const uint32_t* keys;
+  const float* vals;
+  const int* counts;
+  int32_t cap, tiles_m, tiles_n, pad;
+  int64_t p, n, ldy, ldyk;
+  double* part;               // one row of kYSlots per bucket
+};
+size_t sparse_y_smem_bytes(int cap);
+cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st);
+// Dense fallback: BF16 planes of Delta = Omega[nxt] - Omega[cur] when ctrl->dense.
+cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st);
+// X^T in FP32 (p x ldxt).
+cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 
 // -------------------------------------------------------- tcgen05 GEMMs ---
 struct TcOperands;  // defined in the tcgen05 translation unit's header

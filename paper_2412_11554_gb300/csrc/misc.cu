@@ -108,6 +108,22 @@ __global__ void convert_x_bf16_kernel(const float* __restrict__ X, int64_t n, in
   if (nbad) atomicAdd(bad, nbad);
 }
 
+// X^T in FP32 (the rows of X^T are read by the sparse Y update).
+__global__ void transpose_x_f32_kernel(const float* __restrict__ X, int64_t n, int64_t p, float* __restrict__ XT,
+                                       int64_t ldxt) {
+  __shared__ float tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < n && c < p) ? X[r * p + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < p && r < n) XT[c * ldxt + r] = tile[threadIdx.x][i];
+  }
+}
+
 template <class T>
 __global__ void set_identity_kernel(T* __restrict__ Om, int64_t p, int64_t ld) {
   const int64_t total = p * ld;
@@ -408,12 +424,18 @@ __global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles,
 // form ||Y+ - Y||^2 / n <= ||Delta||^2 / tau (identical to the printed test
 // because g is quadratic), or the tau <= 1/L floor; accept or backtrack.
 __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
-                              double* trace) {
+                              double* trace, int* bucket_counts, int nbuckets, const double* part_sparse) {
   if (ctrl->done) return;
   double s[kYSlots];
-  fold_partials<kYSlots>(part, ntiles, 0u, s);
+  // partial sums of whichever Y update ran: the sparse one (one row per
+  // bucket) unless a bucket overflowed and the dense product ran instead
+  const bool sparse_ran = part_sparse != nullptr && !ctrl->dense;
+  fold_partials<kYSlots>(sparse_ran ? part_sparse : part, sparse_ran ? nbuckets : ntiles, 0u, s);
+  // the next trial's prox epilogue starts from empty Delta buckets
+  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[i] = 0;
   if (threadIdx.x != 0) return;
   Ctrl& c = *ctrl;
+  c.dense = 0;
   c.trials += 1;
   if (s[kYBad] > 0.0) {
     c.done = 1;
@@ -557,8 +579,16 @@ cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, con
 }
 
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
-                          double* trace, cudaStream_t st) {
-  decide_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
+                          double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
+                          cudaStream_t st) {
+  decide_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace, bucket_counts, nbuckets, part_sparse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st) {
+  dim3 grid((unsigned)((p + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  transpose_x_f32_kernel<<<grid, block, 0, st>>>(X, n, p, XT, ldxt);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,186 @@
+// Sparse update of Y = Omega X^T after a prox step (mixed precision mode):
+// Y+ = Y + Delta X^T with Delta = Omega+ - Omega.  The iterate is sparse by
+// construction (Sec 3.3; the Remark after Thm 3.3 notes that sparsity cuts
+// the work of the product), and so is each step Delta, so instead of a dense
+// p x p x n product the prox epilogue records the nonzero entries of Delta in
+// one bucket per 32-row group and this kernel applies them row by row:
+//
+//     Y+[i, :] = Y[i, :] + sum_{j : Delta_ij != 0} Delta_ij X^T[j, :]     (FP32)
+//
+// Entries arrive in any order from many CTAs; each block sorts its bucket by
+// (row, column) first, so the sums are formed in a fixed order and the result
+// is the same on every run.  The kernel also writes the BF16 hi/lo planes of
+// Y+ (the A operand of the next gradient GEMM) and the per-block partial sums
+// ||Delta X^T||^2 and ||Y+||^2 for the line search of Algorithm 1.
+#include "internal.h"
+
+namespace accord {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRowsPerBlock = kBucketRows;
+constexpr int kColsPerPass = 256;  // 8 columns a lane per pass
+
+__device__ __forceinline__ void bitonic_sort(uint32_t* key, float* val, int m) {
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int ij = i ^ j;
+        if (ij > i) {
+          const bool up = (i & k) == 0;
+          const uint32_t a = key[i], b = key[ij];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[ij] = a;
+            const float t = val[i];
+            val[i] = val[ij];
+            val[ij] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// first index in [0, m) whose key >= target (keys sorted ascending)
+__device__ __forceinline__ int lower_bound(const uint32_t* key, int m, uint32_t target) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
+  const Ctrl* ctrl = prm.ctrl;
+  if (ctrl->done || ctrl->dense) return;
+  extern __shared__ uint8_t smem_raw[];
+  const int mb = blockIdx.x;  // bucket = 32-row group
+  const int cur = ctrl->cur, nxt = cur ^ 1;
+  const float* __restrict__ Y = prm.y[cur];
+  float* __restrict__ Yp = prm.yw[nxt];
+  __nv_bfloat16* __restrict__ Yh = prm.y_hi[nxt];
+  __nv_bfloat16* __restrict__ Yl = prm.y_lo[nxt];
+  const float* __restrict__ XT = prm.xt;
+
+  int cnt = prm.counts[mb];
+  if (cnt > prm.cap) cnt = prm.cap;  // overflow is handled by the dense path
+  int m = 1;
+  while (m < cnt) m <<= 1;
+  uint32_t* key = reinterpret_cast<uint32_t*>(smem_raw);
+  float* val = reinterpret_cast<float*>(smem_raw + (size_t)prm.cap * sizeof(uint32_t));
+  const uint32_t* gk = prm.keys + (size_t)mb * prm.cap;
+  const float* gv = prm.vals + (size_t)mb * prm.cap;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    key[i] = i < cnt ? gk[i] : 0xFFFFFFFFu;
+    val[i] = i < cnt ? gv[i] : 0.f;
+  }
+  __syncthreads();
+  if (cnt > 1) bitonic_sort(key, val, m);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+  float s_d = 0.f, s_n = 0.f, chk = 0.f;
+  for (int rl = warp; rl < kRowsPerBlock; rl += nwarps) {
+    const int64_t row = (int64_t)mb * kRowsPerBlock + rl;
+    if (row >= prm.p) break;
+    const int lo = lower_bound(key, cnt, (uint32_t)rl << 25);
+    const int hi = (rl + 1 < kRowsPerBlock) ? lower_bound(key, cnt, (uint32_t)(rl + 1) << 25) : cnt;
+    const float* yr = Y + row * prm.ldy;
+    float* ypr = Yp + row * prm.ldy;
+    __nv_bfloat16* hr = Yh + row * prm.ldyk;
+    __nv_bfloat16* lr = Yl + row * prm.ldyk;
+    for (int64_t c0 = 0; c0 < prm.n; c0 += kColsPerPass) {
+      float acc[kColsPerPass / 32];
+#pragma unroll
+      for (int u = 0; u < kColsPerPass / 32; ++u) acc[u] = 0.f;
+      for (int k = lo; k < hi; ++k) {
+        const int64_t j = key[k] & 0x1FFFFFFu;
+        const float d = val[k];
+        const float* xr = XT + j * prm.ldy + c0 + lane;
+#pragma unroll
+        for (int u = 0; u < kColsPerPass / 32; ++u)
+          if (c0 + lane + 32 * u < prm.n) acc[u] = fmaf(d, __ldg(xr + 32 * u), acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kColsPerPass / 32; ++u) {
+        const int64_t c = c0 + lane + 32 * u;
+        if (c < prm.n) {
+          const float yn = yr[c] + acc[u];
+          s_d = fmaf(acc[u], acc[u], s_d);
+          s_n = fmaf(yn, yn, s_n);
+          chk = fmaf(yn, 0.f, chk);
+          ypr[c] = yn;
+          __nv_bfloat16 h, l;
+          split_bf16(yn, h, l);
+          hr[c] = h;
+          lr[c] = l;
+        }
+      }
+    }
+  }
+  // block partial sums: FP32 warp trees, FP64 across warps (fixed order)
+  __shared__ double red[kThreads / 32][3];
+  s_d = warp_sum_f(s_d);
+  s_n = warp_sum_f(s_n);
+  const float bad = __ballot_sync(0xffffffffu, chk != 0.f) ? 1.f : 0.f;
+  if (lane == 0) {
+    red[warp][0] = (double)s_d;
+    red[warp][1] = (double)s_n;
+    red[warp][2] = (double)bad;
+  }
+  __syncthreads();
+  // one partial row per bucket (the fold reads nbuckets rows)
+  if (threadIdx.x < kYSlots) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    if (q < 3)
+      for (int w = 0; w < nwarps; ++w) v += red[w][q];
+    prm.part[(int64_t)mb * kYSlots + q] = v;
+  }
+}
+
+// Dense fallback when a bucket overflowed: BF16 planes of Delta = Omega+ - Omega.
+__global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
+                                    __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk) {
+  if (ctrl->done || !ctrl->dense) return;
+  const float* Om = ctrl->cur ? om1 : om0;
+  const float* Op = ctrl->cur ? om0 : om1;
+  const int64_t total = p * p;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / p, c = i % p;
+    __nv_bfloat16 h, l;
+    split_bf16(Op[r * ld + c] - Om[r * ld + c], h, l);
+    hi[r * ldk + c] = h;
+    lo[r * ldk + c] = l;
+  }
+}
+
+}  // namespace
+
+size_t sparse_y_smem_bytes(int cap) { return (size_t)cap * (sizeof(uint32_t) + sizeof(float)); }
+
+cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
+  const size_t smem = sparse_y_smem_bytes(prm.cap);
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(sparse_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  if (smem > 64 * 1024) return cudaErrorInvalidValue;
+  sparse_y_kernel<<<(unsigned)prm.tiles_m, kThreads, smem, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st) {
+  delta_planes_kernel<<<152 * 16, 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk);
+  return cudaGetLastError();
+}
+
+}  // namespace accord

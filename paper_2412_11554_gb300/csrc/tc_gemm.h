@@ -33,6 +33,15 @@ struct TcParams {
   int64_t ldout64;
   double* part;         // per-tile partial sums or null
   float lam, lam_d, scale, pad;
+  // Sparse Delta buckets (prox mode): when keys != null the epilogue records
+  // the nonzero entries of Delta in the bucket of its 32-row group instead of
+  // writing dense Delta planes; an overflow sets *dense_flag.
+  uint32_t* keys;
+  float* vals;
+  int* counts;
+  int* dense_flag;
+  int32_t cap;
+  int32_t gate_dense;   // 1: run only when ctrl->dense is set (dense fallback)
 };
 
 // Encodes a 2-D BF16 tensor map over a rows x cols matrix with leading
