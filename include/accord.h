@@ -81,7 +81,8 @@ typedef struct accord_opts {
     double  kkt_tol;         /* stop when r(Omega^t) <= kkt_tol (default 1e-8)                  */
     double  lipschitz;       /* > 0: use this L = sigma_max(S); 0: estimate it by Lanczos on
                                 X X^T / n (default 0)                                            */
-    double  lipschitz_tol;   /* relative change of the Ritz value that ends Lanczos (1e-14)    */
+    double  lipschitz_tol;   /* relative change of the Ritz value that ends Lanczos; 0 (default)
+                                = 1e-14 in FP64 mode, 1e-10 in the mixed modes                   */
     void*   stream;          /* cudaStream_t for all work (default NULL)                        */
     double* trace;           /* optional HOST array, trace_cap x ACCORD_TRACE_FIELDS doubles    */
     int64_t trace_cap;       /* rows available in trace (rows beyond are dropped)               */

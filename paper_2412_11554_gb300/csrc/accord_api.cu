@@ -41,7 +41,7 @@ struct Layout {
   int64_t ldk = 0;   // BF16 planes whose columns run over p
   int64_t ldyk = 0;  // BF16 planes whose columns run over n
   int64_t tiles_prox = 0, tiles_y = 0, trace_rows = 0;
-  size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0;
+  size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0, part_fold = 0;
   size_t om[2] = {0, 0}, y[2] = {0, 0};
   size_t x64 = 0, xt64 = 0;                        // FP64 mode
   size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
@@ -85,6 +85,7 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
   L.part_prox = take(c, (size_t)L.tiles_prox * kProxSlots * 8);
   L.part_y = take(c, (size_t)L.tiles_y * kProxSlots * 8);
   L.part_om = take(c, (size_t)p * kProxSlots * 8);
+  L.part_fold = take(c, (size_t)kFoldChunks * kProxSlots * 8);
   for (int b = 0; b < 2; ++b) L.om[b] = take(c, (size_t)p * L.ldo * es);
   if (f64) {
     for (int b = 0; b < 2; ++b) L.y[b] = take(c, (size_t)p * L.ldy * 8);
@@ -434,7 +435,8 @@ int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nla
   if (L.f64) ACCORD_CK(launch_gemm_f64(kModeProx, T.g2, P.st));
   else ACCORD_CK(launch_tc_gemm(kModeProx, T.t2, P.st));
   if (prof.on) ACCORD_CK(prof.mark(prof.prox, P.st));
-  ACCORD_CK(launch_post_prox(P.ctrl, at<double>(P.ws, L.part_prox), L.tiles_prox, T.sp, trace, P.st));
+  ACCORD_CK(launch_post_prox(P.ctrl, at<double>(P.ws, L.part_prox), L.tiles_prox, T.sp, trace,
+                             at<double>(P.ws, L.part_fold), P.st));
   const int64_t ty = L.f64 ? gemm_f64_tiles(L.p, L.n) : tc_tiles(L.p, L.n);
   if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
   if (L.f64) {
@@ -524,28 +526,55 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
       nlaunch += 1;
     }
   }
+  int64_t nomp = 0, nyp = 0;
   if (o.init_from_omega) {
     ACCORD_CK(launch_copy_omega(Omega, p, at<void>(ws, L.om[0]), L.ldo, f64, p, P.st));
+    ACCORD_CK(launch_omega_stats(at<void>(ws, L.om[0]), f64, p, L.ldo, at<double>(ws, L.part_om), &nomp, P.st));
+    if (int e = setup_y(P, 0, 0)) return e;
+    nyp = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
+    nlaunch += f64 ? 3 : 4;
   } else {
+    // Omega^0 = I: its statistics are known and Y^0 = I X^T = X^T exactly
     ACCORD_CK(launch_set_identity(at<void>(ws, L.om[0]), f64, p, L.ldo, P.st));
+    ACCORD_CK(launch_identity_stats(at<double>(ws, L.part_om), p, P.st));
+    nomp = 1;
+    nlaunch += 2;
+    if (f64) {
+      ACCORD_CK(cudaMemcpyAsync(at<double>(ws, L.y[0]), at<double>(ws, L.xt64), (size_t)p * L.ldy * 8,
+                                cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(launch_rows_norm2(at<double>(ws, L.y[0]), 1, p, n, L.ldy, at<double>(ws, L.part_y), &nyp, P.st));
+      nlaunch += 1;
+    } else if (L.sparse) {
+      ACCORD_CK(cudaMemcpyAsync(at<float>(ws, L.y[0]), at<float>(ws, L.xt32), (size_t)p * L.ldy * 4,
+                                cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_hi[0]), at<__nv_bfloat16>(ws, L.xt_hi),
+                                (size_t)p * L.ldyk * 2, cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_lo[0]), at<__nv_bfloat16>(ws, L.xt_lo),
+                                (size_t)p * L.ldyk * 2, cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(launch_rows_norm2(at<float>(ws, L.y[0]), 0, p, n, L.ldy, at<double>(ws, L.part_y), &nyp, P.st));
+      nlaunch += 1;
+    } else {
+      if (int e = setup_y(P, 0, 0)) return e;
+      nyp = tc_tiles(p, n);
+      nlaunch += 2;
+    }
   }
-  int64_t nomp = 0;
-  ACCORD_CK(launch_omega_stats(at<void>(ws, L.om[0]), f64, p, L.ldo, at<double>(ws, L.part_om), &nomp, P.st));
-  if (int e = setup_y(P, 0, 0)) return e;
-  nlaunch += f64 ? 4 : 5;
-  const int64_t ty = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
+  const int64_t ty = nyp;
 
   Ctrl hc;
   double L_given = o.lipschitz;
   if (!(L_given > 0.0)) {
     if (int e = setup_gram(P)) return e;
+    // 0 = automatic: FP64 mode matches a dense eigensolver to rounding; the
+    // mixed mode needs L only to set the tau <= 1/L floor
+    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-10);
     ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st));
     nlaunch += 2;
     const int chunk = 8;
     for (int steps = 0; steps < L.lz_k + chunk; steps += chunk) {
       ACCORD_CK(launch_lanczos_steps(P.ctrl, at<double>(ws, L.gram), n, at<double>(ws, L.lz_v),
                                      at<double>(ws, L.lz_w), at<double>(ws, L.lz_a), at<double>(ws, L.lz_b), n,
-                                     L.lz_k, chunk, o.lipschitz_tol, P.st));
+                                     L.lz_k, chunk, lz_tol, P.st));
       nlaunch += 2 * chunk;
       if (int e = read_ctrl(P, &hc)) return e;
       if (hc.power_done) break;
@@ -669,7 +698,7 @@ void accord_default_opts(accord_opts* o) {
   o->beta = 0.5;
   o->kkt_tol = 1e-8;
   o->lipschitz = 0.0;
-  o->lipschitz_tol = 1e-14;
+  o->lipschitz_tol = 0.0;
   o->stream = nullptr;
   o->trace = nullptr;
   o->trace_cap = 0;

@@ -78,8 +78,14 @@ cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, doubl
 cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
                              int64_t nyp, const SolveParams& sp, double L_given, double* trace,
                              cudaStream_t st);
+constexpr int kFoldChunks = 128;  // first-stage blocks of the prox-partials fold
 cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
-                             double* trace, cudaStream_t st);
+                             double* trace, double* fold_scratch, cudaStream_t st);
+// ||A||^2 partials (kYSlots rows, one per 64 rows of A); *nparts rows written.
+cudaError_t launch_rows_norm2(const void* A, int is_f64, int64_t rows, int64_t cols, int64_t ld, double* part,
+                              int64_t* nparts, cudaStream_t st);
+// One kProxSlots partial row with the statistics of Omega = I.
+cudaError_t launch_identity_stats(double* part, int64_t p, cudaStream_t st);
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                           double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
                           cudaStream_t st);

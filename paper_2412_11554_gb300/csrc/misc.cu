@@ -341,6 +341,59 @@ __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctr
   }
 }
 
+// First stage of a two-stage fold: block b folds the contiguous rows
+// [b * chunk, (b + 1) * chunk) into row b of out (same slot semantics).
+template <int W>
+__global__ void fold_stage1_kernel(const Ctrl* ctrl, const double* __restrict__ part, int64_t rows, int64_t chunk,
+                                   unsigned max_mask, double* __restrict__ out) {
+  if (ctrl != nullptr && ctrl->done) return;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  double s[W];
+  fold_partials<W>(part + r0 * W, r1 > r0 ? r1 - r0 : 0, max_mask, s);
+  if (threadIdx.x < W) out[(int64_t)blockIdx.x * W + threadIdx.x] = s[threadIdx.x];
+}
+
+// ||Y||^2 partials of Y = X^T (Omega^0 = I): one kYSlots row per block of 64
+// rows (slot kYDiff2 = slot kYNorm2, since Y - 0 = Y).
+template <class T>
+__global__ void rows_norm2_kernel(const T* __restrict__ A, int64_t rows, int64_t cols, int64_t ld,
+                                  double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  double s = 0.0, bad = 0.0;
+  for (int64_t r = r0; r < r0 + 64 && r < rows; ++r)
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+      const double v = (double)A[r * ld + c];
+      s = fma(v, v, s);
+      if (!isfinite(v)) bad += 1.0;
+    }
+  __shared__ double sh[2][kRedThreads / 32];
+  s = warp_sum(s);
+  bad = warp_sum(bad);
+  if (threadIdx.x % 32 == 0) {
+    sh[0][threadIdx.x / 32] = s;
+    sh[1][threadIdx.x / 32] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
+    }
+    double* o = part + (int64_t)blockIdx.x * kYSlots;
+    o[kYDiff2] = a;
+    o[kYNorm2] = a;
+    o[kYBad] = b;
+    o[3] = 0.0;
+  }
+}
+
+// Statistics of Omega^0 = I in one partial row: log-diag 0, diag sum p.
+__global__ void identity_stats_kernel(double* part, int64_t p) {
+  if (threadIdx.x < kProxSlots) part[threadIdx.x] = (threadIdx.x == kPDiagSum) ? (double)p : 0.0;
+}
+
 // ------------------------------------------------------ Algorithm 1 loop --
 __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
                                  int64_t nyp, SolveParams sp, double L_given, double* trace) {
@@ -573,8 +626,30 @@ cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, con
 }
 
 cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
-                             double* trace, cudaStream_t st) {
-  post_prox_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
+                             double* trace, double* fold_scratch, cudaStream_t st) {
+  if (fold_scratch != nullptr && ntiles > 4 * kFoldChunks) {
+    // two-stage fixed-order fold: kFoldChunks blocks, then one
+    const int64_t chunk = (ntiles + kFoldChunks - 1) / kFoldChunks;
+    fold_stage1_kernel<kProxSlots><<<kFoldChunks, kRedThreads, 0, st>>>(ctrl, part, ntiles, chunk, 1u << kPKkt,
+                                                                         fold_scratch);
+    post_prox_kernel<<<1, kRedThreads, 0, st>>>(ctrl, fold_scratch, kFoldChunks, sp, trace);
+  } else {
+    post_prox_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_norm2(const void* A, int is_f64, int64_t rows, int64_t cols, int64_t ld, double* part,
+                              int64_t* nparts, cudaStream_t st) {
+  const unsigned g = (unsigned)((rows + 63) / 64);
+  if (is_f64) rows_norm2_kernel<double><<<g, kRedThreads, 0, st>>>((const double*)A, rows, cols, ld, part);
+  else rows_norm2_kernel<float><<<g, kRedThreads, 0, st>>>((const float*)A, rows, cols, ld, part);
+  *nparts = g;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_identity_stats(double* part, int64_t p, cudaStream_t st) {
+  identity_stats_kernel<<<1, 32, 0, st>>>(part, p);
   return cudaGetLastError();
 }
 
