@@ -173,9 +173,47 @@ def pin_line_search_identity():
     return abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
 
 
+def pin_refit_fixed_point():
+    """Eq. 3.8 with phi = 1 on the support of Omega-hat(lambda) returns
+    Omega-hat(lambda): it already satisfies the refit's KKT conditions."""
+    w = workload("ar1", p=50, n=35)
+    r = R.fit(w.X, w.lam, kkt_tol=1e-11, max_iter=8000)
+    rr = R.refit(w.X, w.lam, r.Omega != 0, 1.0, kkt_tol=1e-11, max_iter=8000)
+    return r.status == R.OK and rr.status == R.OK and np.max(np.abs(rr.Omega - r.Omega)) <= 1e-9
+
+
+def pin_refit_restricted_mle():
+    """Eq. 3.8 with phi = 0 is the unpenalised fit restricted to the support:
+    each row equals the exact row solution on it (lambda = 0)."""
+    w = workload("ar1", p=50, n=35)
+    X = w.X.astype(np.float64)
+    S = X.T @ X / X.shape[0]
+    r = R.fit(w.X, w.lam, kkt_tol=1e-10, max_iter=8000)
+    sup = r.Omega != 0
+    r0 = R.refit(w.X, w.lam, sup, 0.0, kkt_tol=1e-11, max_iter=40000)
+    exact = np.zeros_like(r0.Omega)
+    for i in range(S.shape[0]):
+        A = np.nonzero(sup[i])[0]
+        exact[i] = R.row_solution(S, i, A, np.sign(r0.Omega[i, A]), 0.0, 0.0)
+    ok = r0.status == R.OK and not np.any(r0.Omega[~(sup | np.eye(S.shape[0], dtype=bool))])
+    return bool(ok and np.max(np.abs(r0.Omega - exact)) <= 1e-8)
+
+
+def pin_epbic_diagonal():
+    """epBIC (Eq. 3.7) of the diagonal-S closed form: no off-diagonal nonzeros,
+    so 2n(-sum log w_i + 1/2 sum s_i w_i^2)."""
+    s = np.random.Generator(np.random.PCG64(41)).uniform(0.5, 2.0, size=7)
+    n = 30
+    X = orthogonal_design(n, s, 42)
+    w = (-0.2 + np.sqrt(0.04 + 4 * s)) / (2 * s)
+    want = 2 * n * (-np.sum(np.log(w)) + 0.5 * np.sum(s * w * w))
+    return abs(R.epbic(np.diag(w), X, 0.7) - want) <= 1e-10 * abs(want)
+
+
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
-        pin_kkt_descent_path, pin_line_search_identity]
+        pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
+        pin_epbic_diagonal]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
