@@ -83,6 +83,7 @@ typedef struct accord_opts {
                                 X X^T / n (default 0)                                            */
     double  lipschitz_tol;   /* relative change of the Ritz value that ends Lanczos; 0 (default)
                                 = 1e-14 in FP64 mode, 1e-10 in the mixed modes                   */
+    double  epbic_gamma;     /* gamma of the extended pseudo-BIC, Eq. 3.7 (default 0.5)         */
     void*   stream;          /* cudaStream_t for all work (default NULL)                        */
     double* trace;           /* optional HOST array, trace_cap x ACCORD_TRACE_FIELDS doubles    */
     int64_t trace_cap;       /* rows available in trace (rows beyond are dropped)               */
@@ -106,6 +107,9 @@ typedef struct accord_stats {
     double  t_prox_gemm_ms;  /* their summed device time when opts->profile, else 0              */
     double  t_y_gemm_ms;
     int64_t n_launches;      /* kernels this call launched (setup + every queued trial)          */
+    double  logdet_d;        /* sum_i log omega_ii of the returned Omega                         */
+    double  epbic;           /* extended pseudo-BIC of Eq. 3.7 with opts->epbic_gamma:
+                                2n(-log det Omega_D + g) + nnz (log n + 4 gamma log p)           */
 } accord_stats;
 
 /* Fills *opts with the defaults listed above. */
@@ -132,6 +136,17 @@ size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* opts);
  * start or non-finite X), ENONFINITE, EBACKTRACK, ECUDA, EUNSUPPORTED. */
 int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts,
                void* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
+
+/* Bias-corrected refit (Eq. 3.8): Algorithm 1 on
+ *   -log det Omega_D + 1/2 tr(Omega^T Omega S) + phi lambda ||Omega||_1
+ * over the Omega whose entries vanish off the support of Omega_hat (device,
+ * p x p, element type per precision; its nonzero pattern plus the diagonal is
+ * the support).  Off the support the weight is infinite, so those entries
+ * stay 0 and do not enter the KKT residual.  0 <= phi <= 1 (else EINVAL).
+ * Other arguments, workspace and errors as accord_fit; opts->init_from_omega
+ * may start from Omega_hat copied into Omega. */
+int accord_refit(const float* X, int64_t n, int64_t p, double lambda, double phi, const void* Omega_hat,
+                 const accord_opts* opts, void* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
 
 /* Same as accord_fit for FP64 data; requires opts->precision == ACCORD_FP64
  * (else EUNSUPPORTED).  Omega is double. */

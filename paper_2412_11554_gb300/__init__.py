@@ -9,6 +9,7 @@ from .accord import (  # noqa: F401
     accord_default_opts,
     accord_device_check,
     accord_fit,
+    accord_refit,
     accord_grad,
     accord_last_error,
     accord_loss,

@@ -32,7 +32,8 @@ class AccordOpts(ctypes.Structure):
         ("init_from_omega", ctypes.c_int32), ("lipschitz_max_iter", ctypes.c_int32), ("profile", ctypes.c_int32),
         ("sparse_update", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("tau0", ctypes.c_double), ("beta", ctypes.c_double), ("kkt_tol", ctypes.c_double),
-        ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
+        ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("epbic_gamma", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
         ("trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int64),
     ]
 
@@ -44,11 +45,11 @@ class AccordStats(ctypes.Structure):
         ("tau_last", ctypes.c_double), ("L", ctypes.c_double), ("nnz_offdiag", ctypes.c_int64),
         ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
         ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
-        ("n_launches", ctypes.c_int64),
+        ("n_launches", ctypes.c_int64), ("logdet_d", ctypes.c_double), ("epbic", ctypes.c_double),
     ]
 
 
-EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_loss",
+EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc")
 
@@ -75,6 +76,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_fit.restype = i32
     lib.accord_fit_f64.argtypes = [P, i64, i64, dbl, opts_p, P, P, ctypes.c_size_t, stats_p]
     lib.accord_fit_f64.restype = i32
+    lib.accord_refit.argtypes = [P, i64, i64, dbl, dbl, P, opts_p, P, P, ctypes.c_size_t, stats_p]
+    lib.accord_refit.restype = i32
     lib.accord_loss.argtypes = [P, i64, i64, P, dbl, opts_p, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.accord_loss.restype = i32
     lib.accord_grad.argtypes = [P, i64, i64, P, i32, opts_p, P]
@@ -119,6 +122,8 @@ class FitStats:
     t_prox_gemm_ms: float = 0.0
     t_y_gemm_ms: float = 0.0
     n_launches: int = 0
+    logdet_d: float = 0.0
+    epbic: float = 0.0
     trace: np.ndarray | None = None
 
 
@@ -151,9 +156,15 @@ def _check_x(X: torch.Tensor, dtype=torch.float32) -> None:
         raise ValueError(f"X must be a contiguous 2-D CUDA {dtype} tensor")
 
 
+def accord_refit(X: torch.Tensor, lam: float, phi: float, Omega_hat: torch.Tensor, **kw) -> tuple[torch.Tensor, FitStats]:
+    """Bias-corrected refit of Eq. 3.8 on the support of Omega_hat (same
+    keyword arguments as accord_fit)."""
+    return accord_fit(X, lam, _refit=(float(phi), Omega_hat), **kw)
+
+
 def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: torch.Tensor | None = None,
                init_from_omega: bool = False, workspace: torch.Tensor | None = None, trace: bool = False,
-               stream=None, check: bool = True, **opts) -> tuple[torch.Tensor, FitStats]:
+               stream=None, check: bool = True, _refit=None, **opts) -> tuple[torch.Tensor, FitStats]:
     """Fit Omega-hat (Eq. 3.2) with ACCORD-FBS.  X: CUDA float32 (or float64
     with precision='fp64'), n x p.  Remaining keyword arguments set
     accord_opts fields (tau0, beta, tau_warm, max_iter, max_backtracks,
@@ -183,12 +194,19 @@ def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: 
     if workspace is not None:
         ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     st = AccordStats()
-    fn = lib.accord_fit_f64 if x64 else lib.accord_fit
-    status = fn(X.data_ptr(), n, p, float(lam), ctypes.byref(o), Omega.data_ptr(), ws_ptr, ws_bytes,
-                ctypes.byref(st))
+    if _refit is not None:
+        phi, Oh = _refit
+        if x64 or not (Oh.is_cuda and Oh.dtype == odt and Oh.shape == (p, p) and Oh.is_contiguous()):
+            raise ValueError(f"refit needs float32 X and a contiguous {p}x{p} CUDA {odt} Omega_hat")
+        status = lib.accord_refit(X.data_ptr(), n, p, float(lam), phi, Oh.data_ptr(), ctypes.byref(o),
+                                  Omega.data_ptr(), ws_ptr, ws_bytes, ctypes.byref(st))
+    else:
+        fn = lib.accord_fit_f64 if x64 else lib.accord_fit
+        status = fn(X.data_ptr(), n, p, float(lam), ctypes.byref(o), Omega.data_ptr(), ws_ptr, ws_bytes,
+                    ctypes.byref(st))
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms,
-                     st.t_y_gemm_ms, st.n_launches, None)
+                     st.t_y_gemm_ms, st.n_launches, st.logdet_d, st.epbic, None)
     if tr is not None:
         stats.trace = tr[: st.iters + 1].copy()
     if check and status < 0:

@@ -47,6 +47,8 @@ struct Layout {
   size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
   size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed mode
   size_t gram = 0, lz_v = 0, lz_w = 0, lz_a = 0, lz_b = 0;
+  size_t mask = 0;
+  int64_t mask_ld = 0;  // 32-bit words per row of the refit support mask
   int lz_k = 0;
   // sparse Delta update (mixed mode)
   bool sparse = false;
@@ -113,6 +115,8 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
       L.part_sy = take(c, (size_t)L.nbuckets * kYSlots * 8);
     }
   }
+  L.mask_ld = (p + 31) / 32;
+  L.mask = take(c, (size_t)p * L.mask_ld * 4);
   L.gram = take(c, (size_t)n * n * 8);
   int64_t k = lanczos_max < kLanczosMax ? lanczos_max : kLanczosMax;
   if (k > n) k = n;
@@ -173,6 +177,7 @@ int check_opts(const accord_opts& o) {
   if (!(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz)) return kEinval;
   if (o.lipschitz_max_iter < 1) return kEinval;
   if (!(o.lipschitz_tol >= 0.0)) return kEinval;
+  if (!(o.epbic_gamma >= 0.0)) return kEinval;
   if (o.trace_cap < 0) return kEinval;
   return kOk;
 }
@@ -467,7 +472,8 @@ int read_ctrl(const Plan& P, Ctrl* host) {
 }
 
 int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double lam, const accord_opts* optp,
-             void* Omega, void* workspace, size_t ws_bytes, accord_stats* out) {
+             void* Omega, void* workspace, size_t ws_bytes, accord_stats* out, const void* support = nullptr,
+             double phi = 1.0) {
   clear_last_error();
   accord_opts o;
   accord_default_opts(&o);
@@ -498,6 +504,9 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   P.err = &P.ctrl->dev_error;
   const Layout& L = P.L;
   void* ws = workspace;
+  // Eq. 3.8 refit: weight phi * lambda on the support of `support`, infinite
+  // off it (the epilogues read the bitmask built below)
+  if (support != nullptr) lam = phi * lam;
   const double lam_d = o.penalize_diag ? lam : 0.0;
 
   cudaEvent_t ev[3];
@@ -587,6 +596,14 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
 
   TrialPlan T;
   if (int e = make_trial_plan(P, T, lam, lam_d)) return e;
+  if (support != nullptr) {
+    ACCORD_CK(launch_support_mask(support, f64, p, p, at<uint32_t>(ws, L.mask), L.mask_ld, P.st));
+    nlaunch += 1;
+    T.g2.mask = at<uint32_t>(ws, L.mask);
+    T.g2.mask_ld = L.mask_ld;
+    T.t2.mask = at<uint32_t>(ws, L.mask);
+    T.t2.mask_ld = L.mask_ld;
+  }
   SolveParams& sp = T.sp;
   sp.lam = lam;
   sp.lam_d = lam_d;
@@ -671,6 +688,10 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     out->t_prox_gemm_ms = prof.on ? prof.total_ms(prof.prox, live_prox) : 0.0;
     out->t_y_gemm_ms = prof.on ? prof.total_ms(prof.y, hc.trials) : 0.0;
     out->n_launches = nlaunch;
+    // Eq. 3.7 from the returned iterate's sums
+    out->logdet_d = hc.logdiag;
+    out->epbic = 2.0 * (double)n * (-hc.logdiag + hc.g) +
+                 hc.nnz * (std::log((double)n) + 4.0 * o.epbic_gamma * std::log((double)p));
   }
   return hc.status;
 }
@@ -699,6 +720,7 @@ void accord_default_opts(accord_opts* o) {
   o->kkt_tol = 1e-8;
   o->lipschitz = 0.0;
   o->lipschitz_tol = 0.0;
+  o->epbic_gamma = 0.5;
   o->stream = nullptr;
   o->trace = nullptr;
   o->trace_cap = 0;
@@ -715,6 +737,18 @@ size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* optp) {
 int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, void* Omega,
                void* workspace, size_t ws_bytes, accord_stats* out) {
   const int s = fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
+  if (out) out->status = s;
+  return s;
+}
+
+int accord_refit(const float* X, int64_t n, int64_t p, double lambda, double phi, const void* Omega_hat,
+                 const accord_opts* opts, void* Omega, void* workspace, size_t ws_bytes, accord_stats* out) {
+  if (Omega_hat == nullptr || !(phi >= 0.0 && phi <= 1.0)) {
+    if (out) std::memset(out, 0, sizeof(*out));
+    if (out) out->status = ACCORD_EINVAL;
+    return ACCORD_EINVAL;
+  }
+  const int s = fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out, Omega_hat, phi);
   if (out) out->status = s;
   return s;
 }

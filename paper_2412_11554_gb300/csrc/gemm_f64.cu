@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
         const double om = aux[row * prm.ldaux + col];
         const bool dg = (row == col);
         const double a = om - tau * v;
-        const double w = dg ? diag_prox(a, tau, lam_d) : soft_threshold(a, tau * lam);
+        double lam_e = lam;  // Eq. 3.8 refit: infinite weight off the support
+        if (prm.mask != nullptr && !dg && !((prm.mask[row * prm.mask_ld + (col >> 5)] >> (col & 31)) & 1u))
+          lam_e = INFINITY;
+        const double w = dg ? diag_prox(a, tau, lam_d) : soft_threshold(a, tau * lam_e);
         out[row * prm.ldout + col] = w;
         const double d = w - om;
         r.s[kPDelta2] += d * d;
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
           r.s[kPL1Off] += fabs(w);
           r.s[kPNnz] += (w != 0.0) ? 1.0 : 0.0;
         }
-        r.s[kPKkt] = fmax(r.s[kPKkt], kkt_entry(om, v, dg, lam, lam_d));
+        r.s[kPKkt] = fmax(r.s[kPKkt], kkt_entry(om, v, dg, lam_e, lam_d));
         if (!isfinite(w) || !isfinite(v)) r.s[kPBad] += 1.0;
       } else if (MODE == kModeGrad) {
         double gv = v;

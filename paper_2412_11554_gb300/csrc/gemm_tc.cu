@@ -78,6 +78,10 @@ struct EpiArgs {
   int* dense_flag;
   int cap;
   int64_t row0;         // first row of the group
+  // support bitmask of the Eq. 3.8 refit (null: plain fit): bit (i, j) set
+  // where omega_ij may be nonzero; elsewhere the weight is infinite
+  const uint32_t* mask;
+  int64_t mask_ld;      // 32-bit words per row
 };
 
 // Append one nonzero Delta entry to the bucket of its 32-row group.
@@ -190,7 +194,7 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
 // and the diagonal (row == colt); the unchecked form is the hot path.
-template <bool CHECK>
+template <bool CHECK, bool MASK>
 __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
                                            int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
                                            int lane) {
@@ -202,6 +206,7 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
   __nv_bfloat16* ph = sparse ? nullptr : ea.out_hi + row_base * prm.ldplane + colt;
   __nv_bfloat16* pl = sparse ? nullptr : ea.out_lo + row_base * prm.ldplane + colt;
   const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
+  const int64_t mcol = (colt - lane) >> 5;  // mask word of this 32-column chunk
   uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
@@ -218,12 +223,21 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
         sm.r3 += (double)w;
         kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
       } else {
-        const float m = fabsf(a) - tlam;
+        float lam_e = lam, tlam_e = tlam;
+        if (MASK) {
+          // one broadcast load a row: the word covers this chunk's 32 columns
+          const uint32_t mw = __ldg(ea.mask + (row_base + r) * ea.mask_ld + mcol);
+          if (!((mw >> lane) & 1u)) {
+            lam_e = INFINITY;
+            tlam_e = INFINITY;
+          }
+        }
+        const float m = fabsf(a) - tlam_e;
         w = m > 0.f ? copysignf(m, a) : 0.f;
         sl1 += fabsf(w);
         nnz += (w != 0.f) ? 1.f : 0.f;
-        const float kz = fabsf(g) - lam;                 // omega == 0: max(|G| - lambda, 0)
-        const float knz = fabsf(g + copysignf(lam, om));  // omega != 0: |G + lambda sign(omega)|
+        const float kz = fabsf(g) - lam_e;                 // omega == 0: max(|G| - lambda, 0)
+        const float knz = fabsf(g + copysignf(lam_e, om));  // omega != 0: |G + lambda sign(omega)|
         kk = fmaxf(kk, om != 0.f ? knz : kz);
       }
       chk = fmaf(g, 0.f, chk);
@@ -463,6 +477,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.dense_flag = prm.dense_flag;
     ea.cap = prm.cap;
     ea.row0 = 0;
+    ea.mask = prm.mask;
+    ea.mask_ld = prm.mask_ld;
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
     // cp.async needs 16-byte aligned rows
     const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
@@ -524,8 +540,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (full) y_chunk<false>(ea, prm, row_base, colt, v, pre, sm);
             else y_chunk<true>(ea, prm, row_base, colt, v, pre, sm);
           } else if (MODE == kModeProx) {
-            if (full && !diag) prox_chunk<false>(ea, prm, row_base, colt, v, pre, sm, lane);
-            else prox_chunk<true>(ea, prm, row_base, colt, v, pre, sm, lane);
+            if (ea.mask == nullptr) {
+              if (full && !diag) prox_chunk<false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+            } else {
+              if (full && !diag) prox_chunk<false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+            }
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
           } else {

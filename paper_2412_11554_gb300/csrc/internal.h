@@ -40,6 +40,8 @@ struct GemmF64Params {
   double lam, lam_d, scale;
   int32_t a_nxt;
   int32_t smooth;
+  const uint32_t* mask;  // Eq. 3.8 refit support bitmask, or null
+  int64_t mask_ld;
 };
 
 int64_t gemm_f64_tiles(int64_t M, int64_t N);
@@ -63,6 +65,10 @@ cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t l
 // partials written through *nparts.
 cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld, double* part,
                                int64_t* nparts, cudaStream_t st);
+// Support bitmask of the Eq. 3.8 refit: bit (i, j) of word [i][j / 32] is set
+// where Om_ij != 0 or i == j.  Om is p x p with leading dimension ld.
+cudaError_t launch_support_mask(const void* Om, int is_f64, int64_t p, int64_t ld, uint32_t* mask, int64_t mask_ld,
+                                cudaStream_t st);
 // BF16 hi/lo planes of an FP32 matrix (rows x cols, lds) into ldd planes.
 cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds,
                                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldd, cudaStream_t st);

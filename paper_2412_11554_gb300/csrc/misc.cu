@@ -389,6 +389,21 @@ __global__ void rows_norm2_kernel(const T* __restrict__ A, int64_t rows, int64_t
   }
 }
 
+template <class T>
+__global__ void support_mask_kernel(const T* __restrict__ Om, int64_t p, int64_t ld, uint32_t* __restrict__ mask,
+                                    int64_t mask_ld) {
+  const int64_t total = p * mask_ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / mask_ld, w = i % mask_ld;
+    uint32_t bits = 0u;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t c = 32 * w + b;
+      if (c < p && (c == r || Om[r * ld + c] != T(0))) bits |= 1u << b;
+    }
+    mask[i] = bits;
+  }
+}
+
 // Statistics of Omega^0 = I in one partial row: log-diag 0, diag sum p.
 __global__ void identity_stats_kernel(double* part, int64_t p) {
   if (threadIdx.x < kProxSlots) part[threadIdx.x] = (threadIdx.x == kPDiagSum) ? (double)p : 0.0;
@@ -645,6 +660,14 @@ cudaError_t launch_rows_norm2(const void* A, int is_f64, int64_t rows, int64_t c
   if (is_f64) rows_norm2_kernel<double><<<g, kRedThreads, 0, st>>>((const double*)A, rows, cols, ld, part);
   else rows_norm2_kernel<float><<<g, kRedThreads, 0, st>>>((const float*)A, rows, cols, ld, part);
   *nparts = g;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_support_mask(const void* Om, int is_f64, int64_t p, int64_t ld, uint32_t* mask, int64_t mask_ld,
+                                cudaStream_t st) {
+  const unsigned g = grid_for(p * mask_ld, 256);
+  if (is_f64) support_mask_kernel<double><<<g, 256, 0, st>>>((const double*)Om, p, ld, mask, mask_ld);
+  else support_mask_kernel<float><<<g, 256, 0, st>>>((const float*)Om, p, ld, mask, mask_ld);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,9 @@ struct TcParams {
   int* dense_flag;
   int32_t cap;
   int32_t gate_dense;   // 1: run only when ctrl->dense is set (dense fallback)
+  // Eq. 3.8 refit: support bitmask (bit (i, j) of word [i][j / 32]), or null
+  const uint32_t* mask;
+  int64_t mask_ld;
 };
 
 // Encodes a 2-D BF16 tensor map over a rows x cols matrix with leading

@@ -98,5 +98,13 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.accord_fit(dummy, 10, 10, 0.1, ctypes.byref(bad), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
     assert st.status == accord.EINVAL
     assert lib.accord_fit_f64(dummy, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, None) == accord.EUNSUPPORTED
+    # refit: missing Omega_hat, phi outside [0, 1], negative epBIC gamma
+    assert lib.accord_refit(dummy, 10, 10, 0.1, 0.5, None, ctypes.byref(o), dummy, None, 0,
+                            ctypes.byref(st)) == accord.EINVAL
+    assert lib.accord_refit(dummy, 10, 10, 0.1, 1.5, dummy, ctypes.byref(o), dummy, None, 0,
+                            ctypes.byref(st)) == accord.EINVAL
+    bad = accord.accord_default_opts(epbic_gamma=-1.0)
+    assert lib.accord_refit(dummy, 10, 10, 0.1, 0.5, dummy, ctypes.byref(bad), dummy, None, 0,
+                            ctypes.byref(st)) == accord.EINVAL
     for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert accord.accord_status_string(s)

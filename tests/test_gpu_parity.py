@@ -280,3 +280,53 @@ def test_sparse_update_falls_back_when_delta_is_dense(A):
     assert R.kkt_residual(O, R.grad_g(O, Xd), lam, lam) <= 1e-4
     ref = R.fit(X, lam, kkt_tol=1e-7, max_iter=5000)
     assert rel_fro(O, ref.Omega) <= 1e-3
+
+
+# ------------------------------------------------- refit (Eq. 3.8), epBIC ---
+
+@pytest.mark.parametrize("phi", [1.0, 0.5, 0.0])
+def test_fp64_refit_matches_oracle(A, phi):
+    """accord_refit in FP64 on the support of the oracle's Omega-hat follows the
+    oracle refit's iterate sequence; entries off the support stay exactly 0."""
+    w = workload("ar1", p=90, n=60)
+    base = R.fit(w.X, w.lam, kkt_tol=1e-10, max_iter=5000)
+    sup = base.Omega != 0
+    ref = R.refit(w.X, w.lam, sup, phi, kkt_tol=1e-8, max_iter=20000)
+    Om, st = A.accord_refit(dev(w.X), w.lam, phi, dev(base.Omega, torch.float64), precision="fp64",
+                            kkt_tol=1e-8, max_iter=20000)
+    assert st.status == ref.status == R.OK
+    assert st.iters == ref.iters and st.trials == ref.trials
+    O = Om.cpu().numpy()
+    assert rel_fro(O, ref.Omega) <= 1e-9
+    assert not np.any(O[~(sup | np.eye(90, dtype=bool))])
+    assert abs(st.epbic - R.epbic(O, w.X, 0.5)) <= 1e-10 * abs(st.epbic)
+
+
+def test_mixed_refit_matches_oracle(A):
+    w = workload("scalefree", p=500, n=300)
+    base = R.fit(w.X, w.lam, kkt_tol=1e-8, max_iter=5000)
+    sup = base.Omega != 0
+    ref = R.refit(w.X, w.lam, sup, 0.3, kkt_tol=1e-8, max_iter=20000)
+    Om, st = A.accord_refit(dev(w.X), w.lam, 0.3, dev(base.Omega), precision="mixed", kkt_tol=2e-5,
+                            max_iter=20000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    assert rel_fro(O, ref.Omega) <= 1e-4
+    assert not np.any(O[~(sup | np.eye(500, dtype=bool))])
+    assert abs(st.epbic - R.epbic(O, w.X, 0.5)) <= 1e-5 * abs(st.epbic)
+
+
+def test_fit_reports_epbic(A):
+    """epBIC (Eq. 3.7) of the returned iterate for a gamma other than the default."""
+    w = workload("er", p=120, n=80)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-9, epbic_gamma=0.8)
+    O = Om.cpu().numpy()
+    want = R.epbic(O, w.X, 0.8)
+    assert abs(st.epbic - want) <= 1e-10 * abs(want)
+    assert abs(st.logdet_d - float(np.sum(np.log(np.diag(O))))) <= 1e-12 * max(1.0, abs(st.logdet_d))
+
+
+def test_refit_rejects_bad_phi(A):
+    w = workload("ar1", p=40, n=30)
+    _, st = A.accord_refit(dev(w.X), w.lam, 1.5, dev(np.eye(40)), precision="mixed", check=False)
+    assert st.status == -1  # EINVAL
