@@ -210,10 +210,69 @@ def pin_epbic_diagonal():
     return abs(R.epbic(np.diag(w), X, 0.7) - want) <= 1e-10 * abs(want)
 
 
+def pin_path_warm_start():
+    """Warm starts along the lambda path reach the minimiser a cold start
+    reaches (Thm 3.2: it is unique): on a bootstrap subsample, every path
+    estimate equals the cold fit of X[rows] at that lambda."""
+    w = workload("er", p=30, n=40)
+    rows = [np.random.Generator(np.random.PCG64(51)).integers(0, 40, size=35)]
+    lams = [0.5, 0.3, 0.2, 0.12]
+    pr = R.lambda_path(w.X, rows, lams, kkt_tol=1e-11, max_iter=20000)
+    Xs = np.asarray(w.X, dtype=np.float64)[rows[0]]
+    ok = True
+    for k, lam in enumerate(lams):
+        c = R.fit(Xs, lam, kkt_tol=1e-11, max_iter=20000)
+        ok &= pr.fits[0][k].status == R.OK and np.max(np.abs(pr.fits[0][k].Omega - c.Omega)) <= 1e-8
+    return bool(ok)
+
+
+def _diag_regime_lambda(S):
+    """Smallest lambda on a doubling grid at which the diagonal closed form
+    w_i = (-lambda + sqrt(lambda^2 + 4 s_ii)) / (2 s_ii) satisfies the
+    off-diagonal KKT condition |w_i s_ij| <= lambda of Eq. 3.3."""
+    s = np.diag(S)
+    off = np.abs(S - np.diag(s))
+    lam = 1e-3
+    while True:
+        w = (-lam + np.sqrt(lam * lam + 4 * s)) / (2 * s)
+        if np.max(w[:, None] * off) <= lam:
+            return lam, w
+        lam *= 2.0
+
+
+def pin_path_diagonal_regime():
+    """Above that lambda the estimate of every subsample is diagonal with the
+    closed form computed from the subsample's own S; epBIC then has no
+    sparsity term, and the path picks the penalty with the smaller value of
+    2n(-sum log w_i + 1/2 sum s_ii w_i^2)."""
+    X = _gauss(25, 8, 52)
+    rows = [np.arange(25), np.random.Generator(np.random.PCG64(53)).integers(0, 25, size=20)]
+    ok = True
+    want_scores = []
+    lam_hi = 0.0
+    for r in rows:
+        Xs = X[r]
+        lam_hi = max(lam_hi, _diag_regime_lambda(Xs.T @ Xs / len(r))[0])
+    lams = [2.0 * lam_hi, 1.2 * lam_hi]
+    pr = R.lambda_path(X, rows, lams, kkt_tol=1e-12, max_iter=20000)
+    for s, r in enumerate(rows):
+        Xs = X[r]
+        S = Xs.T @ Xs / len(r)
+        d = np.diag(S)
+        sc = []
+        for k, lam in enumerate(lams):
+            w = (-lam + np.sqrt(lam * lam + 4 * d)) / (2 * d)
+            ok &= np.max(np.abs(pr.fits[s][k].Omega - np.diag(w))) <= 1e-10
+            sc.append(2 * len(r) * (-np.sum(np.log(w)) + 0.5 * np.sum(d * w * w)))
+        ok &= pr.best[s] == int(np.argmin(sc))
+        ok &= np.allclose(pr.epbic[:, s], sc, rtol=1e-10)
+    return bool(ok)
+
+
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
-        pin_epbic_diagonal]
+        pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -259,6 +318,25 @@ def test_row_offset_consistency():
     assert k_full == k_blocks
 
 
+def test_bootstrap_sample_compresses_to_weighted_distinct_rows():
+    """The objective sees the data only through S.  A bootstrap sample X[rows]
+    (n_s rows, repeats allowed) and the matrix of its K distinct rows, row j
+    scaled by sqrt(K c_j / n_s) with c_j its multiplicity, have the same S, so
+    Algorithm 1 takes the same steps on both."""
+    w = workload("ar1", p=40, n=30)
+    X = np.asarray(w.X, dtype=np.float64)
+    rows = np.random.Generator(np.random.PCG64(54)).integers(0, 30, size=45)
+    uniq, cnt = np.unique(rows, return_counts=True)
+    K = len(uniq)
+    Xc = X[uniq] * np.sqrt(K * cnt / len(rows))[:, None]
+    Xs = X[rows]
+    np.testing.assert_allclose(Xc.T @ Xc / K, Xs.T @ Xs / len(rows), rtol=0, atol=1e-13)
+    a = R.fit(Xs, w.lam, kkt_tol=1e-10, max_iter=5000)
+    b = R.fit(Xc, w.lam, kkt_tol=1e-10, max_iter=5000)
+    assert a.status == b.status == R.OK and a.ntrials == b.ntrials
+    assert np.max(np.abs(a.Omega - b.Omega)) <= 1e-10
+
+
 # ------------------------------------------------------ planted mistakes ---
 
 MUTANTS = {
@@ -270,6 +348,9 @@ MUTANTS = {
     "grad_missing_1_over_n": ("grad_g", lambda Om, X: (Om @ np.asarray(X, float).T) @ np.asarray(X, float)),
     "g_missing_half": ("smooth_g", lambda Om, X: float(np.sum((Om @ np.asarray(X, float).T) ** 2)) / X.shape[0]),
     "lipschitz_trace": ("lipschitz", lambda X: float(np.trace(np.asarray(X, float) @ np.asarray(X, float).T)) / X.shape[0] / 3),
+    "epbic_missing_2n": ("epbic", lambda Om, X, gm: -float(np.sum(np.log(np.diag(Om)))) + R.smooth_g(Om, X)),
+    "path_ignores_subsample": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
+                               _f(X, [np.arange(np.asarray(X).shape[0])] * len(rows), lams, **kw)),
 }
 
 
