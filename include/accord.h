@@ -210,6 +210,62 @@ int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double*
  * pointer stays valid until the thread's next call. */
 const char* accord_last_error(void);
 
+/* ---- lambda path over subsamples (Sec 3.4) ------------------------------ */
+
+/* One estimate of a path: record [k * n_sub + s] for penalty k, subsample s. */
+typedef struct {
+    int32_t status;          /* ACCORD_OK, ACCORD_NOT_CONVERGED (max_iter steps at this
+                                penalty; the chain still moves on), or an error, which also
+                                ends the chain (its later records carry the same status)   */
+    int32_t iters;           /* accepted steps at this penalty                              */
+    int32_t trials;          /* prox evaluations at this penalty                            */
+    int32_t reserved0;
+    double  lambda;          /* the penalty                                                 */
+    double  f, g, kkt;       /* objective (Eq. 3.2), smooth part, KKT residual (Eq. 3.3)    */
+    double  logdet_d;        /* sum_i log omega_ii                                          */
+    double  epbic;           /* Eq. 3.7 with n = the subsample's row count and
+                                opts->epbic_gamma (+inf after an error)                     */
+    double  tau_last;        /* last accepted step                                          */
+    int64_t nnz_offdiag;     /* ||Omega||_0 off the diagonal                                */
+} accord_path_entry;
+
+/* Tuning by epBIC over a penalty grid (Sec 3.4) on subsamples of one data set.
+ * Subsample s is the data matrix X[rows[row_offsets[s] .. row_offsets[s+1])]
+ * (rows may repeat, as in a bootstrap sample).  For every subsample the
+ * penalties lambdas[0 .. n_lambda) are solved in the given order, each fit
+ * starting from the previous penalty's estimate of that subsample (warm start;
+ * the first starts at Omega = I), with Algorithm 1 and opts as in accord_fit.
+ * All subsamples run together as one batch on the GPU.
+ *   X            device, n x p row-major FP32 (the whole data set)
+ *   rows         host, int32 row indices in [0, n)
+ *   row_offsets  host, n_sub + 1 offsets into rows, row_offsets[0] = 0, each
+ *                subsample non-empty; 1 <= n_sub <= 65535
+ *   lambdas      host, n_lambda >= 1 finite penalties >= 0 (decreasing is the usual path)
+ *   entries      host, n_lambda * n_sub records (required)
+ *   support      device or NULL: n_lambda * n_sub support bitmasks, record
+ *                [k * n_sub + s], each p rows of ceil(p / 32) uint32 words;
+ *                bit j % 32 of word [i][j / 32] is set where omega_ij != 0 or i == j
+ *   omega_best   device or NULL: n_sub dense p x p matrices (element type per
+ *                precision), subsample s's estimate of smallest epBIC
+ *   best_index   host or NULL: n_sub penalty indices of those estimates (-1: none)
+ *   workspace    device, accord_path_workspace_bytes(...) bytes, 256-byte
+ *                aligned, or NULL to allocate (and free) one internally
+ *   out          host or NULL: totals (iters, trials over all estimates; setup
+ *                and solve time; launches)
+ * Returns ACCORD_OK when every estimate converged, ACCORD_NOT_CONVERGED when
+ * some reached max_iter, else the first error among the records (or the
+ * call's own error: EINVAL, EDOMAIN for non-finite data, ENOMEM, ECUDA).
+ * opts->trace, init_from_omega and sparse_update are ignored (the mixed mode
+ * always uses the sparse Delta update with its dense fallback). */
+int accord_path(const float* X, int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets,
+                int64_t n_sub, const double* lambdas, int64_t n_lambda, const accord_opts* opts,
+                accord_path_entry* entries, uint32_t* support, void* omega_best, int32_t* best_index,
+                void* workspace, size_t ws_bytes, accord_stats* out);
+
+/* Workspace bytes of accord_path for these subsamples (0 on invalid arguments). */
+size_t accord_path_workspace_bytes(int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets,
+                                   int64_t n_sub, int64_t n_lambda, const accord_opts* opts);
+
 #ifdef __cplusplus
 }
 #endif

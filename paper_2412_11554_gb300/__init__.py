@@ -9,6 +9,9 @@ from .accord import (  # noqa: F401
     accord_default_opts,
     accord_device_check,
     accord_fit,
+    accord_path,
+    accord_path_workspace_bytes,
+    PathResult,
     accord_refit,
     accord_grad,
     accord_last_error,

@@ -49,9 +49,18 @@ class AccordStats(ctypes.Structure):
     ]
 
 
+class AccordPathEntry(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("trials", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("lambda_", ctypes.c_double), ("f", ctypes.c_double),
+        ("g", ctypes.c_double), ("kkt", ctypes.c_double), ("logdet_d", ctypes.c_double),
+        ("epbic", ctypes.c_double), ("tau_last", ctypes.c_double), ("nnz_offdiag", ctypes.c_int64),
+    ]
+
+
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
-           "accord_loss_f64_noalloc")
+           "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes")
 
 _lib = None
 
@@ -90,6 +99,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_last_error.restype = ctypes.c_char_p
     lib.accord_loss_f64_noalloc.argtypes = [P, i64, i64, P, dbl, i32, P, P]
     lib.accord_loss_f64_noalloc.restype = i32
+    lib.accord_path.argtypes = [P, i64, i64, P, P, i64, P, i64, opts_p, ctypes.POINTER(AccordPathEntry), P, P, P, P,
+                                ctypes.c_size_t, stats_p]
+    lib.accord_path.restype = i32
+    lib.accord_path_workspace_bytes.argtypes = [i64, i64, P, P, i64, i64, opts_p]
+    lib.accord_path_workspace_bytes.restype = ctypes.c_size_t
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -265,6 +279,88 @@ def accord_loss_f64_noalloc(X: torch.Tensor, Omega: torch.Tensor, lam: float, fg
                                          _stream_handle(stream), fg_out.data_ptr())
     if status != OK:
         raise AccordError(status, "accord_loss_f64_noalloc")
+
+
+@dataclasses.dataclass
+class PathResult:
+    """accord_path output.  Arrays are (n_lambda, n_sub): entry [k, s] is the
+    estimate of subsample s at lambdas[k]."""
+    status: int
+    lambdas: np.ndarray
+    entry_status: np.ndarray
+    iters: np.ndarray
+    trials: np.ndarray
+    f: np.ndarray
+    g: np.ndarray
+    kkt: np.ndarray
+    logdet_d: np.ndarray
+    epbic: np.ndarray
+    tau_last: np.ndarray
+    nnz_offdiag: np.ndarray
+    best_index: np.ndarray                   # (n_sub,) index k of the smallest epBIC, -1 if none
+    omega_best: torch.Tensor | None          # (n_sub, p, p) estimates at best_index
+    support: torch.Tensor | None             # (n_lambda, n_sub, p, ceil(p/32)) int32 bit words
+    stats: FitStats
+
+
+def _subsample_arrays(subsamples) -> tuple[np.ndarray, np.ndarray]:
+    idx = [np.ascontiguousarray(np.asarray(s, dtype=np.int32).ravel()) for s in subsamples]
+    rows = np.ascontiguousarray(np.concatenate(idx) if idx else np.zeros(0, np.int32))
+    offs = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(s) for s in idx])]).astype(np.int64))
+    return rows, offs
+
+
+def accord_path_workspace_bytes(n: int, p: int, subsamples, n_lambda: int, **kw) -> int:
+    rows, offs = _subsample_arrays(subsamples)
+    o = accord_default_opts(**kw)
+    return int(load_library().accord_path_workspace_bytes(n, p, rows.ctypes.data, offs.ctypes.data, len(offs) - 1,
+                                                          n_lambda, ctypes.byref(o)))
+
+
+def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed", support: bool = False,
+                omega_best: bool = True, workspace: torch.Tensor | None = None, stream=None, check: bool = True,
+                **opts) -> PathResult:
+    """Lambda path over subsamples (Sec 3.4): X is the CUDA float32 n x p data
+    set, subsamples a list of row-index arrays (repeats allowed), lambdas the
+    penalties in solve order.  Remaining keyword arguments set accord_opts
+    fields (kkt_tol, max_iter, epbic_gamma, ...)."""
+    lib = load_library()
+    _check_x(X, torch.float32)
+    n, p = X.shape
+    rows, offs = _subsample_arrays(subsamples)
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
+    ns, nl = len(offs) - 1, len(lam)
+    prec = PRECISIONS[precision]
+    odt = torch.float64 if prec == FP64 else torch.float32
+    o = accord_default_opts(precision=prec, **opts)
+    o.stream = _stream_handle(stream)
+    ent = (AccordPathEntry * max(nl * ns, 1))()
+    sup = None
+    if support:
+        sup = torch.zeros((nl, ns, p, (p + 31) // 32), dtype=torch.int32, device=X.device)
+    best = torch.zeros((ns, p, p), dtype=odt, device=X.device) if omega_best else None
+    bidx = np.full(max(ns, 1), -1, dtype=np.int32)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = AccordStats()
+    status = lib.accord_path(X.data_ptr(), n, p, rows.ctypes.data, offs.ctypes.data, ns, lam.ctypes.data, nl,
+                             ctypes.byref(o), ent, sup.data_ptr() if sup is not None else None,
+                             best.data_ptr() if best is not None else None, bidx.ctypes.data, ws_ptr, ws_bytes,
+                             ctypes.byref(st))
+    if check and status < 0:
+        raise AccordError(status, "accord_path")
+
+    def col(name, dt):
+        return np.array([getattr(ent[i], name) for i in range(nl * ns)], dtype=dt).reshape(nl, ns)
+
+    stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
+                     st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms, st.t_y_gemm_ms,
+                     st.n_launches, st.logdet_d, st.epbic, None)
+    return PathResult(status, col("lambda_", np.float64), col("status", np.int32), col("iters", np.int32),
+                      col("trials", np.int32), col("f", np.float64), col("g", np.float64), col("kkt", np.float64),
+                      col("logdet_d", np.float64), col("epbic", np.float64), col("tau_last", np.float64),
+                      col("nnz_offdiag", np.int64), bidx[:ns].copy(), best, sup, stats)
 
 
 def accord_status_string(status: int) -> str:

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "accord.h"
+#include "api_util.h"
 #include "internal.h"
 #include "tc_gemm.h"
 
@@ -27,10 +28,6 @@ void set_last_error(const char* where, int line, const char* what) {
 void clear_last_error() { g_last_error[0] = 0; }
 
 namespace {
-
-constexpr size_t kAlign = 1024;
-
-inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Byte offsets of every sub-buffer of the fit workspace.
 struct Layout {
@@ -57,13 +54,6 @@ struct Layout {
   size_t total = 0;
 };
 
-size_t take(size_t& cursor, size_t bytes) {
-  const size_t at = cursor;
-  cursor += (bytes + kAlign - 1) / kAlign * kAlign;
-  return at;
-}
-
-constexpr int kBucketCap = 4096;  // Delta entries a 32-row group can hold
 
 Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max, bool sparse) {
   Layout L;
@@ -130,56 +120,10 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
   return L;
 }
 
-template <class T>
-T* at(void* base, size_t off) {
-  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
-}
-
-struct Guard {  // frees an internally allocated workspace on every exit path
-  void* ptr = nullptr;
-  cudaStream_t st = nullptr;
-  ~Guard() {
-    if (ptr) cudaFreeAsync(ptr, st);
-  }
-};
-
-#define ACCORD_CK(call)                                            \
-  do {                                                             \
-    cudaError_t e_ = (call);                                       \
-    if (e_ != cudaSuccess) {                                       \
-      set_last_error(__FILE__, __LINE__, cudaGetErrorString(e_));  \
-      return kEcuda;                                               \
-    }                                                              \
-  } while (0)
-
-int check_device() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return kEcuda;
-  int major = 0, minor = 0;
-  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return kEcuda;
-  if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return kEcuda;
-  if (major != 10 || minor != 3) return kEunsupported;
-  return kOk;
-}
-
 // The sparse Delta update runs in mixed mode; bucket keys hold a column index
 // in 25 bits.
 bool use_sparse(const accord_opts& o, int64_t p) {
   return o.precision == ACCORD_MIXED_BF16X3 && o.sparse_update != 0 && p < (1 << 25) - 1;
-}
-
-int check_opts(const accord_opts& o) {
-  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
-  if (!(o.beta > 0.0 && o.beta <= 1.0)) return kEinval;
-  if (!std::isfinite(o.tau0)) return kEinval;
-  if (!(o.kkt_tol >= 0.0)) return kEinval;
-  if (o.max_iter < 0 || o.max_backtracks < 0) return kEinval;
-  if (!(o.lipschitz >= 0.0) || !std::isfinite(o.lipschitz)) return kEinval;
-  if (o.lipschitz_max_iter < 1) return kEinval;
-  if (!(o.lipschitz_tol >= 0.0)) return kEinval;
-  if (!(o.epbic_gamma >= 0.0)) return kEinval;
-  if (o.trace_cap < 0) return kEinval;
-  return kOk;
 }
 
 // Device GEMM wrappers that pick the precision's kernel family.

@@ -62,6 +62,22 @@ struct Ctrl {
   double pw_est, pw_prev;
   int32_t pw_iter;
   int32_t dense;      // a Delta bucket overflowed: this trial takes the dense Y GEMM
+  // penalty weights and 1/n of this problem (a batch holds one Ctrl per problem)
+  double lam, lam_d, inv_n;
+  int32_t kdim;       // rows of this problem's data matrix
+  int32_t lam_idx;    // lambda path: index of the current penalty
+  int32_t finished;   // lambda path: every penalty of the chain is done
+  int32_t emit;       // lambda path: 1 = an estimate was completed in this trial, 2 = it is the best so far
+  int32_t emit_lam;   // lambda path: penalty index of that estimate
+  int32_t iters_tot;  // lambda path: accepted steps over the whole chain
+  int32_t trials_tot; // lambda path: prox evaluations over the whole chain
+};
+
+// One estimate of a lambda path (same layout as accord_path_entry).
+struct PathRec {
+  int32_t status, iters, trials, reserved0;
+  double lambda, f, g, kkt, logdet_d, epbic, tau_last;
+  int64_t nnz_offdiag;
 };
 
 struct SolveParams {

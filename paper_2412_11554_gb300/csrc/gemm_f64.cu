@@ -16,12 +16,18 @@ struct Red {  // per-thread epilogue accumulators
 
 template <int MODE>
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
-  const Ctrl* ctrl = prm.ctrl;
+  const bool batch = prm.nprob > 1 || prm.active != nullptr;
+  int b = blockIdx.z;
+  if (prm.active != nullptr) {
+    if (b >= *prm.nactive) return;
+    b = prm.active[b];
+  }
+  const Ctrl* ctrl = prm.ctrl ? prm.ctrl + b : nullptr;
   if (ctrl && ctrl->done) return;
   const int cur = ctrl ? ctrl->cur : 0;
   const int nxt = cur ^ 1;
-  const double* __restrict__ A = prm.A[prm.a_nxt ? nxt : cur];
-  const double* __restrict__ B = prm.B;
+  const double* __restrict__ A = prm.A[prm.a_nxt ? nxt : cur] + b * prm.s_a;
+  const double* __restrict__ B = prm.B + b * prm.s_b;
 
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -69,9 +75,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
 #pragma unroll
   for (int q = 0; q < kProxSlots; ++q) r.s[q] = 0.0;
   const double tau = ctrl ? ctrl->tau : 0.0;
-  const double lam = prm.lam, lam_d = prm.lam_d, scale = prm.scale;
-  double* __restrict__ out = prm.out[nxt];
-  const double* __restrict__ aux = prm.aux[cur];
+  const bool pp = batch && ctrl != nullptr;
+  const double lam = pp ? ctrl->lam : prm.lam, lam_d = pp ? ctrl->lam_d : prm.lam_d;
+  const double scale = (pp && (MODE == kModeProx || MODE == kModeGram)) ? ctrl->inv_n : prm.scale;
+  double* __restrict__ out = prm.out[nxt] ? prm.out[nxt] + b * prm.s_out : nullptr;
+  const double* __restrict__ aux = prm.aux[cur] ? prm.aux[cur] + b * prm.s_aux : nullptr;
 
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
       t = (MODE == kModeProx && tid == kPKkt) ? fmax(t, red[w][tid]) : t + red[w][tid];
     const int slots = (MODE == kModeProx) ? kProxSlots : kYSlots;
     if (tid < slots) {
-      const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+      const int64_t tile = b * prm.s_part + (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
       prm.part[tile * slots + tid] = t;
     }
   }
@@ -148,8 +156,9 @@ int64_t gemm_f64_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N 
 
 cudaError_t launch_gemm_f64(int mode, const GemmF64Params& prm, cudaStream_t st) {
   if (prm.M <= 0 || prm.N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((prm.N + BN - 1) / BN), (unsigned)((prm.M + BM - 1) / BM));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((prm.N + BN - 1) / BN), (unsigned)((prm.M + BM - 1) / BM),
+            (unsigned)(prm.nprob > 1 ? prm.nprob : 1));
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
   switch (mode) {
     case kModeY: gemm_f64_kernel<kModeY><<<grid, NT, 0, st>>>(prm); break;
     case kModeProx: gemm_f64_kernel<kModeProx><<<grid, NT, 0, st>>>(prm); break;

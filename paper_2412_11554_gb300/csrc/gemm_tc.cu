@@ -61,6 +61,32 @@ __device__ __forceinline__ void cta_tile(int T, const TcParams& prm, int rank, i
   mb = mg * kClusterM + rank;
 }
 
+// Flat tile index T of a batch -> problem b and its cluster tile Tl.
+__device__ __forceinline__ int tile_problem(const TcParams& prm, int T, int& Tl) {
+  const int slot = T / prm.ntiles_c;
+  Tl = T - slot * prm.ntiles_c;
+  return prm.active ? prm.active[slot] : slot;
+}
+
+// Problems whose fit has finished (or, for the gated dense fallback, that
+// need no dense product in this trial) contribute no tiles.  The control
+// block does not change while the kernel runs, so every warp role skips the
+// same tiles.
+__device__ __forceinline__ bool skip_problem(const TcParams& prm, int b) {
+  if (prm.ctrl == nullptr) return false;
+  const Ctrl& c = prm.ctrl[b];
+  return c.done || (prm.gate_dense && !c.dense);
+}
+
+// First flat tile >= T (stepping by `stride`) that is not skipped; ntot if none.
+__device__ __forceinline__ int next_tile(const TcParams& prm, int T, int ntot, int stride, int& b, int& Tl) {
+  for (; T < ntot; T += stride) {
+    b = tile_problem(prm, T, Tl);
+    if (!skip_problem(prm, b)) return T;
+  }
+  return ntot;
+}
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
 
 struct EpiArgs {
@@ -302,10 +328,11 @@ __device__ __forceinline__ void gram_chunk(const TcParams& prm, int64_t row_base
 // 16384 / (3 * 32) = 170 registers a thread (168 after allocation rounding).
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams prm) {
-  const Ctrl* ctrl = prm.ctrl;
-  if (ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
-  const int cur = ctrl ? ctrl->cur : 0;
-  const int nxt = cur ^ 1;
+  Ctrl* ctrl = prm.ctrl;
+  const bool batch = prm.nprob > 1 || prm.active != nullptr;
+  if (!batch && ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
+  const int ntot = (prm.active ? *prm.nactive : (prm.nprob > 1 ? prm.nprob : 1)) * prm.ntiles_c;
+  if (ntot <= 0) return;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -350,9 +377,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const int nclusters = gridDim.x / kClusterM;
   constexpr uint16_t kMask = (uint16_t)((1u << kClusterM) - 1u);
 
-  const int asel = prm.a_nxt ? nxt : cur;
-  const CUtensorMap* mA_hi = &prm.a_hi[asel];
-  const CUtensorMap* mA_lo = &prm.a_lo[asel];
   const CUtensorMap* mB_hi = &prm.b_hi;
   const CUtensorMap* mB_lo = &prm.b_lo;
   const uint32_t smem_base = ptx::smem_u32(smem);
@@ -360,8 +384,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (warp == 0) {
     // ------------------------------------------------------ TMA producer --
     if (lane == 0) {
-      ptx::tma_prefetch_desc(mA_hi);
-      ptx::tma_prefetch_desc(mA_lo);
+      for (int q = 0; q < 2; ++q) {
+        ptx::tma_prefetch_desc(&prm.a_hi[q]);
+        ptx::tma_prefetch_desc(&prm.a_lo[q]);
+      }
       ptx::tma_prefetch_desc(mB_hi);
       ptx::tma_prefetch_desc(mB_lo);
       // operand tiles are shared by many CTAs: keep them in L2 (the A operand
@@ -374,20 +400,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       bool filled[kStages];
       for (int q = 0; q < kStages; ++q) { filled[q] = false; fill_ph[q] = 0; }
       bool ok = true;
-      for (int T = cluster_id; T < prm.ntiles_c && ok; T += nclusters) {
+      int b = 0, Tl = 0;
+      for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot && ok;
+           T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl)) {
         int mb, nb;
-        cta_tile(T, prm, rank, mb, nb);
-        for (int kb = 0; kb < prm.num_kb; ++kb) {
+        cta_tile(Tl, prm, rank, mb, nb);
+        const int cb = ctrl ? ctrl[b].cur : 0;
+        const int asel = prm.a_nxt ? (cb ^ 1) : cb;
+        const CUtensorMap* mA_hi = &prm.a_hi[asel];
+        const CUtensorMap* mA_lo = &prm.a_lo[asel];
+        const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
+        const int32_t zb = prm.b_batched ? b : 0;
+        for (int kb = 0; kb < nkb; ++kb) {
           // the slot is free only when every CTA of the cluster released it
           if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
           ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
           const uint32_t st = smem_base + s * kStageBytes;
-          ptx::tma_load_2d(st, mA_hi, &full[s], kb * BK, mb * BM, pol_a);
-          ptx::tma_load_2d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM, pol_a);
+          ptx::tma_load_3d(st, mA_hi, &full[s], kb * BK, mb * BM, b, pol_a);
+          ptx::tma_load_3d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM, b, pol_a);
           const int32_t by = nb * kBN + rank * kBBox;
-          ptx::tma_load_2d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, kMask, pol_keep);
-          ptx::tma_load_2d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by, kMask,
+          ptx::tma_load_3d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, zb, kMask,
                               pol_keep);
+          ptx::tma_load_3d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by, zb,
+                              kMask, pol_keep);
           filled[s] = true;
           fill_ph[s] = ph;
           if (++s == kStages) { s = 0; ph ^= 1u; }
@@ -414,12 +449,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       uint32_t s = 0, ph = 0;
       bool ok = true;
       int i = 0;
-      for (int T = cluster_id; T < prm.ntiles_c && ok; T += nclusters, ++i) {
+      int b = 0, Tl = 0;
+      for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot && ok;
+           T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl), ++i) {
         const uint32_t acc = i & 1, aph = (i >> 1) & 1;
         if (!ptx::mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem_base + acc * kBN;
-        for (int kb = 0; kb < prm.num_kb; ++kb) {
+        const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
+        for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t st = smem_base + s * kStageBytes;
@@ -458,16 +496,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const int h = e >> 2;
     constexpr int kColsPerWarp = kBN / (kEpiWarps / 4);
     float* tbuf = epi_buf + e * 1024;
-    const double tau_d = ctrl ? ctrl->tau : 0.0;
     EpiArgs ea;
-    ea.tau = (float)tau_d;
     ea.lam = prm.lam;
     ea.lam_d = prm.lam_d;
     ea.scale = prm.scale;
-    ea.out = prm.out[nxt];
-    ea.out_hi = prm.out_hi[nxt];
-    ea.out_lo = prm.out_lo[nxt];
-    ea.aux = prm.aux[cur];
     ea.M = prm.M;
     ea.N = prm.N;
     ea.pol_stream = ptx::policy_evict_first();
@@ -480,18 +512,34 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.mask = prm.mask;
     ea.mask_ld = prm.mask_ld;
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
-    // cp.async needs 16-byte aligned rows
-    const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
     int i = 0;
-    for (int T = cluster_id; T < prm.ntiles_c; T += nclusters, ++i) {
+    int b = 0, Tl = 0;
+    for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot;
+         T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl), ++i) {
       int mb, nb;
-      cta_tile(T, prm, rank, mb, nb);
+      cta_tile(Tl, prm, rank, mb, nb);
+      // this tile's problem: its iterate buffers, step and penalty
+      const int cb = ctrl ? ctrl[b].cur : 0, nx = cb ^ 1;
+      ea.out = prm.out[nx] ? prm.out[nx] + b * prm.s_out : nullptr;
+      ea.out_hi = prm.out_hi[nx] ? prm.out_hi[nx] + b * prm.s_plane : nullptr;
+      ea.out_lo = prm.out_lo[nx] ? prm.out_lo[nx] + b * prm.s_plane : nullptr;
+      ea.aux = prm.aux[cb] ? prm.aux[cb] + b * prm.s_aux : nullptr;
+      ea.tau = ctrl ? (float)ctrl[b].tau : 0.f;
+      if (batch && ctrl != nullptr) {
+        ea.lam = (float)ctrl[b].lam;
+        ea.lam_d = (float)ctrl[b].lam_d;
+        if (MODE == kModeProx) ea.scale = (float)ctrl[b].inv_n;
+        ea.dense_flag = &ctrl[b].dense;
+      }
+      double* part_b = prm.part ? prm.part + b * prm.s_part * ((MODE == kModeY) ? kYSlots : kProxSlots) : nullptr;
+      // cp.async needs 16-byte aligned rows
+      const bool aux_async = ea.aux != nullptr && (prm.ldaux % 4) == 0 && ((uintptr_t)ea.aux & 15u) == 0;
       const uint32_t acc = i & 1, aph = (i >> 1) & 1;
       const int64_t row_base = (int64_t)mb * BM + 32 * q;
       const int64_t col_base = (int64_t)nb * kBN + h * kColsPerWarp;
       const bool rows_full = row_base + 32 <= prm.M;
       if (MODE == kModeProx && prm.keys != nullptr) {
-        const int64_t bkt = row_base / 32;  // one bucket per warp row quarter
+        const int64_t bkt = b * prm.s_bkt + row_base / 32;  // one bucket per warp row quarter
         ea.bkey = prm.keys + bkt * prm.cap;
         ea.bval = prm.vals + bkt * prm.cap;
         ea.bcnt = prm.counts + bkt;
@@ -591,13 +639,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       epi_bar();
       if (e == 0) {
-        if ((MODE == kModeY || MODE == kModeProx) && prm.part != nullptr && lane < W && mb < prm.tiles_m) {
+        if ((MODE == kModeY || MODE == kModeProx) && part_b != nullptr && lane < W && mb < prm.tiles_m) {
           double x = red[lane];
           for (int w = 1; w < kEpiWarps; ++w)
             x = (MODE == kModeProx && lane == kPKkt) ? fmax(x, red[w * 8 + lane]) : x + red[w * 8 + lane];
           const int bad_slot = (MODE == kModeProx) ? (int)kPBad : (int)kYBad;
           if (*abort_flag && lane == bad_slot) x += 1.0;
-          prm.part[((int64_t)mb * prm.tiles_n + nb) * W + lane] = x;
+          part_b[((int64_t)mb * prm.tiles_n + nb) * W + lane] = x;
         }
         if (lane == 0) *stop_flag = *abort_flag;
       }
@@ -616,12 +664,49 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   }
 }
 
+// Shared-memory opt-in and the persistent grid size (clusters that fit at
+// once), set up once per device and mode.  Done outside any launch so that a
+// stream capture records launches only.
+template <int MODE>
+cudaError_t configure_mode(int& max_clusters) {
+  static int configured = -1;
+  static int clusters = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured != dev) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kClusterM, 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE>, &cfg) != cudaSuccess || n < 1) {
+      (void)cudaGetLastError();
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      n = sms / kClusterM > 0 ? sms / kClusterM : 1;
+    }
+    clusters = n;
+    configured = dev;
+  }
+  max_clusters = clusters;
+  return cudaSuccess;
+}
+
 template <int MODE>
 cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
-  static int configured = -1;
-  static int max_clusters = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
+  int max_clusters = 0;
+  cudaError_t e = configure_mode<MODE>(max_clusters);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -633,22 +718,8 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    // persistent grid: as many clusters as can be resident at once
-    cfg.gridDim = dim3(kClusterM, 1, 1);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE>, &cfg) != cudaSuccess || n < 1) {
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      n = sms / kClusterM > 0 ? sms / kClusterM : 1;
-    }
-    max_clusters = n;
-    configured = dev;
-  }
-  const int clusters = (int)std::min<int64_t>(prm.ntiles_c, max_clusters);
+  const int64_t tiles_total = (int64_t)(prm.nprob > 1 ? prm.nprob : 1) * prm.ntiles_c;
+  const int clusters = (int)std::min<int64_t>(tiles_total, max_clusters);
   cfg.gridDim = dim3((unsigned)(clusters * kClusterM), 1, 1);
   return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, prm);
 }
@@ -656,6 +727,15 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
 }  // namespace
 
 int tc_box_n() { return kBBox; }
+
+cudaError_t tc_prepare() {
+  int m = 0;
+  cudaError_t e = configure_mode<kModeY>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeProx>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeGrad>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeGram>(m);
+  return e;
+}
 
 int64_t tc_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + kBN - 1) / kBN); }
 
@@ -689,7 +769,7 @@ cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st) {
 
 // ------------------------------------------------------------ tensor maps --
 bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld,
-                      int box_rows) {
+                      int box_rows, int64_t depth, int64_t slice_stride) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (encode == nullptr) {
     cudaDriverEntryPointQueryResult q;
@@ -700,12 +780,16 @@ bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
       return false;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  if (((uintptr_t)base & 15u) != 0 || (ld * 2) % 16 != 0 || rows < 1 || cols < 1) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides,
+  if (depth < 1) depth = 1;
+  if (depth == 1 || slice_stride <= 0) slice_stride = rows * ld;
+  if (((uintptr_t)base & 15u) != 0 || (ld * 2) % 16 != 0 || (slice_stride * 2) % 16 != 0 || rows < 1 || cols < 1 ||
+      slice_stride < rows * ld)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)depth};
+  const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(slice_stride * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims, strides,
                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;

@@ -42,6 +42,13 @@ struct GemmF64Params {
   int32_t smooth;
   const uint32_t* mask;  // Eq. 3.8 refit support bitmask, or null
   int64_t mask_ld;
+  // Batch of problems with the same M, N, K (grid z = problem slot): problem
+  // b = active[slot] (or slot) uses ctrl[b] for its step, penalty and 1/n and
+  // the operands and outputs at + b * stride; finished problems do nothing.
+  int32_t nprob;            // problems (1: a single fit)
+  const int32_t* active;    // device list of problems, or null (0 .. nprob-1)
+  const int32_t* nactive;   // device length of `active`
+  int64_t s_a, s_b, s_out, s_aux, s_part;  // strides: elements (s_part: tiles)
 };
 
 int64_t gemm_f64_tiles(int64_t M, int64_t N);
@@ -76,9 +83,12 @@ cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, in
 // Lanczos estimate of lambda_max of the symmetric n x n matrix K (FP64).
 // V holds (kmax + 1) x n doubles, alpha / beta kmax doubles each, w n.
 constexpr int kLanczosMax = 128;
-cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st);
+// A batch of nprob problems (one Ctrl each) takes its slices of K, V, w and
+// alpha / beta at the given strides (doubles).
+cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st, int nprob = 1, int64_t sV = 0);
 cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
-                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st);
+                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st,
+                                 int nprob = 1, int64_t sK = 0, int64_t sV = 0, int64_t sW = 0, int64_t sAB = 0);
 
 // Control kernels of the Algorithm 1 loop.
 cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,
@@ -99,12 +109,51 @@ cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const 
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st);
 
+// ------------------------------------------------------------ lambda path ---
+// A path runs one chain per subsample; chain c is problem c of the batch and
+// walks the penalties lambdas[0..n_lambda) in order, each fit starting from
+// the previous estimate.
+struct PathDev {
+  Ctrl* ctrl;
+  int32_t nchains, n_lambda;
+  const double* lambdas;   // device, in solve order
+  const double* n_obs;     // device, rows of each chain's subsample (the n of Eq. 3.7)
+  double gamma, log_p;
+  int32_t penalize_diag, pad;
+  PathRec* rec;            // device, n_lambda x nchains, record [k * nchains + c]
+  double* best_epbic;      // device, per chain (initialised to +inf)
+  int32_t* best_idx;       // device, per chain
+  int32_t* active;         // device list of unfinished chains
+  int32_t* nactive;
+};
+// Finishes the per-chain control blocks after L is known: tau0, f and g of
+// Omega^0 = I with Y^0 = X^T (yt0: p x ldy per chain, s_y elements apart).
+cudaError_t launch_batch_ctrl_init(const PathDev& pd, const void* yt0, int is_f64, int64_t p, int64_t ldy,
+                                   int64_t s_y, const SolveParams& sp, double L_given, cudaStream_t st);
+// Batched post_prox / decide: block `slot` serves problem active[slot];
+// partial rows of problem b start at part + b * ntiles rows.
+cudaError_t launch_post_prox_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                   const double* part, int64_t ntiles, const SolveParams& sp, cudaStream_t st);
+cudaError_t launch_decide_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                const double* part, int64_t ntiles, const SolveParams& sp, int* bucket_counts,
+                                int nbuckets, const double* part_sparse, cudaStream_t st);
+// After each trial: record every estimate completed in it (status, sums,
+// epBIC of Eq. 3.7), move its chain to the next penalty (warm start) or
+// finish it, and rebuild the active list.
+cudaError_t launch_path_advance(const PathDev& pd, cudaStream_t st);
+// For each estimate recorded by the last advance: its support bits (if
+// support != null; record k * nchains + c, p rows of mask_ld words) and, when
+// its epBIC is the chain's best so far, a dense copy into omega_best + c p^2.
+cudaError_t launch_path_emit(const PathDev& pd, const void* om0, const void* om1, int is_f64, int64_t p,
+                             int64_t ldo, int64_t s_om, uint32_t* support, int64_t mask_ld, void* omega_best,
+                             cudaStream_t st);
+
 // ------------------------------------------------------ sparse Y update ---
 // Rows of 32 share one bucket of Delta entries: key = (row - 32 b) << 25 | col,
 // value = Delta_ij (FP32), count in counts[b] (may exceed cap: overflow).
 constexpr int kBucketRows = 32;
 struct SparseYParams {
-  const Ctrl* ctrl;
+  const Ctrl* ctrl;           // a batch: one per problem (grid y = problem slot)
   const float* y[2];          // Y (p x ldy FP32), index cur / nxt
   float* yw[2];
   __nv_bfloat16* y_hi[2];     // planes of Y+ (p x ldyk), index nxt
@@ -116,12 +165,22 @@ struct SparseYParams {
   int32_t cap, tiles_m, tiles_n, pad;
   int64_t p, n, ldy, ldyk;
   double* part;               // one row of kYSlots per bucket
+  // batch: problem b = active[slot] (or slot), data at + b * stride
+  const int32_t* active;
+  const int32_t* nactive;
+  int32_t nprob;
+  int64_t s_y, s_yk, s_xt, s_bkt;  // strides: Y (elements), planes, X^T, buckets
 };
 size_t sparse_y_smem_bytes(int cap);
 cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st);
+cudaError_t sparse_y_prepare();  // one-time shared-memory opt-in (before a graph capture)
 // Dense fallback: BF16 planes of Delta = Omega[nxt] - Omega[cur] when ctrl->dense.
+// A batch runs grid y over problem slots (active list or 0 .. nprob-1) with
+// Omega at + b * s_om and the planes at + b * s_pl.
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st);
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st,
+                                int32_t nprob = 1, const int32_t* active = nullptr, const int32_t* nactive = nullptr,
+                                int64_t s_om = 0, int64_t s_pl = 0);
 // X^T in FP32 (p x ldxt).
 cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 

@@ -205,7 +205,17 @@ __global__ void split_planes_kernel(const float* __restrict__ src, int64_t rows,
 // after step j the largest eigenvalue of the tridiagonal T_{j+1} is found by
 // Sturm-count multisection.  Ritz values increase to lambda_max from below.
 
-__global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n) {
+// Lanczos kernels serve one problem or a batch: problem b (block x of init
+// and step, block y of matvec) uses ctrl[b] and its slices of K, V, w, alpha
+// and beta at the strides in LzStrides.
+struct LzStrides {
+  int64_t K, V, w, ab;
+};
+
+__global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n, LzStrides s) {
+  const int b = blockIdx.x;
+  ctrl += b;
+  V += b * s.V;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = 1.0 / sqrt((double)n);
   if (threadIdx.x == 0) {
     ctrl->power_done = 0;
@@ -217,7 +227,12 @@ __global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n) {
 
 // w = K V[j], one warp per row.
 __global__ void lanczos_matvec_kernel(const Ctrl* ctrl, const double* __restrict__ K, int64_t ldk,
-                                      const double* __restrict__ V, double* __restrict__ w, int64_t n) {
+                                      const double* __restrict__ V, double* __restrict__ w, int64_t n, LzStrides st) {
+  const int b = blockIdx.y;
+  ctrl += b;
+  K += b * st.K;
+  V += b * st.V;
+  w += b * st.w;
   if (ctrl->power_done) return;
   const double* v = V + (int64_t)ctrl->pw_iter * n;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -257,7 +272,15 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
 constexpr int kLanczosThreads = 1024;
 __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctrl, double* V, double* w,
                                                                        double* alpha, double* beta, int64_t n,
-                                                                       int kmax, double tol) {
+                                                                       int kmax, double tol, LzStrides st) {
+  {
+    const int b = blockIdx.x;
+    ctrl += b;
+    V += b * st.V;
+    w += b * st.w;
+    alpha += b * st.ab;
+    beta += b * st.ab;
+  }
   if (ctrl->power_done) return;
   __shared__ double sh[kLanczosThreads / 32];
   __shared__ double h[256];
@@ -423,17 +446,20 @@ __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp,
   c.cur = 0;
   c.done = 0;
   c.status = kNotConverged;
+  c.lam = sp.lam;
+  c.lam_d = sp.lam_d;
+  c.inv_n = sp.inv_n;
   c.L = L_given > 0.0 ? L_given : c.pw_est;
   c.inv_L = c.L > 0.0 ? 1.0 / c.L : INFINITY;
   c.tau0 = sp.tau0 > 0.0 ? sp.tau0 : c.inv_L;
   c.tau = c.tau0;
   c.tau_prev = c.tau0;
-  c.g = 0.5 * y[kYNorm2] * sp.inv_n;
+  c.g = 0.5 * y[kYNorm2] * c.inv_n;
   c.logdiag = om[kPLogDiag];
   c.diagsum = om[kPDiagSum];
   c.l1off = om[kPL1Off];
   c.nnz = om[kPNnz];
-  c.f = c.g - c.logdiag + sp.lam * c.l1off + sp.lam_d * c.diagsum;
+  c.f = c.g - c.logdiag + c.lam * c.l1off + c.lam_d * c.diagsum;
   c.kkt = INFINITY;
   if (om[kPBad] > 0.0) {
     c.done = 1;
@@ -447,16 +473,10 @@ __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp,
   trace_put(trace, sp.trace_cap, 0, 6, c.g);
 }
 
-// After the prox GEMM: fold its partials; on the first trial of a step the
-// KKT residual of Omega^t decides convergence (it needs G(Omega^t), which this
-// GEMM has just formed).
-__global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
-                                 double* trace) {
-  if (ctrl->done) return;
-  double s[kProxSlots];
-  fold_partials<kProxSlots>(part, ntiles, 1u << kPKkt, s);
-  if (threadIdx.x != 0) return;
-  Ctrl& c = *ctrl;
+// After the prox GEMM, with its folded partials s: on the first trial of a
+// step the KKT residual of Omega^t decides convergence (it needs G(Omega^t),
+// which this GEMM has just formed); otherwise record the trial's sums.
+__device__ void post_prox_update(Ctrl& c, const double (&s)[kProxSlots], const SolveParams& sp, double* trace) {
   if (c.k == 0) {
     c.kkt = s[kPKkt];
     trace_put(trace, sp.trace_cap, c.t, 1, c.kkt);
@@ -488,21 +508,11 @@ __global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles,
   c.t_nnz = s[kPNnz];
 }
 
-// After GEMM1 on the trial: sufficient-decrease test of Algorithm 1 in the
-// form ||Y+ - Y||^2 / n <= ||Delta||^2 / tau (identical to the printed test
-// because g is quadratic), or the tau <= 1/L floor; accept or backtrack.
-__global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
-                              double* trace, int* bucket_counts, int nbuckets, const double* part_sparse) {
-  if (ctrl->done) return;
-  double s[kYSlots];
-  // partial sums of whichever Y update ran: the sparse one (one row per
-  // bucket) unless a bucket overflowed and the dense product ran instead
-  const bool sparse_ran = part_sparse != nullptr && !ctrl->dense;
-  fold_partials<kYSlots>(sparse_ran ? part_sparse : part, sparse_ran ? nbuckets : ntiles, 0u, s);
-  // the next trial's prox epilogue starts from empty Delta buckets
-  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[i] = 0;
-  if (threadIdx.x != 0) return;
-  Ctrl& c = *ctrl;
+// After the Y update of the trial, with its folded partials s: the
+// sufficient-decrease test of Algorithm 1 in the form
+// ||Y+ - Y||^2 / n <= ||Delta||^2 / tau (identical to the printed test because
+// g is quadratic), or the tau <= 1/L floor; accept or backtrack.
+__device__ void decide_update(Ctrl& c, const double (&s)[kYSlots], const SolveParams& sp, double* trace) {
   c.dense = 0;
   c.trials += 1;
   if (s[kYBad] > 0.0) {
@@ -512,7 +522,7 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
   }
   c.t_dy2 = s[kYDiff2];
   c.t_y2 = s[kYNorm2];
-  const double lhs = c.t_dy2 * sp.inv_n;
+  const double lhs = c.t_dy2 * c.inv_n;
   const double rhs = c.t_d2 / c.tau;
   const bool accept = (lhs <= rhs) || (c.tau <= c.inv_L) || sp.fixed_step;
   if (accept) {
@@ -521,12 +531,12 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
     trace_put(trace, sp.trace_cap, c.t, 5, sqrt(c.t_d2));
     c.t += 1;
     c.cur ^= 1;
-    c.g = 0.5 * c.t_y2 * sp.inv_n;
+    c.g = 0.5 * c.t_y2 * c.inv_n;
     c.logdiag = c.t_logdiag;
     c.diagsum = c.t_diagsum;
     c.l1off = c.t_l1off;
     c.nnz = c.t_nnz;
-    c.f = c.g - c.logdiag + sp.lam * c.l1off + sp.lam_d * c.diagsum;
+    c.f = c.g - c.logdiag + c.lam * c.l1off + c.lam_d * c.diagsum;
     trace_put(trace, sp.trace_cap, c.t, 0, c.f);
     trace_put(trace, sp.trace_cap, c.t, 4, c.nnz);
     trace_put(trace, sp.trace_cap, c.t, 6, c.g);
@@ -541,6 +551,205 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
       return;
     }
     c.tau *= sp.beta;
+  }
+}
+
+__global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
+                                 double* trace) {
+  if (ctrl->done) return;
+  double s[kProxSlots];
+  fold_partials<kProxSlots>(part, ntiles, 1u << kPKkt, s);
+  if (threadIdx.x == 0) post_prox_update(*ctrl, s, sp, trace);
+}
+
+__global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
+                              double* trace, int* bucket_counts, int nbuckets, const double* part_sparse) {
+  if (ctrl->done) return;
+  double s[kYSlots];
+  // partial sums of whichever Y update ran: the sparse one (one row per
+  // bucket) unless a bucket overflowed and the dense product ran instead
+  const bool sparse_ran = part_sparse != nullptr && !ctrl->dense;
+  fold_partials<kYSlots>(sparse_ran ? part_sparse : part, sparse_ran ? nbuckets : ntiles, 0u, s);
+  // the next trial's prox epilogue starts from empty Delta buckets
+  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[i] = 0;
+  if (threadIdx.x == 0) decide_update(*ctrl, s, sp, trace);
+}
+
+// ------------------------------------------------------- batched control --
+__device__ __forceinline__ int slot_problem(const int32_t* active, const int32_t* nactive, int slot) {
+  if (active == nullptr) return slot;
+  return slot < *nactive ? active[slot] : -1;
+}
+
+__global__ void post_prox_batch_kernel(Ctrl* ctrl, const int32_t* active, const int32_t* nactive,
+                                       const double* part, int64_t ntiles, SolveParams sp) {
+  const int b = slot_problem(active, nactive, blockIdx.x);
+  if (b < 0 || ctrl[b].done) return;
+  double s[kProxSlots];
+  fold_partials<kProxSlots>(part + b * ntiles * kProxSlots, ntiles, 1u << kPKkt, s);
+  if (threadIdx.x == 0) post_prox_update(ctrl[b], s, sp, nullptr);
+}
+
+__global__ void decide_batch_kernel(Ctrl* ctrl, const int32_t* active, const int32_t* nactive, const double* part,
+                                    int64_t ntiles, SolveParams sp, int* bucket_counts, int nbuckets,
+                                    const double* part_sparse) {
+  const int b = slot_problem(active, nactive, blockIdx.x);
+  if (b < 0) return;
+  Ctrl& c = ctrl[b];
+  // every problem of the trial starts the next one with empty Delta buckets,
+  // including one whose fit ended in this trial (its prox already filled them)
+  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[(int64_t)b * nbuckets + i] = 0;
+  if (c.done) {
+    if (threadIdx.x == 0) c.dense = 0;
+    return;
+  }
+  double s[kYSlots];
+  const bool sparse_ran = part_sparse != nullptr && !c.dense;
+  if (sparse_ran) fold_partials<kYSlots>(part_sparse + (int64_t)b * nbuckets * kYSlots, nbuckets, 0u, s);
+  else fold_partials<kYSlots>(part + b * ntiles * kYSlots, ntiles, 0u, s);
+  if (threadIdx.x == 0) decide_update(c, s, sp, nullptr);
+}
+
+// One block per chain: g of Y^0 = X^T, then the state of Omega^0 = I.
+template <class T>
+__global__ void batch_ctrl_init_kernel(PathDev pd, const T* __restrict__ yt0, int64_t p, int64_t ldy, int64_t s_y,
+                                       SolveParams sp, double L_given) {
+  const int c = blockIdx.x;
+  const T* y = yt0 + c * s_y;
+  double s = 0.0, bad = 0.0;
+  for (int64_t i = threadIdx.x; i < p * ldy; i += blockDim.x) {
+    const double v = (double)y[i];
+    s = fma(v, v, s);
+    if (!isfinite(v)) bad += 1.0;
+  }
+  __shared__ double sh[2][kRedThreads / 32];
+  s = warp_sum(s);
+  bad = warp_sum(bad);
+  if (threadIdx.x % 32 == 0) {
+    sh[0][threadIdx.x / 32] = s;
+    sh[1][threadIdx.x / 32] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double ys = 0.0, yb = 0.0;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+    ys += sh[0][w];
+    yb += sh[1][w];
+  }
+  Ctrl& C = pd.ctrl[c];
+  C.L = L_given > 0.0 ? L_given : C.pw_est;
+  C.inv_L = C.L > 0.0 ? 1.0 / C.L : INFINITY;
+  C.tau0 = sp.tau0 > 0.0 ? sp.tau0 : C.inv_L;
+  C.tau = C.tau0;
+  C.tau_prev = C.tau0;
+  C.g = 0.5 * ys * C.inv_n;
+  C.logdiag = 0.0;
+  C.diagsum = (double)p;
+  C.l1off = 0.0;
+  C.nnz = 0.0;
+  C.f = C.g + C.lam_d * C.diagsum;
+  C.kkt = INFINITY;
+  if (yb > 0.0 || !isfinite(C.f) || !(C.L > 0.0) || !isfinite(C.tau0)) {
+    C.done = 1;
+    C.status = kEnonfinite;
+  }
+  if (c == 0) {
+    // every chain starts active
+    for (int q = 0; q < pd.nchains; ++q) pd.active[q] = q;
+    *pd.nactive = pd.nchains;
+  }
+}
+
+__global__ void path_advance_kernel(PathDev pd) {
+  for (int c = threadIdx.x; c < pd.nchains; c += blockDim.x) {
+    Ctrl& C = pd.ctrl[c];
+    C.emit = 0;
+    if (C.finished || !C.done) continue;
+    const int k = C.lam_idx;
+    PathRec& r = pd.rec[(int64_t)k * pd.nchains + c];
+    const double n = pd.n_obs[c];
+    r.status = C.status;
+    r.iters = C.t;
+    r.trials = C.trials;
+    r.reserved0 = 0;
+    r.lambda = pd.lambdas[k];
+    r.f = C.f;
+    r.g = C.g;
+    r.kkt = C.kkt;
+    r.logdet_d = C.logdiag;
+    r.tau_last = C.tau_prev;
+    r.nnz_offdiag = (int64_t)C.nnz;
+    // Eq. 3.7: 2n(-log det Omega_D + g) + ||Omega||_0 (log n + 4 gamma log p)
+    r.epbic = 2.0 * n * (-C.logdiag + C.g) + C.nnz * (log(n) + 4.0 * pd.gamma * pd.log_p);
+    C.iters_tot += C.t;
+    C.trials_tot += C.trials;
+    C.emit = 1;
+    C.emit_lam = k;
+    if (C.status >= 0 && r.epbic < pd.best_epbic[c]) {
+      pd.best_epbic[c] = r.epbic;
+      pd.best_idx[c] = k;
+      C.emit |= 2;
+    }
+    if (C.status >= 0 && k + 1 < pd.n_lambda) {
+      // warm start: the next penalty begins at this estimate
+      const double lam = pd.lambdas[k + 1];
+      C.lam_idx = k + 1;
+      C.lam = lam;
+      C.lam_d = pd.penalize_diag ? lam : 0.0;
+      C.f = C.g - C.logdiag + C.lam * C.l1off + C.lam_d * C.diagsum;
+      C.t = 0;
+      C.k = 0;
+      C.trials = 0;
+      C.tau = C.tau0;
+      C.tau_prev = C.tau0;
+      C.kkt = INFINITY;
+      C.status = kNotConverged;
+      C.done = 0;
+    } else {
+      // the chain ends here; an error also ends the penalties after it
+      for (int q = k + 1; q < pd.n_lambda; ++q) {
+        PathRec& z = pd.rec[(int64_t)q * pd.nchains + c];
+        z = PathRec{};
+        z.status = C.status;
+        z.lambda = pd.lambdas[q];
+        z.epbic = INFINITY;
+      }
+      C.finished = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int c = 0; c < pd.nchains; ++c)
+      if (!pd.ctrl[c].finished) pd.active[m++] = c;
+    *pd.nactive = m;
+  }
+}
+
+template <class T>
+__global__ void path_emit_kernel(PathDev pd, const T* __restrict__ om0, const T* __restrict__ om1, int64_t p,
+                                 int64_t ldo, int64_t s_om, uint32_t* __restrict__ support, int64_t mask_ld,
+                                 T* __restrict__ best) {
+  const int c = blockIdx.y;
+  const Ctrl& C = pd.ctrl[c];
+  if (C.emit == 0) return;
+  const T* Om = (C.cur ? om1 : om0) + c * s_om;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  if (support != nullptr) {
+    uint32_t* out = support + ((int64_t)C.emit_lam * pd.nchains + c) * p * mask_ld;
+    for (int64_t i = tid; i < p * mask_ld; i += stride) {
+      const int64_t r = i / mask_ld, w = i % mask_ld;
+      uint32_t bits = 0u;
+      for (int q = 0; q < 32; ++q) {
+        const int64_t col = 32 * w + q;
+        if (col < p && (col == r || Om[r * ldo + col] != T(0))) bits |= 1u << q;
+      }
+      out[i] = bits;
+    }
+  }
+  if ((C.emit & 2) && best != nullptr) {
+    T* dst = best + c * p * p;
+    for (int64_t i = tid; i < p * p; i += stride) dst[i] = Om[(i / p) * ldo + i % p];
   }
 }
 
@@ -617,18 +826,21 @@ cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st) {
-  lanczos_init_kernel<<<1, 256, 0, st>>>(ctrl, V, n);
+cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st, int nprob, int64_t sV) {
+  if (nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
+  lanczos_init_kernel<<<(unsigned)nprob, 256, 0, st>>>(ctrl, V, n, LzStrides{0, sV, 0, 0});
   return cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
-                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st) {
-  if (kmax > 256) return cudaErrorInvalidValue;
-  const unsigned g = (unsigned)((n + 7) / 8);
-  for (int s = 0; s < nsteps; ++s) {
-    lanczos_matvec_kernel<<<g, 256, 0, st>>>(ctrl, K, ldk, V, w, n);
-    lanczos_step_kernel<<<1, kLanczosThreads, 0, st>>>(ctrl, V, w, alpha, beta, n, kmax, tol);
+                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st,
+                                 int nprob, int64_t sK, int64_t sV, int64_t sW, int64_t sAB) {
+  if (kmax > 256 || nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
+  const LzStrides s{sK, sV, sW, sAB};
+  const dim3 g((unsigned)((n + 7) / 8), (unsigned)nprob);
+  for (int q = 0; q < nsteps; ++q) {
+    lanczos_matvec_kernel<<<g, 256, 0, st>>>(ctrl, K, ldk, V, w, n, s);
+    lanczos_step_kernel<<<(unsigned)nprob, kLanczosThreads, 0, st>>>(ctrl, V, w, alpha, beta, n, kmax, tol, s);
   }
   return cudaGetLastError();
 }
@@ -693,6 +905,53 @@ cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* 
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st) {
   loss_finish_kernel<<<1, kRedThreads, 0, st>>>(ompart, nomp, ypart, nyp, lam, lam_d, inv_n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ctrl_init(const PathDev& pd, const void* yt0, int is_f64, int64_t p, int64_t ldy,
+                                   int64_t s_y, const SolveParams& sp, double L_given, cudaStream_t st) {
+  if (pd.nchains < 1 || pd.nchains > 65535) return cudaErrorInvalidValue;
+  if (is_f64)
+    batch_ctrl_init_kernel<double><<<(unsigned)pd.nchains, kRedThreads, 0, st>>>(pd, (const double*)yt0, p, ldy,
+                                                                                   s_y, sp, L_given);
+  else
+    batch_ctrl_init_kernel<float><<<(unsigned)pd.nchains, kRedThreads, 0, st>>>(pd, (const float*)yt0, p, ldy, s_y,
+                                                                                  sp, L_given);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post_prox_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                   const double* part, int64_t ntiles, const SolveParams& sp, cudaStream_t st) {
+  if (nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
+  post_prox_batch_kernel<<<(unsigned)nprob, kRedThreads, 0, st>>>(ctrl, active, nactive, part, ntiles, sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                const double* part, int64_t ntiles, const SolveParams& sp, int* bucket_counts,
+                                int nbuckets, const double* part_sparse, cudaStream_t st) {
+  if (nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
+  decide_batch_kernel<<<(unsigned)nprob, kRedThreads, 0, st>>>(ctrl, active, nactive, part, ntiles, sp,
+                                                              bucket_counts, nbuckets, part_sparse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_advance(const PathDev& pd, cudaStream_t st) {
+  path_advance_kernel<<<1, 256, 0, st>>>(pd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_emit(const PathDev& pd, const void* om0, const void* om1, int is_f64, int64_t p,
+                             int64_t ldo, int64_t s_om, uint32_t* support, int64_t mask_ld, void* omega_best,
+                             cudaStream_t st) {
+  if (pd.nchains < 1 || pd.nchains > 65535) return cudaErrorInvalidValue;
+  const dim3 g(64, (unsigned)pd.nchains);
+  if (is_f64)
+    path_emit_kernel<double><<<g, 256, 0, st>>>(pd, (const double*)om0, (const double*)om1, p, ldo, s_om, support,
+                                                mask_ld, (double*)omega_best);
+  else
+    path_emit_kernel<float><<<g, 256, 0, st>>>(pd, (const float*)om0, (const float*)om1, p, ldo, s_om, support,
+                                               mask_ld, (float*)omega_best);
   return cudaGetLastError();
 }
 

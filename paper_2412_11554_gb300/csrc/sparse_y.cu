@@ -55,25 +55,31 @@ __device__ __forceinline__ int lower_bound(const uint32_t* key, int m, uint32_t 
 }
 
 __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
-  const Ctrl* ctrl = prm.ctrl;
+  int b = blockIdx.y;  // problem slot of a batch (0 for one fit)
+  if (prm.active != nullptr) {
+    if (b >= *prm.nactive) return;
+    b = prm.active[b];
+  }
+  const Ctrl* ctrl = prm.ctrl + b;
   if (ctrl->done || ctrl->dense) return;
   extern __shared__ uint8_t smem_raw[];
   const int mb = blockIdx.x;  // bucket = 32-row group
   const int cur = ctrl->cur, nxt = cur ^ 1;
-  const float* __restrict__ Y = prm.y[cur];
-  float* __restrict__ Yp = prm.yw[nxt];
-  __nv_bfloat16* __restrict__ Yh = prm.y_hi[nxt];
-  __nv_bfloat16* __restrict__ Yl = prm.y_lo[nxt];
-  const float* __restrict__ XT = prm.xt;
+  const float* __restrict__ Y = prm.y[cur] + b * prm.s_y;
+  float* __restrict__ Yp = prm.yw[nxt] + b * prm.s_y;
+  __nv_bfloat16* __restrict__ Yh = prm.y_hi[nxt] + b * prm.s_yk;
+  __nv_bfloat16* __restrict__ Yl = prm.y_lo[nxt] + b * prm.s_yk;
+  const float* __restrict__ XT = prm.xt + b * prm.s_xt;
+  const int64_t bk = b * prm.s_bkt + mb;  // this problem's bucket
 
-  int cnt = prm.counts[mb];
+  int cnt = prm.counts[bk];
   if (cnt > prm.cap) cnt = prm.cap;  // overflow is handled by the dense path
   int m = 1;
   while (m < cnt) m <<= 1;
   uint32_t* key = reinterpret_cast<uint32_t*>(smem_raw);
   float* val = reinterpret_cast<float*>(smem_raw + (size_t)prm.cap * sizeof(uint32_t));
-  const uint32_t* gk = prm.keys + (size_t)mb * prm.cap;
-  const float* gv = prm.vals + (size_t)mb * prm.cap;
+  const uint32_t* gk = prm.keys + (size_t)bk * prm.cap;
+  const float* gv = prm.vals + (size_t)bk * prm.cap;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     key[i] = i < cnt ? gk[i] : 0xFFFFFFFFu;
     val[i] = i < cnt ? gv[i] : 0.f;
@@ -138,16 +144,25 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
     double v = 0.0;
     if (q < 3)
       for (int w = 0; w < nwarps; ++w) v += red[w][q];
-    prm.part[(int64_t)mb * kYSlots + q] = v;
+    prm.part[bk * kYSlots + q] = v;
   }
 }
 
 // Dense fallback when a bucket overflowed: BF16 planes of Delta = Omega+ - Omega.
 __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                    __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk) {
+                                    __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, const int32_t* active,
+                                    const int32_t* nactive, int64_t s_om, int64_t s_pl) {
+  int b = blockIdx.y;
+  if (active != nullptr) {
+    if (b >= *nactive) return;
+    b = active[b];
+  }
+  ctrl += b;
   if (ctrl->done || !ctrl->dense) return;
-  const float* Om = ctrl->cur ? om1 : om0;
-  const float* Op = ctrl->cur ? om0 : om1;
+  const float* Om = (ctrl->cur ? om1 : om0) + b * s_om;
+  const float* Op = (ctrl->cur ? om0 : om1) + b * s_om;
+  hi += b * s_pl;
+  lo += b * s_pl;
   const int64_t total = p * p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / p, c = i % p;
@@ -162,24 +177,37 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
 
 size_t sparse_y_smem_bytes(int cap) { return (size_t)cap * (sizeof(uint32_t) + sizeof(float)); }
 
-cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
-  const size_t smem = sparse_y_smem_bytes(prm.cap);
+cudaError_t sparse_y_prepare() {
   static int configured = -1;
   int dev = 0;
-  cudaGetDevice(&dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(sparse_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    e = cudaFuncSetAttribute(sparse_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
     configured = dev;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
+  const size_t smem = sparse_y_smem_bytes(prm.cap);
+  cudaError_t e = sparse_y_prepare();
+  if (e != cudaSuccess) return e;
   if (smem > 64 * 1024) return cudaErrorInvalidValue;
-  sparse_y_kernel<<<(unsigned)prm.tiles_m, kThreads, smem, st>>>(prm);
+  const unsigned nb = (unsigned)(prm.nprob > 1 ? prm.nprob : 1);
+  if (nb > 65535u) return cudaErrorInvalidConfiguration;
+  sparse_y_kernel<<<dim3((unsigned)prm.tiles_m, nb), kThreads, smem, st>>>(prm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st) {
-  delta_planes_kernel<<<152 * 16, 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk);
+                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st, int32_t nprob,
+                                const int32_t* active, const int32_t* nactive, int64_t s_om, int64_t s_pl) {
+  const unsigned nb = (unsigned)(nprob > 1 ? nprob : 1);
+  if (nb > 65535u) return cudaErrorInvalidConfiguration;
+  const unsigned gx = nb > 1 ? 152u * 16u / nb + 1u : 152u * 16u;
+  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, active, nactive, s_om, s_pl);
   return cudaGetLastError();
 }
 

@@ -11,12 +11,15 @@
 
 namespace accord {
 
+// Operand planes are 3-D tensor maps (K, rows, slice): the slice is the
+// problem of a batch (a lambda path runs one problem per chain), 0 for a
+// single fit.
 struct TcParams {
   CUtensorMap a_hi[2];  // A planes, index (a_nxt ? nxt : cur)
   CUtensorMap a_lo[2];
   CUtensorMap b_hi;     // B planes
   CUtensorMap b_lo;
-  const Ctrl* ctrl;     // null: cur = 0, no early exit
+  Ctrl* ctrl;           // null: cur = 0, no early exit; a batch: one per problem
   int* err;             // device error word (kErr* bits), never null
   int64_t M, N, K;
   int32_t num_kb, tiles_m, tiles_n, ntiles;
@@ -45,18 +48,32 @@ struct TcParams {
   // Eq. 3.8 refit: support bitmask (bit (i, j) of word [i][j / 32]), or null
   const uint32_t* mask;
   int64_t mask_ld;
+  // Batch of problems with the same M and N.  Tile index -> (problem, tile);
+  // problem b uses ctrl[b] (its cur, tau, lambda and 1/n), outputs at
+  // + b * s_out ..., and skips every tile once ctrl[b].done is set (or, with
+  // gate_dense, while ctrl[b].dense is clear).
+  int32_t nprob;             // problems (1: a single fit)
+  int32_t b_batched;         // B planes: slice b (1) or slice 0 for all (0)
+  const int32_t* active;     // device list of the problems to run, or null (0 .. nprob-1)
+  const int32_t* nactive;    // device length of `active`
+  const int32_t* kb_of;      // device K blocks per problem (ragged K), or null (num_kb)
+  int64_t s_out, s_aux, s_plane, s_part, s_bkt;  // strides: elements, elements, elements, tiles, buckets
 };
 
-// Encodes a 2-D BF16 tensor map over a rows x cols matrix with leading
-// dimension ld (elements), box 64 x box_rows, 128-byte swizzle.  Returns false
-// when the driver rejects the arguments.
+// Encodes a 3-D BF16 tensor map over `depth` slices of a rows x cols matrix
+// with leading dimension ld (elements) and slice_stride elements between
+// slices; box 32 (K) x box_rows x 1, 64-byte swizzle.  Returns false when the
+// driver rejects the arguments.
 bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld,
-                      int box_rows);
+                      int box_rows, int64_t depth = 1, int64_t slice_stride = 0);
 
 // Fills the shape fields (num_kb, tiles, bn) for an M x N x K problem.
 void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K);
 int64_t tc_tiles(int64_t M, int64_t N);
 int tc_box_n();  // rows of the B box one CTA loads (its share of the N tile)
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
+// One-time per-device setup of every mode (done lazily by the first launch
+// otherwise); call before capturing launches into a CUDA graph.
+cudaError_t tc_prepare();
 
 }  // namespace accord

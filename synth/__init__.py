@@ -15,5 +15,7 @@ from .generators import (  # noqa: F401
     sample_gaussian,
     orthogonal_design,
     workload,
+    PathWorkload,
+    path_workload,
     WORKLOADS,
 )

@@ -217,3 +217,34 @@ WORKLOADS = {
     "scalefree_p5000_n1000": dict(kind="scalefree", p=5000, n=1000),
     "hubblock_p40000_n1000": dict(kind="hubblock", p=40000, n=1000),
 }
+
+
+@dataclasses.dataclass
+class PathWorkload:
+    name: str
+    X: np.ndarray            # float32, n_total x p (the whole data set)
+    lambdas: np.ndarray      # penalties in solve order (decreasing)
+    subsamples: list         # row-index arrays (bootstrap: drawn with replacement)
+    kkt_tol: float
+    recipe: str
+
+
+def path_workload(p: int = 4000, n_total: int = 400, n_lambda: int = 32, n_sub: int = 16,
+                  lam_lo: float = 0.05, lam_hi: float = 0.5, n_min: int = 200, n_max: int = 400,
+                  kkt_tol: float = 1e-4, k: int = 4) -> PathWorkload:
+    """Penalty grid x bootstrap subsamples of one scale-free data set: n_lambda
+    penalties log-spaced from lam_hi down to lam_lo; n_sub subsamples whose
+    sizes are uniform integers in [n_min, n_max], rows drawn with replacement
+    from the n_total rows.  Seeds: graph 1000 + k, data 2000 + k, subsamples
+    3000 + k."""
+    theta = ba_tree_precision(p, 1000 + k)
+    X = sample_gaussian(theta, n_total, 2000 + k).astype(np.float32)
+    rng = _rng(3000 + k)
+    sizes = rng.integers(n_min, n_max + 1, size=n_sub)
+    subs = [rng.integers(0, n_total, size=int(m)) for m in sizes]
+    lams = np.geomspace(lam_hi, lam_lo, n_lambda)
+    recipe = (f"BA tree m=1 +-U[0.1,0.4] unit diag, p={p}, n_total={n_total}; {n_lambda} penalties log-spaced "
+              f"{lam_hi}..{lam_lo}; {n_sub} bootstrap subsamples, n uniform in [{n_min},{n_max}]; "
+              f"seeds {1000 + k}/{2000 + k}/{3000 + k}")
+    return PathWorkload(name=f"path_p{p}_L{n_lambda}_S{n_sub}", X=np.ascontiguousarray(X), lambdas=lams,
+                        subsamples=subs, kkt_tol=kkt_tol, recipe=recipe)

@@ -49,13 +49,14 @@ def test_binding_covers_every_export():
 def test_struct_layout_matches_c():
     """Compile a probe against the header with gcc and compare sizeof/offsetof
     with the ctypes mirrors."""
-    from paper_2412_11554_gb300.accord import AccordOpts, AccordStats
-    fields = {"accord_opts": AccordOpts, "accord_stats": AccordStats}
+    from paper_2412_11554_gb300.accord import AccordOpts, AccordPathEntry, AccordStats
+    fields = {"accord_opts": AccordOpts, "accord_stats": AccordStats, "accord_path_entry": AccordPathEntry}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for cname, cls in fields.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
-            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {cf}));')
     lines.append("return 0;}")
     with tempfile.TemporaryDirectory() as d:
         src, exe = os.path.join(d, "probe.c"), os.path.join(d, "probe")
@@ -106,5 +107,21 @@ def test_invalid_arguments_rejected_on_host(lib):
     bad = accord.accord_default_opts(epbic_gamma=-1.0)
     assert lib.accord_refit(dummy, 10, 10, 0.1, 0.5, dummy, ctypes.byref(bad), dummy, None, 0,
                             ctypes.byref(st)) == accord.EINVAL
+    # lambda path: argument checks before any device call
+    import numpy as np
+    rows = np.array([0, 1, 2, 2, 5], dtype=np.int32)
+    offs = np.array([0, 3, 5], dtype=np.int64)
+    lams = np.array([0.3, 0.2], dtype=np.float64)
+    ent = (accord.AccordPathEntry * 4)()
+
+    def path(r, of, ns, lm, nl, n=10, p=10):
+        return lib.accord_path(dummy, n, p, r.ctypes.data, of.ctypes.data, ns, lm.ctypes.data, nl, ctypes.byref(o),
+                               ent, None, None, None, None, 0, ctypes.byref(st))
+    assert path(rows, offs, 2, lams, 2, n=5) == accord.EINVAL          # row index 5 >= n
+    assert path(rows, np.array([0, 3, 3], dtype=np.int64), 2, lams, 2) == accord.EINVAL  # empty subsample
+    assert path(rows, offs, 2, np.array([0.3, -1.0]), 2) == accord.EINVAL  # negative penalty
+    assert path(rows, offs, 0, lams, 2) == accord.EINVAL
+    assert lib.accord_path_workspace_bytes(10, 10, rows.ctypes.data, offs.ctypes.data, 2, 2, ctypes.byref(o)) > 0
+    assert lib.accord_path_workspace_bytes(5, 10, rows.ctypes.data, offs.ctypes.data, 2, 2, ctypes.byref(o)) == 0
     for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert accord.accord_status_string(s)

@@ -1,0 +1,139 @@
+"""GPU parity of the lambda path over subsamples (Sec 3.4: penalty grid with
+warm starts, epBIC of Eq. 3.7, the selected estimate) against the oracle's
+lambda_path on the same seeded inputs.
+
+FP64 mode reproduces the oracle's per-estimate iterate counts and reaches its
+estimates to 1e-9 relative Frobenius; the mixed mode is held to the 1e-4 bar of
+the single fit.  The full-size case (p = 4000, 32 penalties x 16 bootstrap
+subsamples of 200..400 rows) is checked through properties the oracle computes
+for sampled subsamples: the FP64 KKT residual and the epBIC of the selected
+estimates, and their support bits.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import accord_ref as R
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_11554_gb300 import build
+    build.build()
+    import paper_2412_11554_gb300 as pkg
+    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
+    return pkg
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def bootstrap(n_total, sizes, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.integers(0, n_total, size=m) for m in sizes]
+
+
+def support_of(words, p):
+    """Decode p rows of ceil(p/32) int32 words into a boolean p x p mask."""
+    w = words.astype(np.uint32)
+    bits = (w[:, :, None] >> np.arange(32, dtype=np.uint32)[None, None, :]) & 1
+    return bits.reshape(p, -1)[:, :p].astype(bool)
+
+
+def test_fp64_path_matches_oracle(A):
+    w = workload("scalefree", p=150, n=80)
+    subs = bootstrap(80, [50, 65, 80], 61)
+    lams = [0.5, 0.35, 0.25, 0.18]
+    ref = R.lambda_path(w.X, subs, lams, kkt_tol=1e-8, max_iter=5000, gamma=0.5)
+    out = A.accord_path(dev(w.X), subs, lams, precision="fp64", kkt_tol=1e-8, max_iter=5000, support=True)
+    assert out.status == 0
+    sup = out.support.cpu().numpy()
+    for s in range(len(subs)):
+        for k in range(len(lams)):
+            r = ref.fits[s][k]
+            assert out.entry_status[k, s] == r.status == R.OK
+            assert out.iters[k, s] == r.iters and out.trials[k, s] == r.trials, (k, s)
+            assert abs(out.f[k, s] - r.f[-1]) <= 1e-11 * abs(r.f[-1])
+            assert out.nnz_offdiag[k, s] == r.nnz[-1]
+            assert abs(out.epbic[k, s] - ref.epbic[k, s]) <= 1e-10 * abs(ref.epbic[k, s])
+            want = (r.Omega != 0) | np.eye(150, dtype=bool)
+            assert np.array_equal(support_of(sup[k, s], 150), want), (k, s)
+        assert out.best_index[s] == ref.best[s]
+        assert rel_fro(out.omega_best[s].cpu().numpy(), ref.Omega_best[s]) <= 1e-9
+
+
+def test_single_chain_single_penalty_equals_fit(A):
+    """A path of one subsample (all rows once) and one penalty is the plain fit."""
+    w = workload("ar1", p=120, n=90)
+    out = A.accord_path(dev(w.X), [np.arange(90)], [w.lam], precision="fp64", kkt_tol=1e-9)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="fp64", kkt_tol=1e-9)
+    assert out.iters[0, 0] == st.iters and out.trials[0, 0] == st.trials
+    assert rel_fro(out.omega_best[0].cpu().numpy(), Om.cpu().numpy()) <= 1e-12
+    assert abs(out.epbic[0, 0] - st.epbic) <= 1e-12 * abs(st.epbic)
+
+
+def test_mixed_path_matches_oracle(A):
+    w = workload("scalefree", p=600, n=300)
+    subs = bootstrap(300, [150, 220, 300], 62)
+    lams = list(np.geomspace(0.4, 0.12, 5))
+    ref = R.lambda_path(w.X, subs, lams, kkt_tol=1e-7, max_iter=5000)
+    out = A.accord_path(dev(w.X), subs, lams, precision="mixed", kkt_tol=2e-5, max_iter=5000)
+    assert out.status == 0, out.entry_status
+    X = np.asarray(w.X, dtype=np.float64)
+    for s, rows in enumerate(subs):
+        n_s = len(rows)
+        pen = np.log(n_s) + 4 * 0.5 * np.log(600)
+        for k in range(len(lams)):
+            r = ref.fits[s][k]
+            # the likelihood part of epBIC to 1e-4; nonzero counts equal up to
+            # entries inside the soft-threshold's rounding band
+            cont = out.epbic[k, s] - out.nnz_offdiag[k, s] * pen
+            cont_ref = ref.epbic[k, s] - r.nnz[-1] * pen
+            assert abs(cont - cont_ref) <= 1e-4 * abs(cont_ref), (k, s)
+            assert abs(int(out.nnz_offdiag[k, s]) - r.nnz[-1]) <= max(2, r.nnz[-1] // 200), (k, s)
+        kb = out.best_index[s]
+        O = out.omega_best[s].double().cpu().numpy()
+        assert rel_fro(O, ref.fits[s][kb].Omega) <= 1e-4
+        Xs = X[rows]
+        assert R.kkt_residual(O, R.grad_g(O, Xs), lams[kb], lams[kb]) <= 1e-4
+
+
+@pytest.mark.slow
+def test_full_size_path_properties(A):
+    """p = 4000, 32 penalties log-spaced in [0.05, 0.5] x 16 bootstrap
+    subsamples with n uniform in [200, 400] of one scale-free data set
+    (n_total = 400), mixed precision, in the launch configuration of the
+    benchmark.  For sampled subsamples the oracle checks the selected estimate:
+    FP64 KKT residual at its penalty, epBIC (Eq. 3.7) recomputed from it, and
+    that its support bits match its nonzero pattern."""
+    from synth import path_workload
+    pw = path_workload()
+    out = A.accord_path(dev(pw.X), pw.subsamples, pw.lambdas, precision="mixed", kkt_tol=pw.kkt_tol,
+                        max_iter=2000, support=True)
+    assert out.status in (0, 1), out.entry_status
+    assert np.all(out.entry_status >= 0)
+    X = np.asarray(pw.X, dtype=np.float64)
+    p = X.shape[1]
+    sup = out.support
+    for s in (0, 7, 15):
+        kb = int(out.best_index[s])
+        assert 0 <= kb < len(pw.lambdas)
+        O = out.omega_best[s].double().cpu().numpy()
+        Xs = X[pw.subsamples[s]]
+        lam = pw.lambdas[kb]
+        if out.entry_status[kb, s] == 0:
+            assert R.kkt_residual(O, R.grad_g(O, Xs), lam, lam) <= 5 * pw.kkt_tol
+        want = R.epbic(O, Xs, 0.5)
+        assert abs(out.epbic[kb, s] - want) <= 1e-4 * abs(want)
+        bits = support_of(sup[kb, s].cpu().numpy(), p)
+        assert np.array_equal(bits, (O != 0) | np.eye(p, dtype=bool))
