@@ -17,5 +17,8 @@ from .generators import (  # noqa: F401
     workload,
     PathWorkload,
     path_workload,
+    DiffWorkload,
+    diff_workload,
+    ar1_random_precision,
     WORKLOADS,
 )

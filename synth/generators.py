@@ -248,3 +248,42 @@ def path_workload(p: int = 4000, n_total: int = 400, n_lambda: int = 32, n_sub: 
               f"seeds {1000 + k}/{2000 + k}/{3000 + k}")
     return PathWorkload(name=f"path_p{p}_L{n_lambda}_S{n_sub}", X=np.ascontiguousarray(X), lambdas=lams,
                         subsamples=subs, kkt_tol=kkt_tol, recipe=recipe)
+
+
+def ar1_random_precision(p: int, extra: float, weight: float, seed: int, rho: float = 0.4) -> sp.csr_matrix:
+    """AR(1) chain (rho off the diagonal) plus a random `extra` fraction of the
+    other off-diagonal pairs with weights +-weight, then made diagonally
+    dominant with the factor-1.5 rule of Sec 5.1 (a dense random graph with
+    these weights is not positive definite otherwise)."""
+    rng = _rng(seed)
+    iu, ju = np.triu_indices(p, k=2)
+    take = rng.random(iu.size) < extra
+    ri, rj = iu[take], ju[take]
+    vals = _signed_uniform(rng, int(take.sum()), weight, weight)
+    chain = np.arange(p - 1)
+    rows = np.concatenate([chain, ri])
+    cols = np.concatenate([chain + 1, rj])
+    v = np.concatenate([np.full(p - 1, rho), vals])
+    off = _assemble(p, rows, cols, v)
+    return _diag_dominant(off, 1.5, 1.0)
+
+
+@dataclasses.dataclass
+class DiffWorkload:
+    name: str
+    X_train: np.ndarray      # float32, n x p
+    X_val: np.ndarray        # float32, n_val x p (held out)
+    lam: float
+    theta: sp.csr_matrix
+    recipe: str
+
+
+def diff_workload(p: int = 2000, n: int = 300, n_val: int = 100, lam: float = 0.2, k: int = 5) -> DiffWorkload:
+    """Training and held-out rows from one AR(1) + 1% random-edge precision
+    (weights +-0.2).  Seeds: graph 1000 + k, data 2000 + k."""
+    theta = ar1_random_precision(p, 0.01, 0.2, 1000 + k)
+    X = sample_gaussian(theta, n + n_val, 2000 + k).astype(np.float32)
+    recipe = (f"AR(1) rho=0.4 + 1% random edges +-0.2, diag rule 1.5, p={p}, n={n} + {n_val} held out, "
+              f"lambda={lam}, seeds {1000 + k}/{2000 + k}")
+    return DiffWorkload(name=f"diff_p{p}_n{n}", X_train=np.ascontiguousarray(X[:n]),
+                        X_val=np.ascontiguousarray(X[n:]), lam=lam, theta=theta, recipe=recipe)

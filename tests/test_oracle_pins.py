@@ -269,10 +269,57 @@ def pin_path_diagonal_regime():
     return bool(ok)
 
 
+def pin_smooth_loss_gradients():
+    """dL/dOmega and dL/dX of the smooth loss equal central finite differences
+    of the loss itself."""
+    X = _gauss(9, 6, 71)
+    O = np.eye(6) + 0.1 * _gauss(6, 6, 72)
+    np.fill_diagonal(O, 1.0 + np.abs(np.diag(O)))
+    GO, GX = R.smooth_loss_grad_omega(O, X), R.smooth_loss_grad_x(O, X)
+    h, ok = 1e-6, True
+    for (i, j) in [(0, 0), (1, 4), (5, 2), (3, 3)]:
+        E = np.zeros_like(O)
+        E[i, j] = h
+        fd = (R.smooth_loss(O + E, X) - R.smooth_loss(O - E, X)) / (2 * h)
+        ok &= abs(fd - GO[i, j]) <= 1e-6 * max(1.0, abs(fd))
+    for (i, j) in [(0, 0), (8, 5), (4, 1)]:
+        E = np.zeros_like(X)
+        E[i, j] = h
+        fd = (R.smooth_loss(O, X + E) - R.smooth_loss(O, X - E)) / (2 * h)
+        ok &= abs(fd - GX[i, j]) <= 1e-6 * max(1.0, abs(fd))
+    return bool(ok)
+
+
+def _exact_fit(X, lam):
+    S = np.asarray(X, dtype=np.float64).T @ np.asarray(X, dtype=np.float64) / X.shape[0]
+    r = R.fit(X, lam, kkt_tol=1e-12, max_iter=100000)
+    return R.polish(r.Omega, S, lam, lam)
+
+
+def pin_implicit_dloglam_fd():
+    """The implicit derivative of the held-out loss in log(lambda) equals the
+    central finite difference (h = 1e-4) of the held-out loss at the exact
+    minimisers for lambda e^(+-h), and dOmega-hat/dlog(lambda) equals the
+    difference quotient of those minimisers (same active set on both sides)."""
+    rng = np.random.Generator(np.random.PCG64(73))
+    X = rng.standard_normal((60, 30))
+    Xt, Xv = X[:40], X[40:]
+    lam, h = 0.25, 1e-4
+    O = _exact_fit(Xt, lam)
+    Op, Om = _exact_fit(Xt, lam * math.exp(h)), _exact_fit(Xt, lam * math.exp(-h))
+    if not (np.array_equal(O != 0, Op != 0) and np.array_equal(O != 0, Om != 0)):
+        return False
+    d, dO = R.implicit_dloglam(O, Xt, Xv, lam)
+    fd = (R.smooth_loss(Op, Xv) - R.smooth_loss(Om, Xv)) / (2 * h)
+    dfd = (Op - Om) / (2 * h)
+    return bool(abs(d - fd) <= 1e-6 * max(1.0, abs(fd)) and np.max(np.abs(dO - dfd)) <= 1e-6 * max(1.0, np.max(np.abs(dfd))))
+
+
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
-        pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime]
+        pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
+        pin_implicit_dloglam_fd]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -349,9 +396,23 @@ MUTANTS = {
     "g_missing_half": ("smooth_g", lambda Om, X: float(np.sum((Om @ np.asarray(X, float).T) ** 2)) / X.shape[0]),
     "lipschitz_trace": ("lipschitz", lambda X: float(np.trace(np.asarray(X, float) @ np.asarray(X, float).T)) / X.shape[0] / 3),
     "epbic_missing_2n": ("epbic", lambda Om, X, gm: -float(np.sum(np.log(np.diag(Om)))) + R.smooth_g(Om, X)),
+    "grad_x_transposed": ("smooth_loss_grad_x", lambda Om, X: np.asarray(X, float) @ Om @ Om.T / X.shape[0]),
+    "implicit_drops_log_term": ("implicit_dloglam", lambda O, Xt, Xv, lam, penalize_diag=True:
+                                _implicit_without_log_term(O, Xt, Xv, lam)),
     "path_ignores_subsample": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
                                _f(X, [np.arange(np.asarray(X).shape[0])] * len(rows), lams, **kw)),
 }
+
+
+def _implicit_without_log_term(O, Xt, Xv, lam):
+    S = R.sample_covariance(Xt)
+    Gv = R.smooth_loss_grad_omega(O, Xv)
+    dO = np.zeros_like(O)
+    for i in range(O.shape[0]):
+        A = np.nonzero(O[i] != 0)[0]
+        v = np.sign(O[i, A])
+        dO[i, A] = -lam * np.linalg.solve(S[np.ix_(A, A)], v)
+    return float(np.sum(Gv * dO)), dO
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
