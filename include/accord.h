@@ -210,6 +210,37 @@ int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double*
  * pointer stays valid until the thread's next call. */
 const char* accord_last_error(void);
 
+/* ---- differentiation ------------------------------------------------------ */
+
+/* Adjoint of the smooth loss L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S)
+ * in the data: GX_out = dL/dX = (1/n) X Omega^T Omega (n x p, device, element type per
+ * precision: double for ACCORD_FP64, float for the mixed mode), formed as
+ * Y^T = X Omega^T and (1/n) Y^T Omega.  dL/dOmega = -diag(1/omega_ii) + Omega S is
+ * accord_grad with smooth = 1.  X: device n x p FP32; Omega: device p x p. */
+int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts* opts,
+                  void* GX_out);
+
+/* Derivative of a held-out loss along the regularisation path:
+ *   dloss = d L(Omega-hat(lambda); X_val) / d log(lambda),
+ * L as in accord_grad_x, Omega-hat = the ACCORD estimate of X_train at lambda,
+ * by implicit differentiation of the stationarity conditions (Eq. 3.3) on the
+ * active set of Omega_hat: row i with active set A (nonzeros of row i, i
+ * included) and signs s solves (S_AA + omega_ii^-2 e_i e_i^T) dw = -lambda v,
+ * v = s off the diagonal and v_i = 1 when opts->penalize_diag (else 0), with
+ * S = X_train^T X_train / n.  Valid where the active set is locally constant.
+ *   X_train   device, n x p FP32;  X_val  device, n_val x p FP32
+ *   Omega_hat device, p x p, element type per opts->precision (a converged estimate)
+ *   dloss, loss_val  host (either may be NULL): the derivative and L(Omega_hat; X_val)
+ *   dOmega    device or NULL: p x p dOmega-hat / dlog(lambda), element type per precision
+ * S, the held-out gradient and the row systems are formed in FP64 in either
+ * precision.  Errors: EINVAL; EUNSUPPORTED when a row's active set has more
+ * than 128 entries; EDOMAIN when a row system is not positive definite (an
+ * active set larger than the training rows can support) or Omega_hat has a
+ * non-positive diagonal. */
+int accord_dloss_dloglam(const float* X_train, int64_t n, const float* X_val, int64_t n_val, int64_t p,
+                         const void* Omega_hat, double lambda, const accord_opts* opts, double* dloss,
+                         double* loss_val, void* dOmega);
+
 /* ---- lambda path over subsamples (Sec 3.4) ------------------------------ */
 
 /* One estimate of a path: record [k * n_sub + s] for penalty k, subsample s. */

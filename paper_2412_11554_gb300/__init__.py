@@ -9,6 +9,8 @@ from .accord import (  # noqa: F401
     accord_default_opts,
     accord_device_check,
     accord_fit,
+    accord_grad_x,
+    accord_dloss_dloglam,
     accord_path,
     accord_path_workspace_bytes,
     PathResult,
@@ -21,3 +23,4 @@ from .accord import (  # noqa: F401
     accord_workspace_bytes,
     load_library,
 )
+from .autograd import SmoothLoss, smooth_loss  # noqa: F401,E402

@@ -60,7 +60,8 @@ class AccordPathEntry(ctypes.Structure):
 
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
-           "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes")
+           "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
+           "accord_dloss_dloglam")
 
 _lib = None
 
@@ -104,6 +105,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_path.restype = i32
     lib.accord_path_workspace_bytes.argtypes = [i64, i64, P, P, i64, i64, opts_p]
     lib.accord_path_workspace_bytes.restype = ctypes.c_size_t
+    lib.accord_grad_x.argtypes = [P, i64, i64, P, opts_p, P]
+    lib.accord_grad_x.restype = i32
+    lib.accord_dloss_dloglam.argtypes = [P, i64, P, i64, i64, P, dbl, opts_p, ctypes.POINTER(dbl),
+                                         ctypes.POINTER(dbl), P]
+    lib.accord_dloss_dloglam.restype = i32
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -279,6 +285,50 @@ def accord_loss_f64_noalloc(X: torch.Tensor, Omega: torch.Tensor, lam: float, fg
                                          _stream_handle(stream), fg_out.data_ptr())
     if status != OK:
         raise AccordError(status, "accord_loss_f64_noalloc")
+
+
+def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """dL/dX = (1/n) X Omega^T Omega of the smooth loss (n x p); precision
+    follows Omega's dtype (float64: FP64 mode, float32: mixed)."""
+    lib = load_library()
+    _check_x(X)
+    n, p = X.shape
+    prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
+    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
+        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA tensor")
+    if out is None:
+        out = torch.empty((n, p), dtype=Omega.dtype, device=X.device)
+    o = accord_default_opts(precision=prec)
+    o.stream = _stream_handle(stream)
+    status = lib.accord_grad_x(X.data_ptr(), n, p, Omega.data_ptr(), ctypes.byref(o), out.data_ptr())
+    if status != OK:
+        raise AccordError(status, "accord_grad_x")
+    return out
+
+
+def accord_dloss_dloglam(X_train: torch.Tensor, X_val: torch.Tensor, Omega_hat: torch.Tensor, lam: float, *,
+                         penalize_diag: bool = True, want_domega: bool = False, stream=None):
+    """(d L_val / d log lambda, L_val, dOmega-hat / d log lambda or None) by
+    implicit differentiation on the active set of Omega_hat (a converged
+    estimate for X_train at lam); precision follows Omega_hat's dtype."""
+    lib = load_library()
+    _check_x(X_train)
+    _check_x(X_val)
+    n, p = X_train.shape
+    if X_val.shape[1] != p:
+        raise ValueError("X_train and X_val need the same number of columns")
+    prec = FP64 if Omega_hat.dtype == torch.float64 else MIXED_BF16X3
+    o = accord_default_opts(precision=prec, penalize_diag=int(penalize_diag))
+    o.stream = _stream_handle(stream)
+    d, lv = ctypes.c_double(), ctypes.c_double()
+    dO = torch.empty((p, p), dtype=Omega_hat.dtype, device=X_train.device) if want_domega else None
+    status = lib.accord_dloss_dloglam(X_train.data_ptr(), n, X_val.data_ptr(), X_val.shape[0], p,
+                                      Omega_hat.data_ptr(), float(lam), ctypes.byref(o), ctypes.byref(d),
+                                      ctypes.byref(lv), dO.data_ptr() if dO is not None else None)
+    if status != OK:
+        raise AccordError(status, "accord_dloss_dloglam")
+    return d.value, lv.value, dO
 
 
 @dataclasses.dataclass

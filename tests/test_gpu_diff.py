@@ -1,0 +1,136 @@
+"""GPU parity of the differentiation entry points against the oracle:
+the smooth loss and its gradients in Omega and X (through the autograd
+Function as well), and the implicit derivative of a held-out loss in
+log(lambda), which is also checked against central finite differences of
+GPU fits (h = 1e-4) at the full differentiation workload (p = 2000,
+300 training + 100 held-out rows, lambda = 0.2)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import accord_ref as R
+from synth import diff_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_11554_gb300 import build
+    build.build()
+    import paper_2412_11554_gb300 as pkg
+    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
+    return pkg
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rand_omega(p, seed, density=0.05):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    O = 0.1 * rng.standard_normal((p, p)) * (rng.random((p, p)) < density)
+    np.fill_diagonal(O, 1.0 + rng.random(p))
+    return O
+
+
+@pytest.mark.parametrize("n,p", [(15, 20), (37, 150), (300, 2000)])
+def test_gradients_match_oracle_fp64(A, n, p):
+    X = np.random.Generator(np.random.PCG64(n + p)).standard_normal((n, p)).astype(np.float32)
+    O = rand_omega(p, 3 * p)
+    Xd = X.astype(np.float64)
+    GO = A.accord_grad(dev(X), dev(O, torch.float64), smooth=True).cpu().numpy()
+    GX = A.accord_grad_x(dev(X), dev(O, torch.float64)).cpu().numpy()
+    rO, rX = R.smooth_loss_grad_omega(O, Xd), R.smooth_loss_grad_x(O, Xd)
+    assert np.max(np.abs(GO - rO)) <= 1e-12 * np.max(np.abs(rO))
+    assert np.max(np.abs(GX - rX)) <= 1e-12 * np.max(np.abs(rX))
+
+
+@pytest.mark.parametrize("n,p", [(37, 150), (300, 2000)])
+def test_gradients_match_oracle_mixed(A, n, p):
+    X = np.random.Generator(np.random.PCG64(n + p)).standard_normal((n, p)).astype(np.float32)
+    O = rand_omega(p, 3 * p).astype(np.float32)
+    Xd, Od = X.astype(np.float64), O.astype(np.float64)
+    GX = A.accord_grad_x(dev(X), dev(O)).double().cpu().numpy()
+    rX = R.smooth_loss_grad_x(Od, Xd)
+    # split-BF16 products: error relative to the sum of |terms| (|X| |Omega^T| |Omega| / n)
+    scale = np.max(np.abs(Xd) @ (np.abs(Od).T @ np.abs(Od))) / n
+    assert np.max(np.abs(GX - rX)) <= 3e-5 * scale
+
+
+def test_autograd_function(A):
+    """SmoothLoss: forward equals the oracle loss; backward gives the oracle
+    gradients in Omega and X; torch.autograd.gradcheck passes in FP64."""
+    n, p = 40, 60
+    X = np.random.Generator(np.random.PCG64(5)).standard_normal((n, p)).astype(np.float32)
+    O = rand_omega(p, 11, density=0.1)
+    Om = dev(O, torch.float64).requires_grad_(True)
+    Xt = dev(X).requires_grad_(True)
+    L = A.smooth_loss(Om, Xt)
+    Xd = X.astype(np.float64)
+    assert abs(L.item() - R.smooth_loss(O, Xd)) <= 1e-12 * abs(L.item())
+    L.backward()
+    assert np.max(np.abs(Om.grad.cpu().numpy() - R.smooth_loss_grad_omega(O, Xd))) <= 1e-11
+    rX = R.smooth_loss_grad_x(O, Xd)
+    assert np.max(np.abs(Xt.grad.double().cpu().numpy() - rX)) <= 1e-6 * np.max(np.abs(rX))  # stored in FP32
+    # chain rule with a non-unit upstream gradient
+    Om.grad = None
+    (3.0 * A.smooth_loss(Om, dev(X))).backward()
+    assert np.max(np.abs(Om.grad.cpu().numpy() - 3.0 * R.smooth_loss_grad_omega(O, Xd))) <= 3e-11
+    O2 = dev(rand_omega(12, 7, density=0.3), torch.float64).requires_grad_(True)
+    X2 = dev(np.random.Generator(np.random.PCG64(6)).standard_normal((10, 12)))
+    assert torch.autograd.gradcheck(lambda o: A.smooth_loss(o, X2), (O2,), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+def test_implicit_derivative_matches_oracle(A):
+    """Same estimate in, same derivative out: the GPU row solves against the
+    oracle's (FP64, p = 300)."""
+    w = diff_workload(p=300, n=120, n_val=60)
+    r = R.fit(w.X_train, w.lam, kkt_tol=1e-10, max_iter=20000)
+    assert r.status == R.OK
+    d_ref, dO_ref = R.implicit_dloglam(r.Omega, w.X_train, w.X_val, w.lam)
+    d, lv, dO = A.accord_dloss_dloglam(dev(w.X_train), dev(w.X_val), dev(r.Omega, torch.float64), w.lam,
+                                       want_domega=True)
+    assert abs(d - d_ref) <= 1e-10 * max(1.0, abs(d_ref))
+    assert abs(lv - R.smooth_loss(r.Omega, w.X_val)) <= 1e-12 * abs(lv)
+    assert np.max(np.abs(dO.cpu().numpy() - dO_ref)) <= 1e-10 * max(1.0, np.max(np.abs(dO_ref)))
+    # penalize_diag off: the diagonal row of the right-hand side is 0
+    r0 = R.fit(w.X_train, w.lam, kkt_tol=1e-10, max_iter=20000, penalize_diag=False)
+    d0_ref, _ = R.implicit_dloglam(r0.Omega, w.X_train, w.X_val, w.lam, penalize_diag=False)
+    d0, _, _ = A.accord_dloss_dloglam(dev(w.X_train), dev(w.X_val), dev(r0.Omega, torch.float64), w.lam,
+                                      penalize_diag=False)
+    assert abs(d0 - d0_ref) <= 1e-10 * max(1.0, abs(d0_ref))
+
+
+def test_implicit_derivative_full_size_finite_differences(A):
+    """p = 2000, n = 300 + 100 held out, lambda = 0.2: the implicit derivative
+    at the FP64 GPU estimate equals the central difference (h = 1e-4) of the
+    held-out loss at the FP64 GPU estimates for lambda e^(+-h); the mixed
+    estimate's derivative agrees to the accuracy of its KKT tolerance."""
+    w = diff_workload()
+    Xt, Xv = dev(w.X_train), dev(w.X_val)
+    h = 1e-4
+    fit = dict(precision="fp64", kkt_tol=1e-10, max_iter=20000)
+    O, st = A.accord_fit(Xt, w.lam, **fit)
+    assert st.status == 0
+    Op, sp = A.accord_fit(Xt, w.lam * math.exp(h), Omega=O.clone(), init_from_omega=True, **fit)
+    Om, sm = A.accord_fit(Xt, w.lam * math.exp(-h), Omega=O.clone(), init_from_omega=True, **fit)
+    assert sp.status == 0 and sm.status == 0
+    on, opn, omn = (O != 0).cpu(), (Op != 0).cpu(), (Om != 0).cpu()
+    assert torch.equal(on, opn) and torch.equal(on, omn), "active set changed inside +-h"
+    d, lv, dO = A.accord_dloss_dloglam(Xt, Xv, O, w.lam, want_domega=True)
+    _, lp, _ = A.accord_dloss_dloglam(Xt, Xv, Op, w.lam * math.exp(h))
+    _, lm, _ = A.accord_dloss_dloglam(Xt, Xv, Om, w.lam * math.exp(-h))
+    fd = (lp - lm) / (2 * h)
+    assert abs(d - fd) <= 1e-5 * abs(fd) + 1e-9, (d, fd)
+    dfd = ((Op - Om) / (2 * h)).cpu().numpy()
+    assert np.max(np.abs(dO.cpu().numpy() - dfd)) <= 1e-4 * np.max(np.abs(dfd))
+    # mixed precision: estimate at KKT 2e-5, derivative in FP64 from it
+    O32, s32 = A.accord_fit(Xt, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=20000)
+    assert s32.status == 0
+    d32, _, _ = A.accord_dloss_dloglam(Xt, Xv, O32, w.lam)
+    assert abs(d32 - fd) <= 2e-2 * abs(fd), (d32, fd)
