@@ -461,6 +461,8 @@ def run_path(args):
                           "subsample_rows": [len(s) for s in pw.subsamples], "distinct_rows": K.astype(int).tolist(),
                           "lambda_range": [float(pw.lambdas[0]), float(pw.lambdas[-1])], "kkt_tol": pw.kkt_tol,
                           "precision": "mixed_bf16x3", "parallelism": "batched chains, CUDA graph",
+                          "autotuned_prox_tiles": {"tile": "128x256", "group_m": int(r0.stats.tile_group_m),
+                                                   "clusters": int(r0.stats.tile_clusters)},
                           "l2": "inputs larger than L2 (16 chains x 64 MB Omega per buffer)"},
                "status": int(r0.status), "estimates_not_converged": int(np.sum(r0.entry_status == 1)),
                "prox_evaluations": int(evals.sum()), "iters_total": int(r0.stats.iters),

@@ -75,7 +75,9 @@ typedef struct accord_opts {
     int32_t sparse_update;   /* mixed mode: 1 (default) forms Y+ = Y + Delta X^T from the nonzero
                                 entries of Delta (the iterate is sparse); 0: dense tensor-core
                                 product every trial.  Ignored in FP64 mode (always dense).    */
-    int32_t reserved1;
+    int32_t autotune;        /* accord_path, mixed mode: 1 (default) times the batched prox GEMM's
+                                tile raster and persistent grid on the first call for a shape
+                                and keeps the fastest; 0: fixed defaults                         */
     double  tau0;            /* initial step (default 1); <= 0 means 1/L                        */
     double  beta;            /* backtracking factor in (0, 1]; 1 = fixed step (default 0.5)     */
     double  kkt_tol;         /* stop when r(Omega^t) <= kkt_tol (default 1e-8)                  */
@@ -110,6 +112,9 @@ typedef struct accord_stats {
     double  logdet_d;        /* sum_i log omega_ii of the returned Omega                         */
     double  epbic;           /* extended pseudo-BIC of Eq. 3.7 with opts->epbic_gamma:
                                 2n(-log det Omega_D + g) + nnz (log n + 4 gamma log p)           */
+    int32_t tile_group_m;    /* accord_path, mixed mode: raster group (cluster rows) of the
+                                batched prox GEMM in use (0 elsewhere)                           */
+    int32_t tile_clusters;   /* ... and its persistent grid in clusters of 2 CTAs                */
 } accord_stats;
 
 /* Fills *opts with the defaults listed above. */

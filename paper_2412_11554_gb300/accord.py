@@ -30,7 +30,7 @@ class AccordOpts(ctypes.Structure):
         ("precision", ctypes.c_int32), ("tau_warm", ctypes.c_int32), ("max_iter", ctypes.c_int32),
         ("max_backtracks", ctypes.c_int32), ("penalize_diag", ctypes.c_int32),
         ("init_from_omega", ctypes.c_int32), ("lipschitz_max_iter", ctypes.c_int32), ("profile", ctypes.c_int32),
-        ("sparse_update", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("sparse_update", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("tau0", ctypes.c_double), ("beta", ctypes.c_double), ("kkt_tol", ctypes.c_double),
         ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("epbic_gamma", ctypes.c_double),
         ("stream", ctypes.c_void_p),
@@ -46,6 +46,7 @@ class AccordStats(ctypes.Structure):
         ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
         ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64), ("logdet_d", ctypes.c_double), ("epbic", ctypes.c_double),
+        ("tile_group_m", ctypes.c_int32), ("tile_clusters", ctypes.c_int32),
     ]
 
 
@@ -145,6 +146,8 @@ class FitStats:
     logdet_d: float = 0.0
     epbic: float = 0.0
     trace: np.ndarray | None = None
+    tile_group_m: int = 0
+    tile_clusters: int = 0
 
 
 def _stream_handle(stream) -> int | None:
@@ -406,7 +409,7 @@ def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed
 
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms, st.t_y_gemm_ms,
-                     st.n_launches, st.logdet_d, st.epbic, None)
+                     st.n_launches, st.logdet_d, st.epbic, None, st.tile_group_m, st.tile_clusters)
     return PathResult(status, col("lambda_", np.float64), col("status", np.int32), col("iters", np.int32),
                       col("trials", np.int32), col("f", np.float64), col("g", np.float64), col("kkt", np.float64),
                       col("logdet_d", np.float64), col("epbic", np.float64), col("tau_last", np.float64),

@@ -659,6 +659,7 @@ void accord_default_opts(accord_opts* o) {
   o->lipschitz_max_iter = 128;
   o->profile = 0;
   o->sparse_update = 1;
+  o->autotune = 1;
   o->tau0 = 1.0;
   o->beta = 0.5;
   o->kkt_tol = 1e-8;

@@ -13,9 +13,12 @@
 // of its distinct rows, row j scaled by sqrt(K c_j / n_s) with c_j its
 // multiplicity: that matrix has the same S = X^T X / n.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "api_util.h"
@@ -92,6 +95,7 @@ struct PathLayout {
   int64_t tiles_prox = 0, tiles_y = 0, nbuckets = 0, sum_k = 0;
   int lz_k = 0;
   size_t ctrl = 0, rec = 0, lambdas = 0, n_obs = 0, best_epbic = 0, best_idx = 0, active = 0, nactive = 0, bad = 0;
+  size_t any_dense = 0;
   size_t kb_of = 0, g_rows = 0, g_scale = 0, g_off = 0;
   size_t part_prox = 0, part_y = 0;
   size_t om[2] = {0, 0}, y[2] = {0, 0};
@@ -128,6 +132,7 @@ PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_
   L.active = take(c, (size_t)B * 4);
   L.nactive = take(c, 64);
   L.bad = take(c, 64);
+  L.any_dense = take(c, 64);
   L.kb_of = take(c, (size_t)B * 4);
   L.g_rows = take(c, (size_t)sum_k * 4);
   L.g_scale = take(c, (size_t)sum_k * 8);
@@ -249,7 +254,7 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
     // bucket overflowed (each kernel checks its chain's flag)
     ACCORD_CK(launch_delta_planes(ctrl, at<float>(ws, L.om[0]), at<float>(ws, L.om[1]), L.p, L.ldo,
                                   at<__nv_bfloat16>(ws, L.dp_hi), at<__nv_bfloat16>(ws, L.dp_lo), L.ldo, st, B,
-                                  P.pd.active, P.pd.nactive, L.p * L.ldo, L.p * L.ldo));
+                                  P.pd.active, P.pd.nactive, L.p * L.ldo, L.p * L.ldo, at<int>(ws, L.any_dense)));
     ACCORD_CK(launch_tc_gemm(kModeY, P.t1, st));
     ACCORD_CK(launch_sparse_y(P.sy, st));
   }
@@ -261,6 +266,71 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
 }
 
 int launches_per_trial(bool f64) { return f64 ? 5 : 7; }
+
+// ------------------------------------------------------------ autotuner ---
+// The batched prox GEMM's tile raster (cluster rows per group) and its
+// persistent grid are picked by timing each candidate on the call's own
+// operands, once per (device, p, K, chains) in the process.  The runs happen
+// before the control blocks are initialised: with tau = 0 the prox returns
+// Omega unchanged, so Delta is empty and no state needs restoring.
+struct TuneChoice {
+  int group_m = 0, clusters = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 4>, TuneChoice> g_tune;
+
+int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
+  int dev = 0;
+  ACCORD_CK(cudaGetDevice(&dev));
+  const std::array<int64_t, 4> key{dev, P.L.p, P.L.kpad, P.L.nchains};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      best = it->second;
+      P.t2.group_m = best.group_m;
+      P.t2.max_clusters = best.clusters;
+      return kOk;
+    }
+  }
+  const int maxc = tc_max_clusters(kModeProx);
+  std::vector<int> grids{maxc};
+  for (int c : {maxc * 3 / 4, maxc / 2})
+    if (c > 0 && c != grids.back()) grids.push_back(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ACCORD_CK(cudaEventCreate(&e0));
+  struct EvPair {
+    cudaEvent_t a, b;
+    ~EvPair() { cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+  } evp{e0, nullptr};
+  ACCORD_CK(cudaEventCreate(&e1));
+  evp.b = e1;
+  float best_ms = 1e30f;
+  for (int g : {1, 2, 4, 8, 16}) {
+    if (g > P.t2.tiles_mc && g != 1) continue;
+    for (int c : grids) {
+      P.t2.group_m = g;
+      P.t2.max_clusters = c;
+      ACCORD_CK(launch_tc_gemm(kModeProx, P.t2, st));  // warm
+      ACCORD_CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < 2; ++r) ACCORD_CK(launch_tc_gemm(kModeProx, P.t2, st));
+      ACCORD_CK(cudaEventRecord(e1, st));
+      ACCORD_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ACCORD_CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.group_m = g;
+        best.clusters = c;
+      }
+    }
+  }
+  P.t2.group_m = best.group_m;
+  P.t2.max_clusters = best.clusters;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return kOk;
+}
 
 int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets, int64_t n_sub,
               const double* lambdas, int64_t n_lambda, const accord_opts* optp, accord_path_entry* entries,
@@ -336,6 +406,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
                             st));
   ACCORD_CK(cudaMemcpyAsync(at<int64_t>(ws, L.g_off), S.off.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
   ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bad), 0, 64, st));
+  ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.any_dense), 0, 64, st));
   ACCORD_CK(cudaMemsetAsync(at<PathRec>(ws, L.rec), 0, (size_t)n_lambda * B * sizeof(PathRec), st));
 
   // --------------------------------------------- data of every chain -----
@@ -448,6 +519,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
   pd.best_idx = at<int32_t>(ws, L.best_idx);
   pd.active = at<int32_t>(ws, L.active);
   pd.nactive = at<int32_t>(ws, L.nactive);
+  pd.any_dense = f64 ? nullptr : at<int>(ws, L.any_dense);
   SolveParams& sp = P.sp;
   sp.tau0 = o.tau0;
   sp.beta = o.beta;
@@ -457,9 +529,6 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
   sp.tau_warm = o.tau_warm;
   sp.fixed_step = o.beta >= 1.0 ? 1 : 0;
   sp.trace_cap = 0;
-  ACCORD_CK(launch_batch_ctrl_init(pd, at<void>(ws, L.y[0]), f64, p, K, p * K, sp, L_given, st));
-  nlaunch += 1;
-
   if (f64) {
     GemmF64Params& g2 = P.g2;  // G = Y X / n, prox, Omega[cur] -> Omega[nxt]
     g2.ctrl = ctrl;
@@ -533,6 +602,12 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     t2.nactive = pd.nactive;
     t2.kb_of = at<int32_t>(ws, L.kb_of);
     t2.s_out = p * L.ldo; t2.s_aux = p * L.ldo; t2.s_part = L.tiles_prox; t2.s_bkt = L.nbuckets;
+    t2.any_dense = at<int>(ws, L.any_dense);
+    // a chain in dense Y mode gets its Delta planes from this epilogue
+    t2.out_hi[0] = t2.out_hi[1] = at<__nv_bfloat16>(ws, L.dp_hi);
+    t2.out_lo[0] = t2.out_lo[1] = at<__nv_bfloat16>(ws, L.dp_lo);
+    t2.ldplane = L.ldo;
+    t2.s_plane = p * L.ldo;
     TcParams& t1 = P.t1;  // dense Y+ = Y + Delta X^T, only for chains whose bucket overflowed
     if (!encode_plane_map(&t1.a_hi[0], at<__nv_bfloat16>(ws, L.dp_hi), p, p, L.ldo, 128, B, p * L.ldo) ||
         !encode_plane_map(&t1.a_lo[0], at<__nv_bfloat16>(ws, L.dp_lo), p, p, L.ldo, 128, B, p * L.ldo) ||
@@ -563,6 +638,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     t1.active = pd.active;
     t1.nactive = pd.nactive;
     t1.s_out = p * K; t1.s_aux = p * K; t1.s_plane = p * K; t1.s_part = L.tiles_y;
+    t1.any_dense = at<int>(ws, L.any_dense);
     SparseYParams& sy = P.sy;
     sy.ctrl = ctrl;
     for (int q = 0; q < 2; ++q) {
@@ -587,6 +663,12 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     sy.nprob = (int32_t)B;
     sy.s_y = p * K; sy.s_yk = p * K; sy.s_xt = p * K; sy.s_bkt = L.nbuckets;
   }
+  TuneChoice tune;
+  if (!f64 && o.autotune) {
+    if (int e = tune_prox(P, st, tune)) return e;
+  }
+  ACCORD_CK(launch_batch_ctrl_init(pd, at<void>(ws, L.y[0]), f64, p, K, p * K, sp, L_given, st));
+  nlaunch += 1;
   ACCORD_CK(cudaEventRecord(ev[1], st));
 
   // ------------------------------------------ captured trial sequence ----
@@ -722,6 +804,8 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     out->t_prox_gemm_ms = prox_ms;
     out->n_launches = nlaunch;
     out->L = hctrl[0].L;
+    out->tile_group_m = f64 ? 0 : P.t2.group_m;
+    out->tile_clusters = f64 ? 0 : (P.t2.max_clusters > 0 ? P.t2.max_clusters : tc_max_clusters(kModeProx));
   }
   return hstatus;
 }

@@ -71,6 +71,9 @@ struct Ctrl {
   int32_t emit_lam;   // lambda path: penalty index of that estimate
   int32_t iters_tot;  // lambda path: accepted steps over the whole chain
   int32_t trials_tot; // lambda path: prox evaluations over the whole chain
+  int32_t ymode;      // batch: 1 = the prox epilogue writes dense Delta planes (Delta too dense for
+                      // the buckets), 0 = it fills the sparse buckets
+  int32_t pad1;
 };
 
 // One estimate of a lambda path (same layout as accord_path_entry).

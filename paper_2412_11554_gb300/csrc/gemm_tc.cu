@@ -75,7 +75,7 @@ __device__ __forceinline__ int tile_problem(const TcParams& prm, int T, int& Tl)
 __device__ __forceinline__ bool skip_problem(const TcParams& prm, int b) {
   if (prm.ctrl == nullptr) return false;
   const Ctrl& c = prm.ctrl[b];
-  return c.done || (prm.gate_dense && !c.dense);
+  return c.done || (prm.gate_dense && !c.dense && !c.ymode);
 }
 
 // First flat tile >= T (stepping by `stride`) that is not skipped; ntot if none.
@@ -109,17 +109,6 @@ struct EpiArgs {
   const uint32_t* mask;
   int64_t mask_ld;      // 32-bit words per row
 };
-
-// Append one nonzero Delta entry to the bucket of its 32-row group.
-__device__ __forceinline__ void bucket_push(const EpiArgs& ea, int r, int64_t colt, float d) {
-  const int pos = atomicAdd(ea.bcnt, 1);
-  if (pos < ea.cap) {
-    ea.bkey[pos] = ((uint32_t)r << 25) | (uint32_t)colt;
-    ea.bval[pos] = d;
-  } else {
-    atomicOr(ea.dense_flag, 1);
-  }
-}
 
 // Per-thread tile partials.  The dense sums run in FP32 over the thread's
 // share of one tile (at most 128 terms) and are folded across warps and tiles
@@ -280,17 +269,42 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
     v[r] = d;
     nzmask |= (d != 0.f) ? (1u << r) : 0u;
   }
-  // Delta is mostly zero: each lane appends only its own nonzero entries
-  if (sparse && nzmask != 0u) {
-    uint32_t m = nzmask;
-    while (m != 0u) {
-      const int r = __ffs(m) - 1;
-      m &= m - 1u;
-      float dr = 0.f;
+  // Delta is mostly zero: each lane appends only its own nonzero entries.
+  // One atomic reserves the whole warp's entries (a warp prefix sum gives
+  // each lane its slots), so a dense Delta does not serialise on the
+  // bucket counter.
+  if (sparse) {
+    const int cnt = __popc(nzmask);
+    int incl = cnt;
 #pragma unroll
-      for (int u = 0; u < 32; ++u)
-        if (u == r) dr = v[u];
-      bucket_push(ea, r, colt, dr);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total > 0) {
+      int base = 0;
+      if (lane == 31) base = atomicAdd(ea.bcnt, total);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      int pos = base + incl - cnt;
+      uint32_t m = nzmask;
+      while (m != 0u) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1u;
+        float dr = 0.f;
+#pragma unroll
+        for (int u = 0; u < 32; ++u)
+          if (u == r) dr = v[u];
+        if (pos < ea.cap) {
+          ea.bkey[pos] = ((uint32_t)r << 25) | (uint32_t)colt;
+          ea.bval[pos] = dr;
+        }
+        ++pos;
+      }
+      if (lane == 31 && base + total > ea.cap) {
+        atomicOr(ea.dense_flag, 1);
+        if (prm.any_dense != nullptr) atomicOr(prm.any_dense, 1);
+      }
     }
   }
   sm.r0 += sd;
@@ -331,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   Ctrl* ctrl = prm.ctrl;
   const bool batch = prm.nprob > 1 || prm.active != nullptr;
   if (!batch && ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
+  if (prm.gate_dense && prm.any_dense != nullptr && *prm.any_dense == 0) return;
   const int ntot = (prm.active ? *prm.nactive : (prm.nprob > 1 ? prm.nprob : 1)) * prm.ntiles_c;
   if (ntot <= 0) return;
 
@@ -538,12 +553,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int64_t row_base = (int64_t)mb * BM + 32 * q;
       const int64_t col_base = (int64_t)nb * kBN + h * kColsPerWarp;
       const bool rows_full = row_base + 32 <= prm.M;
-      if (MODE == kModeProx && prm.keys != nullptr) {
+      // sparse Delta buckets, or (a batch problem in dense mode) Delta planes
+      if (MODE == kModeProx && prm.keys != nullptr && !(batch && ctrl != nullptr && ctrl[b].ymode)) {
         const int64_t bkt = b * prm.s_bkt + row_base / 32;  // one bucket per warp row quarter
         ea.bkey = prm.keys + bkt * prm.cap;
         ea.bval = prm.vals + bkt * prm.cap;
         ea.bcnt = prm.counts + bkt;
         ea.row0 = row_base;
+      } else {
+        ea.bkey = nullptr;
       }
       Sums sm;
       float pre[32];
@@ -718,6 +736,7 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (prm.max_clusters > 0 && prm.max_clusters < max_clusters) max_clusters = prm.max_clusters;
   const int64_t tiles_total = (int64_t)(prm.nprob > 1 ? prm.nprob : 1) * prm.ntiles_c;
   const int clusters = (int)std::min<int64_t>(tiles_total, max_clusters);
   cfg.gridDim = dim3((unsigned)(clusters * kClusterM), 1, 1);
@@ -727,6 +746,17 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
 }  // namespace
 
 int tc_box_n() { return kBBox; }
+
+int tc_max_clusters(int mode) {
+  int m = 0;
+  switch (mode) {
+    case kModeY: configure_mode<kModeY>(m); break;
+    case kModeProx: configure_mode<kModeProx>(m); break;
+    case kModeGrad: configure_mode<kModeGrad>(m); break;
+    default: configure_mode<kModeGram>(m); break;
+  }
+  return m;
+}
 
 cudaError_t tc_prepare() {
   int m = 0;

@@ -125,6 +125,7 @@ struct PathDev {
   int32_t* best_idx;       // device, per chain
   int32_t* active;         // device list of unfinished chains
   int32_t* nactive;
+  int* any_dense;          // device flag: some chain takes the dense Y update next trial (or null)
 };
 // Finishes the per-chain control blocks after L is known: tau0, f and g of
 // Omega^0 = I with Y^0 = X^T (yt0: p x ldy per chain, s_y elements apart).
@@ -134,6 +135,8 @@ cudaError_t launch_batch_ctrl_init(const PathDev& pd, const void* yt0, int is_f6
 // partial rows of problem b start at part + b * ntiles rows.
 cudaError_t launch_post_prox_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
                                    const double* part, int64_t ntiles, const SolveParams& sp, cudaStream_t st);
+// With buckets (part_sparse != null) it also picks each problem's Y-update
+// mode for the next trial (Ctrl::ymode).
 cudaError_t launch_decide_batch(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
                                 const double* part, int64_t ntiles, const SolveParams& sp, int* bucket_counts,
                                 int nbuckets, const double* part_sparse, cudaStream_t st);
@@ -180,7 +183,7 @@ cudaError_t sparse_y_prepare();  // one-time shared-memory opt-in (before a grap
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
                                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st,
                                 int32_t nprob = 1, const int32_t* active = nullptr, const int32_t* nactive = nullptr,
-                                int64_t s_om = 0, int64_t s_pl = 0);
+                                int64_t s_om = 0, int64_t s_pl = 0, const int* any_dense = nullptr);
 // X^T in FP32 (p x ldxt).
 cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 

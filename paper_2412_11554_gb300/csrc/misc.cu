@@ -576,6 +576,7 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
 }
 
 // ------------------------------------------------------- batched control --
+constexpr int kBucketRowsDev = kBucketRows;
 __device__ __forceinline__ int slot_problem(const int32_t* active, const int32_t* nactive, int slot) {
   if (active == nullptr) return slot;
   return slot < *nactive ? active[slot] : -1;
@@ -604,10 +605,19 @@ __global__ void decide_batch_kernel(Ctrl* ctrl, const int32_t* active, const int
     return;
   }
   double s[kYSlots];
-  const bool sparse_ran = part_sparse != nullptr && !c.dense;
+  const bool sparse_ran = part_sparse != nullptr && !c.dense && !c.ymode;
   if (sparse_ran) fold_partials<kYSlots>(part_sparse + (int64_t)b * nbuckets * kYSlots, nbuckets, 0u, s);
   else fold_partials<kYSlots>(part + b * ntiles * kYSlots, ntiles, 0u, s);
-  if (threadIdx.x == 0) decide_update(c, s, sp, nullptr);
+  if (threadIdx.x == 0) {
+    // Y update of the next trial: dense (the prox writes Delta planes) after a
+    // bucket overflowed; back to the buckets once Omega+ has so few nonzeros
+    // (under 16 a row off the diagonal) that Delta fits them with room to spare
+    if (part_sparse != nullptr) {
+      if (c.dense) c.ymode = 1;
+      else if (c.ymode && c.t_nnz < 16.0 * (double)(nbuckets * kBucketRowsDev)) c.ymode = 0;
+    }
+    decide_update(c, s, sp, nullptr);
+  }
 }
 
 // One block per chain: g of Y^0 = X^T, then the state of Omega^0 = I.
@@ -661,6 +671,9 @@ __global__ void batch_ctrl_init_kernel(PathDev pd, const T* __restrict__ yt0, in
 }
 
 __global__ void path_advance_kernel(PathDev pd) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
   for (int c = threadIdx.x; c < pd.nchains; c += blockDim.x) {
     Ctrl& C = pd.ctrl[c];
     C.emit = 0;
@@ -721,8 +734,14 @@ __global__ void path_advance_kernel(PathDev pd) {
   if (threadIdx.x == 0) {
     int m = 0;
     for (int c = 0; c < pd.nchains; ++c)
-      if (!pd.ctrl[c].finished) pd.active[m++] = c;
+      if (!pd.ctrl[c].finished) {
+        pd.active[m++] = c;
+        any |= pd.ctrl[c].ymode;
+      }
     *pd.nactive = m;
+    // the dense Y kernels of the next trial run only if some chain needs them
+    // (a bucket overflow during the trial sets the flag too)
+    if (pd.any_dense != nullptr) *pd.any_dense = any;
   }
 }
 

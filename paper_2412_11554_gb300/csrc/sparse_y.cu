@@ -17,7 +17,7 @@
 namespace accord {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kRowsPerBlock = kBucketRows;
 constexpr int kColsPerPass = 256;  // 8 columns a lane per pass
 
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
     b = prm.active[b];
   }
   const Ctrl* ctrl = prm.ctrl + b;
-  if (ctrl->done || ctrl->dense) return;
+  if (ctrl->done || ctrl->dense || ctrl->ymode) return;
   extern __shared__ uint8_t smem_raw[];
   const int mb = blockIdx.x;  // bucket = 32-row group
   const int cur = ctrl->cur, nxt = cur ^ 1;
@@ -102,7 +102,27 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
       float acc[kColsPerPass / 32];
 #pragma unroll
       for (int u = 0; u < kColsPerPass / 32; ++u) acc[u] = 0.f;
-      for (int k = lo; k < hi; ++k) {
+      int k = lo;
+      if (c0 + kColsPerPass <= prm.n) {
+        // four Delta entries at a time: their X^T rows are independent loads,
+        // so 32 of them are in flight per lane (the walk is latency-bound)
+        for (; k + 4 <= hi; k += 4) {
+          float d[4], x[4][kColsPerPass / 32];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int64_t j = key[k + q] & 0x1FFFFFFu;
+            d[q] = val[k + q];
+            const float* xr = XT + j * prm.ldy + c0 + lane;
+#pragma unroll
+            for (int u = 0; u < kColsPerPass / 32; ++u) x[q][u] = __ldg(xr + 32 * u);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int u = 0; u < kColsPerPass / 32; ++u) acc[u] = fmaf(d[q], x[q][u], acc[u]);
+        }
+      }
+      for (; k < hi; ++k) {
         const int64_t j = key[k] & 0x1FFFFFFu;
         const float d = val[k];
         const float* xr = XT + j * prm.ldy + c0 + lane;
@@ -151,14 +171,16 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
 // Dense fallback when a bucket overflowed: BF16 planes of Delta = Omega+ - Omega.
 __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
                                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, const int32_t* active,
-                                    const int32_t* nactive, int64_t s_om, int64_t s_pl) {
+                                    const int32_t* nactive, int64_t s_om, int64_t s_pl, const int* any_dense) {
+  if (any_dense != nullptr && *any_dense == 0) return;
   int b = blockIdx.y;
   if (active != nullptr) {
     if (b >= *nactive) return;
     b = active[b];
   }
   ctrl += b;
-  if (ctrl->done || !ctrl->dense) return;
+  // overflow in bucket mode only: in dense mode the prox epilogue wrote the planes
+  if (ctrl->done || !ctrl->dense || ctrl->ymode) return;
   const float* Om = (ctrl->cur ? om1 : om0) + b * s_om;
   const float* Op = (ctrl->cur ? om0 : om1) + b * s_om;
   hi += b * s_pl;
@@ -203,11 +225,13 @@ cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
 
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
                                 __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st, int32_t nprob,
-                                const int32_t* active, const int32_t* nactive, int64_t s_om, int64_t s_pl) {
+                                const int32_t* active, const int32_t* nactive, int64_t s_om, int64_t s_pl,
+                                const int* any_dense) {
   const unsigned nb = (unsigned)(nprob > 1 ? nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
   const unsigned gx = nb > 1 ? 152u * 16u / nb + 1u : 152u * 16u;
-  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, active, nactive, s_om, s_pl);
+  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, active, nactive, s_om, s_pl,
+                                                    any_dense);
   return cudaGetLastError();
 }
 

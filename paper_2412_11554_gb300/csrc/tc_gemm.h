@@ -58,6 +58,12 @@ struct TcParams {
   const int32_t* nactive;    // device length of `active`
   const int32_t* kb_of;      // device K blocks per problem (ragged K), or null (num_kb)
   int64_t s_out, s_aux, s_plane, s_part, s_bkt;  // strides: elements, elements, elements, tiles, buckets
+  // Batch: a prox epilogue whose bucket overflows also sets *any_dense; a
+  // gated launch returns at once while *any_dense is clear (no problem needs
+  // the dense product), instead of scanning every problem's tiles.
+  int* any_dense;
+  int32_t max_clusters;  // persistent grid limit in clusters (0: as many as fit at once)
+  int32_t pad_tail;
 };
 
 // Encodes a 3-D BF16 tensor map over `depth` slices of a rows x cols matrix
@@ -75,5 +81,7 @@ cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
 // One-time per-device setup of every mode (done lazily by the first launch
 // otherwise); call before capturing launches into a CUDA graph.
 cudaError_t tc_prepare();
+// Clusters of the persistent grid that fit on the device at once (mode's kernel).
+int tc_max_clusters(int mode);
 
 }  // namespace accord
