@@ -215,6 +215,18 @@ int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double*
  * pointer stays valid until the thread's next call. */
 const char* accord_last_error(void);
 
+/* ---- post-processing (Sec 3.1) ----------------------------------------------- */
+
+/* From an estimate Omega (device p x p, element type per opts->precision):
+ *   Theta_out = T^-1(Omega) = Omega_D Omega, theta_ij = omega_ii omega_ij (the
+ *               precision-matrix estimate), and/or
+ *   Rho_out   = partial correlations rho_ij = -(1/2)(omega_ij / omega_jj + omega_ji / omega_ii),
+ *               rho_ii = 1.
+ * Either output may be NULL (not both); both are device p x p, same element
+ * type, and must not alias Omega.  EDOMAIN when a diagonal entry is not
+ * positive (the outputs are still written). */
+int accord_postprocess(int64_t p, const void* Omega, const accord_opts* opts, void* Theta_out, void* Rho_out);
+
 /* ---- differentiation ------------------------------------------------------ */
 
 /* Adjoint of the smooth loss L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S)

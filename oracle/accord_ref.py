@@ -317,6 +317,22 @@ def lambda_path(X: np.ndarray, rows: list, lambdas, *, gamma: float = 0.5, cold_
     return PathResult(lambdas, fits, score, best, Omega_best)
 
 
+# ------------------------------------------------------ post-processing ---
+
+def theta_hat(Omega: np.ndarray) -> np.ndarray:
+    """Theta-hat = T^-1(Omega-hat) = Omega_D Omega (Sec 3.1): theta_ij = omega_ii omega_ij."""
+    return np.diag(Omega)[:, None] * Omega
+
+
+def partial_correlation(Omega: np.ndarray) -> np.ndarray:
+    """rho_ij = -(1/2)(omega_ij / omega_jj + omega_ji / omega_ii) off the
+    diagonal (Sec 3.1); the diagonal is 1 by convention."""
+    d = np.diag(Omega)
+    R = -0.5 * (Omega / d[None, :] + Omega.T / d[:, None])
+    np.fill_diagonal(R, 1.0)
+    return R
+
+
 # ------------------------------------------------------ differentiation ---
 
 def smooth_loss(Omega: np.ndarray, X: np.ndarray) -> float:

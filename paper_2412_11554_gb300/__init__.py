@@ -10,6 +10,7 @@ from .accord import (  # noqa: F401
     accord_device_check,
     accord_fit,
     accord_grad_x,
+    accord_postprocess,
     accord_dloss_dloglam,
     accord_path,
     accord_path_workspace_bytes,

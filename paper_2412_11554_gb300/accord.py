@@ -62,7 +62,7 @@ class AccordPathEntry(ctypes.Structure):
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
-           "accord_dloss_dloglam")
+           "accord_dloss_dloglam", "accord_postprocess")
 
 _lib = None
 
@@ -106,6 +106,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_path.restype = i32
     lib.accord_path_workspace_bytes.argtypes = [i64, i64, P, P, i64, i64, opts_p]
     lib.accord_path_workspace_bytes.restype = ctypes.c_size_t
+    lib.accord_postprocess.argtypes = [i64, P, opts_p, P, P]
+    lib.accord_postprocess.restype = i32
     lib.accord_grad_x.argtypes = [P, i64, i64, P, opts_p, P]
     lib.accord_grad_x.restype = i32
     lib.accord_dloss_dloglam.argtypes = [P, i64, P, i64, i64, P, dbl, opts_p, ctypes.POINTER(dbl),
@@ -288,6 +290,25 @@ def accord_loss_f64_noalloc(X: torch.Tensor, Omega: torch.Tensor, lam: float, fg
                                          _stream_handle(stream), fg_out.data_ptr())
     if status != OK:
         raise AccordError(status, "accord_loss_f64_noalloc")
+
+
+def accord_postprocess(Omega: torch.Tensor, *, theta: bool = True, rho: bool = True, stream=None):
+    """(Theta-hat = Omega_D Omega, partial correlations) of an estimate (Sec 3.1);
+    either may be skipped (None).  Precision follows Omega's dtype."""
+    lib = load_library()
+    p = Omega.shape[0]
+    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
+        raise ValueError("Omega must be a contiguous square CUDA tensor")
+    prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
+    o = accord_default_opts(precision=prec)
+    o.stream = _stream_handle(stream)
+    T = torch.empty_like(Omega) if theta else None
+    Rh = torch.empty_like(Omega) if rho else None
+    status = lib.accord_postprocess(p, Omega.data_ptr(), ctypes.byref(o), T.data_ptr() if T is not None else None,
+                                    Rh.data_ptr() if Rh is not None else None)
+    if status != OK:
+        raise AccordError(status, "accord_postprocess")
+    return T, Rh
 
 
 def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, out: torch.Tensor | None = None,

@@ -134,3 +134,34 @@ def test_implicit_derivative_full_size_finite_differences(A):
     assert s32.status == 0
     d32, _, _ = A.accord_dloss_dloglam(Xt, Xv, O32, w.lam)
     assert abs(d32 - fd) <= 2e-2 * abs(fd), (d32, fd)
+
+
+@pytest.mark.parametrize("p", [1, 33, 300, 4000])
+def test_postprocess_matches_oracle(A, p):
+    """Theta-hat = Omega_D Omega and the partial correlations of Sec 3.1 on an
+    asymmetric sparse Omega with positive diagonal, ragged tile edges."""
+    O = rand_omega(p, 17 + p)
+    T64, R64 = A.accord_postprocess(dev(O, torch.float64))
+    assert np.max(np.abs(T64.cpu().numpy() - R.theta_hat(O))) <= 1e-15 * max(1.0, np.max(np.abs(R.theta_hat(O))))
+    assert np.max(np.abs(R64.cpu().numpy() - R.partial_correlation(O))) <= 1e-15
+    O32 = O.astype(np.float32)
+    T32, R32 = A.accord_postprocess(dev(O32))
+    Od = O32.astype(np.float64)
+    assert np.max(np.abs(T32.double().cpu().numpy() - R.theta_hat(Od))) <= 1e-6 * max(1.0, np.max(np.abs(O)))
+    assert np.max(np.abs(R32.double().cpu().numpy() - R.partial_correlation(Od))) <= 1e-6
+    _, only_rho = A.accord_postprocess(dev(O, torch.float64), theta=False)
+    assert torch.equal(only_rho, R64)
+
+
+def test_postprocess_recovers_theta(A):
+    """T^-1 undoes T (Thm 3.1): Omega = Theta_D^-1/2 Theta maps back to Theta."""
+    rng = np.random.Generator(np.random.PCG64(91))
+    B = rng.standard_normal((70, 70))
+    Theta = B @ B.T + 70 * np.eye(70)
+    Om = Theta / np.sqrt(np.diag(Theta))[:, None]
+    T, Rh = A.accord_postprocess(dev(Om, torch.float64))
+    assert np.allclose(T.cpu().numpy(), Theta, rtol=1e-14, atol=1e-12)
+    d = np.sqrt(np.diag(Theta))
+    want = -Theta / np.outer(d, d)
+    np.fill_diagonal(want, 1.0)
+    assert np.allclose(Rh.cpu().numpy(), want, rtol=1e-13, atol=1e-14)

@@ -315,11 +315,26 @@ def pin_implicit_dloglam_fd():
     return bool(abs(d - fd) <= 1e-6 * max(1.0, abs(fd)) and np.max(np.abs(dO - dfd)) <= 1e-6 * max(1.0, np.max(np.abs(dfd))))
 
 
+def pin_reparameterisation():
+    """T(Theta) = Theta_D^-1/2 Theta (Thm 3.1) inverts to Theta = Omega_D Omega,
+    and the partial correlations from Omega = T(Theta) equal the textbook
+    -theta_ij / sqrt(theta_ii theta_jj) of the precision matrix."""
+    rng = np.random.Generator(np.random.PCG64(81))
+    B = rng.standard_normal((9, 9))
+    Theta = B @ B.T + 9 * np.eye(9)
+    Om = Theta / np.sqrt(np.diag(Theta))[:, None]
+    d = np.sqrt(np.diag(Theta))
+    rho = -Theta / np.outer(d, d)
+    np.fill_diagonal(rho, 1.0)
+    return bool(np.allclose(R.theta_hat(Om), Theta, rtol=1e-13, atol=1e-13) and
+                np.allclose(R.partial_correlation(Om), rho, rtol=1e-13, atol=1e-13))
+
+
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
         pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
-        pin_implicit_dloglam_fd]
+        pin_implicit_dloglam_fd, pin_reparameterisation]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -399,6 +414,7 @@ MUTANTS = {
     "grad_x_transposed": ("smooth_loss_grad_x", lambda Om, X: np.asarray(X, float) @ Om @ Om.T / X.shape[0]),
     "implicit_drops_log_term": ("implicit_dloglam", lambda O, Xt, Xv, lam, penalize_diag=True:
                                 _implicit_without_log_term(O, Xt, Xv, lam)),
+    "partial_corr_one_sided": ("partial_correlation", lambda Om: -Om / np.diag(Om)[None, :]),
     "path_ignores_subsample": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
                                _f(X, [np.arange(np.asarray(X).shape[0])] * len(rows), lams, **kw)),
 }
