@@ -209,14 +209,14 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
 // and the diagonal (row == colt); the unchecked form is the hot path.
-template <bool CHECK, bool MASK>
+template <bool CHECK, bool MASK, bool SPARSE>
 __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
                                            int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
                                            int lane) {
   float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
-  const bool sparse = ea.bkey != nullptr;
+  constexpr bool sparse = SPARSE;  // Delta to the buckets (else to BF16 planes)
   float* po = ea.out + row_base * prm.ldout + colt;
   __nv_bfloat16* ph = sparse ? nullptr : ea.out_hi + row_base * prm.ldplane + colt;
   __nv_bfloat16* pl = sparse ? nullptr : ea.out_lo + row_base * prm.ldplane + colt;
@@ -606,12 +606,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (full) y_chunk<false>(ea, prm, row_base, colt, v, pre, sm);
             else y_chunk<true>(ea, prm, row_base, colt, v, pre, sm);
           } else if (MODE == kModeProx) {
+            // compile-time variants: full interior chunk, Delta to buckets, no refit mask is the hot one
+            const bool fast = full && !diag;
             if (ea.mask == nullptr) {
-              if (full && !diag) prox_chunk<false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (ea.bkey != nullptr) {
+                if (fast) prox_chunk<false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else prox_chunk<true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              } else {
+                if (fast) prox_chunk<false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else prox_chunk<true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              }
+            } else if (ea.bkey != nullptr) {
+              if (fast) prox_chunk<false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
             } else {
-              if (full && !diag) prox_chunk<false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) prox_chunk<false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
             }
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
