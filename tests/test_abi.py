@@ -123,5 +123,14 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert path(rows, offs, 0, lams, 2) == accord.EINVAL
     assert lib.accord_path_workspace_bytes(10, 10, rows.ctypes.data, offs.ctypes.data, 2, 2, ctypes.byref(o)) > 0
     assert lib.accord_path_workspace_bytes(5, 10, rows.ctypes.data, offs.ctypes.data, 2, 2, ctypes.byref(o)) == 0
+    # post-processing and differentiation: argument checks before any device call
+    assert lib.accord_postprocess(0, dummy, ctypes.byref(o), dummy, None) == accord.EINVAL
+    assert lib.accord_postprocess(10, dummy, ctypes.byref(o), None, None) == accord.EINVAL
+    assert lib.accord_grad_x(dummy, 10, 10, dummy, ctypes.byref(o), None) == accord.EINVAL
+    d = ctypes.c_double()
+    assert lib.accord_dloss_dloglam(dummy, 10, None, 5, 10, dummy, 0.2, ctypes.byref(o), ctypes.byref(d),
+                                    None, None) == accord.EINVAL
+    assert lib.accord_dloss_dloglam(dummy, 10, dummy, 5, 10, dummy, -0.2, ctypes.byref(o), ctypes.byref(d),
+                                    None, None) == accord.EINVAL
     for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert accord.accord_status_string(s)
