@@ -250,11 +250,12 @@ def path_workload(p: int = 4000, n_total: int = 400, n_lambda: int = 32, n_sub: 
                         subsamples=subs, kkt_tol=kkt_tol, recipe=recipe)
 
 
-def ar1_random_precision(p: int, extra: float, weight: float, seed: int, rho: float = 0.4) -> sp.csr_matrix:
-    """AR(1) chain (rho off the diagonal) plus a random `extra` fraction of the
-    other off-diagonal pairs with weights +-weight, then made diagonally
-    dominant with the factor-1.5 rule of Sec 5.1 (a dense random graph with
-    these weights is not positive definite otherwise)."""
+def ar1_random_precision(p: int, extra: float, weight: float, seed: int, rho: float = 0.4,
+                         min_eig: float = 0.2) -> sp.csr_matrix:
+    """Unit diagonal, AR(1) chain (rho off the diagonal) plus a random `extra`
+    fraction of the other off-diagonal pairs with weights +-weight; the
+    diagonal is then raised just enough for the smallest eigenvalue to be
+    min_eig (the rule of the paper's Sec 5.2 simulations)."""
     rng = _rng(seed)
     iu, ju = np.triu_indices(p, k=2)
     take = rng.random(iu.size) < extra
@@ -264,8 +265,11 @@ def ar1_random_precision(p: int, extra: float, weight: float, seed: int, rho: fl
     rows = np.concatenate([chain, ri])
     cols = np.concatenate([chain + 1, rj])
     v = np.concatenate([np.full(p - 1, rho), vals])
-    off = _assemble(p, rows, cols, v)
-    return _diag_dominant(off, 1.5, 1.0)
+    theta = (_assemble(p, rows, cols, v) + sp.eye(p)).tocsr()
+    lmin = float(np.linalg.eigvalsh(theta.toarray())[0])
+    if lmin < min_eig:
+        theta = (theta + (min_eig - lmin) * sp.eye(p)).tocsr()
+    return theta
 
 
 @dataclasses.dataclass
@@ -283,7 +287,7 @@ def diff_workload(p: int = 2000, n: int = 300, n_val: int = 100, lam: float = 0.
     (weights +-0.2).  Seeds: graph 1000 + k, data 2000 + k."""
     theta = ar1_random_precision(p, 0.01, 0.2, 1000 + k)
     X = sample_gaussian(theta, n + n_val, 2000 + k).astype(np.float32)
-    recipe = (f"AR(1) rho=0.4 + 1% random edges +-0.2, diag rule 1.5, p={p}, n={n} + {n_val} held out, "
+    recipe = (f"AR(1) rho=0.4 + 1% random edges +-0.2, min eigenvalue 0.2, p={p}, n={n} + {n_val} held out, "
               f"lambda={lam}, seeds {1000 + k}/{2000 + k}")
     return DiffWorkload(name=f"diff_p{p}_n{n}", X_train=np.ascontiguousarray(X[:n]),
                         X_val=np.ascontiguousarray(X[n:]), lam=lam, theta=theta, recipe=recipe)
