@@ -134,7 +134,9 @@ def test_implicit_derivative_full_size_finite_differences(A):
     fd = (lp - lm) / (2 * h)
     assert abs(d - fd) <= 1e-4 * abs(fd) + 1e-9, (d, fd)
     dfd = (Opc - Omc) / (2 * h)
-    keep = ~changed
+    # rows decouple: compare the rows whose active set stays fixed
+    keep = ~np.any(changed, axis=1)
+    assert keep.sum() >= 1990
     assert np.max(np.abs(dO.cpu().numpy()[keep] - dfd[keep])) <= 1e-4 * np.max(np.abs(dfd[keep]))
     # mixed precision: estimate at KKT 2e-5, derivative in FP64 from it
     O32, s32 = A.accord_fit(Xt, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=20000)
