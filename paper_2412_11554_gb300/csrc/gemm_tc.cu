@@ -43,6 +43,12 @@ constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
 constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
 constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 block per epilogue warp
 constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + 1024;
+// Tail after the epilogue buffers: 2 kStages + 5 mbarriers, the TMEM slot and
+// two flags, then the epilogue's FP64 partials [kEpiWarps][8] from kRedOffset.
+constexpr size_t kRedOffset = 128;
+static_assert((2 * kStages + 5) * 8 + 12 <= kRedOffset, "barriers overlap the epilogue partials");
+static_assert(kRedOffset + kEpiWarps * 8 * 8 <= 1024, "epilogue partials overflow the shared-memory tail");
+static_assert(kSmemBytes <= 232448, "more dynamic shared memory than one CTA may use");
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& mb, int& nb) {
   const int per_group = group_m * tiles_n;
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* stop_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
-  double* red = reinterpret_cast<double*>(smem + kStages * kStageBytes + kEpiBufBytes + 128);  // [kEpiWarps][8]
+  double* red = reinterpret_cast<double*>(smem + kStages * kStageBytes + kEpiBufBytes + kRedOffset);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
