@@ -520,7 +520,7 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     if (int e = setup_gram(P)) return e;
     // 0 = automatic: FP64 mode matches a dense eigensolver to rounding; the
     // mixed mode needs L only to set the tau <= 1/L floor
-    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-10);
+    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-8);
     ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st));
     nlaunch += 2;
     const int chunk = 8;

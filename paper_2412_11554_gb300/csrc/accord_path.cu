@@ -483,7 +483,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     gg.s_a = gg.s_b = K * L.ldo;
     gg.s_out = K * K;
     ACCORD_CK(launch_gemm_f64(kModeGram, gg, st));
-    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-10);
+    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-8);
     ACCORD_CK(launch_lanczos_init(ctrl, at<double>(ws, L.lz_v), K, st, (int)B, (int64_t)(L.lz_k + 1) * K));
     nlaunch += 2;
     const int chunk = 8;
