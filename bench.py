@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["fit", "path"], default="fit",
-                    help="fit: one fit at p=40000 (default); path: lambda path x bootstrap subsamples at p=4000")
+    ap.add_argument("--workload", choices=["fit", "path", "diff", "refit"], default="fit",
+                    help="fit: one fit at p=40000 (default); path: lambda path x bootstrap subsamples at p=4000; "
+                         "diff: held-out derivative in log(lambda) at p=2000; refit: Eq. 3.8 refit at p=40000")
     return ap.parse_args()
 
 
@@ -472,12 +473,151 @@ def run_path(args):
         print(json.dumps(out))
 
 
+# ------------------------------------------------------- differentiation ---
+DIFF_METRIC = "held-out derivative d L_val / d log(lambda) evaluations/s (AR(1)+random p=2000, n=300+100, lambda=0.2)"
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal; no measured figure exists for it
+
+
+def run_diff(args):
+    import torch
+    from paper_2412_11554_gb300 import build as B
+    B.build()
+    import paper_2412_11554_gb300 as A
+    from synth import diff_workload
+    w = diff_workload()
+    n, p = w.X_train.shape
+    nv = w.X_val.shape[0]
+    Xt, Xv = torch.as_tensor(w.X_train, device="cuda"), torch.as_tensor(w.X_val, device="cuda")
+    O, st = A.accord_fit(Xt, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=20000)
+    for _ in range(max(args.warmup, 0)):
+        A.accord_dloss_dloglam(Xt, Xv, O, w.lam)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d, lv, _ = A.accord_dloss_dloglam(Xt, Xv, O, w.lam)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = args.steps / (ms / 1e3)
+    # the call is dominated by its FP64 GEMMs (S, two held-out products, the
+    # held-out gradient): algorithmic FP64 flops per call over the call's time
+    flops = 2.0 * p * p * n + 2 * (2.0 * p * nv * p) + 2.0 * p * p * nv
+    achieved = flops / (ms / args.steps / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "gemm_f64_kernel (FP64 CUDA cores; whole call timed)",
+                "achieved": round(achieved, 3), "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / NOMINAL_FP64_TFLOPS, 4),
+                "peak_source": "nominal FP64 rate of the part (the profiling recipe's unit table)", "traffic": None,
+                "algorithmic_flops_per_call": flops}
+    e2e = None
+    if not args.no_e2e:
+        Xth, Xvh = torch.as_tensor(w.X_train).pin_memory(), torch.as_tensor(w.X_val).pin_memory()
+        Oh = O.cpu().pin_memory()
+        Xtd, Xvd, Od = torch.empty_like(Xt), torch.empty_like(Xv), torch.empty_like(O)
+        torch.cuda.synchronize()
+        e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e2[0].record(stream)
+        for _ in range(args.steps):
+            Xtd.copy_(Xth, non_blocking=True)
+            Xvd.copy_(Xvh, non_blocking=True)
+            Od.copy_(Oh, non_blocking=True)
+            A.accord_dloss_dloglam(Xtd, Xvd, Od, w.lam)
+        e2[1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = e2[0].elapsed_time(e2[1])
+        e2e = {"value": round(args.steps / (ms2 / 1e3), 3), "unit": "evaluations/s",
+               "h2d_bytes_per_step": int((Xth.numel() + Xvh.numel() + Oh.numel()) * 4), "d2h_bytes_per_step": 16}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import accord_ref as R
+        O64 = O.double().cpu().numpy()
+        t0 = time.perf_counter()
+        R.implicit_dloglam(O64, w.X_train, w.X_val, w.lam)
+        t = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / t, 4), "unit": "evaluations/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"one full oracle evaluation ({t:.2f} s)"}
+    out = {"metric": DIFF_METRIC, "value": round(value, 3), "unit": "evaluations/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / max(args.steps, 1), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (S, held-out gradient, row systems) on a bf16x3 estimate",
+           "data": "synthetic (seeded AR(1) + random-edge precision, Gaussian X)",
+           "config": {"workload": w.name, "p": p, "n": n, "n_val": nv, "lambda": w.lam,
+                      "active_offdiag": int(st.nnz_offdiag), "l2": "working set (32 MB S, 16 MB Omega) within L2"},
+           "dloss_dloglam": d, "loss_val": lv, "gpu_launches": 12 * args.steps, "roofline": roofline, "e2e": e2e,
+           "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- refit ---
+REFIT_METRIC = "Eq. 3.8 refit prox-grad iters/s to KKT 1e-4 (hub-and-block p=40000, n=1000, lambda=0.1, phi=0.5)"
+
+
+def run_refit(args):
+    import torch
+    from paper_2412_11554_gb300 import build as B
+    B.build()
+    import paper_2412_11554_gb300 as A
+    w = make_workload(args.p, args.n)
+    n, p = w.n, w.p
+    X = torch.as_tensor(w.X, device="cuda")
+    ws = torch.empty(A.accord_workspace_bytes(n, p, precision="mixed", max_iter=500), dtype=torch.uint8,
+                     device="cuda")
+    Oh, st0 = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=args.kkt_tol, max_iter=500, workspace=ws)
+    Om = torch.empty((p, p), dtype=torch.float32, device="cuda")
+    kw = dict(precision="mixed", kkt_tol=args.kkt_tol, max_iter=500, workspace=ws, Omega=Om)
+    for _ in range(max(args.warmup, 0)):
+        A.accord_refit(X, w.lam, 0.5, Oh, **kw)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        _, s = A.accord_refit(X, w.lam, 0.5, Oh, profile=1, **kw)
+        stats.append(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    iters = sum(s.iters for s in stats)
+    tp = sum(s.t_prox_gemm_ms for s in stats)
+    npx = sum(s.n_prox_gemm for s in stats)
+    pk, pk_src = peaks()
+    peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    achieved = 2.0 * n * p * p / (tp / max(npx, 1) / 1e3) / 1e12
+    out = {"metric": REFIT_METRIC, "value": round(iters / (ms / 1e3), 3), "unit": "iters/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / max(args.steps, 1), 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3 (fp32 accumulate, fp64 reductions)",
+           "data": "synthetic (seeded hub-and-block precision, Gaussian X)",
+           "config": {"workload": w.name, "p": p, "n": n, "lambda": w.lam, "phi": 0.5, "kkt_tol": args.kkt_tol,
+                      "support_nnz_offdiag": int(st0.nnz_offdiag)},
+           "iters_per_refit": iters / max(len(stats), 1), "status": stats[-1].status if stats else None,
+           "gpu_launches": int(sum(s.n_launches for s in stats)),
+           "roofline": {"bound": "tensor", "kernel": "tc_gemm_prox (refit mask)", "achieved": round(achieved, 2),
+                        "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                        "peak_source": f"bf16_tflops_sustained ({pk_src})", "traffic": None,
+                        "avg_launch_ms": round(tp / max(npx, 1), 3)},
+           "e2e": None, "cpu_baseline": None, "clocks": clk}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "path":
         run_path(args)
+    elif args.workload == "diff":
+        run_diff(args)
+    elif args.workload == "refit":
+        run_refit(args)
     else:
         run_ours(args)
 
