@@ -249,8 +249,9 @@ int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const
  *   Omega_hat device, p x p, element type per opts->precision (a converged estimate)
  *   dloss, loss_val  host (either may be NULL): the derivative and L(Omega_hat; X_val)
  *   dOmega    device or NULL: p x p dOmega-hat / dlog(lambda), element type per precision
- * S, the held-out gradient and the row systems are formed in FP64 in either
- * precision.  Errors: EINVAL; EUNSUPPORTED when a row's active set has more
+ * FP64 mode forms S and the held-out products with FP64 GEMMs; the mixed mode
+ * uses the split-BF16 tensor-core products (FP32 accumulation, S written in
+ * FP64, FP64 reductions).  The row systems are FP64 in both.  Errors: EINVAL; EUNSUPPORTED when a row's active set has more
  * than 128 entries; EDOMAIN when a row system is not positive definite (an
  * active set larger than the training rows can support) or Omega_hat has a
  * non-positive diagonal. */

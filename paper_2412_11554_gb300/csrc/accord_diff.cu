@@ -301,6 +301,7 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   const size_t S_off = take(c, (size_t)p * p * 8), Gv_off = take(c, (size_t)p * p * 8);
   const size_t om_off = take(c, (size_t)p * p * 8);
   const size_t x_off = take(c, (size_t)n * ldk * 8), xt_off = take(c, (size_t)p * ldn * 8);
+  const size_t g32_off = take(c, f64 ? 0 : (size_t)p * p * 4);  // mixed mode: FP32 held-out gradient
   Guard g;
   if (cudaMallocAsync(&g.ptr, c, st) != cudaSuccess) return kEnomem;
   g.st = st;
@@ -311,26 +312,56 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   if (f64) ACCORD_CK(cudaMemcpyAsync(Om64, Omega_hat, (size_t)p * p * 8, cudaMemcpyDeviceToDevice, st));
   else to_f64_kernel<float><<<blocks_for(p * p), 256, 0, st>>>(static_cast<const float*>(Omega_hat), p * p, Om64);
   ACCORD_CK(cudaGetLastError());
-  // S = X^T X / n of the training rows (FP64)
-  ACCORD_CK(launch_convert_x_f64(Xt, nullptr, n, p, at<double>(ws, x_off), ldk, at<double>(ws, xt_off), ldn, err,
-                                 st));
-  GemmF64Params gs{};
-  gs.A[0] = gs.A[1] = at<double>(ws, xt_off);
-  gs.lda = ldn;
-  gs.B = at<double>(ws, xt_off);
-  gs.ldb = ldn;
-  gs.M = p; gs.N = p; gs.K = n;
-  gs.out[0] = gs.out[1] = at<double>(ws, S_off);
-  gs.ldout = p;
-  gs.scale = 1.0 / (double)n;
-  ACCORD_CK(launch_gemm_f64(kModeGram, gs, st));
-  // held-out loss and its gradient -diag(1/omega) + Omega S_val (FP64)
-  accord_opts o64 = o;
-  o64.precision = ACCORD_FP64;
-  o64.penalize_diag = 0;
   double f = 0.0, gval = 0.0;
-  if (int e = accord_loss(Xv, n_val, p, Om64, 0.0, &o64, &f, &gval)) return e;
-  if (int e = accord_grad(Xv, n_val, p, Om64, 1, &o64, at<double>(ws, Gv_off))) return e;
+  if (f64) {
+    // S = X^T X / n of the training rows and the held-out loss and gradient
+    // -diag(1/omega) + Omega S_val, all in FP64
+    ACCORD_CK(launch_convert_x_f64(Xt, nullptr, n, p, at<double>(ws, x_off), ldk, at<double>(ws, xt_off), ldn, err,
+                                   st));
+    GemmF64Params gs{};
+    gs.A[0] = gs.A[1] = at<double>(ws, xt_off);
+    gs.lda = ldn;
+    gs.B = at<double>(ws, xt_off);
+    gs.ldb = ldn;
+    gs.M = p; gs.N = p; gs.K = n;
+    gs.out[0] = gs.out[1] = at<double>(ws, S_off);
+    gs.ldout = p;
+    gs.scale = 1.0 / (double)n;
+    ACCORD_CK(launch_gemm_f64(kModeGram, gs, st));
+    accord_opts o64 = o;
+    o64.precision = ACCORD_FP64;
+    o64.penalize_diag = 0;
+    if (int e = accord_loss(Xv, n_val, p, Om64, 0.0, &o64, &f, &gval)) return e;
+    if (int e = accord_grad(Xv, n_val, p, Om64, 1, &o64, at<double>(ws, Gv_off))) return e;
+  } else {
+    // mixed mode: the same products on the split-BF16 tensor-core path (FP32
+    // accumulation, FP64 output of S and FP64 reductions), the row systems in FP64
+    __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(at<double>(ws, x_off));
+    __nv_bfloat16* xl = xh + (size_t)n * ldk;
+    __nv_bfloat16* xth = reinterpret_cast<__nv_bfloat16*>(at<double>(ws, xt_off));
+    __nv_bfloat16* xtl = xth + (size_t)p * ldn;
+    ACCORD_CK(launch_convert_x_bf16(Xt, n, p, xh, xl, ldk, xth, xtl, ldn, err, st));
+    TcParams t{};
+    if (!encode_plane_map(&t.a_hi[0], xth, p, n, ldn, 128) || !encode_plane_map(&t.a_lo[0], xtl, p, n, ldn, 128) ||
+        !encode_plane_map(&t.b_hi, xth, p, n, ldn, tc_box_n()) || !encode_plane_map(&t.b_lo, xtl, p, n, ldn, tc_box_n()))
+      return kEcuda;
+    t.a_hi[1] = t.a_hi[0];
+    t.a_lo[1] = t.a_lo[0];
+    t.err = err + 1;
+    tc_shape(t, p, p, n);
+    t.out64 = at<double>(ws, S_off);
+    t.ldout64 = p;
+    t.scale = (float)(1.0 / (double)n);
+    ACCORD_CK(launch_tc_gemm(kModeGram, t, st));
+    accord_opts om = o;
+    om.precision = ACCORD_MIXED_BF16X3;
+    om.penalize_diag = 0;
+    if (int e = accord_loss(Xv, n_val, p, Omega_hat, 0.0, &om, &f, &gval)) return e;
+    float* G32 = at<float>(ws, g32_off);
+    if (int e = accord_grad(Xv, n_val, p, Omega_hat, 1, &om, G32)) return e;
+    to_f64_kernel<float><<<blocks_for(p * p), 256, 0, st>>>(G32, p * p, at<double>(ws, Gv_off));
+    ACCORD_CK(cudaGetLastError());
+  }
   // per-row implicit solves
   static int configured = -1;
   int dev = 0;

@@ -106,6 +106,21 @@ def test_implicit_derivative_matches_oracle(A):
     assert abs(d0 - d0_ref) <= 1e-10 * max(1.0, abs(d0_ref))
 
 
+def test_mixed_derivative_matches_fp64_on_same_estimate(A):
+    """The mixed mode (tensor-core S and held-out products) against the FP64
+    mode on the same FP32 estimate (p = 2000)."""
+    w = diff_workload()
+    Xt, Xv = dev(w.X_train), dev(w.X_val)
+    O32, st = A.accord_fit(Xt, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=20000)
+    assert st.status == 0
+    d32, l32, dO32 = A.accord_dloss_dloglam(Xt, Xv, O32, w.lam, want_domega=True)
+    d64, l64, dO64 = A.accord_dloss_dloglam(Xt, Xv, O32.double(), w.lam, want_domega=True)
+    assert abs(d32 - d64) <= 1e-3 * abs(d64), (d32, d64)
+    assert abs(l32 - l64) <= 1e-5 * abs(l64)
+    dd = dO64.cpu().numpy()
+    assert np.max(np.abs(dO32.double().cpu().numpy() - dd)) <= 1e-3 * np.max(np.abs(dd))
+
+
 def test_implicit_derivative_full_size_finite_differences(A):
     """p = 2000, n = 300 + 100 held out, lambda = 0.2: the implicit derivative
     at the FP64 GPU estimate equals the central difference (h = 1e-4) of the
