@@ -187,6 +187,4 @@ cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float*
 // X^T in FP32 (p x ldxt).
 cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 
-// -------------------------------------------------------- tcgen05 GEMMs ---
-struct TcOperands;  // defined in the tcgen05 translation unit's header
 }  // namespace accord

@@ -189,24 +189,11 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with 128-byte swizzling: rows of 128 bytes, 8-row swizzle atoms 1024 bytes
-// apart (stride byte offset), leading byte offset unused (1), descriptor
-// version 1 (bits 46-47), layout type SWIZZLE_128B (2, bits 61-63).  The
-// tile base must be 1024-byte aligned; stepping K by 16 BF16 elements within
-// the atom adds 32 bytes to the start address.
-__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Same for 64-byte swizzling: rows of 64 bytes (32 BF16), 8-row swizzle atoms
-// 512 bytes apart, layout type SWIZZLE_64B (4).  Stepping K by 16 elements
-// adds 32 bytes to the start address.
+// with 64-byte swizzling: rows of 64 bytes (32 BF16), 8-row swizzle atoms 512
+// bytes apart (stride byte offset), leading byte offset unused (1), descriptor
+// version 1 (bits 46-47), layout type SWIZZLE_64B (4, bits 61-63).  The tile
+// base must be 512-byte aligned; stepping K by 16 elements adds 32 bytes to
+// the start address.
 __device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
