@@ -36,20 +36,26 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 3; 2000 for --workload diff, whose step is ~1 ms, so that the "
+                         "clock sampler sees the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--p", type=int, default=40000)
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--kkt-tol", type=float, default=1e-4)
     ap.add_argument("--fp64-iters", type=int, default=2, help="FP64 iterations timed for the comparison (0: skip)")
+    ap.add_argument("--tf32-fits", type=int, default=1, help="TF32x3 fits timed for the comparison (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["fit", "path", "diff", "refit"], default="fit",
                     help="fit: one fit at p=40000 (default); path: lambda path x bootstrap subsamples at p=4000; "
                          "diff: held-out derivative in log(lambda) at p=2000; refit: Eq. 3.8 refit at p=40000")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2000 if args.workload == "diff" else 3
+    return args
 
 
 def make_workload(p, n):
@@ -287,6 +293,35 @@ def run_ours(args):
                 "time_to_kkt_s_extrapolated": round((s64.t_setup_ms + per_iter * mean_iters) / 1e3, 2),
                 "note": "per-iteration rate measured; time to KKT extrapolated with the mixed run's iteration count"}
 
+    # ----- TF32x3 mode on the same workload (whole fits to the same KKT) -----
+    tf32 = None
+    if args.tf32_fits > 0:
+        Ot = torch.empty((p, p), dtype=torch.float32, device="cuda")
+        st32 = []
+        torch.cuda.synchronize()
+        e3 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e3[0].record(stream)
+        for _ in range(args.tf32_fits):
+            _, s32 = A.accord_fit(X, w.lam, precision="tf32x3", kkt_tol=args.kkt_tol, max_iter=500, Omega=Ot,
+                                  profile=1)
+            st32.append(s32)
+        e3[1].record(stream)
+        torch.cuda.synchronize()
+        del Ot
+        ms3 = e3[0].elapsed_time(e3[1])
+        it3 = sum(s.iters for s in st32)
+        tp3 = sum(s.t_prox_gemm_ms for s in st32) / max(sum(s.n_prox_gemm for s in st32), 1)
+        # TF32 dense peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
+        peak32 = peak * 1.1 / 2.25
+        ach32 = flops / (tp3 / 1e3) / 1e12
+        tf32 = {"fits": len(st32), "iters_per_s": round(it3 / (ms3 / 1e3), 3),
+                "time_to_kkt_s": round(ms3 / len(st32) / 1e3, 3), "iters_per_fit": it3 / len(st32),
+                "final_kkt": st32[-1].kkt, "status": st32[-1].status,
+                "prox_gemm_ms": round(tp3, 3), "prox_achieved_tflops": round(ach32, 2),
+                "prox_executed_frac_of_tf32_peak": round(3 * ach32 / peak32, 4),
+                "tf32_peak_tflops": round(peak32, 1),
+                "peak_note": "measured sustained BF16 peak x nominal TF32/BF16 ratio 1.1/2.25"}
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         X64 = w.X.astype(np.float64)
@@ -313,7 +348,8 @@ def run_ours(args):
             "setup_ms": round(sum(s.t_setup_ms for s in stats) / max(len(stats), 1), 2),
             "final_kkt": stats[-1].kkt if stats else None, "status": stats[-1].status if stats else None,
             "gpu_launches": int(sum(s.n_launches for s in stats)),
-            "roofline": roofline, "e2e": e2e, "fp64_gpu": fp64, "cpu_baseline": cpu, "clocks": clk,
+            "roofline": roofline, "e2e": e2e, "fp64_gpu": fp64, "tf32x3_gpu": tf32, "cpu_baseline": cpu,
+            "clocks": clk,
             "kernel_source_digest": digest,
         }
         print(json.dumps(out))

@@ -51,6 +51,13 @@ extern "C" {
 #define ACCORD_FP64          0    /* FP64 GEMMs, FP64 iterate                           */
 #define ACCORD_MIXED_BF16X3  1    /* tcgen05 BF16 hi+lo split GEMMs (3 products),
                                      FP32 accumulation, FP32 iterate, FP64 reductions   */
+#define ACCORD_MIXED_TF32X3  2    /* as BF16X3 with TF32 hi+lo planes (kind::tf32 MMAs):
+                                     hi+lo carry an operand to 2^-24 instead of 2^-18,
+                                     so a product's error is that of its FP32
+                                     accumulation: more accurate than BF16X3 when n is
+                                     small (tens of samples), about as accurate from n
+                                     of a few hundred.  Half the tensor rate and twice
+                                     the plane bytes of BF16X3; same API data types.    */
 
 /* Columns of one trace row (one row per iterate Omega^t, t = 0..iters). */
 #define ACCORD_TRACE_FIELDS  8
@@ -63,7 +70,7 @@ extern "C" {
 #define ACCORD_TRACE_G       6    /* g(Omega^t) = ||Omega^t X^T||_F^2 / (2n)             */
 
 typedef struct accord_opts {
-    int32_t precision;       /* ACCORD_FP64 or ACCORD_MIXED_BF16X3 (default MIXED)          */
+    int32_t precision;       /* ACCORD_FP64, ACCORD_MIXED_BF16X3 (default) or ACCORD_MIXED_TF32X3 */
     int32_t tau_warm;        /* 0: every outer step starts at tau0 (Algorithm 1 as printed);
                                 1: starts at min(tau0, tau_{t-1}/beta)                         */
     int32_t max_iter;        /* accepted steps allowed (default 500)                           */

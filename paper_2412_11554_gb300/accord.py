@@ -19,8 +19,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "lib
 
 OK, NOT_CONVERGED = 0, 1
 EINVAL, EDOMAIN, ENONFINITE, EBACKTRACK, ENOMEM, ECUDA, EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
-FP64, MIXED_BF16X3 = 0, 1
-PRECISIONS = {"fp64": FP64, "mixed": MIXED_BF16X3, "bf16x3": MIXED_BF16X3}
+FP64, MIXED_BF16X3, MIXED_TF32X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED_BF16X3, "bf16x3": MIXED_BF16X3, "tf32x3": MIXED_TF32X3}
 TRACE_FIELDS = 8
 TRACE_COLUMNS = ("f", "kkt", "tau", "ntrials", "nnz", "delta", "g", "reserved")
 
@@ -311,14 +311,14 @@ def accord_postprocess(Omega: torch.Tensor, *, theta: bool = True, rho: bool = T
     return T, Rh
 
 
-def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, out: torch.Tensor | None = None,
-                  stream=None) -> torch.Tensor:
+def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, precision: str | None = None,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """dL/dX = (1/n) X Omega^T Omega of the smooth loss (n x p); precision
-    follows Omega's dtype (float64: FP64 mode, float32: mixed)."""
+    defaults to Omega's dtype (float64: FP64 mode, float32: BF16x3)."""
     lib = load_library()
     _check_x(X)
     n, p = X.shape
-    prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
+    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
     if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
         raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA tensor")
     if out is None:
@@ -332,17 +332,19 @@ def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, out: torch.Tensor | N
 
 
 def accord_dloss_dloglam(X_train: torch.Tensor, X_val: torch.Tensor, Omega_hat: torch.Tensor, lam: float, *,
-                         penalize_diag: bool = True, want_domega: bool = False, stream=None):
+                         penalize_diag: bool = True, want_domega: bool = False, precision: str | None = None,
+                         stream=None):
     """(d L_val / d log lambda, L_val, dOmega-hat / d log lambda or None) by
     implicit differentiation on the active set of Omega_hat (a converged
-    estimate for X_train at lam); precision follows Omega_hat's dtype."""
+    estimate for X_train at lam); precision defaults to Omega_hat's dtype
+    (float64: FP64 mode, float32: BF16x3)."""
     lib = load_library()
     _check_x(X_train)
     _check_x(X_val)
     n, p = X_train.shape
     if X_val.shape[1] != p:
         raise ValueError("X_train and X_val need the same number of columns")
-    prec = FP64 if Omega_hat.dtype == torch.float64 else MIXED_BF16X3
+    prec = PRECISIONS[precision] if precision else (FP64 if Omega_hat.dtype == torch.float64 else MIXED_BF16X3)
     o = accord_default_opts(precision=prec, penalize_diag=int(penalize_diag))
     o.stream = _stream_handle(stream)
     d, lv = ctypes.c_double(), ctypes.c_double()

@@ -35,8 +35,9 @@ struct Layout {
   int64_t n = 0, p = 0;
   int64_t ldo = 0;   // Omega (elements)
   int64_t ldy = 0;   // Y (elements)
-  int64_t ldk = 0;   // BF16 planes whose columns run over p
-  int64_t ldyk = 0;  // BF16 planes whose columns run over n
+  int pt = kPlaneBf16;  // operand-plane type of the mixed modes
+  int64_t ldk = 0;   // operand planes whose columns run over p
+  int64_t ldyk = 0;  // operand planes whose columns run over n
   int64_t tiles_prox = 0, tiles_y = 0, trace_rows = 0;
   size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0, part_fold = 0;
   size_t om[2] = {0, 0}, y[2] = {0, 0};
@@ -55,9 +56,12 @@ struct Layout {
 };
 
 
-Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max, bool sparse) {
+Layout make_layout(int64_t n, int64_t p, int precision, int max_iter, int lanczos_max, bool sparse) {
   Layout L;
+  const bool f64 = precision == ACCORD_FP64;
   L.f64 = f64;
+  L.pt = plane_type(precision);
+  const size_t pe = plane_bytes(L.pt);
   L.n = n;
   L.p = p;
   L.ldo = round_up(p, 8);
@@ -85,16 +89,16 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
     L.xt64 = take(c, (size_t)p * L.ldy * 8);
   } else {
     for (int b = 0; b < 2; ++b) L.y[b] = take(c, (size_t)p * L.ldy * 4);
-    L.om_hi = take(c, (size_t)p * L.ldk * 2);
-    L.om_lo = take(c, (size_t)p * L.ldk * 2);
+    L.om_hi = take(c, (size_t)p * L.ldk * pe);
+    L.om_lo = take(c, (size_t)p * L.ldk * pe);
     for (int b = 0; b < 2; ++b) {
-      L.y_hi[b] = take(c, (size_t)p * L.ldyk * 2);
-      L.y_lo[b] = take(c, (size_t)p * L.ldyk * 2);
+      L.y_hi[b] = take(c, (size_t)p * L.ldyk * pe);
+      L.y_lo[b] = take(c, (size_t)p * L.ldyk * pe);
     }
-    L.x_hi = take(c, (size_t)n * L.ldk * 2);
-    L.x_lo = take(c, (size_t)n * L.ldk * 2);
-    L.xt_hi = take(c, (size_t)p * L.ldyk * 2);
-    L.xt_lo = take(c, (size_t)p * L.ldyk * 2);
+    L.x_hi = take(c, (size_t)n * L.ldk * pe);
+    L.x_lo = take(c, (size_t)n * L.ldk * pe);
+    L.xt_hi = take(c, (size_t)p * L.ldyk * pe);
+    L.xt_lo = take(c, (size_t)p * L.ldyk * pe);
     L.sparse = sparse;
     if (sparse) {
       L.nbuckets = (p + kBucketRows - 1) / kBucketRows;
@@ -123,7 +127,7 @@ Layout make_layout(int64_t n, int64_t p, bool f64, int max_iter, int lanczos_max
 // The sparse Delta update runs in mixed mode; bucket keys hold a column index
 // in 25 bits.
 bool use_sparse(const accord_opts& o, int64_t p) {
-  return o.precision == ACCORD_MIXED_BF16X3 && o.sparse_update != 0 && p < (1 << 25) - 1;
+  return o.precision != ACCORD_FP64 && o.sparse_update != 0 && p < (1 << 25) - 1;
 }
 
 // Device GEMM wrappers that pick the precision's kernel family.
@@ -155,23 +159,23 @@ int setup_y(const Plan& P, int src, int dst) {
     ACCORD_CK(launch_gemm_f64(kModeY, g, P.st));
     return kOk;
   }
-  ACCORD_CK(launch_split_planes(at<float>(ws, L.om[src]), L.p, L.p, L.ldo, at<__nv_bfloat16>(ws, L.om_hi),
-                                at<__nv_bfloat16>(ws, L.om_lo), L.ldk, P.st));
+  ACCORD_CK(launch_split_planes(at<float>(ws, L.om[src]), L.p, L.p, L.ldo, at<void>(ws, L.om_hi),
+                                at<void>(ws, L.om_lo), L.ldk, L.pt, P.st));
   TcParams t{};
-  if (!encode_plane_map(&t.a_hi[0], at<__nv_bfloat16>(ws, L.om_hi), L.p, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t.a_lo[0], at<__nv_bfloat16>(ws, L.om_lo), L.p, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
-      !encode_plane_map(&t.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+  if (!encode_plane_map(&t.a_hi[0], at<void>(ws, L.om_hi), L.pt, L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.a_lo[0], at<void>(ws, L.om_lo), L.pt, L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.b_hi, at<void>(ws, L.x_hi), L.pt, L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, at<void>(ws, L.x_lo), L.pt, L.n, L.p, L.ldk, tc_box_n()))
     return kEcuda;
   t.a_hi[1] = t.a_hi[0];
   t.a_lo[1] = t.a_lo[0];
   t.ctrl = nullptr;
   t.err = P.err;
-  tc_shape(t, L.p, L.n, L.p);
+  tc_shape(t, L.p, L.n, L.p, L.pt);
   t.out[0] = t.out[1] = at<float>(ws, L.y[dst]);
   t.ldout = L.ldy;
-  t.out_hi[0] = t.out_hi[1] = at<__nv_bfloat16>(ws, L.y_hi[dst]);
-  t.out_lo[0] = t.out_lo[1] = at<__nv_bfloat16>(ws, L.y_lo[dst]);
+  t.out_hi[0] = t.out_hi[1] = at<void>(ws, L.y_hi[dst]);
+  t.out_lo[0] = t.out_lo[1] = at<void>(ws, L.y_lo[dst]);
   t.ldplane = L.ldyk;
   t.aux[0] = t.aux[1] = nullptr;
   t.part = at<double>(ws, L.part_y);
@@ -198,15 +202,15 @@ int setup_gram(const Plan& P) {
     return kOk;
   }
   TcParams t{};
-  if (!encode_plane_map(&t.a_hi[0], at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t.a_lo[0], at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
-      !encode_plane_map(&t.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+  if (!encode_plane_map(&t.a_hi[0], at<void>(ws, L.x_hi), L.pt, L.n, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.a_lo[0], at<void>(ws, L.x_lo), L.pt, L.n, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t.b_hi, at<void>(ws, L.x_hi), L.pt, L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, at<void>(ws, L.x_lo), L.pt, L.n, L.p, L.ldk, tc_box_n()))
     return kEcuda;
   t.a_hi[1] = t.a_hi[0];
   t.a_lo[1] = t.a_lo[0];
   t.err = P.err;
-  tc_shape(t, L.n, L.n, L.p);
+  tc_shape(t, L.n, L.n, L.p, L.pt);
   t.out64 = at<double>(ws, L.gram);
   t.ldout64 = L.n;
   t.scale = 1.f / (float)L.n;
@@ -268,22 +272,22 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
   }
   TcParams& t2 = T.t2;
   for (int b = 0; b < 2; ++b) {
-    if (!encode_plane_map(&t2.a_hi[b], at<__nv_bfloat16>(ws, L.y_hi[b]), L.p, L.n, L.ldyk, 128) ||
-        !encode_plane_map(&t2.a_lo[b], at<__nv_bfloat16>(ws, L.y_lo[b]), L.p, L.n, L.ldyk, 128))
+    if (!encode_plane_map(&t2.a_hi[b], at<void>(ws, L.y_hi[b]), L.pt, L.p, L.n, L.ldyk, 128) ||
+        !encode_plane_map(&t2.a_lo[b], at<void>(ws, L.y_lo[b]), L.pt, L.p, L.n, L.ldyk, 128))
       return kEcuda;
   }
-  if (!encode_plane_map(&t2.b_hi, at<__nv_bfloat16>(ws, L.xt_hi), L.p, L.n, L.ldyk, tc_box_n()) ||
-      !encode_plane_map(&t2.b_lo, at<__nv_bfloat16>(ws, L.xt_lo), L.p, L.n, L.ldyk, tc_box_n()))
+  if (!encode_plane_map(&t2.b_hi, at<void>(ws, L.xt_hi), L.pt, L.p, L.n, L.ldyk, tc_box_n()) ||
+      !encode_plane_map(&t2.b_lo, at<void>(ws, L.xt_lo), L.pt, L.p, L.n, L.ldyk, tc_box_n()))
     return kEcuda;
   t2.ctrl = P.ctrl;
   t2.err = P.err;
   t2.a_nxt = 0;
-  tc_shape(t2, L.p, L.p, L.n);
+  tc_shape(t2, L.p, L.p, L.n, L.pt);
   t2.out[0] = at<float>(ws, L.om[0]);
   t2.out[1] = at<float>(ws, L.om[1]);
   t2.ldout = L.ldo;
-  t2.out_hi[0] = t2.out_hi[1] = at<__nv_bfloat16>(ws, L.om_hi);
-  t2.out_lo[0] = t2.out_lo[1] = at<__nv_bfloat16>(ws, L.om_lo);
+  t2.out_hi[0] = t2.out_hi[1] = at<void>(ws, L.om_hi);
+  t2.out_lo[0] = t2.out_lo[1] = at<void>(ws, L.om_lo);
   t2.ldplane = L.ldk;
   t2.aux[0] = at<float>(ws, L.om[0]);
   t2.aux[1] = at<float>(ws, L.om[1]);
@@ -294,23 +298,23 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
   t2.scale = (float)(1.0 / (double)L.n);
 
   TcParams& t1 = T.t1;
-  if (!encode_plane_map(&t1.a_hi[0], at<__nv_bfloat16>(ws, L.om_hi), L.p, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t1.a_lo[0], at<__nv_bfloat16>(ws, L.om_lo), L.p, L.p, L.ldk, 128) ||
-      !encode_plane_map(&t1.b_hi, at<__nv_bfloat16>(ws, L.x_hi), L.n, L.p, L.ldk, tc_box_n()) ||
-      !encode_plane_map(&t1.b_lo, at<__nv_bfloat16>(ws, L.x_lo), L.n, L.p, L.ldk, tc_box_n()))
+  if (!encode_plane_map(&t1.a_hi[0], at<void>(ws, L.om_hi), L.pt, L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t1.a_lo[0], at<void>(ws, L.om_lo), L.pt, L.p, L.p, L.ldk, 128) ||
+      !encode_plane_map(&t1.b_hi, at<void>(ws, L.x_hi), L.pt, L.n, L.p, L.ldk, tc_box_n()) ||
+      !encode_plane_map(&t1.b_lo, at<void>(ws, L.x_lo), L.pt, L.n, L.p, L.ldk, tc_box_n()))
     return kEcuda;
   t1.a_hi[1] = t1.a_hi[0];
   t1.a_lo[1] = t1.a_lo[0];
   t1.ctrl = P.ctrl;
   t1.err = P.err;
   t1.a_nxt = 1;
-  tc_shape(t1, L.p, L.n, L.p);
+  tc_shape(t1, L.p, L.n, L.p, L.pt);
   t1.out[0] = at<float>(ws, L.y[0]);
   t1.out[1] = at<float>(ws, L.y[1]);
   t1.ldout = L.ldy;
   for (int b = 0; b < 2; ++b) {
-    t1.out_hi[b] = at<__nv_bfloat16>(ws, L.y_hi[b]);
-    t1.out_lo[b] = at<__nv_bfloat16>(ws, L.y_lo[b]);
+    t1.out_hi[b] = at<void>(ws, L.y_hi[b]);
+    t1.out_lo[b] = at<void>(ws, L.y_lo[b]);
   }
   t1.ldplane = L.ldyk;
   t1.aux[0] = at<float>(ws, L.y[0]);
@@ -332,8 +336,8 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
     for (int b = 0; b < 2; ++b) {
       sy.y[b] = at<float>(ws, L.y[b]);
       sy.yw[b] = at<float>(ws, L.y[b]);
-      sy.y_hi[b] = at<__nv_bfloat16>(ws, L.y_hi[b]);
-      sy.y_lo[b] = at<__nv_bfloat16>(ws, L.y_lo[b]);
+      sy.y_hi[b] = at<void>(ws, L.y_hi[b]);
+      sy.y_lo[b] = at<void>(ws, L.y_lo[b]);
     }
     sy.xt = at<float>(ws, L.xt32);
     sy.keys = at<uint32_t>(ws, L.bkt_keys);
@@ -347,6 +351,7 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
     sy.ldy = L.ldy;
     sy.ldyk = L.ldyk;
     sy.part = at<double>(ws, L.part_sy);
+    sy.ptype = L.pt;
   }
   return kOk;
 }
@@ -394,7 +399,7 @@ int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nla
     // Y+ = Y + Delta X^T: sparse update, or the dense fallback when a bucket
     // overflowed (each kernel checks ctrl->dense and exits when not its turn)
     ACCORD_CK(launch_delta_planes(P.ctrl, at<float>(P.ws, L.om[0]), at<float>(P.ws, L.om[1]), L.p, L.ldo,
-                                  at<__nv_bfloat16>(P.ws, L.om_hi), at<__nv_bfloat16>(P.ws, L.om_lo), L.ldk, P.st));
+                                  at<void>(P.ws, L.om_hi), at<void>(P.ws, L.om_lo), L.ldk, L.pt, P.st));
     ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
     ACCORD_CK(launch_sparse_y(T.sy, P.st));
     nlaunch += 2;
@@ -433,7 +438,7 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   if (!f64 && (n > 2147483647LL / 2 || p > 2147483647LL / 2)) return kEinval;
 
   Plan P;
-  P.L = make_layout(n, p, f64, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p));
+  P.L = make_layout(n, p, o.precision, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p));
   P.st = static_cast<cudaStream_t>(o.stream);
   Guard guard;
   if (workspace == nullptr) {
@@ -470,9 +475,9 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     ACCORD_CK(launch_convert_x_f64(X32, X64in, n, p, at<double>(ws, L.x64), L.ldo, at<double>(ws, L.xt64), L.ldy,
                                    at<int>(ws, L.bad), P.st));
   } else {
-    ACCORD_CK(launch_convert_x_bf16(X32, n, p, at<__nv_bfloat16>(ws, L.x_hi), at<__nv_bfloat16>(ws, L.x_lo), L.ldk,
-                                    at<__nv_bfloat16>(ws, L.xt_hi), at<__nv_bfloat16>(ws, L.xt_lo), L.ldyk,
-                                    at<int>(ws, L.bad), P.st));
+    ACCORD_CK(launch_convert_x_planes(X32, n, p, at<void>(ws, L.x_hi), at<void>(ws, L.x_lo), L.ldk,
+                                      at<void>(ws, L.xt_hi), at<void>(ws, L.xt_lo), L.ldyk, at<int>(ws, L.bad), L.pt,
+                                      P.st));
     if (L.sparse) {
       ACCORD_CK(launch_transpose_x_f32(X32, n, p, at<float>(ws, L.xt32), L.ldy, P.st));
       ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bkt_cnt), 0, (size_t)L.nbuckets * 4, P.st));
@@ -500,10 +505,10 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     } else if (L.sparse) {
       ACCORD_CK(cudaMemcpyAsync(at<float>(ws, L.y[0]), at<float>(ws, L.xt32), (size_t)p * L.ldy * 4,
                                 cudaMemcpyDeviceToDevice, P.st));
-      ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_hi[0]), at<__nv_bfloat16>(ws, L.xt_hi),
-                                (size_t)p * L.ldyk * 2, cudaMemcpyDeviceToDevice, P.st));
-      ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_lo[0]), at<__nv_bfloat16>(ws, L.xt_lo),
-                                (size_t)p * L.ldyk * 2, cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(cudaMemcpyAsync(at<void>(ws, L.y_hi[0]), at<void>(ws, L.xt_hi), (size_t)p * L.ldyk * plane_bytes(L.pt),
+                                cudaMemcpyDeviceToDevice, P.st));
+      ACCORD_CK(cudaMemcpyAsync(at<void>(ws, L.y_lo[0]), at<void>(ws, L.xt_lo), (size_t)p * L.ldyk * plane_bytes(L.pt),
+                                cudaMemcpyDeviceToDevice, P.st));
       ACCORD_CK(launch_rows_norm2(at<float>(ws, L.y[0]), 0, p, n, L.ldy, at<double>(ws, L.part_y), &nyp, P.st));
       nlaunch += 1;
     } else {
@@ -676,7 +681,7 @@ size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* optp) {
   accord_default_opts(&o);
   if (optp) o = *optp;
   if (n < 1 || p < 1 || check_opts(o) != kOk) return 0;
-  return make_layout(n, p, o.precision == ACCORD_FP64, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p)).total;
+  return make_layout(n, p, o.precision, o.max_iter, o.lipschitz_max_iter, use_sparse(o, p)).total;
 }
 
 int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, void* Omega,

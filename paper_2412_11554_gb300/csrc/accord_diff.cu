@@ -176,7 +176,7 @@ unsigned blocks_for(int64_t count) {
 
 int check_x_omega(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts& o) {
   if (X == nullptr || Omega == nullptr || n < 1 || p < 1) return kEinval;
-  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
+  if (!known_precision(o.precision)) return kEinval;
   return check_device();
 }
 
@@ -188,6 +188,8 @@ int read_err(const int* err, cudaStream_t st, int* host) {
 
 int grad_x_impl(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts& o, void* GX) {
   const bool f64 = o.precision == ACCORD_FP64;
+  const int pt = plane_type(o.precision);
+  const size_t pe = plane_bytes(pt);
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   const int64_t ldk = round_up(p, 8), ldn = round_up(n, 8);
   size_t c = 0;
@@ -200,15 +202,15 @@ int grad_x_impl(const float* X, int64_t n, int64_t p, const void* Omega, const a
     om_a = take(c, (size_t)p * ldk * 8);         // Omega copy
     omt_a = take(c, (size_t)p * ldk * 8);        // Omega^T
   } else {
-    x_a = take(c, (size_t)n * ldk * 2);          // X planes
-    x_b = take(c, (size_t)n * ldk * 2);
-    tmp = take(c, (size_t)p * ldn * 2 * 2);      // X^T planes (written by the conversion)
-    yt_a = take(c, (size_t)n * ldk * 2);         // Y^T planes
-    yt_b = take(c, (size_t)n * ldk * 2);
-    om_a = take(c, (size_t)p * ldk * 2);         // Omega planes
-    om_b = take(c, (size_t)p * ldk * 2);
-    omt_a = take(c, (size_t)p * ldk * 2);        // Omega^T planes
-    omt_b = take(c, (size_t)p * ldk * 2);
+    x_a = take(c, (size_t)n * ldk * pe);         // X planes
+    x_b = take(c, (size_t)n * ldk * pe);
+    tmp = take(c, (size_t)p * ldn * pe * 2);     // X^T planes (written by the conversion)
+    yt_a = take(c, (size_t)n * ldk * pe);        // Y^T planes
+    yt_b = take(c, (size_t)n * ldk * pe);
+    om_a = take(c, (size_t)p * ldk * pe);        // Omega planes
+    om_b = take(c, (size_t)p * ldk * pe);
+    omt_a = take(c, (size_t)p * ldk * pe);       // Omega^T planes
+    omt_b = take(c, (size_t)p * ldk * pe);
   }
   const size_t f32t = take(c, f64 ? 0 : (size_t)p * ldk * 4);  // Omega^T in FP32
   Guard g;
@@ -242,40 +244,41 @@ int grad_x_impl(const float* X, int64_t n, int64_t p, const void* Omega, const a
     b.scale = 1.0 / (double)n;
     ACCORD_CK(launch_gemm_f64(kModeGram, b, st));
   } else {
-    __nv_bfloat16* xh = at<__nv_bfloat16>(ws, x_a);
-    __nv_bfloat16* xl = at<__nv_bfloat16>(ws, x_b);
-    __nv_bfloat16* xth = at<__nv_bfloat16>(ws, tmp);
-    __nv_bfloat16* xtl = xth + (size_t)p * ldn;
-    ACCORD_CK(launch_convert_x_bf16(X, n, p, xh, xl, ldk, xth, xtl, ldn, err, st));
+    void* xh = at<void>(ws, x_a);
+    void* xl = at<void>(ws, x_b);
+    void* xth = at<void>(ws, tmp);
+    void* xtl = at<char>(ws, tmp) + (size_t)p * ldn * pe;
+    ACCORD_CK(launch_convert_x_planes(X, n, p, xh, xl, ldk, xth, xtl, ldn, err, pt, st));
     const float* Om = static_cast<const float*>(Omega);
-    ACCORD_CK(launch_split_planes(Om, p, p, p, at<__nv_bfloat16>(ws, om_a), at<__nv_bfloat16>(ws, om_b), ldk, st));
+    ACCORD_CK(launch_split_planes(Om, p, p, p, at<void>(ws, om_a), at<void>(ws, om_b), ldk, pt, st));
     ACCORD_CK(launch_transpose_x_f32(Om, p, p, at<float>(ws, f32t), ldk, st));
-    ACCORD_CK(launch_split_planes(at<float>(ws, f32t), p, p, ldk, at<__nv_bfloat16>(ws, omt_a),
-                                  at<__nv_bfloat16>(ws, omt_b), ldk, st));
+    ACCORD_CK(launch_split_planes(at<float>(ws, f32t), p, p, ldk, at<void>(ws, omt_a), at<void>(ws, omt_b), ldk, pt,
+                                  st));
     TcParams a{};  // Y^T = X Omega^T, stored as planes
-    if (!encode_plane_map(&a.a_hi[0], xh, n, p, ldk, 128) || !encode_plane_map(&a.a_lo[0], xl, n, p, ldk, 128) ||
-        !encode_plane_map(&a.b_hi, at<__nv_bfloat16>(ws, om_a), p, p, ldk, tc_box_n()) ||
-        !encode_plane_map(&a.b_lo, at<__nv_bfloat16>(ws, om_b), p, p, ldk, tc_box_n()))
+    if (!encode_plane_map(&a.a_hi[0], xh, pt, n, p, ldk, 128) ||
+        !encode_plane_map(&a.a_lo[0], xl, pt, n, p, ldk, 128) ||
+        !encode_plane_map(&a.b_hi, at<void>(ws, om_a), pt, p, p, ldk, tc_box_n()) ||
+        !encode_plane_map(&a.b_lo, at<void>(ws, om_b), pt, p, p, ldk, tc_box_n()))
       return kEcuda;
     a.a_hi[1] = a.a_hi[0];
     a.a_lo[1] = a.a_lo[0];
     a.err = err + 1;
-    tc_shape(a, n, p, p);
-    a.out_hi[0] = a.out_hi[1] = at<__nv_bfloat16>(ws, yt_a);
-    a.out_lo[0] = a.out_lo[1] = at<__nv_bfloat16>(ws, yt_b);
+    tc_shape(a, n, p, p, pt);
+    a.out_hi[0] = a.out_hi[1] = at<void>(ws, yt_a);
+    a.out_lo[0] = a.out_lo[1] = at<void>(ws, yt_b);
     a.ldplane = ldk;
     a.scale = 1.f;
     ACCORD_CK(launch_tc_gemm(kModeY, a, st));
     TcParams b{};  // dL/dX = (1/n) Y^T Omega
-    if (!encode_plane_map(&b.a_hi[0], at<__nv_bfloat16>(ws, yt_a), n, p, ldk, 128) ||
-        !encode_plane_map(&b.a_lo[0], at<__nv_bfloat16>(ws, yt_b), n, p, ldk, 128) ||
-        !encode_plane_map(&b.b_hi, at<__nv_bfloat16>(ws, omt_a), p, p, ldk, tc_box_n()) ||
-        !encode_plane_map(&b.b_lo, at<__nv_bfloat16>(ws, omt_b), p, p, ldk, tc_box_n()))
+    if (!encode_plane_map(&b.a_hi[0], at<void>(ws, yt_a), pt, n, p, ldk, 128) ||
+        !encode_plane_map(&b.a_lo[0], at<void>(ws, yt_b), pt, n, p, ldk, 128) ||
+        !encode_plane_map(&b.b_hi, at<void>(ws, omt_a), pt, p, p, ldk, tc_box_n()) ||
+        !encode_plane_map(&b.b_lo, at<void>(ws, omt_b), pt, p, p, ldk, tc_box_n()))
       return kEcuda;
     b.a_hi[1] = b.a_hi[0];
     b.a_lo[1] = b.a_lo[0];
     b.err = err + 1;
-    tc_shape(b, n, p, p);
+    tc_shape(b, n, p, p, pt);
     b.out[0] = b.out[1] = static_cast<float*>(GX);
     b.ldout = p;
     b.scale = (float)(1.0 / (double)n);
@@ -294,6 +297,7 @@ int grad_x_impl(const float* X, int64_t n, int64_t p, const void* Omega, const a
 int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64_t p, const void* Omega_hat,
                double lambda, const accord_opts& o, double* dloss, double* loss_val, void* dOmega) {
   const bool f64 = o.precision == ACCORD_FP64;
+  const int pt = plane_type(o.precision);
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   const int64_t ldk = round_up(p, 8), ldn = round_up(n, 8);
   size_t c = 0;
@@ -334,27 +338,31 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
     if (int e = accord_loss(Xv, n_val, p, Om64, 0.0, &o64, &f, &gval)) return e;
     if (int e = accord_grad(Xv, n_val, p, Om64, 1, &o64, at<double>(ws, Gv_off))) return e;
   } else {
-    // mixed mode: the same products on the split-BF16 tensor-core path (FP32
-    // accumulation, FP64 output of S and FP64 reductions), the row systems in FP64
-    __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(at<double>(ws, x_off));
-    __nv_bfloat16* xl = xh + (size_t)n * ldk;
-    __nv_bfloat16* xth = reinterpret_cast<__nv_bfloat16*>(at<double>(ws, xt_off));
-    __nv_bfloat16* xtl = xth + (size_t)p * ldn;
-    ACCORD_CK(launch_convert_x_bf16(Xt, n, p, xh, xl, ldk, xth, xtl, ldn, err, st));
+    // mixed modes: the same products on the split-operand tensor-core path
+    // (FP32 accumulation, FP64 output of S and FP64 reductions), the row
+    // systems in FP64.  Both planes of X (and of X^T) fit in the FP64 buffer.
+    const size_t pe = plane_bytes(pt);
+    void* xh = at<void>(ws, x_off);
+    void* xl = at<char>(ws, x_off) + (size_t)n * ldk * pe;
+    void* xth = at<void>(ws, xt_off);
+    void* xtl = at<char>(ws, xt_off) + (size_t)p * ldn * pe;
+    ACCORD_CK(launch_convert_x_planes(Xt, n, p, xh, xl, ldk, xth, xtl, ldn, err, pt, st));
     TcParams t{};
-    if (!encode_plane_map(&t.a_hi[0], xth, p, n, ldn, 128) || !encode_plane_map(&t.a_lo[0], xtl, p, n, ldn, 128) ||
-        !encode_plane_map(&t.b_hi, xth, p, n, ldn, tc_box_n()) || !encode_plane_map(&t.b_lo, xtl, p, n, ldn, tc_box_n()))
+    if (!encode_plane_map(&t.a_hi[0], xth, pt, p, n, ldn, 128) ||
+        !encode_plane_map(&t.a_lo[0], xtl, pt, p, n, ldn, 128) ||
+        !encode_plane_map(&t.b_hi, xth, pt, p, n, ldn, tc_box_n()) ||
+        !encode_plane_map(&t.b_lo, xtl, pt, p, n, ldn, tc_box_n()))
       return kEcuda;
     t.a_hi[1] = t.a_hi[0];
     t.a_lo[1] = t.a_lo[0];
     t.err = err + 1;
-    tc_shape(t, p, p, n);
+    tc_shape(t, p, p, n, pt);
     t.out64 = at<double>(ws, S_off);
     t.ldout64 = p;
     t.scale = (float)(1.0 / (double)n);
     ACCORD_CK(launch_tc_gemm(kModeGram, t, st));
     accord_opts om = o;
-    om.precision = ACCORD_MIXED_BF16X3;
+    om.precision = o.precision;
     om.penalize_diag = 0;
     if (int e = accord_loss(Xv, n_val, p, Omega_hat, 0.0, &om, &f, &gval)) return e;
     float* G32 = at<float>(ws, g32_off);

@@ -44,7 +44,8 @@ struct Scratch {
 
 int check_common(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts& o) {
   if (X == nullptr || Omega == nullptr || n < 1 || p < 1) return kEinval;
-  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
+  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3 && o.precision != ACCORD_MIXED_TF32X3)
+    return kEinval;
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return kEcuda;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -56,8 +57,9 @@ int check_common(const float* X, int64_t n, int64_t p, const void* Omega, const 
 // Sizes of one scratch allocation (two passes: measure, then carve).
 struct EvalBuffers {
   double *x64 = nullptr, *xt64 = nullptr, *y64 = nullptr;
-  __nv_bfloat16 *om_hi = nullptr, *om_lo = nullptr, *x_hi = nullptr, *x_lo = nullptr;
-  __nv_bfloat16 *xt_hi = nullptr, *xt_lo = nullptr, *y_hi = nullptr, *y_lo = nullptr;
+  int pt = kPlaneBf16;  // operand-plane type (mixed modes)
+  void *om_hi = nullptr, *om_lo = nullptr, *x_hi = nullptr, *x_lo = nullptr;
+  void *xt_hi = nullptr, *xt_lo = nullptr, *y_hi = nullptr, *y_lo = nullptr;
   double *part_y = nullptr, *part_om = nullptr, *res = nullptr;
   int* err = nullptr;
 };
@@ -73,15 +75,16 @@ void carve(Bump& b, EvalBuffers& B, bool f64, bool need_y, int64_t n, int64_t p,
     B.xt64 = b.take<double>((size_t)p * ldyk);
     if (need_y) B.y64 = b.take<double>((size_t)p * ldyk);
   } else {
-    B.om_hi = b.take<__nv_bfloat16>((size_t)p * ldk);
-    B.om_lo = b.take<__nv_bfloat16>((size_t)p * ldk);
-    B.x_hi = b.take<__nv_bfloat16>((size_t)n * ldk);
-    B.x_lo = b.take<__nv_bfloat16>((size_t)n * ldk);
-    B.xt_hi = b.take<__nv_bfloat16>((size_t)p * ldyk);
-    B.xt_lo = b.take<__nv_bfloat16>((size_t)p * ldyk);
+    const size_t pe = plane_bytes(B.pt);
+    B.om_hi = b.take<char>((size_t)p * ldk * pe);
+    B.om_lo = b.take<char>((size_t)p * ldk * pe);
+    B.x_hi = b.take<char>((size_t)n * ldk * pe);
+    B.x_lo = b.take<char>((size_t)n * ldk * pe);
+    B.xt_hi = b.take<char>((size_t)p * ldyk * pe);
+    B.xt_lo = b.take<char>((size_t)p * ldyk * pe);
     if (need_y) {
-      B.y_hi = b.take<__nv_bfloat16>((size_t)p * ldyk);
-      B.y_lo = b.take<__nv_bfloat16>((size_t)p * ldyk);
+      B.y_hi = b.take<char>((size_t)p * ldyk * pe);
+      B.y_lo = b.take<char>((size_t)p * ldyk * pe);
     }
   }
 }
@@ -105,12 +108,13 @@ int eval_y(const EvalBuffers& B, bool f64, const float* X, const void* Omega, in
     EVAL_CK(launch_gemm_f64(kModeY, g, st));
     return kOk;
   }
-  EVAL_CK(launch_convert_x_bf16(X, n, p, B.x_hi, B.x_lo, ldk, B.xt_hi, B.xt_lo, ldyk, B.err, st));
-  EVAL_CK(launch_split_planes(static_cast<const float*>(Omega), p, p, p, B.om_hi, B.om_lo, ldk, st));
+  EVAL_CK(launch_convert_x_planes(X, n, p, B.x_hi, B.x_lo, ldk, B.xt_hi, B.xt_lo, ldyk, B.err, B.pt, st));
+  EVAL_CK(launch_split_planes(static_cast<const float*>(Omega), p, p, p, B.om_hi, B.om_lo, ldk, B.pt, st));
   TcParams t{};
-  if (!encode_plane_map(&t.a_hi[0], B.om_hi, p, p, ldk, 128) || !encode_plane_map(&t.a_lo[0], B.om_lo, p, p, ldk, 128) ||
-      !encode_plane_map(&t.b_hi, B.x_hi, n, p, ldk, tc_box_n()) ||
-      !encode_plane_map(&t.b_lo, B.x_lo, n, p, ldk, tc_box_n()))
+  if (!encode_plane_map(&t.a_hi[0], B.om_hi, B.pt, p, p, ldk, 128) ||
+      !encode_plane_map(&t.a_lo[0], B.om_lo, B.pt, p, p, ldk, 128) ||
+      !encode_plane_map(&t.b_hi, B.x_hi, B.pt, n, p, ldk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, B.x_lo, B.pt, n, p, ldk, tc_box_n()))
   {
     set_last_error(__FILE__, __LINE__, "cuTensorMapEncodeTiled rejected an operand");
     return kEcuda;
@@ -118,7 +122,7 @@ int eval_y(const EvalBuffers& B, bool f64, const float* X, const void* Omega, in
   t.a_hi[1] = t.a_hi[0];
   t.a_lo[1] = t.a_lo[0];
   t.err = B.err + 1;
-  tc_shape(t, p, n, p);
+  tc_shape(t, p, n, p, B.pt);
   t.out_hi[0] = t.out_hi[1] = store_y ? B.y_hi : nullptr;
   t.out_lo[0] = t.out_lo[1] = store_y ? B.y_lo : nullptr;
   t.ldplane = ldyk;
@@ -162,6 +166,7 @@ int accord_loss(const float* X, int64_t n, int64_t p, const void* Omega, double 
   const int64_t tiles = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
   Bump meas;
   EvalBuffers B;
+  B.pt = o.precision == ACCORD_MIXED_TF32X3 ? kPlaneTf32 : kPlaneBf16;
   carve(meas, B, f64, false, n, p, tiles);
   Scratch s;
   if (cudaMallocAsync(&s.ptr, meas.used, st) != cudaSuccess) return kEnomem;
@@ -197,6 +202,7 @@ int accord_grad(const float* X, int64_t n, int64_t p, const void* Omega, int smo
   const int64_t ldyk = round_up(n, 8);
   Bump meas;
   EvalBuffers B;
+  B.pt = o.precision == ACCORD_MIXED_TF32X3 ? kPlaneTf32 : kPlaneBf16;
   carve(meas, B, f64, true, n, p, tiles);
   Scratch s;
   if (cudaMallocAsync(&s.ptr, meas.used, st) != cudaSuccess) return kEnomem;
@@ -222,14 +228,15 @@ int accord_grad(const float* X, int64_t n, int64_t p, const void* Omega, int smo
     EVAL_CK(launch_gemm_f64(kModeGrad, g, st));
   } else {
     TcParams t{};
-    if (!encode_plane_map(&t.a_hi[0], B.y_hi, p, n, ldyk, 128) || !encode_plane_map(&t.a_lo[0], B.y_lo, p, n, ldyk, 128) ||
-        !encode_plane_map(&t.b_hi, B.xt_hi, p, n, ldyk, tc_box_n()) ||
-        !encode_plane_map(&t.b_lo, B.xt_lo, p, n, ldyk, tc_box_n()))
+    if (!encode_plane_map(&t.a_hi[0], B.y_hi, B.pt, p, n, ldyk, 128) ||
+        !encode_plane_map(&t.a_lo[0], B.y_lo, B.pt, p, n, ldyk, 128) ||
+        !encode_plane_map(&t.b_hi, B.xt_hi, B.pt, p, n, ldyk, tc_box_n()) ||
+        !encode_plane_map(&t.b_lo, B.xt_lo, B.pt, p, n, ldyk, tc_box_n()))
       return kEcuda;
     t.a_hi[1] = t.a_hi[0];
     t.a_lo[1] = t.a_lo[0];
     t.err = B.err + 1;
-    tc_shape(t, p, p, n);
+    tc_shape(t, p, p, n, B.pt);
     t.out[0] = t.out[1] = static_cast<float*>(G_out);
     t.ldout = p;
     t.aux[0] = t.aux[1] = static_cast<const float*>(Omega);

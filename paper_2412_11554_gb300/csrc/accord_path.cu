@@ -41,9 +41,10 @@ struct GatherParams {
   double* x64;           // K x p rows (FP64), ld ldx, chain stride sx
   double* xt64;          // p x K (FP64, FP64 mode), ld ldt, chain stride st
   float* xt32;           // p x K (FP32, mixed mode)
-  __nv_bfloat16 *x_hi, *x_lo;    // K x p planes (mixed mode), ld ldx
-  __nv_bfloat16 *xt_hi, *xt_lo;  // p x K planes (mixed mode), ld ldt
+  void *x_hi, *x_lo;    // K x p planes (mixed modes, type pt), ld ldx
+  void *xt_hi, *xt_lo;  // p x K planes (mixed modes, type pt), ld ldt
   int64_t ldx, sx, ldt, st, sxp, stp;
+  int pt;
   int* bad;
 };
 
@@ -63,12 +64,7 @@ __global__ void gather_kernel(GatherParams g) {
     tile[i][threadIdx.x] = v;
     if (col < g.p) {
       if (g.x64) g.x64[c * g.sx + j * g.ldx + col] = v;
-      if (g.x_hi) {
-        __nv_bfloat16 h, l;
-        split_bf16((float)v, h, l);
-        g.x_hi[c * g.sxp + j * g.ldx + col] = h;
-        g.x_lo[c * g.sxp + j * g.ldx + col] = l;
-      }
+      if (g.x_hi) store_split(g.x_hi, g.x_lo, c * g.sxp + j * g.ldx + col, (float)v, g.pt);
     }
   }
   __syncthreads();
@@ -78,12 +74,7 @@ __global__ void gather_kernel(GatherParams g) {
     const double v = tile[threadIdx.x][i];
     if (g.xt64) g.xt64[c * g.st + col * g.ldt + j] = v;
     if (g.xt32) g.xt32[c * g.st + col * g.ldt + j] = (float)v;
-    if (g.xt_hi) {
-      __nv_bfloat16 h, l;
-      split_bf16((float)v, h, l);
-      g.xt_hi[c * g.stp + col * g.ldt + j] = h;
-      g.xt_lo[c * g.stp + col * g.ldt + j] = l;
-    }
+    if (g.xt_hi) store_split(g.xt_hi, g.xt_lo, c * g.stp + col * g.ldt + j, (float)v, g.pt);
   }
   if (nbad) atomicAdd(g.bad, nbad);
 }
@@ -91,6 +82,7 @@ __global__ void gather_kernel(GatherParams g) {
 // ------------------------------------------------------------ layout ------
 struct PathLayout {
   bool f64 = true;
+  int pt = kPlaneBf16;  // operand-plane type of the mixed modes
   int64_t p = 0, nchains = 0, n_lambda = 0, kmax = 0, kpad = 0, ldo = 0;
   int64_t tiles_prox = 0, tiles_y = 0, nbuckets = 0, sum_k = 0;
   int lz_k = 0;
@@ -106,10 +98,13 @@ struct PathLayout {
   size_t total = 0;
 };
 
-PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_t kmax, int64_t sum_k, bool f64,
+PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_t kmax, int64_t sum_k, int precision,
                             int lanczos_max) {
   PathLayout L;
+  const bool f64 = precision == ACCORD_FP64;
   L.f64 = f64;
+  L.pt = plane_type(precision);
+  const size_t pe = plane_bytes(L.pt);
   L.p = p;
   L.nchains = nchains;
   L.n_lambda = n_lambda;
@@ -146,15 +141,15 @@ PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_
     L.xt64 = take(c, (size_t)B * p * K * 8);
   } else {
     for (int q = 0; q < 2; ++q) {
-      L.y_hi[q] = take(c, (size_t)B * p * K * 2);
-      L.y_lo[q] = take(c, (size_t)B * p * K * 2);
+      L.y_hi[q] = take(c, (size_t)B * p * K * pe);
+      L.y_lo[q] = take(c, (size_t)B * p * K * pe);
     }
-    L.x_hi = take(c, (size_t)B * K * L.ldo * 2);
-    L.x_lo = take(c, (size_t)B * K * L.ldo * 2);
-    L.xt_hi = take(c, (size_t)B * p * K * 2);
-    L.xt_lo = take(c, (size_t)B * p * K * 2);
-    L.dp_hi = take(c, (size_t)B * p * L.ldo * 2);
-    L.dp_lo = take(c, (size_t)B * p * L.ldo * 2);
+    L.x_hi = take(c, (size_t)B * K * L.ldo * pe);
+    L.x_lo = take(c, (size_t)B * K * L.ldo * pe);
+    L.xt_hi = take(c, (size_t)B * p * K * pe);
+    L.xt_lo = take(c, (size_t)B * p * K * pe);
+    L.dp_hi = take(c, (size_t)B * p * L.ldo * pe);
+    L.dp_lo = take(c, (size_t)B * p * L.ldo * pe);
     L.xt32 = take(c, (size_t)B * p * K * 4);
     L.bkt_keys = take(c, (size_t)B * L.nbuckets * kBucketCap * 4);
     L.bkt_vals = take(c, (size_t)B * L.nbuckets * kBucketCap * 4);
@@ -253,7 +248,7 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
     // sparse Y+ = Y + Delta X^T, or the dense product for a chain whose Delta
     // bucket overflowed (each kernel checks its chain's flag)
     ACCORD_CK(launch_delta_planes(ctrl, at<float>(ws, L.om[0]), at<float>(ws, L.om[1]), L.p, L.ldo,
-                                  at<__nv_bfloat16>(ws, L.dp_hi), at<__nv_bfloat16>(ws, L.dp_lo), L.ldo, st, B,
+                                  at<void>(ws, L.dp_hi), at<void>(ws, L.dp_lo), L.ldo, L.pt, st, B,
                                   P.pd.active, P.pd.nactive, L.p * L.ldo, L.p * L.ldo, at<int>(ws, L.any_dense)));
     ACCORD_CK(launch_tc_gemm(kModeY, P.t1, st));
     ACCORD_CK(launch_sparse_y(P.sy, st));
@@ -277,12 +272,12 @@ struct TuneChoice {
   int group_m = 0, clusters = 0;
 };
 std::mutex g_tune_mu;
-std::map<std::array<int64_t, 4>, TuneChoice> g_tune;
+std::map<std::array<int64_t, 5>, TuneChoice> g_tune;
 
 int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
   int dev = 0;
   ACCORD_CK(cudaGetDevice(&dev));
-  const std::array<int64_t, 4> key{dev, P.L.p, P.L.kpad, P.L.nchains};
+  const std::array<int64_t, 5> key{dev, P.L.p, P.L.kpad, P.L.nchains, P.L.pt};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -293,7 +288,7 @@ int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
       return kOk;
     }
   }
-  const int maxc = tc_max_clusters(kModeProx);
+  const int maxc = tc_max_clusters(kModeProx, P.L.pt);
   std::vector<int> grids{maxc};
   for (int c : {maxc * 3 / 4, maxc / 2})
     if (c > 0 && c != grids.back()) grids.push_back(c);
@@ -349,7 +344,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
   const bool f64 = o.precision == ACCORD_FP64;
 
   PathPlan P;
-  P.L = make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), f64, o.lipschitz_max_iter);
+  P.L = make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), o.precision, o.lipschitz_max_iter);
   const PathLayout& L = P.L;
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   Guard guard;
@@ -386,7 +381,8 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     C.lam = lambdas[0];
     C.lam_d = o.penalize_diag ? lambdas[0] : 0.0;
     C.kkt = INFINITY;
-    hkb[c] = (int32_t)((Kc + 31) / 32);
+    const int64_t bk = tc_bk(P.L.pt);  // K blocks of the mixed prox GEMM (unused in FP64 mode)
+    hkb[c] = (int32_t)((Kc + bk - 1) / bk);
   }
   std::vector<double> hbest(B, INFINITY);
   std::vector<int32_t> hbidx(B, -1);
@@ -428,11 +424,12 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     g.xt64 = at<double>(ws, L.xt64);
   } else {
     g.xt32 = at<float>(ws, L.xt32);
-    g.x_hi = at<__nv_bfloat16>(ws, L.x_hi);
-    g.x_lo = at<__nv_bfloat16>(ws, L.x_lo);
-    g.xt_hi = at<__nv_bfloat16>(ws, L.xt_hi);
-    g.xt_lo = at<__nv_bfloat16>(ws, L.xt_lo);
+    g.x_hi = at<void>(ws, L.x_hi);
+    g.x_lo = at<void>(ws, L.x_lo);
+    g.xt_hi = at<void>(ws, L.xt_hi);
+    g.xt_lo = at<void>(ws, L.xt_lo);
   }
+  g.pt = L.pt;
   g.bad = at<int>(ws, L.bad);
   {
     const dim3 grid((unsigned)((p + 31) / 32), (unsigned)(K / 32), (unsigned)B), block(32, 8);
@@ -451,14 +448,13 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
   } else {
     ACCORD_CK(cudaMemcpyAsync(at<float>(ws, L.y[0]), at<float>(ws, L.xt32), (size_t)B * p * K * 4,
                               cudaMemcpyDeviceToDevice, st));
-    ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_hi[0]), at<__nv_bfloat16>(ws, L.xt_hi), (size_t)B * p * K * 2,
-                              cudaMemcpyDeviceToDevice, st));
-    ACCORD_CK(cudaMemcpyAsync(at<__nv_bfloat16>(ws, L.y_lo[0]), at<__nv_bfloat16>(ws, L.xt_lo), (size_t)B * p * K * 2,
-                              cudaMemcpyDeviceToDevice, st));
+    const size_t pbytes = (size_t)B * p * K * plane_bytes(L.pt);
+    ACCORD_CK(cudaMemcpyAsync(at<void>(ws, L.y_hi[0]), at<void>(ws, L.xt_hi), pbytes, cudaMemcpyDeviceToDevice, st));
+    ACCORD_CK(cudaMemcpyAsync(at<void>(ws, L.y_lo[0]), at<void>(ws, L.xt_lo), pbytes, cudaMemcpyDeviceToDevice, st));
     // the other Y buffer's K padding must read as zero too
     ACCORD_CK(cudaMemsetAsync(at<float>(ws, L.y[1]), 0, (size_t)B * p * K * 4, st));
-    ACCORD_CK(cudaMemsetAsync(at<__nv_bfloat16>(ws, L.y_hi[1]), 0, (size_t)B * p * K * 2, st));
-    ACCORD_CK(cudaMemsetAsync(at<__nv_bfloat16>(ws, L.y_lo[1]), 0, (size_t)B * p * K * 2, st));
+    ACCORD_CK(cudaMemsetAsync(at<void>(ws, L.y_hi[1]), 0, pbytes, st));
+    ACCORD_CK(cudaMemsetAsync(at<void>(ws, L.y_lo[1]), 0, pbytes, st));
     ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bkt_cnt), 0, (size_t)B * L.nbuckets * 4, st));
   }
 
@@ -575,15 +571,15 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     ACCORD_CK(sparse_y_prepare());
     TcParams& t2 = P.t2;  // prox GEMM over the chains still running
     for (int q = 0; q < 2; ++q)
-      if (!encode_plane_map(&t2.a_hi[q], at<__nv_bfloat16>(ws, L.y_hi[q]), p, K, K, 128, B, p * K) ||
-          !encode_plane_map(&t2.a_lo[q], at<__nv_bfloat16>(ws, L.y_lo[q]), p, K, K, 128, B, p * K))
+      if (!encode_plane_map(&t2.a_hi[q], at<void>(ws, L.y_hi[q]), L.pt, p, K, K, 128, B, p * K) ||
+          !encode_plane_map(&t2.a_lo[q], at<void>(ws, L.y_lo[q]), L.pt, p, K, K, 128, B, p * K))
         return kEcuda;
-    if (!encode_plane_map(&t2.b_hi, at<__nv_bfloat16>(ws, L.xt_hi), p, K, K, tc_box_n(), B, p * K) ||
-        !encode_plane_map(&t2.b_lo, at<__nv_bfloat16>(ws, L.xt_lo), p, K, K, tc_box_n(), B, p * K))
+    if (!encode_plane_map(&t2.b_hi, at<void>(ws, L.xt_hi), L.pt, p, K, K, tc_box_n(), B, p * K) ||
+        !encode_plane_map(&t2.b_lo, at<void>(ws, L.xt_lo), L.pt, p, K, K, tc_box_n(), B, p * K))
       return kEcuda;
     t2.ctrl = ctrl;
     t2.err = &ctrl[0].dev_error;
-    tc_shape(t2, p, p, K);
+    tc_shape(t2, p, p, K, L.pt);
     t2.out[0] = at<float>(ws, L.om[0]);
     t2.out[1] = at<float>(ws, L.om[1]);
     t2.ldout = L.ldo;
@@ -604,27 +600,27 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     t2.s_out = p * L.ldo; t2.s_aux = p * L.ldo; t2.s_part = L.tiles_prox; t2.s_bkt = L.nbuckets;
     t2.any_dense = at<int>(ws, L.any_dense);
     // a chain in dense Y mode gets its Delta planes from this epilogue
-    t2.out_hi[0] = t2.out_hi[1] = at<__nv_bfloat16>(ws, L.dp_hi);
-    t2.out_lo[0] = t2.out_lo[1] = at<__nv_bfloat16>(ws, L.dp_lo);
+    t2.out_hi[0] = t2.out_hi[1] = at<void>(ws, L.dp_hi);
+    t2.out_lo[0] = t2.out_lo[1] = at<void>(ws, L.dp_lo);
     t2.ldplane = L.ldo;
     t2.s_plane = p * L.ldo;
     TcParams& t1 = P.t1;  // dense Y+ = Y + Delta X^T, only for chains whose bucket overflowed
-    if (!encode_plane_map(&t1.a_hi[0], at<__nv_bfloat16>(ws, L.dp_hi), p, p, L.ldo, 128, B, p * L.ldo) ||
-        !encode_plane_map(&t1.a_lo[0], at<__nv_bfloat16>(ws, L.dp_lo), p, p, L.ldo, 128, B, p * L.ldo) ||
-        !encode_plane_map(&t1.b_hi, at<__nv_bfloat16>(ws, L.x_hi), K, p, L.ldo, tc_box_n(), B, K * L.ldo) ||
-        !encode_plane_map(&t1.b_lo, at<__nv_bfloat16>(ws, L.x_lo), K, p, L.ldo, tc_box_n(), B, K * L.ldo))
+    if (!encode_plane_map(&t1.a_hi[0], at<void>(ws, L.dp_hi), L.pt, p, p, L.ldo, 128, B, p * L.ldo) ||
+        !encode_plane_map(&t1.a_lo[0], at<void>(ws, L.dp_lo), L.pt, p, p, L.ldo, 128, B, p * L.ldo) ||
+        !encode_plane_map(&t1.b_hi, at<void>(ws, L.x_hi), L.pt, K, p, L.ldo, tc_box_n(), B, K * L.ldo) ||
+        !encode_plane_map(&t1.b_lo, at<void>(ws, L.x_lo), L.pt, K, p, L.ldo, tc_box_n(), B, K * L.ldo))
       return kEcuda;
     t1.a_hi[1] = t1.a_hi[0];
     t1.a_lo[1] = t1.a_lo[0];
     t1.ctrl = ctrl;
     t1.err = &ctrl[0].dev_error;
-    tc_shape(t1, p, K, p);
+    tc_shape(t1, p, K, p, L.pt);
     t1.out[0] = at<float>(ws, L.y[0]);
     t1.out[1] = at<float>(ws, L.y[1]);
     t1.ldout = K;
     for (int q = 0; q < 2; ++q) {
-      t1.out_hi[q] = at<__nv_bfloat16>(ws, L.y_hi[q]);
-      t1.out_lo[q] = at<__nv_bfloat16>(ws, L.y_lo[q]);
+      t1.out_hi[q] = at<void>(ws, L.y_hi[q]);
+      t1.out_lo[q] = at<void>(ws, L.y_lo[q]);
     }
     t1.ldplane = K;
     t1.aux[0] = at<float>(ws, L.y[0]);
@@ -644,8 +640,8 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     for (int q = 0; q < 2; ++q) {
       sy.y[q] = at<float>(ws, L.y[q]);
       sy.yw[q] = at<float>(ws, L.y[q]);
-      sy.y_hi[q] = at<__nv_bfloat16>(ws, L.y_hi[q]);
-      sy.y_lo[q] = at<__nv_bfloat16>(ws, L.y_lo[q]);
+      sy.y_hi[q] = at<void>(ws, L.y_hi[q]);
+      sy.y_lo[q] = at<void>(ws, L.y_lo[q]);
     }
     sy.xt = at<float>(ws, L.xt32);
     sy.keys = at<uint32_t>(ws, L.bkt_keys);
@@ -662,6 +658,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     sy.nactive = pd.nactive;
     sy.nprob = (int32_t)B;
     sy.s_y = p * K; sy.s_yk = p * K; sy.s_xt = p * K; sy.s_bkt = L.nbuckets;
+    sy.ptype = L.pt;
   }
   TuneChoice tune;
   if (!f64 && o.autotune) {
@@ -805,7 +802,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     out->n_launches = nlaunch;
     out->L = hctrl[0].L;
     out->tile_group_m = f64 ? 0 : P.t2.group_m;
-    out->tile_clusters = f64 ? 0 : (P.t2.max_clusters > 0 ? P.t2.max_clusters : tc_max_clusters(kModeProx));
+    out->tile_clusters = f64 ? 0 : (P.t2.max_clusters > 0 ? P.t2.max_clusters : tc_max_clusters(kModeProx, L.pt));
   }
   return hstatus;
 }
@@ -828,7 +825,7 @@ size_t accord_path_workspace_bytes(int64_t n, int64_t p, const int32_t* rows, co
     return 0;
   Subsamples S;
   if (compress_subsamples(rows, row_offsets, n_sub, n, S) != kOk) return 0;
-  return make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), o.precision == ACCORD_FP64,
+  return make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), o.precision,
                           o.lipschitz_max_iter)
       .total;
 }

@@ -52,7 +52,7 @@ extern "C" int accord_postprocess(int64_t p, const void* Omega, const accord_opt
   accord_default_opts(&o);
   if (optp) o = *optp;
   if (Omega == nullptr || p < 1 || (Theta_out == nullptr && Rho_out == nullptr)) return kEinval;
-  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
+  if (!known_precision(o.precision)) return kEinval;
   if (int e = check_device()) return e;
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   const int64_t nb = (p + 31) / 32;

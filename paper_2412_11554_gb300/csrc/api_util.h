@@ -56,8 +56,15 @@ int check_device() {
   return kOk;
 }
 
+// Operand-plane type of a mixed precision mode (unused in FP64 mode).
+int plane_type(int precision) { return precision == ACCORD_MIXED_TF32X3 ? kPlaneTf32 : kPlaneBf16; }
+
+bool known_precision(int precision) {
+  return precision == ACCORD_FP64 || precision == ACCORD_MIXED_BF16X3 || precision == ACCORD_MIXED_TF32X3;
+}
+
 int check_opts(const accord_opts& o) {
-  if (o.precision != ACCORD_FP64 && o.precision != ACCORD_MIXED_BF16X3) return kEinval;
+  if (!known_precision(o.precision)) return kEinval;
   if (!(o.beta > 0.0 && o.beta <= 1.0)) return kEinval;
   if (!std::isfinite(o.tau0)) return kEinval;
   if (!(o.kkt_tol >= 0.0)) return kEinval;

@@ -4,6 +4,7 @@
 // layouts.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -143,6 +144,55 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// ------------------------------------------------------- operand planes ---
+// The mixed modes carry each FP32 tensor-core operand x as two planes with
+// x ~= hi + lo:
+//   kPlaneBf16  hi = bf16(x), lo = bf16(x - hi); 2 bytes an element, hi + lo
+//               within 2^-18 |x| of x (8 significant bits each);
+//   kPlaneTf32  hi = tf32(x), lo = tf32(x - hi), each in an FP32 word whose
+//               13 low mantissa bits are zero; 4 bytes an element, within
+//               2^-24 |x| (11 significant bits each).
+// x - hi is exact in FP32 in both cases (hi is x rounded to fewer bits).
+enum : int { kPlaneBf16 = 0, kPlaneTf32 = 1 };
+__host__ __device__ constexpr size_t plane_bytes(int pt) { return pt == kPlaneTf32 ? 4 : 2; }
+
+// x rounded to TF32 (11 significant bits, nearest, ties away from zero),
+// returned as an FP32 value with the low 13 mantissa bits cleared.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r & 0xFFFFE000u);
+}
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - hi);
+}
+
+template <int PT> struct Plane;
+template <> struct Plane<kPlaneBf16> {
+  using E = __nv_bfloat16;
+  __device__ static __forceinline__ void split(float x, E& hi, E& lo) { split_bf16(x, hi, lo); }
+};
+template <> struct Plane<kPlaneTf32> {
+  using E = float;
+  __device__ static __forceinline__ void split(float x, E& hi, E& lo) { split_tf32(x, hi, lo); }
+};
+
+// Writes the split of x to element idx of the planes hi / lo (type pt).
+__device__ __forceinline__ void store_split(void* hi, void* lo, int64_t idx, float x, int pt) {
+  if (pt == kPlaneTf32) {
+    float h, l;
+    split_tf32(x, h, l);
+    static_cast<float*>(hi)[idx] = h;
+    static_cast<float*>(lo)[idx] = l;
+  } else {
+    __nv_bfloat16 h, l;
+    split_bf16(x, h, l);
+    static_cast<__nv_bfloat16*>(hi)[idx] = h;
+    static_cast<__nv_bfloat16*>(lo)[idx] = l;
+  }
 }
 
 }  // namespace accord

@@ -1,14 +1,17 @@
-// Persistent tcgen05 GEMM C = A * B^T on split-BF16 operands, with the fused
-// epilogues of ACCORD-FBS (mixed precision mode).
+// Persistent tcgen05 GEMM C = A * B^T on split operands, with the fused
+// epilogues of ACCORD-FBS (mixed precision modes).
 //
-// Each FP32 operand x is carried as two BF16 planes, hi = bf16(x) and
-// lo = bf16(x - hi); every 128 x BN x 16 slice issues three MMAs into one FP32
-// TMEM accumulator, A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below
-// FP32 resolution of the sum), which recovers ~16 significant bits per operand.
+// Each FP32 operand x is carried as two planes x ~= hi + lo, BF16 (kind::f16
+// MMAs; hi + lo within 2^-18 of x) or TF32 (kind::tf32 MMAs; within 2^-24).
+// Every 32-byte K slice of a 128 x BN tile issues three MMAs into one FP32
+// TMEM accumulator, A_hi B_hi + A_hi B_lo + A_lo B_hi; the lo*lo term is
+// below the resolution of the split.  A plane row of a pipeline stage is 64
+// bytes (32 BF16 or 16 TF32 of K), so the shared-memory layout, descriptors
+// and stage sizes are the same for both types.
 //
 // Warp roles (one CTA per SM, persistent over output tiles):
-//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo tiles (32 BF16 of K a row)
-//               into a 4-deep shared-memory ring (64-byte swizzle), one
+//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo tiles (64 bytes of K a
+//               row) into a 4-deep shared-memory ring (64-byte swizzle), one
 //               mbarrier per stage.
 //   warp 1      TMEM allocator and single-thread MMA issuer (tcgen05.mma).
 //   warps 2..9  epilogue: tcgen05.ld from a double-buffered TMEM accumulator,
@@ -26,7 +29,9 @@ namespace accord {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 32;               // BF16 elements per 64-byte swizzle row
+constexpr int kRowBytes = 64;        // K bytes of a plane row per stage (one 64-byte swizzle row)
+template <int PT>
+constexpr int kBK = kRowBytes / (int)plane_bytes(PT);  // K elements per stage: 32 BF16 or 16 TF32
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 64 + kEpiThreads;
@@ -36,9 +41,9 @@ constexpr int kStages = 4;
 // 1/kClusterM of the shared B tile and multicasts it to all of them.
 constexpr int kClusterM = 2;
 constexpr int kBBox = kBN / kClusterM;                 // B rows one CTA loads
-constexpr uint32_t kBSliceBytes = kBBox * BK * 2;
-constexpr uint32_t kABytes = BM * BK * 2;
-constexpr uint32_t kBBytes = kBN * BK * 2;
+constexpr uint32_t kBSliceBytes = kBBox * kRowBytes;
+constexpr uint32_t kABytes = BM * kRowBytes;
+constexpr uint32_t kBBytes = kBN * kRowBytes;
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
 constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
 constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 block per epilogue warp
@@ -98,8 +103,8 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"
 struct EpiArgs {
   float tau, lam, lam_d, scale;
   float* out;
-  __nv_bfloat16* out_hi;
-  __nv_bfloat16* out_lo;
+  void* out_hi;
+  void* out_lo;
   const float* aux;
   int64_t M, N;
   uint64_t pol_stream;  // L2 evict-first policy for the iterate stream
@@ -180,16 +185,32 @@ __device__ __forceinline__ void load_column(const float* __restrict__ src, int64
   }
 }
 
+// Split of x to the operand planes at ph / pl (L2 policy pol).
+template <int PT>
+__device__ __forceinline__ void st_split_hint(typename Plane<PT>::E* ph, typename Plane<PT>::E* pl, float x,
+                                              uint64_t pol) {
+  typename Plane<PT>::E h, l;
+  Plane<PT>::split(x, h, l);
+  if constexpr (PT == kPlaneTf32) {
+    ptx::st_f32_hint(ph, h, pol);
+    ptx::st_f32_hint(pl, l, pol);
+  } else {
+    ptx::st_b16_hint(ph, __bfloat16_as_ushort(h), pol);
+    ptx::st_b16_hint(pl, __bfloat16_as_ushort(l), pol);
+  }
+}
+
 // Y+ = Y + Delta X^T (aux = Y) or Y = Omega X^T (aux = null) for column colt.
-template <bool CHECK>
+template <int PT, bool CHECK>
 __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base, int64_t colt,
                                         const float (&v)[32], const float (&pre)[32], Sums& sm) {
   float sd = 0.f, sn = 0.f, chk = 0.f;
   const bool cok = !CHECK || colt < ea.N;
   const bool has_aux = ea.aux != nullptr;
+  using E = typename Plane<PT>::E;
   float* po = ea.out ? ea.out + row_base * prm.ldout + colt : nullptr;
-  __nv_bfloat16* ph = ea.out_hi ? ea.out_hi + row_base * prm.ldplane + colt : nullptr;
-  __nv_bfloat16* pl = ea.out_lo ? ea.out_lo + row_base * prm.ldplane + colt : nullptr;
+  E* ph = ea.out_hi ? static_cast<E*>(ea.out_hi) + row_base * prm.ldplane + colt : nullptr;
+  E* pl = ea.out_lo ? static_cast<E*>(ea.out_lo) + row_base * prm.ldplane + colt : nullptr;
   const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
@@ -200,12 +221,7 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
     sn = fmaf(yn, yn, sn);
     chk = fmaf(yn, 0.f, chk);
     if (po) ptx::st_f32_hint(po + r * ldo, yn, ea.pol_stream);
-    if (ph) {
-      const __nv_bfloat16 hb = __float2bfloat16_rn(yn);
-      ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
-      ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(yn - __bfloat162float(hb))),
-                       ea.pol_stream);
-    }
+    if (ph) st_split_hint<PT>(ph + r * ldp, pl + r * ldp, yn, ea.pol_stream);
   }
   sm.r0 += sd;
   sm.r1 += sn;
@@ -215,17 +231,18 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
 // and the diagonal (row == colt); the unchecked form is the hot path.
-template <bool CHECK, bool MASK, bool SPARSE>
+template <int PT, bool CHECK, bool MASK, bool SPARSE>
 __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
                                            int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
                                            int lane) {
   float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
-  constexpr bool sparse = SPARSE;  // Delta to the buckets (else to BF16 planes)
+  constexpr bool sparse = SPARSE;  // Delta to the buckets (else to operand planes)
+  using E = typename Plane<PT>::E;
   float* po = ea.out + row_base * prm.ldout + colt;
-  __nv_bfloat16* ph = sparse ? nullptr : ea.out_hi + row_base * prm.ldplane + colt;
-  __nv_bfloat16* pl = sparse ? nullptr : ea.out_lo + row_base * prm.ldplane + colt;
+  E* ph = sparse ? nullptr : static_cast<E*>(ea.out_hi) + row_base * prm.ldplane + colt;
+  E* pl = sparse ? nullptr : static_cast<E*>(ea.out_lo) + row_base * prm.ldplane + colt;
   const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
   const int64_t mcol = (colt - lane) >> 5;  // mask word of this 32-column chunk
   uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
@@ -265,12 +282,7 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
       d = w - om;
       sd = fmaf(d, d, sd);
       ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
-      if (!sparse) {
-        const __nv_bfloat16 hb = __float2bfloat16_rn(d);
-        ptx::st_b16_hint(ph + r * ldp, __bfloat16_as_ushort(hb), ea.pol_stream);
-        ptx::st_b16_hint(pl + r * ldp, __bfloat16_as_ushort(__float2bfloat16_rn(d - __bfloat162float(hb))),
-                         ea.pol_stream);
-      }
+      if (!sparse) st_split_hint<PT>(ph + r * ldp, pl + r * ldp, d, ea.pol_stream);
     }
     v[r] = d;
     nzmask |= (d != 0.f) ? (1u << r) : 0u;
@@ -346,8 +358,9 @@ __device__ __forceinline__ void gram_chunk(const TcParams& prm, int64_t row_base
 
 // 320 threads = 10 warps; two SM sub-partitions hold 3 of them, so at most
 // 16384 / (3 * 32) = 170 registers a thread (168 after allocation rounding).
-template <int MODE>
+template <int MODE, int PT>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams prm) {
+  constexpr int BK = kBK<PT>;
   Ctrl* ctrl = prm.ctrl;
   const bool batch = prm.nprob > 1 || prm.active != nullptr;
   if (!batch && ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   } else if (warp == 1) {
     // -------------------------------------------------------- MMA issuer --
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, kBN);
+      constexpr uint32_t idesc = PT == kPlaneTf32 ? ptx::idesc_tf32_f32(BM, kBN) : ptx::idesc_bf16_f32(BM, kBN);
       uint32_t s = 0, ph = 0;
       bool ok = true;
       int i = 0;
@@ -487,11 +500,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint64_t b_hi = ptx::sdesc_k64(st + 2 * kABytes);
           const uint64_t b_lo = ptx::sdesc_k64(st + 2 * kABytes + kBBytes);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
-            ptx::mma_f16(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
-            ptx::mma_f16(d, a_hi + off, b_lo + off, idesc, 1u);
-            ptx::mma_f16(d, a_hi + off, b_hi + off, idesc, 1u);
+          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+            const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4: K = 16 BF16 or 8 TF32
+            if constexpr (PT == kPlaneTf32) {
+              ptx::mma_tf32(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+              ptx::mma_tf32(d, a_hi + off, b_lo + off, idesc, 1u);
+              ptx::mma_tf32(d, a_hi + off, b_hi + off, idesc, 1u);
+            } else {
+              ptx::mma_f16(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+              ptx::mma_f16(d, a_hi + off, b_lo + off, idesc, 1u);
+              ptx::mma_f16(d, a_hi + off, b_hi + off, idesc, 1u);
+            }
           }
           ptx::mma_commit_mc(&empty[s], kMask);  // release the slot in every CTA
           if (++s == kStages) { s = 0; ph ^= 1u; }
@@ -609,25 +628,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (row_base >= prm.M || col0 >= prm.N) continue;  // warp-uniform
           const bool diag = (row_base == col0);
           if (MODE == kModeY) {
-            if (full) y_chunk<false>(ea, prm, row_base, colt, v, pre, sm);
-            else y_chunk<true>(ea, prm, row_base, colt, v, pre, sm);
+            if (full) y_chunk<PT, false>(ea, prm, row_base, colt, v, pre, sm);
+            else y_chunk<PT, true>(ea, prm, row_base, colt, v, pre, sm);
           } else if (MODE == kModeProx) {
             // compile-time variants: full interior chunk, Delta to buckets, no refit mask is the hot one
             const bool fast = full && !diag;
             if (ea.mask == nullptr) {
               if (ea.bkey != nullptr) {
-                if (fast) prox_chunk<false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else prox_chunk<true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
               } else {
-                if (fast) prox_chunk<false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else prox_chunk<true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
               }
             } else if (ea.bkey != nullptr) {
-              if (fast) prox_chunk<false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
             } else {
-              if (fast) prox_chunk<false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
             }
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
@@ -699,9 +718,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 }
 
 // Shared-memory opt-in and the persistent grid size (clusters that fit at
-// once), set up once per device and mode.  Done outside any launch so that a
-// stream capture records launches only.
-template <int MODE>
+// once), set up once per device, mode and plane type.  Done outside any launch
+// so that a stream capture records launches only.
+template <int MODE, int PT>
 cudaError_t configure_mode(int& max_clusters) {
   static int configured = -1;
   static int clusters = 0;
@@ -709,7 +728,8 @@ cudaError_t configure_mode(int& max_clusters) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (configured != dev) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -723,7 +743,7 @@ cudaError_t configure_mode(int& max_clusters) {
     cfg.numAttrs = 1;
     cfg.gridDim = dim3(kClusterM, 1, 1);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE, PT>, &cfg) != cudaSuccess || n < 1) {
       (void)cudaGetLastError();
       int sms = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -736,10 +756,10 @@ cudaError_t configure_mode(int& max_clusters) {
   return cudaSuccess;
 }
 
-template <int MODE>
+template <int MODE, int PT>
 cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   int max_clusters = 0;
-  cudaError_t e = configure_mode<MODE>(max_clusters);
+  cudaError_t e = configure_mode<MODE, PT>(max_clusters);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -756,40 +776,67 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   const int64_t tiles_total = (int64_t)(prm.nprob > 1 ? prm.nprob : 1) * prm.ntiles_c;
   const int clusters = (int)std::min<int64_t>(tiles_total, max_clusters);
   cfg.gridDim = dim3((unsigned)(clusters * kClusterM), 1, 1);
-  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, prm);
+  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, PT>, prm);
+}
+
+template <int PT>
+int max_clusters_of(int mode) {
+  int m = 0;
+  switch (mode) {
+    case kModeY: configure_mode<kModeY, PT>(m); break;
+    case kModeProx: configure_mode<kModeProx, PT>(m); break;
+    case kModeGrad: configure_mode<kModeGrad, PT>(m); break;
+    default: configure_mode<kModeGram, PT>(m); break;
+  }
+  return m;
+}
+
+template <int PT>
+cudaError_t prepare_type() {
+  int m = 0;
+  cudaError_t e = configure_mode<kModeY, PT>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeProx, PT>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeGrad, PT>(m);
+  if (e == cudaSuccess) e = configure_mode<kModeGram, PT>(m);
+  return e;
+}
+
+template <int PT>
+cudaError_t launch_type(int mode, const TcParams& prm, cudaStream_t st) {
+  switch (mode) {
+    case kModeY: return launch_mode<kModeY, PT>(prm, st);
+    case kModeProx: return launch_mode<kModeProx, PT>(prm, st);
+    case kModeGrad: return launch_mode<kModeGrad, PT>(prm, st);
+    case kModeGram: return launch_mode<kModeGram, PT>(prm, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 int tc_box_n() { return kBBox; }
 
-int tc_max_clusters(int mode) {
-  int m = 0;
-  switch (mode) {
-    case kModeY: configure_mode<kModeY>(m); break;
-    case kModeProx: configure_mode<kModeProx>(m); break;
-    case kModeGrad: configure_mode<kModeGrad>(m); break;
-    default: configure_mode<kModeGram>(m); break;
-  }
-  return m;
+int tc_bk(int pt) { return pt == kPlaneTf32 ? kBK<kPlaneTf32> : kBK<kPlaneBf16>; }
+
+int tc_max_clusters(int mode, int pt) {
+  return pt == kPlaneTf32 ? max_clusters_of<kPlaneTf32>(mode) : max_clusters_of<kPlaneBf16>(mode);
 }
 
 cudaError_t tc_prepare() {
-  int m = 0;
-  cudaError_t e = configure_mode<kModeY>(m);
-  if (e == cudaSuccess) e = configure_mode<kModeProx>(m);
-  if (e == cudaSuccess) e = configure_mode<kModeGrad>(m);
-  if (e == cudaSuccess) e = configure_mode<kModeGram>(m);
+  cudaError_t e = prepare_type<kPlaneBf16>();
+  if (e == cudaSuccess) e = prepare_type<kPlaneTf32>();
   return e;
 }
 
 int64_t tc_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + kBN - 1) / kBN); }
 
-void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K) {
+void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K, int pt) {
+  const int bk = tc_bk(pt);
+  prm.ptype = pt;
   prm.M = M;
   prm.N = N;
   prm.K = K;
-  prm.num_kb = (int32_t)((K + BK - 1) / BK);
+  prm.num_kb = (int32_t)((K + bk - 1) / bk);
   prm.tiles_m = (int32_t)((M + BM - 1) / BM);
   prm.tiles_n = (int32_t)((N + kBN - 1) / kBN);
   prm.ntiles = prm.tiles_m * prm.tiles_n;
@@ -804,17 +851,13 @@ void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K) {
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st) {
   if (prm.ntiles <= 0) return cudaSuccess;
   if (prm.ntiles_c <= 0) return cudaErrorInvalidValue;
-  switch (mode) {
-    case kModeY: return launch_mode<kModeY>(prm, st);
-    case kModeProx: return launch_mode<kModeProx>(prm, st);
-    case kModeGrad: return launch_mode<kModeGrad>(prm, st);
-    case kModeGram: return launch_mode<kModeGram>(prm, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (prm.ptype == kPlaneTf32) return launch_type<kPlaneTf32>(mode, prm, st);
+  if (prm.ptype == kPlaneBf16) return launch_type<kPlaneBf16>(mode, prm, st);
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------ tensor maps --
-bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld,
+bool encode_plane_map(CUtensorMap* map, const void* base, int pt, int64_t rows, int64_t cols, int64_t ld,
                       int box_rows, int64_t depth, int64_t slice_stride) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (encode == nullptr) {
@@ -826,18 +869,21 @@ bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
       return false;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
+  if (pt != kPlaneBf16 && pt != kPlaneTf32) return false;
+  const int64_t es = (int64_t)plane_bytes(pt);
   if (depth < 1) depth = 1;
   if (depth == 1 || slice_stride <= 0) slice_stride = rows * ld;
-  if (((uintptr_t)base & 15u) != 0 || (ld * 2) % 16 != 0 || (slice_stride * 2) % 16 != 0 || rows < 1 || cols < 1 ||
-      slice_stride < rows * ld)
+  if (((uintptr_t)base & 15u) != 0 || (ld * es) % 16 != 0 || (slice_stride * es) % 16 != 0 || rows < 1 ||
+      cols < 1 || slice_stride < rows * ld)
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)depth};
-  const cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(slice_stride * 2)};
-  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(slice_stride * es)};
+  const cuuint32_t box[3] = {(cuuint32_t)tc_bk(pt), (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims, strides,
-                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt = pt == kPlaneTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = encode(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

@@ -58,10 +58,9 @@ cudaError_t launch_gemm_f64(int mode, const GemmF64Params& prm, cudaStream_t st)
 cudaError_t launch_convert_x_f64(const float* X32, const double* X64in, int64_t n, int64_t p,
                                  double* X64, int64_t ldx, double* XT64, int64_t ldxt,
                                  int* bad_flag, cudaStream_t st);
-cudaError_t launch_convert_x_bf16(const float* X32, int64_t n, int64_t p,
-                                  __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int64_t ldx,
-                                  __nv_bfloat16* XThi, __nv_bfloat16* XTlo, int64_t ldxt,
-                                  int* bad_flag, cudaStream_t st);
+// Operand planes (type pt, kPlaneBf16 or kPlaneTf32) of X and X^T.
+cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void* Xhi, void* Xlo, int64_t ldx,
+                                    void* XThi, void* XTlo, int64_t ldxt, int* bad_flag, int pt, cudaStream_t st);
 // Omega^0 = I in an internal buffer with leading dimension ld (elements).
 cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st);
 // Copy between a dense p x p user array (ld = p) and an internal buffer.
@@ -76,9 +75,9 @@ cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld
 // where Om_ij != 0 or i == j.  Om is p x p with leading dimension ld.
 cudaError_t launch_support_mask(const void* Om, int is_f64, int64_t p, int64_t ld, uint32_t* mask, int64_t mask_ld,
                                 cudaStream_t st);
-// BF16 hi/lo planes of an FP32 matrix (rows x cols, lds) into ldd planes.
-cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldd, cudaStream_t st);
+// hi/lo planes (type pt) of an FP32 matrix (rows x cols, lds) into ldd planes.
+cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds, void* hi, void* lo,
+                                int64_t ldd, int pt, cudaStream_t st);
 
 // Lanczos estimate of lambda_max of the symmetric n x n matrix K (FP64).
 // V holds (kmax + 1) x n doubles, alpha / beta kmax doubles each, w n.
@@ -159,13 +158,13 @@ struct SparseYParams {
   const Ctrl* ctrl;           // a batch: one per problem (grid y = problem slot)
   const float* y[2];          // Y (p x ldy FP32), index cur / nxt
   float* yw[2];
-  __nv_bfloat16* y_hi[2];     // planes of Y+ (p x ldyk), index nxt
-  __nv_bfloat16* y_lo[2];
+  void* y_hi[2];              // planes of Y+ (p x ldyk, type ptype), index nxt
+  void* y_lo[2];
   const float* xt;            // X^T, p x ldy FP32
   const uint32_t* keys;
   const float* vals;
   const int* counts;
-  int32_t cap, tiles_m, tiles_n, pad;
+  int32_t cap, tiles_m, tiles_n, ptype;
   int64_t p, n, ldy, ldyk;
   double* part;               // one row of kYSlots per bucket
   // batch: problem b = active[slot] (or slot), data at + b * stride
@@ -177,11 +176,11 @@ struct SparseYParams {
 size_t sparse_y_smem_bytes(int cap);
 cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st);
 cudaError_t sparse_y_prepare();  // one-time shared-memory opt-in (before a graph capture)
-// Dense fallback: BF16 planes of Delta = Omega[nxt] - Omega[cur] when ctrl->dense.
+// Dense fallback: planes (type pt) of Delta = Omega[nxt] - Omega[cur] when ctrl->dense.
 // A batch runs grid y over problem slots (active list or 0 .. nprob-1) with
 // Omega at + b * s_om and the planes at + b * s_pl.
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st,
+                                void* hi, void* lo, int64_t ldk, int pt, cudaStream_t st,
                                 int32_t nprob = 1, const int32_t* active = nullptr, const int32_t* nactive = nullptr,
                                 int64_t s_om = 0, int64_t s_pl = 0, const int* any_dense = nullptr);
 // X^T in FP32 (p x ldxt).

@@ -75,10 +75,10 @@ __global__ void convert_x_f64_kernel(const Tin* __restrict__ X, int64_t n, int64
   if (nbad) atomicAdd(bad, nbad);
 }
 
-__global__ void convert_x_bf16_kernel(const float* __restrict__ X, int64_t n, int64_t p,
-                                      __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo,
-                                      int64_t ldx, __nv_bfloat16* __restrict__ XThi,
-                                      __nv_bfloat16* __restrict__ XTlo, int64_t ldxt, int* bad) {
+// Operand planes (type pt) of X (n x ldx) and of X^T (p x ldxt), plus a count
+// of the non-finite entries of X.
+__global__ void convert_x_planes_kernel(const float* __restrict__ X, int64_t n, int64_t p, void* Xhi, void* Xlo,
+                                        int64_t ldx, void* XThi, void* XTlo, int64_t ldxt, int* bad, int pt) {
   __shared__ float tile[32][33];
   const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
   int nbad = 0;
@@ -88,22 +88,14 @@ __global__ void convert_x_bf16_kernel(const float* __restrict__ X, int64_t n, in
     if (r < n && c < p) {
       v = X[r * p + c];
       if (!isfinite(v)) ++nbad;
-      __nv_bfloat16 h, l;
-      split_bf16(v, h, l);
-      Xhi[r * ldx + c] = h;
-      Xlo[r * ldx + c] = l;
+      store_split(Xhi, Xlo, r * ldx + c, v, pt);
     }
     tile[i][threadIdx.x] = v;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int64_t c = c0 + i, r = r0 + threadIdx.x;
-    if (c < p && r < n) {
-      __nv_bfloat16 h, l;
-      split_bf16(tile[threadIdx.x][i], h, l);
-      XThi[c * ldxt + r] = h;
-      XTlo[c * ldxt + r] = l;
-    }
+    if (c < p && r < n) store_split(XThi, XTlo, c * ldxt + r, tile[threadIdx.x][i], pt);
   }
   if (nbad) atomicAdd(bad, nbad);
 }
@@ -185,17 +177,12 @@ __global__ void omega_stats_kernel(const T* __restrict__ Om, int64_t p, int64_t 
 }
 
 __global__ void split_planes_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
-                                    int64_t lds, __nv_bfloat16* __restrict__ hi,
-                                    __nv_bfloat16* __restrict__ lo, int64_t ldd) {
+                                    int64_t lds, void* hi, void* lo, int64_t ldd, int pt) {
   const int64_t total = rows * ldd;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / ldd, c = i % ldd;
-    const float v = c < cols ? src[r * lds + c] : 0.f;
-    __nv_bfloat16 h, l;
-    split_bf16(v, h, l);
-    hi[i] = h;
-    lo[i] = l;
+    store_split(hi, lo, i, c < cols ? src[r * lds + c] : 0.f, pt);
   }
 }
 
@@ -806,12 +793,11 @@ cudaError_t launch_convert_x_f64(const float* X32, const double* X64in, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_x_bf16(const float* X32, int64_t n, int64_t p, __nv_bfloat16* Xhi,
-                                  __nv_bfloat16* Xlo, int64_t ldx, __nv_bfloat16* XThi,
-                                  __nv_bfloat16* XTlo, int64_t ldxt, int* bad, cudaStream_t st) {
+cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void* Xhi, void* Xlo, int64_t ldx,
+                                    void* XThi, void* XTlo, int64_t ldxt, int* bad, int pt, cudaStream_t st) {
   dim3 grid((unsigned)((p + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  convert_x_bf16_kernel<<<grid, block, 0, st>>>(X32, n, p, Xhi, Xlo, ldx, XThi, XTlo, ldxt, bad);
+  convert_x_planes_kernel<<<grid, block, 0, st>>>(X32, n, p, Xhi, Xlo, ldx, XThi, XTlo, ldxt, bad, pt);
   return cudaGetLastError();
 }
 
@@ -839,9 +825,9 @@ cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldd, cudaStream_t st) {
-  split_planes_kernel<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, hi, lo, ldd);
+cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, int64_t lds, void* hi, void* lo,
+                                int64_t ldd, int pt, cudaStream_t st) {
+  split_planes_kernel<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, hi, lo, ldd, pt);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 //
 // Entries arrive in any order from many CTAs; each block sorts its bucket by
 // (row, column) first, so the sums are formed in a fixed order and the result
-// is the same on every run.  The kernel also writes the BF16 hi/lo planes of
-// Y+ (the A operand of the next gradient GEMM) and the per-block partial sums
+// is the same on every run.  The kernel also writes the hi/lo operand planes
+// of Y+ (BF16 or TF32: the A operand of the next gradient GEMM) and the
+// per-block partial sums
 // ||Delta X^T||^2 and ||Y+||^2 for the line search of Algorithm 1.
 #include "internal.h"
 
@@ -54,7 +55,9 @@ __device__ __forceinline__ int lower_bound(const uint32_t* key, int m, uint32_t 
   return lo;
 }
 
+template <int PT>
 __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
+  using E = typename Plane<PT>::E;
   int b = blockIdx.y;  // problem slot of a batch (0 for one fit)
   if (prm.active != nullptr) {
     if (b >= *prm.nactive) return;
@@ -67,8 +70,8 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
   const int cur = ctrl->cur, nxt = cur ^ 1;
   const float* __restrict__ Y = prm.y[cur] + b * prm.s_y;
   float* __restrict__ Yp = prm.yw[nxt] + b * prm.s_y;
-  __nv_bfloat16* __restrict__ Yh = prm.y_hi[nxt] + b * prm.s_yk;
-  __nv_bfloat16* __restrict__ Yl = prm.y_lo[nxt] + b * prm.s_yk;
+  E* __restrict__ Yh = static_cast<E*>(prm.y_hi[nxt]) + b * prm.s_yk;
+  E* __restrict__ Yl = static_cast<E*>(prm.y_lo[nxt]) + b * prm.s_yk;
   const float* __restrict__ XT = prm.xt + b * prm.s_xt;
   const int64_t bk = b * prm.s_bkt + mb;  // this problem's bucket
 
@@ -96,8 +99,8 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
     const int hi = (rl + 1 < kRowsPerBlock) ? lower_bound(key, cnt, (uint32_t)(rl + 1) << 25) : cnt;
     const float* yr = Y + row * prm.ldy;
     float* ypr = Yp + row * prm.ldy;
-    __nv_bfloat16* hr = Yh + row * prm.ldyk;
-    __nv_bfloat16* lr = Yl + row * prm.ldyk;
+    E* hr = Yh + row * prm.ldyk;
+    E* lr = Yl + row * prm.ldyk;
     for (int64_t c0 = 0; c0 < prm.n; c0 += kColsPerPass) {
       float acc[kColsPerPass / 32];
 #pragma unroll
@@ -139,8 +142,8 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
           s_n = fmaf(yn, yn, s_n);
           chk = fmaf(yn, 0.f, chk);
           ypr[c] = yn;
-          __nv_bfloat16 h, l;
-          split_bf16(yn, h, l);
+          E h, l;
+          Plane<PT>::split(yn, h, l);
           hr[c] = h;
           lr[c] = l;
         }
@@ -168,9 +171,9 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
   }
 }
 
-// Dense fallback when a bucket overflowed: BF16 planes of Delta = Omega+ - Omega.
+// Dense fallback when a bucket overflowed: planes (type pt) of Delta = Omega+ - Omega.
 __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                    __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, const int32_t* active,
+                                    void* hi, void* lo, int64_t ldk, int pt, const int32_t* active,
                                     const int32_t* nactive, int64_t s_om, int64_t s_pl, const int* any_dense) {
   if (any_dense != nullptr && *any_dense == 0) return;
   int b = blockIdx.y;
@@ -183,15 +186,10 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
   if (ctrl->done || !ctrl->dense || ctrl->ymode) return;
   const float* Om = (ctrl->cur ? om1 : om0) + b * s_om;
   const float* Op = (ctrl->cur ? om0 : om1) + b * s_om;
-  hi += b * s_pl;
-  lo += b * s_pl;
   const int64_t total = p * p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / p, c = i % p;
-    __nv_bfloat16 h, l;
-    split_bf16(Op[r * ld + c] - Om[r * ld + c], h, l);
-    hi[r * ldk + c] = h;
-    lo[r * ldk + c] = l;
+    store_split(hi, lo, b * s_pl + r * ldk + c, Op[r * ld + c] - Om[r * ld + c], pt);
   }
 }
 
@@ -205,7 +203,9 @@ cudaError_t sparse_y_prepare() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (configured != dev) {
-    e = cudaFuncSetAttribute(sparse_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    e = cudaFuncSetAttribute(sparse_y_kernel<kPlaneBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sparse_y_kernel<kPlaneTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
     configured = dev;
   }
@@ -219,19 +219,21 @@ cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
   if (smem > 64 * 1024) return cudaErrorInvalidValue;
   const unsigned nb = (unsigned)(prm.nprob > 1 ? prm.nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
-  sparse_y_kernel<<<dim3((unsigned)prm.tiles_m, nb), kThreads, smem, st>>>(prm);
+  const dim3 grid((unsigned)prm.tiles_m, nb);
+  if (prm.ptype == kPlaneTf32) sparse_y_kernel<kPlaneTf32><<<grid, kThreads, smem, st>>>(prm);
+  else sparse_y_kernel<kPlaneBf16><<<grid, kThreads, smem, st>>>(prm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st, int32_t nprob,
+                                void* hi, void* lo, int64_t ldk, int pt, cudaStream_t st, int32_t nprob,
                                 const int32_t* active, const int32_t* nactive, int64_t s_om, int64_t s_pl,
                                 const int* any_dense) {
   const unsigned nb = (unsigned)(nprob > 1 ? nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
   const unsigned gx = nb > 1 ? 152u * 16u / nb + 1u : 152u * 16u;
-  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, active, nactive, s_om, s_pl,
-                                                    any_dense);
+  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, pt, active, nactive, s_om,
+                                                    s_pl, any_dense);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
-// Parameters of the tcgen05 split-BF16 GEMM C = A * B^T (A: M x K, B: N x K,
-// BF16 hi/lo planes, K contiguous) and its host launcher.
+// Parameters of the tcgen05 split-operand GEMM C = A * B^T (A: M x K,
+// B: N x K, hi/lo planes of BF16 or TF32, K contiguous) and its host launcher.
 #pragma once
 
 #include <cuda.h>
@@ -27,8 +27,8 @@ struct TcParams {
   int32_t a_nxt, smooth, group_m, bn;
   float* out[2];        // FP32 output (Y+, Omega+ or G), index nxt
   int64_t ldout;
-  __nv_bfloat16* out_hi[2];  // BF16 planes of the output, index nxt
-  __nv_bfloat16* out_lo[2];
+  void* out_hi[2];      // operand planes of the output (type ptype), index nxt
+  void* out_lo[2];
   int64_t ldplane;
   const float* aux[2];  // old Y (Y mode) or Omega (prox / grad), index cur
   int64_t ldaux;
@@ -63,18 +63,21 @@ struct TcParams {
   // the dense product), instead of scanning every problem's tiles.
   int* any_dense;
   int32_t max_clusters;  // persistent grid limit in clusters (0: as many as fit at once)
-  int32_t pad_tail;
+  int32_t ptype;         // plane type of the operands and plane outputs: kPlaneBf16 / kPlaneTf32
 };
 
-// Encodes a 3-D BF16 tensor map over `depth` slices of a rows x cols matrix
-// with leading dimension ld (elements) and slice_stride elements between
-// slices; box 32 (K) x box_rows x 1, 64-byte swizzle.  Returns false when the
-// driver rejects the arguments.
-bool encode_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld,
+// Encodes a 3-D tensor map over `depth` slices of a rows x cols plane of type
+// pt with leading dimension ld (elements) and slice_stride elements between
+// slices; box (64 bytes of K) x box_rows x 1, 64-byte swizzle.  Returns false
+// when the driver rejects the arguments.
+bool encode_plane_map(CUtensorMap* map, const void* base, int pt, int64_t rows, int64_t cols, int64_t ld,
                       int box_rows, int64_t depth = 1, int64_t slice_stride = 0);
 
-// Fills the shape fields (num_kb, tiles, bn) for an M x N x K problem.
-void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K);
+// K elements one pipeline stage covers (64 bytes of a plane row).
+int tc_bk(int pt);
+// Fills the shape fields (num_kb, tiles, bn) and the plane type pt of an
+// M x N x K problem (the K blocking depends on pt).
+void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K, int pt);
 int64_t tc_tiles(int64_t M, int64_t N);
 int tc_box_n();  // rows of the B box one CTA loads (its share of the N tile)
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
@@ -82,6 +85,6 @@ cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
 // otherwise); call before capturing launches into a CUDA graph.
 cudaError_t tc_prepare();
 // Clusters of the persistent grid that fit on the device at once (mode's kernel).
-int tc_max_clusters(int mode);
+int tc_max_clusters(int mode, int pt = 0);
 
 }  // namespace accord

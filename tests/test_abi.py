@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -82,6 +83,17 @@ def test_defaults_and_workspace_sizing(lib):
     assert big >= 2 * 4 * 40000 ** 2
     assert accord.accord_workspace_bytes(0, 10) == 0
     assert accord.accord_workspace_bytes(10, 10, beta=1.5) == 0
+    # TF32x3 planes take 4 bytes an element instead of 2: the five plane pairs
+    # (X, X^T, Y twice, Delta) grow by 2 * 2 * (2 n p + 3 p n + p^2) bytes at
+    # most the 1 KB rounding of each sub-buffer
+    n, p = 1000, 4000
+    bf = accord.accord_workspace_bytes(n, p, precision="bf16x3")
+    tf = accord.accord_workspace_bytes(n, p, precision="tf32x3")
+    grow = 2 * 2 * (n * p + n * p + 2 * p * n + p * p)
+    assert abs((tf - bf) - grow) <= 16 * 1024
+    ptf = accord.accord_path_workspace_bytes(200, 300, [np.arange(150), np.arange(200)], 2, precision="tf32x3")
+    pbf = accord.accord_path_workspace_bytes(200, 300, [np.arange(150), np.arange(200)], 2, precision="bf16x3")
+    assert ptf > pbf > 0
 
 
 def test_invalid_arguments_rejected_on_host(lib):

@@ -1,0 +1,191 @@
+"""GPU parity of the TF32x3 mode (precision "tf32x3"): the split-TF32 tcgen05
+products against float64 references of the same contractions, and fits, the
+refit, the lambda path and the held-out derivative against the FP64 oracle,
+at tolerances below the floor of the BF16x3 mode.
+
+Tolerances.  Each FP32 operand x is carried as hi = tf32(x) and
+lo = tf32(x - hi) (11 significant bits each, round to nearest), so hi + lo
+represents x to 2^-24 relative, FP32's own resolution (BF16x3: 8 bits each,
+2^-18).  The products accumulate in FP32 in TMEM, one accumulator update per
+MMA: a TF32 MMA covers 8 elements of K, a BF16 MMA 16, so over K terms the
+TF32x3 product makes 3K/8 updates against 3K/16.  Where K is small the
+split decides and TF32x3 is far more accurate; from K of a few hundred both
+modes sit at the accumulation floor (measured on GB300: 4e-7 .. 7e-7 of
+sum_k |a_ik b_kj| for K = 100 .. 1000 in both modes, TF32x3 slightly above
+BF16x3 at the largest K).  The tests hold one TF32x3 product to 3e-6 of that
+sum and two chained products (dL/dX) to 1e-5 (BF16x3: 2e-5 and 3e-5), and
+require the TF32x3 error below the BF16x3 error of the same product where
+K <= 16.  Fits are asked for an internal KKT of 1e-6; the FP64 KKT residual
+of the result carries the gradient's accumulation error (~5e-6), so it is
+held to 1e-5, and the estimate to 1e-5 relative Frobenius of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import accord_ref as R
+from synth import diff_workload, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_11554_gb300 import build
+    build.build()
+    import paper_2412_11554_gb300 as pkg
+    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
+    return pkg
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,p", [(64, 128), (100, 333), (257, 520), (1000, 1000), (5, 17)])
+def test_tf32_grad_against_fp64_reference(A, n, p):
+    """Omega S through the split-TF32 GEMMs (both products, ragged tiles and a
+    K that is not a multiple of the 16-element stage) vs float64, with the
+    BF16x3 error of the same product printed beside it."""
+    g = torch.Generator().manual_seed(n * 1000 + p)
+    X = torch.randn(n, p, generator=g, dtype=torch.float64)
+    Om = torch.randn(p, p, generator=g, dtype=torch.float64) * 0.1
+    Om.diagonal().copy_(1.0 + torch.rand(p, generator=g, dtype=torch.float64))
+    X32, Om32 = X.float(), Om.float()
+    ref = (Om32.double() @ X32.double().T) @ X32.double() / n
+    scale = (Om32.double().abs() @ (X32.double().T.abs() @ X32.double().abs())).max() / n
+    Xc, Oc = X32.cuda().contiguous(), Om32.cuda().contiguous()
+    Gt = A.accord_grad(Xc, Oc, precision="tf32x3").double().cpu()
+    Gb = A.accord_grad(Xc, Oc, precision="bf16x3").double().cpu()
+    et = float((Gt - ref).abs().max() / scale)
+    eb = float((Gb - ref).abs().max() / scale)
+    print(f"n={n} p={p}: tf32x3 {et:.2e}, bf16x3 {eb:.2e} of the scale")
+    assert et <= 3e-6
+    if n <= 16:
+        assert et < eb / 4  # the split decides here: 2^-24 against 2^-18
+    Gs = A.accord_grad(Xc, Oc, smooth=True, precision="tf32x3").double().cpu()
+    refs = ref - torch.diag(1.0 / Om32.double().diagonal())
+    assert float((Gs - refs).abs().max() / scale) <= 3e-6
+
+
+def test_tf32_grad_x_and_loss(A):
+    rng = np.random.Generator(np.random.PCG64(18))
+    n, p = 300, 700
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    Om = (0.05 * rng.standard_normal((p, p)) * (rng.random((p, p)) < 0.05)).astype(np.float32)
+    np.fill_diagonal(Om, (1.0 + rng.random(p)).astype(np.float32))
+    Xd, Od = X.astype(np.float64), Om.astype(np.float64)
+    f, g = A.accord_loss(dev(X), dev(Om), 0.2, precision="tf32x3")
+    assert abs(g - R.smooth_g(Od, Xd)) <= 1e-5 * abs(g)
+    assert abs(f - R.objective(Od, Xd, 0.2)) <= 1e-5 * abs(f)
+    GX = A.accord_grad_x(dev(X), dev(Om), precision="tf32x3").double().cpu().numpy()
+    rX = R.smooth_loss_grad_x(Od, Xd)
+    scale = np.max(np.abs(Xd) @ (np.abs(Od).T @ np.abs(Od))) / n
+    assert np.max(np.abs(GX - rX)) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("kind,p,n", [("scalefree", 600, 400), ("hubblock", 400, 130), ("er", 77, 45)])
+def test_tf32_fit_matches_oracle(A, kind, p, n):
+    """TF32x3 fit to KKT 1e-6: 1e-5 relative Frobenius of the oracle's
+    estimate, the FP64 KKT residual of the result within the gradient's
+    accumulation error, and the same support outside the soft-threshold band.
+    A BF16x3 fit asked for the same tolerance is run beside it for the
+    record (not asserted)."""
+    w = workload(kind, p=p, n=n)
+    ref = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=20000)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="tf32x3", kkt_tol=1e-6, max_iter=20000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    Xd = w.X.astype(np.float64)
+    kkt = R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam)
+    err = rel_fro(O, ref.Omega)
+    Ob, sb = A.accord_fit(dev(w.X), w.lam, precision="bf16x3", kkt_tol=1e-6, max_iter=2000, check=False)
+    errb = rel_fro(Ob.double().cpu().numpy(), ref.Omega)
+    print(f"{kind} p={p}: tf32x3 rel_fro {err:.2e}, FP64 KKT {kkt:.2e}, iters {st.iters}; "
+          f"bf16x3 at KKT 1e-6: status {sb.status}, iters {sb.iters}, rel_fro {errb:.2e}")
+    assert err <= 1e-5
+    assert kkt <= 1e-5
+    off = ~np.eye(p, dtype=bool)
+    G_ref = R.grad_g(ref.Omega, Xd)
+    diff = ((O != 0) != (ref.Omega != 0)) & off
+    border = (np.abs(ref.Omega) <= 1e-5) | (np.abs(w.lam - np.abs(G_ref)) <= 1e-5)
+    assert int(np.sum(diff & ~border)) == 0
+
+
+def test_tf32_sparse_and_dense_y_updates_agree(A):
+    """The sparse Delta update and the dense tensor-core Y product in TF32x3
+    give the same estimate; a tiny lambda (dense Omega-hat) takes the dense
+    fallback after the buckets overflow and still meets the FP64 KKT bar."""
+    w = workload("hubblock", p=600, n=300)
+    X = dev(w.X)
+    Os, ss = A.accord_fit(X, w.lam, precision="tf32x3", kkt_tol=1e-6, max_iter=5000, sparse_update=1)
+    Od, sd = A.accord_fit(X, w.lam, precision="tf32x3", kkt_tol=1e-6, max_iter=5000, sparse_update=0)
+    assert ss.status == 0 and sd.status == 0
+    assert rel_fro(Os.double().cpu().numpy(), Od.double().cpu().numpy()) <= 1e-5
+    rng = np.random.Generator(np.random.PCG64(9))
+    Xs = rng.standard_normal((600, 300)).astype(np.float32)
+    lam = 1e-3
+    Om, st = A.accord_fit(dev(Xs), lam, precision="tf32x3", kkt_tol=1e-6, max_iter=5000, sparse_update=1)
+    assert st.status == 0
+    O = Om.double().cpu().numpy()
+    assert R.kkt_residual(O, R.grad_g(O, Xs.astype(np.float64)), lam, lam) <= 1e-5
+
+
+def test_tf32_refit_matches_oracle(A):
+    w = workload("scalefree", p=500, n=300)
+    base = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=5000)
+    sup = base.Omega != 0
+    ref = R.refit(w.X, w.lam, sup, 0.3, kkt_tol=1e-9, max_iter=20000)
+    Om, st = A.accord_refit(dev(w.X), w.lam, 0.3, dev(base.Omega), precision="tf32x3", kkt_tol=1e-6,
+                            max_iter=20000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    assert rel_fro(O, ref.Omega) <= 1e-5
+    assert not np.any(O[~(sup | np.eye(500, dtype=bool))])
+
+
+def test_tf32_path_matches_oracle(A):
+    """The batched lambda path in TF32x3 (ragged subsample sizes, so K blocks
+    differ per chain): epBIC of every estimate and the selected estimates."""
+    w = workload("scalefree", p=600, n=300)
+    rng = np.random.Generator(np.random.PCG64(62))
+    subs = [rng.integers(0, 300, size=m) for m in (150, 221, 300)]
+    lams = list(np.geomspace(0.4, 0.12, 5))
+    ref = R.lambda_path(w.X, subs, lams, kkt_tol=1e-9, max_iter=20000)
+    out = A.accord_path(dev(w.X), subs, lams, precision="tf32x3", kkt_tol=1e-6, max_iter=20000)
+    assert out.status == 0, out.entry_status
+    for s, rows in enumerate(subs):
+        # epBIC = likelihood part + nnz * (log n_s + 4 gamma log p): the first
+        # to 1e-5, the nonzero counts equal up to one entry in the rounding band
+        pen = np.log(len(rows)) + 4 * 0.5 * np.log(600)
+        for k in range(len(lams)):
+            r = ref.fits[s][k]
+            cont = out.epbic[k, s] - out.nnz_offdiag[k, s] * pen
+            cont_ref = ref.epbic[k, s] - r.nnz[-1] * pen
+            assert abs(cont - cont_ref) <= 1e-5 * abs(cont_ref), (k, s)
+            assert abs(int(out.nnz_offdiag[k, s]) - r.nnz[-1]) <= 1, (k, s)
+        kb = int(out.best_index[s])
+        assert kb == int(ref.best[s])
+        O = out.omega_best[s].double().cpu().numpy()
+        assert rel_fro(O, ref.fits[s][kb].Omega) <= 1e-5
+
+
+def test_tf32_derivative_matches_fp64_on_same_estimate(A):
+    """The held-out derivative with TF32x3 products against the FP64 mode on
+    the same FP32 estimate (p = 2000): ten times tighter than the BF16x3 bar."""
+    w = diff_workload()
+    Xt, Xv = dev(w.X_train), dev(w.X_val)
+    O32, st = A.accord_fit(Xt, w.lam, precision="tf32x3", kkt_tol=1e-6, max_iter=20000)
+    assert st.status == 0
+    d32, l32, dO32 = A.accord_dloss_dloglam(Xt, Xv, O32, w.lam, want_domega=True, precision="tf32x3")
+    d64, l64, dO64 = A.accord_dloss_dloglam(Xt, Xv, O32.double(), w.lam, want_domega=True)
+    assert abs(d32 - d64) <= 1e-4 * abs(d64), (d32, d64)
+    assert abs(l32 - l64) <= 1e-6 * abs(l64)
+    dd = dO64.cpu().numpy()
+    assert np.max(np.abs(dO32.double().cpu().numpy() - dd)) <= 1e-4 * np.max(np.abs(dd))
