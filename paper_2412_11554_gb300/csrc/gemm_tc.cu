@@ -561,8 +561,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       // this tile's problem: its iterate buffers, step and penalty
       const int cb = ctrl ? ctrl[b].cur : 0, nx = cb ^ 1;
       ea.out = prm.out[nx] ? prm.out[nx] + b * prm.s_out : nullptr;
-      ea.out_hi = prm.out_hi[nx] ? prm.out_hi[nx] + b * prm.s_plane : nullptr;
-      ea.out_lo = prm.out_lo[nx] ? prm.out_lo[nx] + b * prm.s_plane : nullptr;
+      using PE = typename Plane<PT>::E;  // s_plane counts plane elements
+      ea.out_hi = prm.out_hi[nx] ? static_cast<PE*>(prm.out_hi[nx]) + b * prm.s_plane : nullptr;
+      ea.out_lo = prm.out_lo[nx] ? static_cast<PE*>(prm.out_lo[nx]) + b * prm.s_plane : nullptr;
       ea.aux = prm.aux[cb] ? prm.aux[cb] + b * prm.s_aux : nullptr;
       ea.tau = ctrl ? (float)ctrl[b].tau : 0.f;
       if (batch && ctrl != nullptr) {
