@@ -234,6 +234,22 @@ const char* accord_last_error(void);
  * positive (the outputs are still written). */
 int accord_postprocess(int64_t p, const void* Omega, const accord_opts* opts, void* Theta_out, void* Rho_out);
 
+/* Compressed sparse rows of an estimate (Sec 3.1: the estimated graph is the
+ * nonzero pattern of Omega-hat): the entries of Omega (device p x p,
+ * row-major, element type per opts->precision) that are not +-0, row by row
+ * in increasing column order; a NaN counts as nonzero.
+ *   row_ptr  device int64_t[p + 1]: row i's entries are [row_ptr[i], row_ptr[i+1]);
+ *   col_idx  device int32_t[cap]: their columns;
+ *   vals     device [cap], Omega's element type: their values;
+ *   cap      entries col_idx and vals can hold;
+ *   *nnz     host: the number of nonzeros (written on every return after the
+ *            argument checks).
+ * When *nnz exceeds cap the call returns ACCORD_ENOMEM having written row_ptr
+ * only: call again with cap >= *nnz.  p must be below 2^31.  Synchronises the
+ * stream once, to read the count; the fill is queued after it. */
+int accord_to_csr(int64_t p, const void* Omega, const accord_opts* opts, int64_t* row_ptr, int32_t* col_idx,
+                  void* vals, int64_t cap, int64_t* nnz);
+
 /* ---- differentiation ------------------------------------------------------ */
 
 /* Adjoint of the smooth loss L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S)

@@ -11,6 +11,7 @@ from .accord import (  # noqa: F401
     accord_fit,
     accord_grad_x,
     accord_postprocess,
+    accord_to_csr,
     accord_dloss_dloglam,
     accord_path,
     accord_path_workspace_bytes,

@@ -62,7 +62,7 @@ class AccordPathEntry(ctypes.Structure):
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
-           "accord_dloss_dloglam", "accord_postprocess")
+           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr")
 
 _lib = None
 
@@ -108,6 +108,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_path_workspace_bytes.restype = ctypes.c_size_t
     lib.accord_postprocess.argtypes = [i64, P, opts_p, P, P]
     lib.accord_postprocess.restype = i32
+    lib.accord_to_csr.argtypes = [i64, P, opts_p, P, P, P, i64, ctypes.POINTER(i64)]
+    lib.accord_to_csr.restype = i32
     lib.accord_grad_x.argtypes = [P, i64, i64, P, opts_p, P]
     lib.accord_grad_x.restype = i32
     lib.accord_dloss_dloglam.argtypes = [P, i64, P, i64, i64, P, dbl, opts_p, ctypes.POINTER(dbl),
@@ -309,6 +311,36 @@ def accord_postprocess(Omega: torch.Tensor, *, theta: bool = True, rho: bool = T
     if status != OK:
         raise AccordError(status, "accord_postprocess")
     return T, Rh
+
+
+def accord_to_csr(Omega: torch.Tensor, *, nnz_hint: int | None = None, stream=None):
+    """(row_ptr int64 [p + 1], col_idx int32 [nnz], vals [nnz]) CUDA tensors of
+    the nonzero entries of Omega, row by row in column order.  nnz_hint sizes
+    the first attempt (e.g. FitStats.nnz_offdiag + p); a short buffer costs one
+    more call.  The element type follows Omega's dtype."""
+    lib = load_library()
+    p = Omega.shape[0]
+    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
+        raise ValueError("Omega must be a contiguous square CUDA tensor")
+    prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
+    o = accord_default_opts(precision=prec)
+    o.stream = _stream_handle(stream)
+    row_ptr = torch.empty(p + 1, dtype=torch.int64, device=Omega.device)
+    cap = int(nnz_hint) if nnz_hint is not None else p
+    nnz = ctypes.c_int64()
+    for _ in range(2):
+        cols = torch.empty(max(cap, 1), dtype=torch.int32, device=Omega.device)
+        vals = torch.empty(max(cap, 1), dtype=Omega.dtype, device=Omega.device)
+        status = lib.accord_to_csr(p, Omega.data_ptr(), ctypes.byref(o), row_ptr.data_ptr(), cols.data_ptr(),
+                                   vals.data_ptr(), cap, ctypes.byref(nnz))
+        if status == ENOMEM and nnz.value > cap:
+            cap = nnz.value
+            continue
+        break
+    if status != OK:
+        raise AccordError(status, "accord_to_csr")
+    k = nnz.value
+    return row_ptr, cols[:k], vals[:k]
 
 
 def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, precision: str | None = None,

@@ -27,7 +27,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Werror=pointer-arith",
          "--diag-error=1143", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "misc.cu", "sparse_y.cu", "accord_api.cu", "accord_eval.cu",
-           "accord_noalloc.cu", "accord_path.cu", "accord_diff.cu", "accord_post.cu"]
+           "accord_noalloc.cu", "accord_path.cu", "accord_diff.cu", "accord_post.cu", "accord_sparse.cu"]
 
 
 def _nvcc() -> str:

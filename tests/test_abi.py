@@ -100,6 +100,16 @@ def test_invalid_arguments_rejected_on_host(lib):
     """Argument checks happen before any device call, so they work here."""
     from paper_2412_11554_gb300 import accord
     o = accord.accord_default_opts()
+    # sparse export: missing Omega / row_ptr / nnz, p < 1, buffers missing for cap > 0
+    nz = ctypes.c_int64(-1)
+    dptr = ctypes.c_void_p(16)
+    assert lib.accord_to_csr(10, None, ctypes.byref(o), dptr, dptr, dptr, 4, ctypes.byref(nz)) == accord.EINVAL
+    assert nz.value == 0
+    assert lib.accord_to_csr(10, dptr, ctypes.byref(o), None, dptr, dptr, 4, ctypes.byref(nz)) == accord.EINVAL
+    assert lib.accord_to_csr(10, dptr, ctypes.byref(o), dptr, dptr, dptr, 4, None) == accord.EINVAL
+    assert lib.accord_to_csr(0, dptr, ctypes.byref(o), dptr, dptr, dptr, 4, ctypes.byref(nz)) == accord.EINVAL
+    assert lib.accord_to_csr(10, dptr, ctypes.byref(o), dptr, None, None, 4, ctypes.byref(nz)) == accord.EINVAL
+    assert lib.accord_to_csr(1 << 31, dptr, ctypes.byref(o), dptr, dptr, dptr, 4, ctypes.byref(nz)) == accord.EINVAL
     st = accord.AccordStats()
     dummy = ctypes.c_void_p(16)
     assert lib.accord_fit(None, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
