@@ -18,6 +18,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -158,10 +159,21 @@ def cpu_threads():
 
 
 # ---------------------------------------------------------------- ours -----
+def _code_only(src):
+    """Source text without comments and blank space, so that a change to a
+    comment does not count as a change to the kernel (string literals in
+    these files hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_digest():
+    """Digest of the prox kernel's code (its translation unit and the two
+    headers it inlines), comments excluded."""
     h = hashlib.sha256()
     for name in ("gemm_tc.cu", "tc_ptx.cuh", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2412_11554_gb300", "csrc", name), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_2412_11554_gb300", "csrc", name)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -79,10 +79,10 @@ typedef struct accord_opts {
     int32_t init_from_omega; /* 1: Omega holds the starting iterate on entry; 0: Omega^0 = I   */
     int32_t lipschitz_max_iter; /* Lanczos steps allowed for L, at most 128 (default 128)    */
     int32_t profile;         /* 1: time every GEMM launch with CUDA events (stats t_*_gemm_ms)  */
-    int32_t sparse_update;   /* mixed mode: 1 (default) forms Y+ = Y + Delta X^T from the nonzero
+    int32_t sparse_update;   /* mixed modes: 1 (default) forms Y+ = Y + Delta X^T from the nonzero
                                 entries of Delta (the iterate is sparse); 0: dense tensor-core
                                 product every trial.  Ignored in FP64 mode (always dense).    */
-    int32_t autotune;        /* accord_path, mixed mode: 1 (default) times the batched prox GEMM's
+    int32_t autotune;        /* accord_path, mixed modes: 1 (default) times the batched prox GEMM's
                                 tile raster and persistent grid on the first call for a shape
                                 and keeps the fastest; 0: fixed defaults                         */
     double  tau0;            /* initial step (default 1); <= 0 means 1/L                        */
@@ -119,7 +119,7 @@ typedef struct accord_stats {
     double  logdet_d;        /* sum_i log omega_ii of the returned Omega                         */
     double  epbic;           /* extended pseudo-BIC of Eq. 3.7 with opts->epbic_gamma:
                                 2n(-log det Omega_D + g) + nnz (log n + 4 gamma log p)           */
-    int32_t tile_group_m;    /* accord_path, mixed mode: raster group (cluster rows) of the
+    int32_t tile_group_m;    /* accord_path, mixed modes: raster group (cluster rows) of the
                                 batched prox GEMM in use (0 elsewhere)                           */
     int32_t tile_clusters;   /* ... and its persistent grid in clusters of 2 CTAs                */
 } accord_stats;
@@ -254,7 +254,7 @@ int accord_to_csr(int64_t p, const void* Omega, const accord_opts* opts, int64_t
 
 /* Adjoint of the smooth loss L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S)
  * in the data: GX_out = dL/dX = (1/n) X Omega^T Omega (n x p, device, element type per
- * precision: double for ACCORD_FP64, float for the mixed mode), formed as
+ * precision: double for ACCORD_FP64, float for the mixed modes), formed as
  * Y^T = X Omega^T and (1/n) Y^T Omega.  dL/dOmega = -diag(1/omega_ii) + Omega S is
  * accord_grad with smooth = 1.  X: device n x p FP32; Omega: device p x p. */
 int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts* opts,
@@ -272,9 +272,10 @@ int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const
  *   Omega_hat device, p x p, element type per opts->precision (a converged estimate)
  *   dloss, loss_val  host (either may be NULL): the derivative and L(Omega_hat; X_val)
  *   dOmega    device or NULL: p x p dOmega-hat / dlog(lambda), element type per precision
- * FP64 mode forms S and the held-out products with FP64 GEMMs; the mixed mode
- * uses the split-BF16 tensor-core products (FP32 accumulation, S written in
- * FP64, FP64 reductions).  The row systems are FP64 in both.  Errors: EINVAL; EUNSUPPORTED when a row's active set has more
+ * FP64 mode forms S and the held-out products with FP64 GEMMs; the mixed modes
+ * use their split-operand tensor-core products (FP32 accumulation, S written
+ * in FP64, FP64 reductions).  The row systems are FP64 in all modes.
+ * Errors: EINVAL; EUNSUPPORTED when a row's active set has more
  * than 128 entries; EDOMAIN when a row system is not positive definite (an
  * active set larger than the training rows can support) or Omega_hat has a
  * non-positive diagonal. */
@@ -327,8 +328,8 @@ typedef struct {
  * Returns ACCORD_OK when every estimate converged, ACCORD_NOT_CONVERGED when
  * some reached max_iter, else the first error among the records (or the
  * call's own error: EINVAL, EDOMAIN for non-finite data, ENOMEM, ECUDA).
- * opts->trace, init_from_omega and sparse_update are ignored (the mixed mode
- * always uses the sparse Delta update with its dense fallback). */
+ * opts->trace, init_from_omega and sparse_update are ignored (the mixed modes
+ * always use the sparse Delta update with its dense fallback). */
 int accord_path(const float* X, int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets,
                 int64_t n_sub, const double* lambdas, int64_t n_lambda, const accord_opts* opts,
                 accord_path_entry* entries, uint32_t* support, void* omega_best, int32_t* best_index,

@@ -43,12 +43,12 @@ struct Layout {
   size_t om[2] = {0, 0}, y[2] = {0, 0};
   size_t x64 = 0, xt64 = 0;                        // FP64 mode
   size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
-  size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed mode
+  size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed modes
   size_t gram = 0, lz_v = 0, lz_w = 0, lz_a = 0, lz_b = 0;
   size_t mask = 0;
   int64_t mask_ld = 0;  // 32-bit words per row of the refit support mask
   int lz_k = 0;
-  // sparse Delta update (mixed mode)
+  // sparse Delta update (mixed modes)
   bool sparse = false;
   int64_t nbuckets = 0;
   size_t xt32 = 0, bkt_keys = 0, bkt_vals = 0, bkt_cnt = 0, part_sy = 0;
@@ -124,7 +124,7 @@ Layout make_layout(int64_t n, int64_t p, int precision, int max_iter, int lanczo
   return L;
 }
 
-// The sparse Delta update runs in mixed mode; bucket keys hold a column index
+// The sparse Delta update runs in the mixed modes; bucket keys hold a column index
 // in 25 bits.
 bool use_sparse(const accord_opts& o, int64_t p) {
   return o.precision != ACCORD_FP64 && o.sparse_update != 0 && p < (1 << 25) - 1;
@@ -524,7 +524,7 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   if (!(L_given > 0.0)) {
     if (int e = setup_gram(P)) return e;
     // 0 = automatic: FP64 mode matches a dense eigensolver to rounding; the
-    // mixed mode needs L only to set the tau <= 1/L floor
+    // the mixed modes need L only to set the tau <= 1/L floor
     const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-8);
     ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st));
     nlaunch += 2;

@@ -305,7 +305,7 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   const size_t S_off = take(c, (size_t)p * p * 8), Gv_off = take(c, (size_t)p * p * 8);
   const size_t om_off = take(c, (size_t)p * p * 8);
   const size_t x_off = take(c, (size_t)n * ldk * 8), xt_off = take(c, (size_t)p * ldn * 8);
-  const size_t g32_off = take(c, f64 ? 0 : (size_t)p * p * 4);  // mixed mode: FP32 held-out gradient
+  const size_t g32_off = take(c, f64 ? 0 : (size_t)p * p * 4);  // mixed modes: FP32 held-out gradient
   Guard g;
   if (cudaMallocAsync(&g.ptr, c, st) != cudaSuccess) return kEnomem;
   g.st = st;

@@ -40,7 +40,7 @@ struct GatherParams {
   int64_t kpad;          // rows of every chain's matrix (zero beyond its K)
   double* x64;           // K x p rows (FP64), ld ldx, chain stride sx
   double* xt64;          // p x K (FP64, FP64 mode), ld ldt, chain stride st
-  float* xt32;           // p x K (FP32, mixed mode)
+  float* xt32;           // p x K (FP32, mixed modes)
   void *x_hi, *x_lo;    // K x p planes (mixed modes, type pt), ld ldx
   void *xt_hi, *xt_lo;  // p x K planes (mixed modes, type pt), ld ldt
   int64_t ldx, sx, ldt, st, sxp, stp;

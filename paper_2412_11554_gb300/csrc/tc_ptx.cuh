@@ -201,11 +201,11 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with 64-byte swizzling: rows of 64 bytes (32 BF16), 8-row swizzle atoms 512
-// bytes apart (stride byte offset), leading byte offset unused (1), descriptor
-// version 1 (bits 46-47), layout type SWIZZLE_64B (4, bits 61-63).  The tile
-// base must be 512-byte aligned; stepping K by 16 elements adds 32 bytes to
-// the start address.
+// with 64-byte swizzling: rows of 64 bytes (32 BF16 or 16 TF32), 8-row swizzle
+// atoms 512 bytes apart (stride byte offset), leading byte offset unused (1),
+// descriptor version 1 (bits 46-47), layout type SWIZZLE_64B (4, bits 61-63).
+// The tile base must be 512-byte aligned; stepping K by one MMA (16 BF16 or 8
+// TF32) adds 32 bytes to the start address.
 __device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
