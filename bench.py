@@ -419,7 +419,9 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": round(1e3 * t / max(args.steps, 1), 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": w.name, "p": p, "n": w.n, "lambda": w.lam, "kkt_tol": args.kkt_tol},
+           "config": {"workload": w.name, "p": p, "n": w.n, "lambda": w.lam, "kkt_tol": args.kkt_tol,
+                      "precision": "fp64_oracle", "tau0": 1.0, "beta": 0.5,
+                      "parallelism": f"host cores ({cores})", "l2": "not applicable (CPU)"},
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"per step one accepted FBS iteration on {rows} of {p} rows, scaled"},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
