@@ -71,6 +71,42 @@ def test_struct_layout_matches_c():
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, f
 
 
+def test_plain_c_program_links_and_calls_the_library(lib):
+    """A C11 program built with gcc against include/accord.h and linked with
+    libaccord.so: defaults, workspace sizing, status strings and host-side
+    argument errors, with no device work."""
+    src = r"""
+#include <stdio.h>
+#include <string.h>
+#include "accord.h"
+int main(void) {
+  accord_opts o;
+  accord_default_opts(&o);
+  if (o.precision != ACCORD_MIXED_BF16X3 || o.max_iter != 500) return 1;
+  size_t bf = accord_workspace_bytes(1000, 4000, &o);
+  o.precision = ACCORD_MIXED_TF32X3;
+  size_t tf = accord_workspace_bytes(1000, 4000, &o);
+  o.precision = ACCORD_FP64;
+  size_t f64 = accord_workspace_bytes(1000, 4000, &o);
+  if (!(bf > 0 && tf > bf && f64 > 0)) return 2;
+  if (strlen(accord_status_string(ACCORD_ENOMEM)) == 0) return 3;
+  long long nnz = -1;
+  if (accord_to_csr(0, (void*)16, &o, (int64_t*)16, NULL, NULL, 0, (int64_t*)&nnz) != ACCORD_EINVAL) return 4;
+  if (accord_fit(NULL, 10, 10, 0.1, &o, (void*)16, NULL, 0, NULL) != ACCORD_EINVAL) return 5;
+  printf("ok %zu %zu %zu\n", bf, tf, f64);
+  return 0;
+}
+"""
+    libdir = os.path.dirname(lib._name)
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "use.c"), os.path.join(d, "use")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), "-o", exe, c,
+                        "-L", libdir, "-laccord", f"-Wl,-rpath,{libdir}"], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok "), (r.returncode, r.stdout, r.stderr)
+
+
 def test_defaults_and_workspace_sizing(lib):
     from paper_2412_11554_gb300 import accord
     o = accord.accord_default_opts()

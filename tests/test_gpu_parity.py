@@ -342,37 +342,39 @@ def _f1(a, b):
     return 2.0 * tp / max(np.sum(pa) + np.sum(pb), 1)
 
 
-def test_scalefree_p5000_mixed_against_fp64(A):
-    """Scale-free p=5000, n=1000, lambda=0.15 at full size: the mixed BF16x3
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_scalefree_p5000_mixed_against_fp64(A, precision):
+    """Scale-free p=5000, n=1000, lambda=0.15 at full size: the mixed
     estimate against the FP64 GPU estimate (itself held to the oracle's iterate
     sequence at smaller sizes): relative Frobenius <= 1e-4, support F1, and
     the mixed estimate's KKT residual evaluated in FP64."""
     w = workload("scalefree")
     X = dev(w.X)
     O64, s64 = A.accord_fit(X, w.lam, precision="fp64", kkt_tol=1e-7, max_iter=3000)
-    O32, s32 = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=3000)
+    O32, s32 = A.accord_fit(X, w.lam, precision=precision, kkt_tol=2e-5, max_iter=3000)
     assert s64.status == 0 and s32.status == 0
     a, b = O32.double().cpu().numpy(), O64.cpu().numpy()
     err = rel_fro(a, b)
     f1 = _f1(a, b)
     G = A.accord_grad(X, O32.double()).cpu().numpy()
     kkt = R.kkt_residual(a, G, w.lam, w.lam)
-    print(f"p=5000 mixed vs fp64: rel_fro {err:.2e}, support F1 {f1:.6f}, FP64 KKT of mixed {kkt:.2e}")
+    print(f"p=5000 {precision} vs fp64: rel_fro {err:.2e}, support F1 {f1:.6f}, FP64 KKT {kkt:.2e}")
     assert err <= 1e-4
     assert f1 >= 0.999
     assert kkt <= 1e-4
 
 
-def test_hubblock_p40000_sampled_rows(A):
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_hubblock_p40000_sampled_rows(A, precision):
     """The benchmark's configuration (hub-and-block p=40000, n=1000,
-    lambda=0.1, mixed precision, KKT 1e-4): 24 sampled rows of the estimate
+    lambda=0.1, KKT 1e-4) in both mixed modes: 24 sampled rows of the estimate
     checked in FP64 by the oracle, row by row.  Rows decouple (proof of Thm
     3.2), so each row's KKT residual and its exact solution on its own
     support and signs (the row solve of Eq. 3.3) need only that row."""
     w = workload("hubblock")
     n, p = w.X.shape
     X = dev(w.X)
-    Om, st = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=1e-4, max_iter=500)
+    Om, st = A.accord_fit(X, w.lam, precision=precision, kkt_tol=1e-4, max_iter=500)
     assert st.status == 0
     Xd = w.X.astype(np.float64)
     rows = np.random.Generator(np.random.PCG64(99)).choice(p, size=24, replace=False)
@@ -387,6 +389,7 @@ def test_hubblock_p40000_sampled_rows(A):
         exact = R.row_solution(Xa.T @ Xa / n, pos, np.arange(len(act)), np.sign(Orows[k, act]), w.lam, w.lam)
         rel = float(np.max(np.abs(Orows[k, act] - exact)) / np.max(np.abs(exact)))
         worst_kkt, worst_rel = max(worst_kkt, kkt), max(worst_rel, rel)
-    print(f"p=40000 sampled rows: worst FP64 KKT {worst_kkt:.2e}, worst rel. to the exact row solution {worst_rel:.2e}")
+    print(f"p=40000 {precision} sampled rows: worst FP64 KKT {worst_kkt:.2e}, "
+          f"worst rel. to the exact row solution {worst_rel:.2e}")
     assert worst_kkt <= 1.5e-4
     assert worst_rel <= 1e-3
