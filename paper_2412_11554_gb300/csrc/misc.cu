@@ -3,6 +3,7 @@
 // L = sigma_max(S) (Sec 3.2) and the device-side accept / backtrack logic of
 // Algorithm 1.  All reductions of partial sums run in one block in a fixed
 // order, so every result is reproducible run to run.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -116,24 +117,23 @@ __global__ void transpose_x_f32_kernel(const float* __restrict__ X, int64_t n, i
   }
 }
 
+// Row-parallel: a block takes rows r, r + gridDim.x, ..., its threads sweep
+// the row's columns contiguously (no index division per element).
 template <class T>
 __global__ void set_identity_kernel(T* __restrict__ Om, int64_t p, int64_t ld) {
-  const int64_t total = p * ld;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / ld, c = i % ld;
-    Om[i] = (r == c) ? T(1) : T(0);
+  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+    T* row = Om + r * ld;
+    for (int64_t c = threadIdx.x; c < ld; c += blockDim.x) row[c] = (r == c) ? T(1) : T(0);
   }
 }
 
 template <class T>
 __global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
                                   int64_t ldd, int64_t p) {
-  const int64_t total = p * p;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / p, c = i % p;
-    dst[r * ldd + c] = src[r * lds + c];
+  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+    const T* s = src + r * lds;
+    T* d = dst + r * ldd;
+    for (int64_t c = threadIdx.x; c < p; c += blockDim.x) d[c] = s[c];
   }
 }
 
@@ -802,17 +802,17 @@ cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void
 }
 
 cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st) {
-  const unsigned g = grid_for(p * ld, 256);
-  if (is_f64) set_identity_kernel<double><<<g, 256, 0, st>>>((double*)Om, p, ld);
-  else set_identity_kernel<float><<<g, 256, 0, st>>>((float*)Om, p, ld);
+  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
+  if (is_f64) set_identity_kernel<double><<<g, 512, 0, st>>>((double*)Om, p, ld);
+  else set_identity_kernel<float><<<g, 512, 0, st>>>((float*)Om, p, ld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
                               int64_t p, cudaStream_t st) {
-  const unsigned g = grid_for(p * p, 256);
-  if (is_f64) copy_omega_kernel<double><<<g, 256, 0, st>>>((const double*)src, lds, (double*)dst, ldd, p);
-  else copy_omega_kernel<float><<<g, 256, 0, st>>>((const float*)src, lds, (float*)dst, ldd, p);
+  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
+  if (is_f64) copy_omega_kernel<double><<<g, 512, 0, st>>>((const double*)src, lds, (double*)dst, ldd, p);
+  else copy_omega_kernel<float><<<g, 512, 0, st>>>((const float*)src, lds, (float*)dst, ldd, p);
   return cudaGetLastError();
 }
 

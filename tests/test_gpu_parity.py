@@ -393,3 +393,52 @@ def test_hubblock_p40000_sampled_rows(A, precision):
           f"worst rel. to the exact row solution {worst_rel:.2e}")
     assert worst_kkt <= 1.5e-4
     assert worst_rel <= 1e-3
+
+
+# --------------------------------------------- closed forms, degenerate data ---
+
+PRECISION_TOL = {"fp64": (1e-10, 1e-8), "bf16x3": (2e-5, 1e-4), "tf32x3": (2e-5, 1e-4)}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "tf32x3"])
+def test_closed_form_estimates(A, precision):
+    """Cases with a closed-form minimiser, checked without the oracle:
+    lambda = 0 with n > p gives D^-1/2 S^-1 with D = diag(S^-1) (Sec 3.1);
+    lambda above every |S_ij| off the diagonal gives a diagonal estimate with
+    omega_ii = (-lambda + sqrt(lambda^2 + 4 s_ii)) / (2 s_ii); a zero column j
+    of X (a constant variable) gives omega_jj = 1 / lambda and nothing else in
+    row or column j."""
+    kkt, bar = PRECISION_TOL[precision]
+    rng = np.random.Generator(np.random.PCG64(77))
+    # lambda = 0, n > p
+    X = rng.standard_normal((400, 60)).astype(np.float32)
+    Xd = X.astype(np.float64)
+    S = Xd.T @ Xd / 400
+    Si = np.linalg.inv(S)
+    want = np.diag(1.0 / np.sqrt(np.diag(Si))) @ Si
+    Om, st = A.accord_fit(dev(X), 0.0, precision=precision, kkt_tol=kkt, max_iter=20000)
+    assert st.status == 0, st
+    assert rel_fro(Om.double().cpu().numpy(), want) <= bar
+    # lambda above every off-diagonal |S_ij|: a diagonal estimate
+    X = rng.standard_normal((50, 80)).astype(np.float32)
+    Xd = X.astype(np.float64)
+    S = Xd.T @ Xd / 50
+    lam = 1.01 * np.max(np.abs(S - np.diag(np.diag(S))))
+    s = np.diag(S)
+    want = np.diag((-lam + np.sqrt(lam * lam + 4 * s)) / (2 * s))
+    Om, st = A.accord_fit(dev(X), lam, precision=precision, kkt_tol=kkt, max_iter=20000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    assert not np.any(O - np.diag(np.diag(O)))
+    assert rel_fro(O, want) <= bar
+    # a zero column
+    X = rng.standard_normal((60, 40)).astype(np.float32)
+    X[:, 7] = 0.0
+    lam = 0.3
+    Om, st = A.accord_fit(dev(X), lam, precision=precision, kkt_tol=kkt, max_iter=20000)
+    assert st.status == 0, st
+    O = Om.double().cpu().numpy()
+    assert abs(O[7, 7] - 1.0 / lam) <= bar * (1.0 / lam)
+    assert not np.any(np.delete(O[7], 7)) and not np.any(np.delete(O[:, 7], 7))
+    ref = R.fit(X, lam, kkt_tol=1e-10, max_iter=20000)
+    assert rel_fro(O, ref.Omega) <= bar
