@@ -1,4 +1,4 @@
-// Sparse update of Y = Omega X^T after a prox step (mixed precision mode):
+// Sparse update of Y = Omega X^T after a prox step (mixed precision modes):
 // Y+ = Y + Delta X^T with Delta = Omega+ - Omega.  The iterate is sparse by
 // construction (Sec 3.3; the Remark after Thm 3.3 notes that sparsity cuts
 // the work of the product), and so is each step Delta, so instead of a dense
