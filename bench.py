@@ -271,6 +271,24 @@ def run_ours(args):
                 "avg_launch_ms": {"tc_gemm_prox": round(tp / max(npx, 1), 3), "y_update": round(ty / max(ny, 1), 3)},
                 "gemm_share_of_step": round((tp + ty) / ms, 3)}
 
+    # ----- the Y update, the second kernel: Y+ = Y + Delta X^T from the buckets -----
+    # algorithmic bytes per launch: Y in, Y+ out and its two BF16 planes
+    # (12 pn), X^T read once (4 pn) and the bucket entries (8 bytes each).
+    # The kernel itself gathers one X^T row (4n bytes) per entry, most of
+    # them from L2; that volume is reported beside it.
+    ent = sum(s.delta_entries for s in stats) / max(ny, 1)
+    if ent > 0 and ty > 0:
+        hbm = float(pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+        t_y = ty / max(ny, 1) / 1e3
+        by = 16.0 * p * n + 8.0 * ent
+        moved = 12.0 * p * n + 8.0 * ent + 4.0 * n * ent
+        roofline["y_update"] = {"bound": "hbm", "kernel": "sparse_y_kernel", "achieved": round(by / t_y / 1e9, 1),
+                                "peak": hbm, "unit": "GB/s", "frac": round(by / t_y / 1e9 / hbm, 4),
+                                "algorithmic_bytes_per_launch": round(by), "delta_entries_per_launch": round(ent),
+                                "gathered_bytes_per_launch": round(moved),
+                                "gathered_gbs": round(moved / t_y / 1e9, 1),
+                                "note": "gathered: one X^T row per applied Delta entry, mostly served by L2"}
+
     # ----- end to end through the public API with host buffers -----
     # Each step: X from pinned host memory, the fit, and the estimate back to
     # pinned host memory as compressed sparse rows (accord_to_csr: the exact

@@ -122,6 +122,8 @@ typedef struct accord_stats {
     int32_t tile_group_m;    /* accord_path, mixed modes: raster group (cluster rows) of the
                                 batched prox GEMM in use (0 elsewhere)                           */
     int32_t tile_clusters;   /* ... and its persistent grid in clusters of 2 CTAs                */
+    int64_t delta_entries;   /* mixed modes, single fit: nonzero Delta entries the sparse Y
+                                update applied, summed over the trials (0 elsewhere)             */
 } accord_stats;
 
 /* Fills *opts with the defaults listed above. */

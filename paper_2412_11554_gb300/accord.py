@@ -46,7 +46,7 @@ class AccordStats(ctypes.Structure):
         ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
         ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64), ("logdet_d", ctypes.c_double), ("epbic", ctypes.c_double),
-        ("tile_group_m", ctypes.c_int32), ("tile_clusters", ctypes.c_int32),
+        ("tile_group_m", ctypes.c_int32), ("tile_clusters", ctypes.c_int32), ("delta_entries", ctypes.c_int64),
     ]
 
 
@@ -152,6 +152,7 @@ class FitStats:
     trace: np.ndarray | None = None
     tile_group_m: int = 0
     tile_clusters: int = 0
+    delta_entries: int = 0
 
 
 def _stream_handle(stream) -> int | None:
@@ -233,7 +234,8 @@ def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: 
                     ctypes.byref(st))
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms,
-                     st.t_y_gemm_ms, st.n_launches, st.logdet_d, st.epbic, None)
+                     st.t_y_gemm_ms, st.n_launches, st.logdet_d, st.epbic, None,
+                     delta_entries=st.delta_entries)
     if tr is not None:
         stats.trace = tr[: st.iters + 1].copy()
     if check and status < 0:

@@ -39,7 +39,7 @@ struct Layout {
   int64_t ldk = 0;   // operand planes whose columns run over p
   int64_t ldyk = 0;  // operand planes whose columns run over n
   int64_t tiles_prox = 0, tiles_y = 0, trace_rows = 0;
-  size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0, part_fold = 0;
+  size_t ctrl = 0, trace = 0, part_prox = 0, part_y = 0, part_om = 0, bad = 0, part_fold = 0, dent = 0;
   size_t om[2] = {0, 0}, y[2] = {0, 0};
   size_t x64 = 0, xt64 = 0;                        // FP64 mode
   size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
@@ -77,6 +77,7 @@ Layout make_layout(int64_t n, int64_t p, int precision, int max_iter, int lanczo
   size_t c = 0;
   L.ctrl = take(c, sizeof(Ctrl));
   L.bad = take(c, 64);
+  L.dent = take(c, 64);  // Delta entries applied by the sparse Y update (a counter)
   L.trace = take(c, (size_t)L.trace_rows * kTraceFields * 8);
   L.part_prox = take(c, (size_t)L.tiles_prox * kProxSlots * 8);
   L.part_y = take(c, (size_t)L.tiles_y * kProxSlots * 8);
@@ -409,7 +410,8 @@ int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nla
   if (prof.on) ACCORD_CK(prof.mark(prof.y, P.st));
   ACCORD_CK(launch_decide(P.ctrl, at<double>(P.ws, L.part_y), ty, T.sp, trace,
                           L.sparse ? at<int>(P.ws, L.bkt_cnt) : nullptr, (int)L.nbuckets,
-                          L.sparse ? at<double>(P.ws, L.part_sy) : nullptr, P.st));
+                          L.sparse ? at<double>(P.ws, L.part_sy) : nullptr, P.st,
+                          L.sparse ? at<unsigned long long>(P.ws, L.dent) : nullptr));
   nlaunch += 4;
   return kOk;
 }
@@ -470,6 +472,7 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   int64_t nlaunch = 0;
   ACCORD_CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), P.st));
   ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.bad), 0, 64, P.st));
+  ACCORD_CK(cudaMemsetAsync(at<int>(ws, L.dent), 0, 64, P.st));
   ACCORD_CK(cudaMemsetAsync(at<double>(ws, L.trace), 0xff, (size_t)L.trace_rows * kTraceFields * 8, P.st));
   if (f64) {
     ACCORD_CK(launch_convert_x_f64(X32, X64in, n, p, at<double>(ws, L.x64), L.ldo, at<double>(ws, L.xt64), L.ldy,
@@ -613,8 +616,13 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     ACCORD_CK(cudaMemcpyAsync(o.trace, at<double>(ws, L.trace), (size_t)rows * kTraceFields * 8,
                               cudaMemcpyDeviceToHost, P.st));
   }
+  unsigned long long dent = 0;
+  if (L.sparse)
+    ACCORD_CK(cudaMemcpyAsync(&dent, at<unsigned long long>(ws, L.dent), sizeof(dent), cudaMemcpyDeviceToHost,
+                              P.st));
   ACCORD_CK(cudaStreamSynchronize(P.st));
   if (out) {
+    out->delta_entries = (int64_t)dent;
     out->iters = hc.t;
     out->trials = hc.trials;
     out->status = hc.status;

@@ -101,9 +101,11 @@ cudaError_t launch_rows_norm2(const void* A, int is_f64, int64_t rows, int64_t c
                               int64_t* nparts, cudaStream_t st);
 // One kProxSlots partial row with the statistics of Omega = I.
 cudaError_t launch_identity_stats(double* part, int64_t p, cudaStream_t st);
+// delta_entries (or null): adds the number of Delta entries the sparse Y
+// update applied in this trial.
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                           double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
-                          cudaStream_t st);
+                          cudaStream_t st, unsigned long long* delta_entries = nullptr);
 // Loss helper: reduce Omega stats and Y partials into out[0] = f, out[1] = g.
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st);

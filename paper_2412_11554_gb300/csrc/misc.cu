@@ -550,15 +550,33 @@ __global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles,
 }
 
 __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
-                              double* trace, int* bucket_counts, int nbuckets, const double* part_sparse) {
+                              double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
+                              unsigned long long* delta_entries) {
   if (ctrl->done) return;
   double s[kYSlots];
   // partial sums of whichever Y update ran: the sparse one (one row per
   // bucket) unless a bucket overflowed and the dense product ran instead
   const bool sparse_ran = part_sparse != nullptr && !ctrl->dense;
   fold_partials<kYSlots>(sparse_ran ? part_sparse : part, sparse_ran ? nbuckets : ntiles, 0u, s);
-  // the next trial's prox epilogue starts from empty Delta buckets
-  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[i] = 0;
+  // Delta entries the sparse update applied in this trial (none overflowed
+  // when it ran), then empty buckets for the next trial's prox epilogue
+  unsigned long long cnt = 0;
+  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) {
+    if (sparse_ran) cnt += (unsigned long long)bucket_counts[i];
+    bucket_counts[i] = 0;
+  }
+  if (delta_entries != nullptr && sparse_ran) {
+    __shared__ unsigned long long red[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+      *delta_entries += t;
+    }
+  }
   if (threadIdx.x == 0) decide_update(*ctrl, s, sp, trace);
 }
 
@@ -895,8 +913,9 @@ cudaError_t launch_identity_stats(double* part, int64_t p, cudaStream_t st) {
 
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                           double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
-                          cudaStream_t st) {
-  decide_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace, bucket_counts, nbuckets, part_sparse);
+                          cudaStream_t st, unsigned long long* delta_entries) {
+  decide_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace, bucket_counts, nbuckets, part_sparse,
+                                           delta_entries);
   return cudaGetLastError();
 }
 

@@ -253,6 +253,11 @@ def test_sparse_delta_update_matches_dense_and_oracle(A):
     Os, ss = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=5000, sparse_update=1)
     Od, sd = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=5000, sparse_update=0)
     assert ss.status == 0 and sd.status == 0
+    # the sparse update reports the Delta entries it applied: at least the
+    # off-diagonal nonzeros of the result (each entered once from Omega^0 = I),
+    # at most p^2 a trial; the dense product applies none
+    assert ss.nnz_offdiag <= ss.delta_entries <= ss.trials * 600 * 600
+    assert sd.delta_entries == 0
     Os, Od = Os.double().cpu().numpy(), Od.double().cpu().numpy()
     assert rel_fro(Os, ref.Omega) <= 1e-4
     assert rel_fro(Od, ref.Omega) <= 1e-4
