@@ -335,8 +335,9 @@ def run_ours(args):
 
         e2e = e2e_loop(False)
         e2e["result"] = "Omega-hat as compressed sparse rows (accord_to_csr), exact"
-        e2e_dense = e2e_loop(True)
-        e2e_dense["result"] = "Omega-hat dense, p x p FP32"
+        if world == 1:  # informational; it pins p^2 floats of host memory per rank
+            e2e_dense = e2e_loop(True)
+            e2e_dense["result"] = "Omega-hat dense, p x p FP32"
 
     # ----- FP64 GPU path on the same workload (few iterations, per-iteration rate) -----
     fp64 = None
