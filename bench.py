@@ -330,6 +330,12 @@ def run_ours(args):
             torch.cuda.synchronize()
             barrier()
             ms2 = e2[0].elapsed_time(e2[1])
+            if world > 1:  # whole job: iterations of all ranks over the slowest rank's time
+                tt2 = torch.tensor([ms2, float(it2)], device="cuda", dtype=torch.float64)
+                mx2 = tt2.clone()
+                dist.all_reduce(mx2, op=dist.ReduceOp.MAX)
+                dist.all_reduce(tt2, op=dist.ReduceOp.SUM)
+                ms2, it2 = float(mx2[0]), float(tt2[1])
             return {"value": round(it2 / (ms2 / 1e3), 3), "unit": UNIT,
                     "h2d_bytes_per_step": int(Xh.numel() * 4), "d2h_bytes_per_step": int(d2h)}
 
