@@ -8,6 +8,7 @@ the sources nor the flags changed.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import shutil
@@ -49,14 +50,28 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit and link libaccord.so; returns its path."""
+    """Compile every translation unit and link libaccord.so; returns its path.
+    Processes that call this at once (one per GPU) serialise on a file lock:
+    the first builds, the others find the stamp current and return."""
     stamp = os.path.join(LIBDIR, ".stamp")
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
+
+    def current() -> bool:
+        return os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig
+
+    if not force and current():
         return LIB
+    os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and current():
+            return LIB
+        return _build_locked(dig, stamp, verbose)
+
+
+def _build_locked(dig: str, stamp: str, verbose: bool) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
