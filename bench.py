@@ -618,10 +618,10 @@ def run_diff(args):
     achieved = bytes_alg / (ms / args.steps / 1e3) / 1e9
     pk, pk_src = peaks()
     peak = float(pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-    roofline = {"bound": "hbm", "kernel": "whole accord_dloss_dloglam call (15 launches)",
+    roofline = {"bound": "hbm", "kernel": "whole accord_dloss_dloglam call (12 launches)",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
                 "peak_source": f"hbm_gbs ({pk_src})", "traffic": None, "algorithmic_bytes_per_call": bytes_alg,
-                "note": "latency-bound at p=2000: 15 launches and 2000 small row systems per call"}
+                "note": "latency-bound at p=2000: 12 launches and 2000 small row systems per call"}
     e2e = None
     if not args.no_e2e:
         Xth, Xvh = torch.as_tensor(w.X_train).pin_memory(), torch.as_tensor(w.X_val).pin_memory()
@@ -656,7 +656,7 @@ def run_diff(args):
            "data": "synthetic (seeded AR(1) + random-edge precision, Gaussian X)",
            "config": {"workload": w.name, "p": p, "n": n, "n_val": nv, "lambda": w.lam,
                       "active_offdiag": int(st.nnz_offdiag), "l2": "working set (32 MB S, 16 MB Omega) within L2"},
-           "dloss_dloglam": d, "loss_val": lv, "gpu_launches": 15 * args.steps, "roofline": roofline, "e2e": e2e,
+           "dloss_dloglam": d, "loss_val": lv, "gpu_launches": 12 * args.steps, "roofline": roofline, "e2e": e2e,
            "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(out))
 

@@ -301,6 +301,10 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   const int64_t ldk = round_up(p, 8), ldn = round_up(n, 8);
   size_t c = 0;
+  // error words: [0] non-finite training rows, [1] row-system bits (1: an
+  // active set over 128 entries, 2: not positive definite), [2] non-finite
+  // held-out rows, [3] device error bits of the GEMMs
+  // results: res[0] = dloss, res[1..2] = f, g of the held-out loss
   const size_t err_off = take(c, 64), res_off = take(c, 64), contrib_off = take(c, (size_t)p * 8);
   const size_t S_off = take(c, (size_t)p * p * 8), Gv_off = take(c, (size_t)p * p * 8);
   const size_t om_off = take(c, (size_t)p * p * 8);
@@ -316,7 +320,7 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   if (f64) ACCORD_CK(cudaMemcpyAsync(Om64, Omega_hat, (size_t)p * p * 8, cudaMemcpyDeviceToDevice, st));
   else to_f64_kernel<float><<<blocks_for(p * p), 256, 0, st>>>(static_cast<const float*>(Omega_hat), p * p, Om64);
   ACCORD_CK(cudaGetLastError());
-  double f = 0.0, gval = 0.0;
+  double* res = at<double>(ws, res_off);
   if (f64) {
     // S = X^T X / n of the training rows and the held-out loss and gradient
     // -diag(1/omega) + Omega S_val, all in FP64
@@ -335,8 +339,8 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
     accord_opts o64 = o;
     o64.precision = ACCORD_FP64;
     o64.penalize_diag = 0;
-    if (int e = accord_loss(Xv, n_val, p, Om64, 0.0, &o64, &f, &gval)) return e;
-    if (int e = accord_grad(Xv, n_val, p, Om64, 1, &o64, at<double>(ws, Gv_off))) return e;
+    if (int e = eval_loss_grad_async(Xv, n_val, p, Om64, o64, 0.0, res + 1, 1, at<double>(ws, Gv_off), err + 2))
+      return e;
   } else {
     // mixed modes: the same products on the split-operand tensor-core path
     // (FP32 accumulation, FP64 output of S and FP64 reductions), the row
@@ -355,18 +359,16 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
       return kEcuda;
     t.a_hi[1] = t.a_hi[0];
     t.a_lo[1] = t.a_lo[0];
-    t.err = err + 1;
+    t.err = err + 3;
     tc_shape(t, p, p, n, pt);
     t.out64 = at<double>(ws, S_off);
     t.ldout64 = p;
     t.scale = (float)(1.0 / (double)n);
     ACCORD_CK(launch_tc_gemm(kModeGram, t, st));
     accord_opts om = o;
-    om.precision = o.precision;
     om.penalize_diag = 0;
-    if (int e = accord_loss(Xv, n_val, p, Omega_hat, 0.0, &om, &f, &gval)) return e;
     float* G32 = at<float>(ws, g32_off);
-    if (int e = accord_grad(Xv, n_val, p, Omega_hat, 1, &om, G32)) return e;
+    if (int e = eval_loss_grad_async(Xv, n_val, p, Omega_hat, om, 0.0, res + 1, 1, G32, err + 2)) return e;
     to_f64_kernel<float><<<blocks_for(p * p), 256, 0, st>>>(G32, p * p, at<double>(ws, Gv_off));
     ACCORD_CK(cudaGetLastError());
   }
@@ -392,13 +394,19 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
         at<double>(ws, S_off), Om64, at<double>(ws, Gv_off), p, lambda, pen, at<double>(ws, contrib_off),
         static_cast<float*>(dOmega), err + 1);
   ACCORD_CK(cudaGetLastError());
-  sum_kernel<<<1, 512, 0, st>>>(at<double>(ws, contrib_off), p, at<double>(ws, res_off));
+  sum_kernel<<<1, 512, 0, st>>>(at<double>(ws, contrib_off), p, res);
   ACCORD_CK(cudaGetLastError());
-  double d = 0.0;
-  ACCORD_CK(cudaMemcpyAsync(&d, at<double>(ws, res_off), 8, cudaMemcpyDeviceToHost, st));
-  int h[2] = {0, 0};
-  if (int e = read_err(err, st, h)) return e;
-  if (h[0] != 0) return kEdomain;
+  // one readback for the whole call
+  double hres[3] = {0.0, 0.0, 0.0};
+  int h[4] = {0, 0, 0, 0};
+  ACCORD_CK(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  ACCORD_CK(cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, st));
+  ACCORD_CK(cudaStreamSynchronize(st));
+  if (h[0] != 0 || h[2] != 0) return kEdomain;
+  if (h[3] != 0) {
+    set_last_error(__FILE__, __LINE__, "device error bits (an mbarrier wait timed out)");
+    return kEcuda;
+  }
   if (h[1] & 1) {
     set_last_error(__FILE__, __LINE__, "a row's active set exceeds 128 entries");
     return kEunsupported;
@@ -407,8 +415,8 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
     set_last_error(__FILE__, __LINE__, "a row's active-set system is not positive definite");
     return kEdomain;
   }
-  if (dloss) *dloss = d;
-  if (loss_val) *loss_val = f;
+  if (dloss) *dloss = hres[0];
+  if (loss_val) *loss_val = hres[1];
   return kOk;
 }
 

@@ -146,7 +146,80 @@ int finish_errors(const EvalBuffers& B, cudaStream_t st) {
   return kOk;
 }
 
+// f and g of Eq. 3.2 / Eq. 3.4 into res[0], res[1] (device) from the Y
+// partials of eval_y and the statistics of Omega.
+int loss_into(const EvalBuffers& B, const void* Omega, bool f64, int64_t n, int64_t p, int64_t tiles,
+              double lambda, double lam_d, double* res, cudaStream_t st) {
+  int64_t nomp = 0;
+  EVAL_CK(launch_omega_stats(Omega, f64, p, p, B.part_om, &nomp, st));
+  EVAL_CK(launch_loss_finish(B.part_om, nomp, B.part_y, tiles, lambda, lam_d, 1.0 / (double)n, res, st));
+  return kOk;
+}
+
+// G_out = Omega S (smooth = 0) or -diag(1/omega) + Omega S (smooth = 1) from
+// the Y stored by eval_y: the second product (1/n) Y X.
+int grad_into(const EvalBuffers& B, const void* Omega, bool f64, int64_t n, int64_t p, int smooth, void* G_out,
+              cudaStream_t st) {
+  const int64_t ldyk = round_up(n, 8);
+  if (f64) {
+    GemmF64Params g{};
+    g.A[0] = g.A[1] = B.y64;
+    g.lda = ldyk;
+    g.B = B.xt64;
+    g.ldb = ldyk;
+    g.M = p; g.N = p; g.K = n;
+    g.out[0] = g.out[1] = static_cast<double*>(G_out);
+    g.ldout = p;
+    g.aux[0] = g.aux[1] = static_cast<const double*>(Omega);
+    g.ldaux = p;
+    g.scale = 1.0 / (double)n;
+    g.smooth = smooth ? 1 : 0;
+    EVAL_CK(launch_gemm_f64(kModeGrad, g, st));
+    return kOk;
+  }
+  TcParams t{};
+  if (!encode_plane_map(&t.a_hi[0], B.y_hi, B.pt, p, n, ldyk, 128) ||
+      !encode_plane_map(&t.a_lo[0], B.y_lo, B.pt, p, n, ldyk, 128) ||
+      !encode_plane_map(&t.b_hi, B.xt_hi, B.pt, p, n, ldyk, tc_box_n()) ||
+      !encode_plane_map(&t.b_lo, B.xt_lo, B.pt, p, n, ldyk, tc_box_n()))
+    return kEcuda;
+  t.a_hi[1] = t.a_hi[0];
+  t.a_lo[1] = t.a_lo[0];
+  t.err = B.err + 1;
+  tc_shape(t, p, p, n, B.pt);
+  t.out[0] = t.out[1] = static_cast<float*>(G_out);
+  t.ldout = p;
+  t.aux[0] = t.aux[1] = static_cast<const float*>(Omega);
+  t.ldaux = p;
+  t.scale = (float)(1.0 / (double)n);
+  t.smooth = smooth ? 1 : 0;
+  EVAL_CK(launch_tc_gemm(kModeGrad, t, st));
+  return kOk;
+}
+
 }  // namespace
+
+int eval_loss_grad_async(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts& o,
+                         double lambda, double* res, int smooth, void* G_out, int* err) {
+  const bool f64 = o.precision == ACCORD_FP64;
+  cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+  const int64_t tiles = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
+  Bump meas;
+  EvalBuffers B;
+  B.pt = o.precision == ACCORD_MIXED_TF32X3 ? kPlaneTf32 : kPlaneBf16;
+  carve(meas, B, f64, true, n, p, tiles);
+  Scratch s;
+  if (cudaMallocAsync(&s.ptr, meas.used, st) != cudaSuccess) return kEnomem;
+  s.st = st;  // freed in stream order after the work queued below
+  Bump b;
+  b.base = static_cast<char*>(s.ptr);
+  carve(b, B, f64, true, n, p, tiles);
+  B.err = err;  // the caller's error words
+  if (int e = eval_y(B, f64, X, Omega, n, p, true, st)) return e;
+  if (int e = loss_into(B, Omega, f64, n, p, tiles, lambda, o.penalize_diag ? lambda : 0.0, res, st)) return e;
+  return grad_into(B, Omega, f64, n, p, smooth, G_out, st);
+}
+
 }  // namespace accord
 
 using namespace accord;
@@ -176,10 +249,7 @@ int accord_loss(const float* X, int64_t n, int64_t p, const void* Omega, double 
   carve(b, B, f64, false, n, p, tiles);
   EVAL_CK(cudaMemsetAsync(B.err, 0, 64, st));
   if (int e = eval_y(B, f64, X, Omega, n, p, false, st)) return e;
-  int64_t nomp = 0;
-  EVAL_CK(launch_omega_stats(Omega, f64, p, p, B.part_om, &nomp, st));
-  const double lam_d = o.penalize_diag ? lambda : 0.0;
-  EVAL_CK(launch_loss_finish(B.part_om, nomp, B.part_y, tiles, lambda, lam_d, 1.0 / (double)n, B.res, st));
+  if (int e = loss_into(B, Omega, f64, n, p, tiles, lambda, o.penalize_diag ? lambda : 0.0, B.res, st)) return e;
   double h[2] = {0, 0};
   EVAL_CK(cudaMemcpyAsync(h, B.res, sizeof(h), cudaMemcpyDeviceToHost, st));
   if (int e = finish_errors(B, st)) return e;
@@ -212,39 +282,7 @@ int accord_grad(const float* X, int64_t n, int64_t p, const void* Omega, int smo
   carve(b, B, f64, true, n, p, tiles);
   EVAL_CK(cudaMemsetAsync(B.err, 0, 64, st));
   if (int e = eval_y(B, f64, X, Omega, n, p, true, st)) return e;
-  if (f64) {
-    GemmF64Params g{};
-    g.A[0] = g.A[1] = B.y64;
-    g.lda = ldyk;
-    g.B = B.xt64;
-    g.ldb = ldyk;
-    g.M = p; g.N = p; g.K = n;
-    g.out[0] = g.out[1] = static_cast<double*>(G_out);
-    g.ldout = p;
-    g.aux[0] = g.aux[1] = static_cast<const double*>(Omega);
-    g.ldaux = p;
-    g.scale = 1.0 / (double)n;
-    g.smooth = smooth ? 1 : 0;
-    EVAL_CK(launch_gemm_f64(kModeGrad, g, st));
-  } else {
-    TcParams t{};
-    if (!encode_plane_map(&t.a_hi[0], B.y_hi, B.pt, p, n, ldyk, 128) ||
-        !encode_plane_map(&t.a_lo[0], B.y_lo, B.pt, p, n, ldyk, 128) ||
-        !encode_plane_map(&t.b_hi, B.xt_hi, B.pt, p, n, ldyk, tc_box_n()) ||
-        !encode_plane_map(&t.b_lo, B.xt_lo, B.pt, p, n, ldyk, tc_box_n()))
-      return kEcuda;
-    t.a_hi[1] = t.a_hi[0];
-    t.a_lo[1] = t.a_lo[0];
-    t.err = B.err + 1;
-    tc_shape(t, p, p, n, B.pt);
-    t.out[0] = t.out[1] = static_cast<float*>(G_out);
-    t.ldout = p;
-    t.aux[0] = t.aux[1] = static_cast<const float*>(Omega);
-    t.ldaux = p;
-    t.scale = (float)(1.0 / (double)n);
-    t.smooth = smooth ? 1 : 0;
-    EVAL_CK(launch_tc_gemm(kModeGrad, t, st));
-  }
+  if (int e = grad_into(B, Omega, f64, n, p, smooth, G_out, st)) return e;
   return finish_errors(B, st);
 }
 

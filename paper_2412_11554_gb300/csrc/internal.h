@@ -110,6 +110,15 @@ cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const 
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st);
 
+// --------------------------------------------------- loss and gradient ---
+// The loss parts res[0] = f, res[1] = g (device doubles) and the gradient
+// G_out (smooth = 0: Omega S; 1: -diag(1/omega) + Omega S) of X at Omega,
+// queued on opts.stream without waiting: one Y = Omega X^T serves both.
+// err (device, 2 ints): [0] counts non-finite entries of X, [1] collects
+// device error bits.  Scratch memory is freed in stream order.
+int eval_loss_grad_async(const float* X, int64_t n, int64_t p, const void* Omega, const struct accord_opts& o,
+                         double lambda, double* res, int smooth, void* G_out, int* err);
+
 // ------------------------------------------------------------ lambda path ---
 // A path runs one chain per subsample; chain c is problem c of the batch and
 // walks the penalties lambdas[0..n_lambda) in order, each fit starting from
