@@ -36,13 +36,19 @@ __device__ void fold_partials(const double* __restrict__ part, int64_t rows, uns
     if (lane == 0) sh[warp][q] = t;
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < W; ++q) {
+  // lane q of warp 0 folds slot q over the warps (FP64 is a slow pipe on this
+  // part: one thread a slot, not every thread every slot), then all read it
+  __shared__ double tot[W];
+  if (threadIdx.x < W) {
+    const int q = threadIdx.x;
     double t = sh[0][q];
     for (int w = 1; w < (int)(blockDim.x / 32); ++w)
       t = ((max_mask >> q) & 1u) ? fmax(t, sh[w][q]) : t + sh[w][q];
-    out[q] = t;
+    tot[q] = t;
   }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < W; ++q) out[q] = tot[q];
   __syncthreads();
 }
 
