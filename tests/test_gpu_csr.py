@@ -11,17 +11,6 @@ pytestmark = pytest.mark.gpu
 sp = pytest.importorskip("scipy.sparse")
 
 
-@pytest.fixture(scope="module")
-def A():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2412_11554_gb300 import build
-    build.build()
-    import paper_2412_11554_gb300 as pkg
-    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
-    return pkg
-
-
 def check_csr(A, O, **kw):
     """accord_to_csr(O) equals scipy's CSR of O (which drops +-0, keeps NaN)."""
     rp, ci, va = A.accord_to_csr(torch.as_tensor(O, device="cuda"), **kw)

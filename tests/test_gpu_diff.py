@@ -16,17 +16,6 @@ from synth import diff_workload
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def A():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2412_11554_gb300 import build
-    build.build()
-    import paper_2412_11554_gb300 as pkg
-    assert pkg.accord_device_check() == 0, "libaccord needs an sm_103 (GB300) device"
-    return pkg
-
-
 def dev(x, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
 
