@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="instead of timing: the fixed call sequence the ncu summaries were captured from "
+                         "(path: one accord_path with per-launch events; diff: a fit, three derivative and "
+                         "X-gradient calls, and three post-processing calls at p=16000)")
     ap.add_argument("--workload", choices=["fit", "path", "diff", "refit"], default="fit",
                     help="fit: one fit at p=40000 (default); path: lambda path x bootstrap subsamples at p=4000; "
                          "diff: held-out derivative in log(lambda) at p=2000; refit: Eq. 3.8 refit at p=40000")
@@ -756,9 +760,47 @@ def run_refit(args):
     print(json.dumps(out))
 
 
+def run_profile_sequence(args):
+    """The call sequences of profiles/path_p4000_L32_S16.md and
+    profiles/diff_p2000.md, for ncu to capture: no timing, a few statistics."""
+    import torch
+    from paper_2412_11554_gb300 import build as B
+    B.build()
+    import paper_2412_11554_gb300 as A
+    if args.workload == "path":
+        from synth import path_workload
+        pw = path_workload()
+        X = torch.as_tensor(pw.X, device="cuda")
+        r = A.accord_path(X, pw.subsamples, pw.lambdas, profile=1, omega_best=False, tau_warm=0, precision="mixed",
+                          kkt_tol=pw.kkt_tol, max_iter=2000)
+        torch.cuda.synchronize()
+        print(json.dumps({"solve_ms": r.stats.t_solve_ms, "prox_ms": r.stats.t_prox_gemm_ms,
+                          "prox_launches": r.stats.n_prox_gemm, "iters": r.stats.iters, "trials": r.stats.trials,
+                          "status": r.status}))
+    elif args.workload == "diff":
+        from synth import diff_workload
+        w = diff_workload()
+        Xt, Xv = torch.as_tensor(w.X_train, device="cuda"), torch.as_tensor(w.X_val, device="cuda")
+        O, st = A.accord_fit(Xt, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=20000)
+        for _ in range(3):
+            d, lv, _ = A.accord_dloss_dloglam(Xt, Xv, O, w.lam)
+            A.accord_grad_x(Xt, O)
+        p = 16000
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        Om = torch.eye(p, device="cuda") + 0.01 * (torch.rand(p, p, device="cuda", generator=gen) < 0.01).float()
+        for _ in range(3):
+            A.accord_postprocess(Om)
+        torch.cuda.synchronize()
+        print(json.dumps({"dloss": d, "status": st.status, "nnz_offdiag": st.nnz_offdiag}))
+    else:
+        raise SystemExit("--profile-run applies to --workload path or diff")
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_run:
+        run_profile_sequence(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "path":
         run_path(args)
