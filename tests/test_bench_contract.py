@@ -1,0 +1,56 @@
+"""Host-side checks of bench.py (no GPU): the committed ncu traffic belongs to
+the prox kernel's current code, a comment edit does not change the kernel's
+digest, and the reference arm (the FP64 oracle on the host cores) prints one
+JSON line with the contract's keys, from rank 0 only."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_committed_traffic_matches_the_kernel_code():
+    """profiles/traffic.json was captured from the prox kernel as it is now,
+    so bench.py reports its DRAM traffic instead of null."""
+    t = bench.profiled_traffic("tc_gemm_prox", bench.kernel_digest())
+    assert t is not None and t > 8 * 40000 ** 2  # at least Omega in and Omega+ out
+
+
+def test_digest_ignores_comments_and_blank_space():
+    code = "int f(int x) {\n  return x + 1;  // add one\n}\n"
+    commented = "/* the successor */\nint f(int x) {\n\n  return x + 1;\n}\n"
+    changed = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench._code_only(code) == bench._code_only(commented)
+    assert bench._code_only(code) != bench._code_only(changed)
+
+
+def _run(args, env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                          env=env, cwd=ROOT, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _run(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-seconds", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"]["workload"] == "hubblock_p40000_n1000"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
