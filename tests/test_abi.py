@@ -192,3 +192,22 @@ def test_invalid_arguments_rejected_on_host(lib):
                                     None, None) == accord.EINVAL
     for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert accord.accord_status_string(s)
+
+
+def test_binding_rejects_bad_arguments_on_the_host(lib):
+    """The Python binding checks tensors before any device call: CPU tensors,
+    wrong dtypes and shapes, unknown precision names."""
+    import torch
+    from paper_2412_11554_gb300 import accord
+    X = torch.zeros(4, 6)
+    with pytest.raises(ValueError):
+        accord.accord_fit(X, 0.1)                           # not a CUDA tensor
+    with pytest.raises(ValueError):
+        accord.accord_fit(X.double(), 0.1)                  # float64 X needs precision="fp64" (and CUDA)
+    with pytest.raises(KeyError):
+        accord.accord_fit(X, 0.1, precision="fp16")         # no such mode
+    with pytest.raises(ValueError):
+        accord.accord_to_csr(torch.zeros(3, 4))             # not square, not CUDA
+    with pytest.raises(ValueError):
+        accord.accord_postprocess(torch.zeros(3, 3))        # not CUDA
+    assert set(accord.PRECISIONS) == {"fp64", "mixed", "bf16x3", "tf32x3"}
