@@ -72,9 +72,9 @@ def test_struct_layout_matches_c():
 
 
 def test_plain_c_program_links_and_calls_the_library(lib):
-    """A C11 program built with gcc against include/accord.h and linked with
-    libaccord.so: defaults, workspace sizing, status strings and host-side
-    argument errors, with no device work."""
+    """A program built against include/accord.h as C11 (gcc) and as C++17
+    (g++) and linked with libaccord.so: defaults, workspace sizing, status
+    strings and host-side argument errors, with no device work."""
     src = r"""
 #include <stdio.h>
 #include <string.h>
@@ -98,13 +98,15 @@ int main(void) {
 }
 """
     libdir = os.path.dirname(lib._name)
-    with tempfile.TemporaryDirectory() as d:
-        c, exe = os.path.join(d, "use.c"), os.path.join(d, "use")
-        open(c, "w").write(src)
-        subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), "-o", exe, c,
-                        "-L", libdir, "-laccord", f"-Wl,-rpath,{libdir}"], check=True)
-        r = subprocess.run([exe], capture_output=True, text=True)
-    assert r.returncode == 0 and r.stdout.startswith("ok "), (r.returncode, r.stdout, r.stderr)
+    # the same program as C11 and as C++17 (the header's extern "C" block)
+    for compiler, std, ext in (("gcc", "-std=c11", "c"), ("g++", "-std=c++17", "cpp")):
+        with tempfile.TemporaryDirectory() as d:
+            c, exe = os.path.join(d, "use." + ext), os.path.join(d, "use")
+            open(c, "w").write(src)
+            subprocess.run([compiler, std, "-Wall", "-Werror", "-I", os.path.dirname(HEADER), "-o", exe, c,
+                            "-L", libdir, "-laccord", f"-Wl,-rpath,{libdir}"], check=True)
+            r = subprocess.run([exe], capture_output=True, text=True)
+        assert r.returncode == 0 and r.stdout.startswith("ok "), (compiler, r.returncode, r.stdout, r.stderr)
 
 
 def test_defaults_and_workspace_sizing(lib):
