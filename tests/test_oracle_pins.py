@@ -82,6 +82,25 @@ def pin_f_identity():
     return abs(R.objective(np.eye(8), X, lam) - (np.trace(S) / 2 + lam * 8)) <= 1e-12
 
 
+def pin_objective_diagonal():
+    """f at a diagonal Omega = diag(d), away from I: tr(Omega^T Omega S) keeps
+    only d_i^2 s_ii, so f = 1/2 sum d_i^2 s_ii - sum log d_i + lambda sum d_i
+    (Eq. 3.2), whatever the off-diagonal entries of S.  Per coordinate that is
+    1/2 s d^2 - log d + lambda d, minimised at d = (-lambda + sqrt(lambda^2 +
+    4 s)) / (2 s); f there lies below f one percent to either side."""
+    X = _gauss(30, 6, 33)
+    S = X.T @ X / 30
+    s = np.diag(S)
+    lam = 0.21
+    d = np.random.Generator(np.random.PCG64(34)).uniform(0.3, 3.0, size=6)
+    want = 0.5 * np.sum(d * d * s) - np.sum(np.log(d)) + lam * np.sum(d)
+    ok = abs(R.objective(np.diag(d), X, lam) - want) <= 1e-12 * abs(want)
+    dstar = (-lam + np.sqrt(lam * lam + 4 * s)) / (2 * s)
+    f0 = R.objective(np.diag(dstar), X, lam)
+    ok &= f0 < R.objective(np.diag(1.01 * dstar), X, lam) and f0 < R.objective(np.diag(0.99 * dstar), X, lam)
+    return bool(ok)
+
+
 def pin_diagonal_S():
     """Diagonal S: omega_ii = (-lambda + sqrt(lambda^2 + 4 s_i)) / (2 s_i) and
     omega_ij = 0 (Eq. 3.3 with z_ii = 1); without the diagonal penalty
@@ -330,7 +349,7 @@ def pin_reparameterisation():
                 np.allclose(R.partial_correlation(Om), rho, rtol=1e-13, atol=1e-13))
 
 
-PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity,
+PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
         pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
@@ -417,6 +436,18 @@ MUTANTS = {
     "partial_corr_one_sided": ("partial_correlation", lambda Om: -Om / np.diag(Om)[None, :]),
     "path_ignores_subsample": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
                                _f(X, [np.arange(np.asarray(X).shape[0])] * len(rows), lams, **kw)),
+    "kkt_drops_diag_lambda": ("kkt_residual", lambda Om, G, lam, lam_d, row0=0, _f=R.kkt_residual:
+                              _f(Om, G, lam, 0.0, row0=row0)),
+    "refit_finite_off_support": ("refit", lambda X, lam, support, phi, penalize_diag=True, **kw:
+                                 R.fit(X, np.where(np.asarray(support, bool) | np.eye(support.shape[0], dtype=bool),
+                                                   phi * lam, lam),
+                                       lam_diag=(phi * lam if penalize_diag else 0.0), **kw)),
+    "epbic_counts_diagonal": ("epbic", lambda Om, X, gm, _f=R.epbic:
+                              _f(Om, X, gm) + Om.shape[0] * (np.log(np.asarray(X).shape[0])
+                                                             + 4 * gm * np.log(Om.shape[0]))),
+    "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
+                               _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
+                               + float(np.sum(np.log(R.diag_entries(Om))))),
 }
 
 
