@@ -232,16 +232,24 @@ def pin_epbic_diagonal():
 def pin_path_warm_start():
     """Warm starts along the lambda path reach the minimiser a cold start
     reaches (Thm 3.2: it is unique): on a bootstrap subsample, every path
-    estimate equals the cold fit of X[rows] at that lambda."""
+    estimate equals the cold fit of X[rows] at that lambda, and every fit
+    after the first starts from the previous penalty's estimate."""
     w = workload("er", p=30, n=40)
     rows = [np.random.Generator(np.random.PCG64(51)).integers(0, 40, size=35)]
     lams = [0.5, 0.3, 0.2, 0.12]
     pr = R.lambda_path(w.X, rows, lams, kkt_tol=1e-11, max_iter=20000)
     Xs = np.asarray(w.X, dtype=np.float64)[rows[0]]
     ok = True
+    prev = np.eye(30)
     for k, lam in enumerate(lams):
         c = R.fit(Xs, lam, kkt_tol=1e-11, max_iter=20000)
         ok &= pr.fits[0][k].status == R.OK and np.max(np.abs(pr.fits[0][k].Omega - c.Omega)) <= 1e-8
+        # warm start (Sec 3.4): the fit at lambda_k begins at the estimate of
+        # lambda_{k-1} (I for the first), so its first objective value is f of
+        # that estimate at the new penalty
+        f0 = R.objective(prev, Xs, lam)
+        ok &= abs(pr.fits[0][k].f[0] - f0) <= 1e-12 * abs(f0)
+        prev = pr.fits[0][k].Omega
     return bool(ok)
 
 
@@ -445,6 +453,13 @@ MUTANTS = {
     "epbic_counts_diagonal": ("epbic", lambda Om, X, gm, _f=R.epbic:
                               _f(Om, X, gm) + Om.shape[0] * (np.log(np.asarray(X).shape[0])
                                                              + 4 * gm * np.log(Om.shape[0]))),
+    "prox_threshold_without_tau": ("prox", lambda A, tau, lam, lam_d, row0=0, _f=R.prox:
+                                   _f(A, tau, np.asarray(lam) / tau, lam_d, row0=row0)),
+    "trial_steps_uphill": ("fbs_trial", lambda Om, Y, G, X, tau, lam, lam_d, row0=0, _f=R.fbs_trial:
+                           _f(Om, Y, -G, X, tau, lam, lam_d, row0=row0)),
+    "path_cold_starts": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
+                         _f(X, rows, lams, **{**kw, "cold_every": 1})),
+    "epbic_distinct_rows": ("epbic", lambda Om, X, gm, _f=R.epbic: _f(Om, np.unique(np.asarray(X), axis=0), gm)),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
