@@ -229,6 +229,24 @@ def pin_epbic_diagonal():
     return abs(R.epbic(np.diag(w), X, 0.7) - want) <= 1e-10 * abs(want)
 
 
+def pin_epbic_edges():
+    """The edge terms of Eq. 3.7 on an Omega with k off-diagonal nonzeros (a
+    tridiagonal one, k = 2(p - 1)): gamma enters only through 4 gamma k log p,
+    so two gammas differ by 4 (g1 - g0) k log p; and duplicating every row of
+    X keeps S and doubles n, so with L the bracket of Eq. 3.7,
+    E(X_dup) - 2 E(X) = k (log 2n - 2 log n) - 4 gamma k log p."""
+    n, p = 25, 9
+    X = _gauss(n, p, 41)
+    Om = np.eye(p) * 1.3 + np.diag(np.full(p - 1, 0.2), 1) - np.diag(np.full(p - 1, 0.15), -1)
+    k = 2 * (p - 1)
+    g0, g1 = 0.0, 0.75
+    ok = abs((R.epbic(Om, X, g1) - R.epbic(Om, X, g0)) - 4 * (g1 - g0) * k * np.log(p)) <= 1e-9
+    Xd = np.vstack([X, X])
+    want = k * (np.log(2 * n) - 2 * np.log(n)) - 4 * g1 * k * np.log(p)
+    ok &= abs((R.epbic(Om, Xd, g1) - 2 * R.epbic(Om, X, g1)) - want) <= 1e-9
+    return bool(ok)
+
+
 def pin_path_warm_start():
     """Warm starts along the lambda path reach the minimiser a cold start
     reaches (Thm 3.2: it is unique): on a bootstrap subsample, every path
@@ -360,7 +378,7 @@ def pin_reparameterisation():
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
-        pin_epbic_diagonal, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
+        pin_epbic_diagonal, pin_epbic_edges, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
         pin_implicit_dloglam_fd, pin_reparameterisation]
 
 
@@ -460,6 +478,12 @@ MUTANTS = {
     "path_cold_starts": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
                          _f(X, rows, lams, **{**kw, "cold_every": 1})),
     "epbic_distinct_rows": ("epbic", lambda Om, X, gm, _f=R.epbic: _f(Om, np.unique(np.asarray(X), axis=0), gm)),
+    "theta_hat_right_scaled": ("theta_hat", lambda Om: Om * np.diag(Om)[None, :]),
+    "epbic_ignores_gamma": ("epbic", lambda Om, X, gm, _f=R.epbic: _f(Om, X, 0.0)),
+    "implicit_sign_flipped": ("implicit_dloglam", lambda O, Xt, Xv, lam, penalize_diag=True, _f=R.implicit_dloglam:
+                              tuple(-v for v in _f(O, Xt, Xv, lam, penalize_diag=penalize_diag))),
+    "covariance_n_minus_1": ("sample_covariance", lambda X: np.asarray(X, float).T @ np.asarray(X, float)
+                             / (np.asarray(X).shape[0] - 1)),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
