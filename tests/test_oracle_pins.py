@@ -247,6 +247,40 @@ def pin_epbic_edges():
     return bool(ok)
 
 
+def pin_kkt_min_norm_subgradient():
+    """The KKT residual of Eq. 3.3 is the largest entry (in magnitude) of the
+    minimum-norm element of the subdifferential of f, found here by search:
+    off the diagonal the set is {G_ij + lambda z} with z = sign(omega_ij), or
+    z in [-1, 1] (a fine grid) where omega_ij = 0; on the diagonal it is
+    G_ii - 1/omega_ii + lambda_d. Each entry is checked alone: every other
+    entry of G sits at a stationary value, so the residual is that entry's."""
+    rng = np.random.Generator(np.random.PCG64(43))
+    p, lam, lam_d = 6, 0.3, 0.25
+    Om = rng.normal(size=(p, p)) * (rng.random((p, p)) < 0.5)
+    np.fill_diagonal(Om, rng.uniform(0.5, 2.0, size=p))
+    G0 = np.where(Om != 0, -lam * np.sign(Om), 0.0)
+    np.fill_diagonal(G0, 1.0 / np.diag(Om) - lam_d)
+    if R.kkt_residual(Om, G0, lam, lam_d) > 1e-12:
+        return False
+    z = np.linspace(-1.0, 1.0, 40001)
+    kinds = set()
+    for i in range(p):
+        for j in range(p):
+            g = rng.normal(scale=0.5)
+            if i == j:
+                want, kind = abs(g - 1.0 / Om[i, i] + lam_d), "diag"
+            elif Om[i, j] != 0:
+                want, kind = abs(g + lam * np.sign(Om[i, j])), "nonzero"
+            else:
+                want, kind = float(np.min(np.abs(g + lam * z))), "zero"
+            kinds.add(kind)
+            G = G0.copy()
+            G[i, j] = g
+            if abs(R.kkt_residual(Om, G, lam, lam_d) - want) > 1e-4 * lam:
+                return False
+    return kinds == {"diag", "nonzero", "zero"}
+
+
 def pin_path_warm_start():
     """Warm starts along the lambda path reach the minimiser a cold start
     reaches (Thm 3.2: it is unique): on a bootstrap subsample, every path
@@ -378,7 +412,7 @@ def pin_reparameterisation():
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
-        pin_epbic_diagonal, pin_epbic_edges, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
+        pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
         pin_implicit_dloglam_fd, pin_reparameterisation]
 
 
@@ -484,10 +518,22 @@ MUTANTS = {
                               tuple(-v for v in _f(O, Xt, Xv, lam, penalize_diag=penalize_diag))),
     "covariance_n_minus_1": ("sample_covariance", lambda X: np.asarray(X, float).T @ np.asarray(X, float)
                              / (np.asarray(X).shape[0] - 1)),
+    "partial_corr_zero_diagonal": ("partial_correlation", lambda Om, _f=R.partial_correlation:
+                                   _f(Om) - np.eye(Om.shape[0])),
+    "path_selects_largest_epbic": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
+                                   _path_argmax(_f(X, rows, lams, **kw))),
+    "kkt_nonzero_as_zero": ("kkt_residual", lambda Om, G, lam, lam_d, row0=0, _f=R.kkt_residual:
+                            _f(np.zeros_like(Om) + np.where(np.eye(Om.shape[0], Om.shape[1], k=row0) > 0, Om, 0.0),
+                               G, lam, lam_d, row0=row0)),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
 }
+
+
+def _path_argmax(pr):
+    best = [int(np.argmax(pr.epbic[:, s])) for s in range(pr.epbic.shape[1])]
+    return R.PathResult(pr.lambdas, pr.fits, pr.epbic, best, [pr.fits[s][b].Omega for s, b in enumerate(best)])
 
 
 def _implicit_without_log_term(O, Xt, Xv, lam):
