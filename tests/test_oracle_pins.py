@@ -181,6 +181,37 @@ def pin_kkt_descent_path():
     return bool(ok)
 
 
+def _tail_slopes(e, floor):
+    """Slopes of log e over the middle and last thirds of the iterations where
+    e stays above the rounding floor."""
+    t = np.nonzero(e > floor)[0]
+    k = len(t) // 3
+    return [np.polyfit(tt, np.log(e[tt]), 1)[0] for tt in (t[k:2 * k], t[2 * k:])]
+
+
+def pin_linear_rate():
+    """Thm 3.3, both step-size cases (i: beta = 1, tau = 1/L; ii: backtracking
+    with beta = 1/2): f(Omega^t) - f* decays at a steady geometric rate, with
+    f* taken from the exact row solve on the converged support; the steps
+    ||Omega^(t+1) - Omega^t|| decay geometrically too (the iterate bound)."""
+    w = workload("ar1", p=60, n=40)
+    X = w.X.astype(np.float64)
+    S = X.T @ X / X.shape[0]
+    L = R.lipschitz(X)
+    ok = True
+    for kw in (dict(beta=1.0, tau0=1.0 / L), dict(beta=0.5)):
+        r = R.fit(X, w.lam, kkt_tol=1e-13, max_iter=20000, **kw)
+        ok &= r.status == R.OK
+        P = R.polish(r.Omega, S, w.lam, w.lam)
+        f_star = R.objective(P, X, w.lam)
+        e = np.array(r.f) - f_star
+        ok &= bool(e.min() >= -1e-13 * abs(f_star))
+        for ee, floor in ((e, 1e-11 * abs(f_star)), (np.array(r.delta_fro), 1e-9)):
+            s1, s2 = _tail_slopes(ee, floor)
+            ok &= s1 < 0 and s2 < 0 and abs(s1 - s2) <= 0.25 * abs(s2)
+    return bool(ok)
+
+
 def pin_line_search_identity():
     """g(O+) - g(O) - <Delta, grad g(O)> = ||Delta X^T||^2 / (2n) (g is quadratic),
     so the printed and difference forms of the test agree away from rounding."""
@@ -411,7 +442,7 @@ def pin_reparameterisation():
 
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
-        pin_kkt_descent_path, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
+        pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
         pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
         pin_implicit_dloglam_fd, pin_reparameterisation]
 
