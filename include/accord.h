@@ -25,6 +25,12 @@
  *     No call aborts, throws or traps the GPU; device loops are bounded.
  *   - Only compute capability 10.3 (GB300, sm_103a) is supported; any other
  *     device gives ACCORD_EUNSUPPORTED.  There is no CPU fallback.
+ *   - Host threads: the first call of an entry point on a device sets kernel
+ *     attributes (shared memory opt-in, persistent grid size) and caches them
+ *     in unsynchronised process-wide variables.  Make that first call from one
+ *     thread; after it, calls from several threads on their own streams and
+ *     workspaces are independent (the tile autotuner's table is locked),
+ *     except accord_loss_f64_noalloc, whose scratch array all calls share.
  */
 #ifndef ACCORD_H_
 #define ACCORD_H_
@@ -218,8 +224,9 @@ int accord_device_check(void);
 int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double* Omega, double lambda,
                             int penalize_diag, void* stream, double* fg_out);
 
-/* Description of the first failure of the calling thread's most recent
- * accord_fit / accord_loss / accord_grad call ("" when it succeeded): the
+/* Description of the first failure of the calling thread's most recent call
+ * of an entry point that queues GPU work (fit, refit, path, loss, gradients,
+ * derivative, post-processing, CSR export; "" when it succeeded): the
  * source location and the CUDA error string or the device error bits.  The
  * pointer stays valid until the thread's next call. */
 const char* accord_last_error(void);

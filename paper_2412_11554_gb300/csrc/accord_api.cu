@@ -713,7 +713,6 @@ int accord_refit(const float* X, int64_t n, int64_t p, double lambda, double phi
 
 int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, double* Omega,
                    void* workspace, size_t ws_bytes, accord_stats* out) {
-  if (X == nullptr) return kEinval;
   const int s = fit_impl(nullptr, X, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
   if (out) out->status = s;
   return s;

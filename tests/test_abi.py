@@ -159,6 +159,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.accord_fit(dummy, 10, 10, 0.1, ctypes.byref(bad), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
     assert st.status == accord.EINVAL
     assert lib.accord_fit_f64(dummy, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, None) == accord.EUNSUPPORTED
+    st.status, st.iters = 99, 99                        # a NULL X still fills the stats
+    assert lib.accord_fit_f64(None, 10, 10, 0.1, ctypes.byref(o), dummy, None, 0, ctypes.byref(st)) == accord.EINVAL
+    assert (st.status, st.iters) == (accord.EINVAL, 0)
     # refit: missing Omega_hat, phi outside [0, 1], negative epBIC gamma
     assert lib.accord_refit(dummy, 10, 10, 0.1, 0.5, None, ctypes.byref(o), dummy, None, 0,
                             ctypes.byref(st)) == accord.EINVAL
