@@ -179,9 +179,62 @@ def accord_workspace_bytes(n: int, p: int, **kw) -> int:
     return int(load_library().accord_workspace_bytes(n, p, ctypes.byref(accord_default_opts(**kw))))
 
 
-def _check_x(X: torch.Tensor, dtype=torch.float32) -> None:
-    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == dtype and X.dim() == 2 and X.is_contiguous()):
-        raise ValueError(f"X must be a contiguous 2-D CUDA {dtype} tensor")
+def _check_tensor(t, name: str, dtype, shape=None, ndim: int | None = None) -> None:
+    """Raise ValueError unless t is a contiguous tensor of the given dtype (one
+    dtype or a tuple) and shape, on the current CUDA device.  The library reads
+    raw device pointers with the element type and extents it is told, so a
+    host tensor, a narrower dtype or a smaller shape must never reach it.
+    dtype and shape are checked first, so they are reported for host tensors too."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch.Tensor")
+    dts = dtype if isinstance(dtype, tuple) else (dtype,)
+    if t.dtype not in dts:
+        raise ValueError(f"{name} must be {' or '.join(str(d) for d in dts)}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must be {ndim}-D, got {t.dim()}-D")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, not the current device cuda:{torch.cuda.current_device()}")
+
+
+def _check_x(X: torch.Tensor, dtype=torch.float32, name: str = "X") -> None:
+    _check_tensor(X, name, dtype, ndim=2)
+
+
+def _omega_dtype(prec: int) -> torch.dtype:
+    """Element type of Omega (and of every p x p output) in a precision mode."""
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+def _check_workspace(workspace: torch.Tensor | None) -> tuple[int | None, int]:
+    if workspace is None:
+        return None, 0
+    if not isinstance(workspace, torch.Tensor):
+        raise ValueError("workspace must be a torch.Tensor")
+    _check_tensor(workspace, "workspace", workspace.dtype)
+    return workspace.data_ptr(), workspace.numel() * workspace.element_size()
+
+
+def _precision_of(precision: str | None, Omega: torch.Tensor) -> int:
+    """The named mode, else the one Omega's dtype implies (float64: FP64,
+    otherwise BF16x3); a named mode must then match Omega's dtype."""
+    if precision:
+        return PRECISIONS[precision]
+    return FP64 if isinstance(Omega, torch.Tensor) and Omega.dtype == torch.float64 else MIXED_BF16X3
+
+
+def _check_square(Omega: torch.Tensor) -> int:
+    """p of a square float32 / float64 Omega on the current CUDA device."""
+    if not isinstance(Omega, torch.Tensor) or Omega.dim() != 2:
+        raise ValueError("Omega must be a 2-D torch.Tensor")
+    p = Omega.shape[0]
+    _check_tensor(Omega, "Omega", (torch.float32, torch.float64), (p, p))
+    return p
 
 
 def accord_refit(X: torch.Tensor, lam: float, phi: float, Omega_hat: torch.Tensor, **kw) -> tuple[torch.Tensor, FitStats]:
@@ -204,13 +257,18 @@ def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: 
     if x64 and prec != FP64:
         raise ValueError("float64 X requires precision='fp64'")
     n, p = X.shape
-    odt = torch.float64 if prec == FP64 else torch.float32
+    odt = _omega_dtype(prec)
+    ws_ptr, ws_bytes = _check_workspace(workspace)
+    if _refit is not None:
+        if x64:
+            raise ValueError("refit needs float32 X")
+        _check_tensor(_refit[1], "Omega_hat", odt, (p, p))
     if Omega is None:
         if init_from_omega:
             raise ValueError("init_from_omega needs Omega")
         Omega = torch.empty((p, p), dtype=odt, device=X.device)
-    elif not (Omega.is_cuda and Omega.dtype == odt and Omega.shape == (p, p) and Omega.is_contiguous()):
-        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA {odt} tensor")
+    else:
+        _check_tensor(Omega, "Omega", odt, (p, p))
     o = accord_default_opts(precision=prec, init_from_omega=int(init_from_omega), **opts)
     o.stream = _stream_handle(stream)
     tr = None
@@ -218,14 +276,9 @@ def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: 
         tr = np.full((o.max_iter + 2, TRACE_FIELDS), np.nan)
         o.trace = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         o.trace_cap = tr.shape[0]
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     st = AccordStats()
     if _refit is not None:
         phi, Oh = _refit
-        if x64 or not (Oh.is_cuda and Oh.dtype == odt and Oh.shape == (p, p) and Oh.is_contiguous()):
-            raise ValueError(f"refit needs float32 X and a contiguous {p}x{p} CUDA {odt} Omega_hat")
         status = lib.accord_refit(X.data_ptr(), n, p, float(lam), phi, Oh.data_ptr(), ctypes.byref(o),
                                   Omega.data_ptr(), ws_ptr, ws_bytes, ctypes.byref(st))
     else:
@@ -248,11 +301,12 @@ def accord_loss(X: torch.Tensor, Omega: torch.Tensor, lam: float, *, precision: 
     """(f, g) of Eq. 3.2 / Eq. 3.4 at Omega; precision follows Omega's dtype."""
     lib = load_library()
     _check_x(X)
-    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
+    n, p = X.shape
+    prec = _precision_of(precision, Omega)
+    _check_tensor(Omega, "Omega", _omega_dtype(prec), (p, p))
     o = accord_default_opts(precision=prec, penalize_diag=int(penalize_diag))
     o.stream = _stream_handle(stream)
     f, g = ctypes.c_double(), ctypes.c_double()
-    n, p = X.shape
     status = lib.accord_loss(X.data_ptr(), n, p, Omega.data_ptr(), float(lam), ctypes.byref(o), ctypes.byref(f),
                              ctypes.byref(g))
     if status != OK:
@@ -265,12 +319,17 @@ def accord_grad(X: torch.Tensor, Omega: torch.Tensor, smooth: bool = False, *, p
     """Omega S (smooth=False) or -Omega_D^-1 + Omega S (smooth=True)."""
     lib = load_library()
     _check_x(X)
-    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
-    o = accord_default_opts(precision=prec)
-    o.stream = _stream_handle(stream)
     n, p = X.shape
+    prec = _precision_of(precision, Omega)
+    _check_tensor(Omega, "Omega", _omega_dtype(prec), (p, p))
     if out is None:
         out = torch.empty_like(Omega)
+    else:
+        _check_tensor(out, "out", Omega.dtype, (p, p))
+        if out.data_ptr() == Omega.data_ptr():
+            raise ValueError("out must not alias Omega")
+    o = accord_default_opts(precision=prec)
+    o.stream = _stream_handle(stream)
     status = lib.accord_grad(X.data_ptr(), n, p, Omega.data_ptr(), int(bool(smooth)), ctypes.byref(o),
                              out.data_ptr())
     if status != OK:
@@ -286,10 +345,10 @@ def accord_loss_f64_noalloc(X: torch.Tensor, Omega: torch.Tensor, lam: float, fg
     lib = load_library()
     _check_x(X, torch.float64)
     n, p = X.shape
-    if not (Omega.is_cuda and Omega.dtype == torch.float64 and Omega.shape == (p, p) and Omega.is_contiguous()):
-        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA float64 tensor")
-    if not (fg_out.is_cuda and fg_out.dtype == torch.float64 and fg_out.numel() >= 2):
-        raise ValueError("fg_out must be a CUDA float64 tensor with at least 2 elements")
+    _check_tensor(Omega, "Omega", torch.float64, (p, p))
+    _check_tensor(fg_out, "fg_out", torch.float64)
+    if fg_out.numel() < 2:
+        raise ValueError("fg_out must hold at least 2 elements")
     status = lib.accord_loss_f64_noalloc(X.data_ptr(), n, p, Omega.data_ptr(), float(lam), int(bool(penalize_diag)),
                                          _stream_handle(stream), fg_out.data_ptr())
     if status != OK:
@@ -300,9 +359,7 @@ def accord_postprocess(Omega: torch.Tensor, *, theta: bool = True, rho: bool = T
     """(Theta-hat = Omega_D Omega, partial correlations) of an estimate (Sec 3.1);
     either may be skipped (None).  Precision follows Omega's dtype."""
     lib = load_library()
-    p = Omega.shape[0]
-    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
-        raise ValueError("Omega must be a contiguous square CUDA tensor")
+    p = _check_square(Omega)
     prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
     o = accord_default_opts(precision=prec)
     o.stream = _stream_handle(stream)
@@ -321,9 +378,7 @@ def accord_to_csr(Omega: torch.Tensor, *, nnz_hint: int | None = None, stream=No
     the first attempt (e.g. FitStats.nnz_offdiag + p); a short buffer costs one
     more call.  The element type follows Omega's dtype."""
     lib = load_library()
-    p = Omega.shape[0]
-    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
-        raise ValueError("Omega must be a contiguous square CUDA tensor")
+    p = _check_square(Omega)
     prec = FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3
     o = accord_default_opts(precision=prec)
     o.stream = _stream_handle(stream)
@@ -352,11 +407,12 @@ def accord_grad_x(X: torch.Tensor, Omega: torch.Tensor, *, precision: str | None
     lib = load_library()
     _check_x(X)
     n, p = X.shape
-    prec = PRECISIONS[precision] if precision else (FP64 if Omega.dtype == torch.float64 else MIXED_BF16X3)
-    if not (Omega.is_cuda and Omega.shape == (p, p) and Omega.is_contiguous()):
-        raise ValueError(f"Omega must be a contiguous {p}x{p} CUDA tensor")
+    prec = _precision_of(precision, Omega)
+    _check_tensor(Omega, "Omega", _omega_dtype(prec), (p, p))
     if out is None:
         out = torch.empty((n, p), dtype=Omega.dtype, device=X.device)
+    else:
+        _check_tensor(out, "out", Omega.dtype, (n, p))
     o = accord_default_opts(precision=prec)
     o.stream = _stream_handle(stream)
     status = lib.accord_grad_x(X.data_ptr(), n, p, Omega.data_ptr(), ctypes.byref(o), out.data_ptr())
@@ -373,12 +429,13 @@ def accord_dloss_dloglam(X_train: torch.Tensor, X_val: torch.Tensor, Omega_hat: 
     estimate for X_train at lam); precision defaults to Omega_hat's dtype
     (float64: FP64 mode, float32: BF16x3)."""
     lib = load_library()
-    _check_x(X_train)
-    _check_x(X_val)
+    _check_x(X_train, name="X_train")
+    _check_x(X_val, name="X_val")
     n, p = X_train.shape
     if X_val.shape[1] != p:
         raise ValueError("X_train and X_val need the same number of columns")
-    prec = PRECISIONS[precision] if precision else (FP64 if Omega_hat.dtype == torch.float64 else MIXED_BF16X3)
+    prec = _precision_of(precision, Omega_hat)
+    _check_tensor(Omega_hat, "Omega_hat", _omega_dtype(prec), (p, p))
     o = accord_default_opts(precision=prec, penalize_diag=int(penalize_diag))
     o.stream = _stream_handle(stream)
     d, lv = ctypes.c_double(), ctypes.c_double()
@@ -437,6 +494,7 @@ def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed
     lib = load_library()
     _check_x(X, torch.float32)
     n, p = X.shape
+    ws_ptr, ws_bytes = _check_workspace(workspace)
     rows, offs = _subsample_arrays(subsamples)
     lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
     ns, nl = len(offs) - 1, len(lam)
@@ -450,9 +508,6 @@ def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed
         sup = torch.zeros((nl, ns, p, (p + 31) // 32), dtype=torch.int32, device=X.device)
     best = torch.zeros((ns, p, p), dtype=odt, device=X.device) if omega_best else None
     bidx = np.full(max(ns, 1), -1, dtype=np.int32)
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     st = AccordStats()
     status = lib.accord_path(X.data_ptr(), n, p, rows.ctypes.data, offs.ctypes.data, ns, lam.ctypes.data, nl,
                              ctypes.byref(o), ent, sup.data_ptr() if sup is not None else None,

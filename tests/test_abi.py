@@ -216,3 +216,94 @@ def test_binding_rejects_bad_arguments_on_the_host(lib):
     with pytest.raises(ValueError):
         accord.accord_postprocess(torch.zeros(3, 3))        # not CUDA
     assert set(accord.PRECISIONS) == {"fp64", "mixed", "bf16x3", "tf32x3"}
+
+
+def test_tensor_validator_on_host_tensors():
+    """The binding's validator reports dtype, shape and layout mistakes before
+    the device check, so each shows up here on host tensors."""
+    import torch
+    from paper_2412_11554_gb300 import accord
+    chk = accord._check_tensor
+    with pytest.raises(ValueError, match="torch.Tensor"):
+        chk(np.zeros((3, 3)), "Omega", torch.float64)
+    with pytest.raises(ValueError, match="must be torch.float64"):
+        chk(torch.zeros(3, 3), "Omega", torch.float64, (3, 3))
+    with pytest.raises(ValueError, match=r"shape \(3, 3\)"):
+        chk(torch.zeros(3, 4, dtype=torch.float64), "Omega", torch.float64, (3, 3))
+    with pytest.raises(ValueError, match="2-D"):
+        chk(torch.zeros(12), "X", torch.float32, ndim=2)
+    with pytest.raises(ValueError, match="contiguous"):
+        chk(torch.zeros(4, 4).t()[:, :3], "X", torch.float32, ndim=2)
+    with pytest.raises(ValueError, match="CUDA"):
+        chk(torch.zeros(3, 3), "Omega", (torch.float32, torch.float64), (3, 3))
+    assert accord._omega_dtype(accord.FP64) == torch.float64
+    assert accord._omega_dtype(accord.MIXED_BF16X3) == accord._omega_dtype(accord.MIXED_TF32X3) == torch.float32
+    assert accord._precision_of(None, torch.zeros(2, 2, dtype=torch.float64)) == accord.FP64
+    assert accord._precision_of(None, torch.zeros(2, 2)) == accord.MIXED_BF16X3
+    assert accord._precision_of("tf32x3", torch.zeros(2, 2, dtype=torch.float64)) == accord.MIXED_TF32X3
+
+
+def test_binding_validates_every_caller_tensor(monkeypatch):
+    """Every tensor a caller passes goes through the validator, with the dtype
+    and shape the precision mode fixes, before the library sees its pointer.
+    Recorded on the host with a fake library; the real validator then rejects
+    any mismatch, a host tensor or another device."""
+    import torch
+    from paper_2412_11554_gb300 import accord
+    seen = {}
+
+    def record(t, name, dtype, shape=None, ndim=None):
+        seen[t.data_ptr()] = (name, dtype if isinstance(dtype, tuple) else (dtype,), shape)
+
+    calls = []
+
+    class FakeLib:
+        def __getattr__(self, fn):
+            def call(*args):
+                calls.append(fn)
+                return 0
+            return call
+
+    class Stream:
+        cuda_stream = 0
+
+    monkeypatch.setattr(accord, "_check_tensor", record)
+    monkeypatch.setattr(accord, "load_library", lambda path=None: FakeLib())
+    n, p = 6, 4
+    X, Xv, X64 = torch.zeros(n, p), torch.zeros(3, p), torch.zeros(n, p, dtype=torch.float64)
+    O32, O64 = torch.zeros(p, p), torch.zeros(p, p, dtype=torch.float64)
+    O32b, G32, GX = torch.zeros(p, p), torch.zeros(p, p), torch.zeros(n, p)
+    fg, ws = torch.zeros(2, dtype=torch.float64), torch.zeros(64, dtype=torch.uint8)
+    f32, f64, both = (torch.float32,), (torch.float64,), (torch.float32, torch.float64)
+    S = Stream()
+    cases = [
+        ("accord_fit", lambda: accord.accord_fit(X, 0.1, Omega=O32, workspace=ws, stream=S),
+         {X: f32, O32: f32, ws: (torch.uint8,)}),
+        ("accord_fit", lambda: accord.accord_fit(X, 0.1, precision="fp64", Omega=O64, stream=S), {X: f32, O64: f64}),
+        ("accord_refit", lambda: accord.accord_refit(X, 0.1, 0.5, O32, Omega=O32b, stream=S),
+         {X: f32, O32: f32, O32b: f32}),
+        ("accord_loss", lambda: accord.accord_loss(X, O32, 0.1, precision="fp64", stream=S), {X: f32, O32: f64}),
+        ("accord_grad", lambda: accord.accord_grad(X, O32, out=G32, stream=S), {X: f32, O32: f32, G32: f32}),
+        ("accord_grad", lambda: accord.accord_grad(X, O64, precision="tf32x3", stream=S), {X: f32, O64: f32}),
+        ("accord_loss_f64_noalloc", lambda: accord.accord_loss_f64_noalloc(X64, O64, 0.1, fg, stream=S),
+         {X64: f64, O64: f64, fg: f64}),
+        ("accord_postprocess", lambda: accord.accord_postprocess(O32, stream=S), {O32: both}),
+        ("accord_to_csr", lambda: accord.accord_to_csr(O64, stream=S), {O64: both}),
+        ("accord_grad_x", lambda: accord.accord_grad_x(X, O32, out=GX, stream=S), {X: f32, O32: f32, GX: f32}),
+        ("accord_dloss_dloglam", lambda: accord.accord_dloss_dloglam(X, Xv, O64, 0.1, precision="mixed", stream=S),
+         {X: f32, Xv: f32, O64: f32}),
+        ("accord_path", lambda: accord.accord_path(X, [np.arange(3)], [0.1], workspace=ws, stream=S),
+         {X: f32, ws: (torch.uint8,)}),
+    ]
+    for fn, run, want in cases:
+        seen.clear()
+        calls.clear()
+        run()
+        assert fn in calls, fn
+        for t, dts in want.items():
+            assert t.data_ptr() in seen, (fn, t.shape)
+            assert seen[t.data_ptr()][1] == dts, (fn, seen[t.data_ptr()])
+        # square p x p operands are checked at that shape
+        for t in (O32, O64, O32b, G32):
+            if t.data_ptr() in seen and seen[t.data_ptr()][2] is not None:
+                assert tuple(seen[t.data_ptr()][2]) == (p, p), fn
