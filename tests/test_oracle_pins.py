@@ -461,6 +461,20 @@ def test_printed_and_difference_tests_agree_on_chain():
     assert all(r.printed_form_agrees[:100])
 
 
+@pytest.mark.parametrize("kind,p,n,iters", [("scalefree", 1000, 300, 30), ("hubblock", 1000, 300, 30),
+                                             ("scalefree", 5000, 1000, 3)])
+def test_printed_and_difference_tests_agree_on_graph_workloads(kind, p, n, iters):
+    """The two forms of Algorithm 1's sufficient-decrease test (the printed one,
+    and the difference form ||Delta X^T||^2 / n <= ||Delta||^2 / tau that the
+    kernels evaluate) reach the same verdict on every trial of the scale-free
+    and hub-and-block workloads, the former also at its full size p = 5000,
+    n = 1000 (first iterations)."""
+    w = workload(kind, p=p, n=n)
+    r = R.fit(w.X, w.lam, kkt_tol=1e-4, max_iter=iters)
+    assert r.status in (R.OK, R.NOT_CONVERGED) and r.trials > r.iters
+    assert all(r.printed_form_agrees)
+
+
 def test_kkt_residual_definition_small():
     """r = 0 exactly at a brute-force minimiser's KKT point up to rounding, and
     positive when one entry is perturbed."""
