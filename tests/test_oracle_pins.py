@@ -119,6 +119,35 @@ def pin_diagonal_S():
     return bool(ok)
 
 
+def pin_diagonal_penalty_both_ways():
+    """The chain workload (p = 200, n = 100, lambda = 0.2) fitted with and
+    without lambda on the diagonal (Eq. 3.2 as printed, and the off-diagonal
+    reading).  Each fit meets the KKT conditions of its own objective.  f
+    separates over rows and the diagonal penalty adds lambda * omega_ii, a term
+    increasing in omega_ii, to row i's objective, so no diagonal entry grows
+    when it is added.  Also, since f_1 = f_0 + lambda tr(Omega) with
+    omega_ii > 0, f_0(Omega-hat_0) < f_1(Omega-hat_1) <= f_1(Omega-hat_0)."""
+    w = workload("ar1")
+    X = w.X.astype(np.float64)
+    S = X.T @ X / X.shape[0]
+    fits = {}
+    ok = True
+    for pen in (True, False):
+        lam_d = w.lam if pen else 0.0
+        r = R.fit(X, w.lam, kkt_tol=1e-10, max_iter=5000, penalize_diag=pen)
+        ok &= r.status == R.OK
+        O = R.polish(r.Omega, S, w.lam, lam_d)
+        ok &= R.kkt_residual(O, R.grad_g(O, X), w.lam, lam_d) <= 1e-11
+        fits[pen] = O
+    O1, O0 = fits[True], fits[False]
+    ok &= bool(np.all(np.diag(O1) <= np.diag(O0) + 1e-12))
+    ok &= bool(np.sum(np.diag(O0) - np.diag(O1)) > 1e-3)
+    f0 = R.objective(O0, X, w.lam, penalize_diag=False)
+    f1 = R.objective(O1, X, w.lam, penalize_diag=True)
+    ok &= f0 < f1 <= R.objective(O0, X, w.lam, penalize_diag=True) + 1e-12
+    return bool(ok)
+
+
 def pin_identity_S():
     """S = I and lambda = 0 give Omega-hat = I (reached from a perturbed start)."""
     X = orthogonal_design(30, np.ones(6), 17)
@@ -441,10 +470,11 @@ def pin_reparameterisation():
 
 
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
-        pin_diagonal_S, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
-        pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point, pin_refit_restricted_mle,
-        pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient, pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients,
-        pin_implicit_dloglam_fd, pin_reparameterisation]
+        pin_diagonal_S, pin_diagonal_penalty_both_ways, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
+        pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point,
+        pin_refit_restricted_mle, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
+        pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients, pin_implicit_dloglam_fd,
+        pin_reparameterisation]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -570,6 +600,8 @@ MUTANTS = {
     "kkt_nonzero_as_zero": ("kkt_residual", lambda Om, G, lam, lam_d, row0=0, _f=R.kkt_residual:
                             _f(np.zeros_like(Om) + np.where(np.eye(Om.shape[0], Om.shape[1], k=row0) > 0, Om, 0.0),
                                G, lam, lam_d, row0=row0)),
+    "fit_always_penalizes_diagonal": ("fit", lambda X, lam, _f=R.fit, **kw: _f(X, lam, **{**kw, "penalize_diag": True})),
+    "diag_prox_lambda_sign_flipped": ("diag_prox", lambda y, tau, lam_d, _f=R.diag_prox: _f(y, tau, -lam_d)),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
