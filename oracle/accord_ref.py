@@ -68,7 +68,8 @@ def grad_g(Omega: np.ndarray, X: np.ndarray) -> np.ndarray:
 
 
 def diag_entries(Omega: np.ndarray, row0: int = 0) -> np.ndarray:
-    """Entries omega_ii of a block of rows [row0, row0 + m) of Omega."""
+    """Entries omega_ii of a block of rows [row0, row0 + m) of Omega: the
+    entries of Omega_D in the log-barrier -log det Omega_D of Eq. 3.2."""
     m = Omega.shape[0]
     idx = np.arange(m)
     return Omega[idx, row0 + idx]
@@ -170,6 +171,8 @@ def fbs_trial(Omega: np.ndarray, Y: np.ndarray, G: np.ndarray, X: np.ndarray, ta
 
 @dataclasses.dataclass
 class FitResult:
+    """Output of `fit`: the last iterate of Algorithm 1 and its per-iteration
+    log (objective of Eq. 3.2, KKT residual of Eq. 3.3, accepted steps)."""
     Omega: np.ndarray
     status: int
     iters: int                 # accepted steps taken
@@ -278,6 +281,8 @@ def refit(X: np.ndarray, lam: float, support: np.ndarray, phi: float, *, penaliz
 
 @dataclasses.dataclass
 class PathResult:
+    """Output of `lambda_path` (Sec 3.4): every estimate of the grid and the
+    one each subsample selects by the smallest epBIC (Eq. 3.7)."""
     lambdas: list              # penalty values, in the order they were solved
     fits: list                 # fits[s][k]: FitResult of subsample s at lambdas[k]
     epbic: np.ndarray          # (n_lambda, n_sub) Eq. 3.7 of each estimate
@@ -347,7 +352,8 @@ def smooth_loss_grad_omega(Omega: np.ndarray, X: np.ndarray) -> np.ndarray:
 
 
 def smooth_loss_grad_x(Omega: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """dL/dX: only g depends on X, and g = ||Omega X^T||_F^2 / (2n), so
+    """dL/dX of the smooth part of Eq. 3.2: only g (Eq. 3.4) depends on X,
+    and g = ||Omega X^T||_F^2 / (2n), so
     dL/dX = (1/n) (Omega X^T)^T Omega = (1/n) X Omega^T Omega."""
     X = np.asarray(X, dtype=np.float64)
     return (Omega @ X.T).T @ Omega / X.shape[0]
@@ -415,7 +421,9 @@ def row_solution(S: np.ndarray, i: int, active: np.ndarray, signs: np.ndarray,
 
 def polish(Omega: np.ndarray, S: np.ndarray, lam: float, lam_d: float, rows=None) -> np.ndarray:
     """Re-solve each requested row exactly on the support and signs of Omega
-    (row_solution); a converged Omega becomes the minimiser to rounding."""
+    (row_solution: Eq. 3.3 restricted to the row's active set; f separates
+    over rows, proof of Thm 3.2); a converged Omega becomes the minimiser to
+    rounding."""
     out = np.array(Omega, dtype=np.float64)
     p = Omega.shape[0]
     for i in (range(p) if rows is None else rows):
@@ -464,7 +472,8 @@ def brute_force(S: np.ndarray, lam: float, lam_d: float) -> np.ndarray:
 
 
 def row_objective(S: np.ndarray, i: int, w: np.ndarray, lam: float, lam_d: float) -> float:
-    """Row i's share of f: -log w_i + 1/2 w^T S w + lambda sum_{j != i} |w_j| + lambda_d w_i."""
+    """Row i's share of f (Eq. 3.2 split over the rows of Omega, proof of
+    Thm 3.2): -log w_i + 1/2 w^T S w + lambda sum_{j != i} |w_j| + lambda_d w_i."""
     if w[i] <= 0:
         return math.inf
     off = np.abs(w).sum() - abs(w[i])
