@@ -454,6 +454,33 @@ def pin_implicit_dloglam_fd():
     return bool(abs(d - fd) <= 1e-6 * max(1.0, abs(fd)) and np.max(np.abs(dO - dfd)) <= 1e-6 * max(1.0, np.max(np.abs(dfd))))
 
 
+def pin_implicit_dloglam_diagonal():
+    """Diagonal S (orthogonal training columns): Omega-hat(lambda) is diagonal
+    with omega_i = (-lambda + sqrt(lambda^2 + 4 s_i)) / (2 s_i) (Eq. 3.3), so
+    the held-out loss sum_i [-log omega_i + 1/2 omega_i^2 (S_val)_ii] has the
+    derivative sum_i (-1/omega_i + omega_i (S_val)_ii) lambda d omega_i/d lambda,
+    d omega_i/d lambda = (lambda / sqrt(lambda^2 + 4 s_i) - 1) / (2 s_i).  Without
+    the diagonal penalty omega_i = 1/sqrt(s_i) does not move: both are 0.  The
+    estimate is written from the closed form, not fitted."""
+    rng = np.random.Generator(np.random.PCG64(81))
+    s = rng.uniform(0.3, 3.0, size=9)
+    Xt = orthogonal_design(40, s, 82)
+    Xv = rng.standard_normal((25, 9)) * rng.uniform(0.5, 2.0, size=9)
+    sv = np.diag(Xv.T @ Xv) / Xv.shape[0]
+    ok = True
+    for lam in (0.05, 0.4, 2.0):
+        root = np.sqrt(lam * lam + 4 * s)
+        w = (-lam + root) / (2 * s)
+        dw = lam * (lam / root - 1.0) / (2 * s)          # d omega_i / d log(lambda)
+        want = float(np.sum((-1.0 / w + w * sv) * dw))
+        d, dO = R.implicit_dloglam(np.diag(w), Xt, Xv, lam)
+        ok &= abs(d - want) <= 1e-10 * max(1.0, abs(want))
+        ok &= np.max(np.abs(dO - np.diag(dw))) <= 1e-10 * np.max(np.abs(dw))
+        d0, dO0 = R.implicit_dloglam(np.diag(1.0 / np.sqrt(s)), Xt, Xv, lam, penalize_diag=False)
+        ok &= abs(d0) <= 1e-12 and np.max(np.abs(dO0)) <= 1e-12
+    return bool(ok)
+
+
 def pin_reparameterisation():
     """T(Theta) = Theta_D^-1/2 Theta (Thm 3.1) inverts to Theta = Omega_D Omega,
     and the partial correlations from Omega = T(Theta) equal the textbook
@@ -474,7 +501,7 @@ PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_id
         pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point,
         pin_refit_restricted_mle, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
         pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients, pin_implicit_dloglam_fd,
-        pin_reparameterisation]
+        pin_implicit_dloglam_diagonal, pin_reparameterisation]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
