@@ -323,3 +323,18 @@ def test_largest_single_gpu_fit_sizes(lib):
         # the per-p^2 growth quoted in the header
         per = accord.accord_workspace_bytes(1000, p_max, precision=prec) / p_max ** 2
         assert abs(per - (12.3 if prec == "bf16x3" else 16.5)) < 0.1, (prec, per)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every binding call raises; nothing falls
+    back to another implementation."""
+    import torch
+    from paper_2412_11554_gb300 import accord
+    monkeypatch.setattr(accord, "_LIB_PATH", str(tmp_path / "libaccord.so"))
+    monkeypatch.setattr(accord, "_lib", None)
+    for call in (lambda: accord.accord_default_opts(),
+                 lambda: accord.accord_workspace_bytes(10, 10),
+                 lambda: accord.accord_fit(torch.zeros(4, 6), 0.1),
+                 lambda: accord.accord_status_string(0)):
+        with pytest.raises(RuntimeError, match="libaccord.so not found"):
+            call()
