@@ -694,7 +694,7 @@ size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* optp) {
 
 int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, void* Omega,
                void* workspace, size_t ws_bytes, accord_stats* out) {
-  const int s = fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
+  const int s = abi_call([&] { return fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out); });
   if (out) out->status = s;
   return s;
 }
@@ -706,14 +706,15 @@ int accord_refit(const float* X, int64_t n, int64_t p, double lambda, double phi
     if (out) out->status = ACCORD_EINVAL;
     return ACCORD_EINVAL;
   }
-  const int s = fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out, Omega_hat, phi);
+  const int s =
+      abi_call([&] { return fit_impl(X, nullptr, n, p, lambda, opts, Omega, workspace, ws_bytes, out, Omega_hat, phi); });
   if (out) out->status = s;
   return s;
 }
 
 int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const accord_opts* opts, double* Omega,
                    void* workspace, size_t ws_bytes, accord_stats* out) {
-  const int s = fit_impl(nullptr, X, n, p, lambda, opts, Omega, workspace, ws_bytes, out);
+  const int s = abi_call([&] { return fit_impl(nullptr, X, n, p, lambda, opts, Omega, workspace, ws_bytes, out); });
   if (out) out->status = s;
   return s;
 }

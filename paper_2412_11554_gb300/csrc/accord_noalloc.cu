@@ -32,15 +32,19 @@ void* g_scratch_addr[kMaxDevices] = {};
 // Device address of the scratch array on the current device, looked up once
 // per device with that device current.
 cudaError_t scratch_address(int dev, void** out) {
-  std::lock_guard<std::mutex> guard(g_lock);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = ptr;
+  try {  // std::mutex::lock may throw; no exception leaves the C ABI
+    std::lock_guard<std::mutex> guard(g_lock);
+    if (g_scratch_addr[dev] == nullptr) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return e;
+      g_scratch_addr[dev] = ptr;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+  } catch (...) {
+    return cudaErrorUnknown;
   }
-  *out = g_scratch_addr[dev];
-  return cudaSuccess;
 }
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }

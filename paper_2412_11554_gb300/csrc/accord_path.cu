@@ -180,27 +180,31 @@ struct Subsamples {
 };
 
 int compress_subsamples(const int32_t* rows, const int64_t* row_offsets, int64_t n_sub, int64_t n, Subsamples& S) {
+  // Multiplicities come from a sorted copy of each subsample's indices, so the
+  // host memory grows with the subsample, never with n.
   S.off.assign(1, 0);
-  std::vector<int32_t> count(n, 0);
+  std::vector<int32_t> sorted;
   for (int64_t s = 0; s < n_sub; ++s) {
     const int64_t a = row_offsets[s], b = row_offsets[s + 1];
     if (b <= a) return kEinval;
-    std::vector<int32_t> uniq;
-    for (int64_t i = a; i < b; ++i) {
-      const int32_t r = rows[i];
+    sorted.assign(rows + a, rows + b);
+    for (int32_t r : sorted)
       if (r < 0 || r >= n) return kEinval;
-      if (count[r]++ == 0) uniq.push_back(r);
+    std::sort(sorted.begin(), sorted.end());
+    const int64_t first = (int64_t)S.rows.size();
+    std::vector<int64_t> count;
+    for (size_t i = 0; i < sorted.size();) {
+      size_t j = i + 1;
+      while (j < sorted.size() && sorted[j] == sorted[i]) ++j;
+      S.rows.push_back(sorted[i]);
+      count.push_back((int64_t)(j - i));
+      i = j;
     }
-    std::sort(uniq.begin(), uniq.end());
-    const double ns = (double)(b - a), K = (double)uniq.size();
-    for (int32_t r : uniq) {
-      S.rows.push_back(r);
-      S.scale.push_back(std::sqrt(K * (double)count[r] / ns));
-      count[r] = 0;
-    }
+    const double ns = (double)(b - a), K = (double)count.size();
+    for (int64_t c : count) S.scale.push_back(std::sqrt(K * (double)c / ns));
     S.off.push_back((int64_t)S.rows.size());
     S.n_obs.push_back(ns);
-    S.kmax = std::max<int64_t>(S.kmax, (int64_t)uniq.size());
+    S.kmax = std::max<int64_t>(S.kmax, (int64_t)S.rows.size() - first);
   }
   return kOk;
 }
@@ -823,19 +827,26 @@ size_t accord_path_workspace_bytes(int64_t n, int64_t p, const int32_t* rows, co
   if (check_path_args(reinterpret_cast<const float*>(16), n, p, rows, row_offsets, n_sub, &lam0, 1, o) != kOk ||
       n_lambda < 1)
     return 0;
-  Subsamples S;
-  if (compress_subsamples(rows, row_offsets, n_sub, n, S) != kOk) return 0;
-  return make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), o.precision,
-                          o.lipschitz_max_iter)
-      .total;
+  size_t total = 0;
+  abi_call([&]() -> int {
+    Subsamples S;
+    if (int e = compress_subsamples(rows, row_offsets, n_sub, n, S)) return e;
+    total = make_path_layout(p, n_sub, n_lambda, S.kmax, (int64_t)S.rows.size(), o.precision,
+                             o.lipschitz_max_iter)
+                .total;
+    return kOk;
+  });
+  return total;
 }
 
 int accord_path(const float* X, int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets, int64_t n_sub,
                 const double* lambdas, int64_t n_lambda, const accord_opts* opts, accord_path_entry* entries,
                 uint32_t* support, void* omega_best, int32_t* best_index, void* workspace, size_t ws_bytes,
                 accord_stats* out) {
-  const int s = path_impl(X, n, p, rows, row_offsets, n_sub, lambdas, n_lambda, opts, entries, support, omega_best,
-                          best_index, workspace, ws_bytes, out);
+  const int s = abi_call([&] {
+    return path_impl(X, n, p, rows, row_offsets, n_sub, lambdas, n_lambda, opts, entries, support, omega_best,
+                     best_index, workspace, ws_bytes, out);
+  });
   if (out) out->status = s;
   return s;
 }

@@ -4,6 +4,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <new>
+#include <stdexcept>
 #include <cuda_runtime.h>
 
 #include "accord.h"
@@ -45,6 +47,25 @@ struct Guard {  // frees an internally allocated workspace on every exit path
       return kEcuda;                                               \
     }                                                              \
   } while (0)
+
+// Runs an entry point's body so that no C++ exception leaves the C ABI: a
+// failed host allocation (std::vector, std::map) becomes ACCORD_ENOMEM, any
+// other exception ACCORD_EINVAL, each with a line in accord_last_error.
+template <class F>
+int abi_call(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    set_last_error(__FILE__, __LINE__, "host memory allocation failed");
+    return kEnomem;
+  } catch (const std::length_error&) {
+    set_last_error(__FILE__, __LINE__, "host buffer size out of range");
+    return kEnomem;
+  } catch (...) {
+    set_last_error(__FILE__, __LINE__, "unexpected host exception");
+    return kEinval;
+  }
+}
 
 int check_device() {
   int dev = 0;

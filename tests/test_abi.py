@@ -338,3 +338,32 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
                  lambda: accord.accord_status_string(0)):
         with pytest.raises(RuntimeError, match="libaccord.so not found"):
             call()
+
+
+def test_path_sizing_needs_no_memory_in_n(lib):
+    """Subsample bookkeeping grows with the subsamples, not with n: a data
+    set of 2^40 rows sizes like one of 10 (run in a child process, which an
+    abort would end alone), and repeated rows count once, so a bootstrap
+    sample sizes like its distinct rows."""
+    code = r'''
+import ctypes, numpy as np
+from paper_2412_11554_gb300 import accord
+lib = accord.load_library()
+o = accord.accord_default_opts()
+def size(n, rows, offs):
+    rows = np.asarray(rows, dtype=np.int32); offs = np.asarray(offs, dtype=np.int64)
+    return lib.accord_path_workspace_bytes(n, 50, rows.ctypes.data, offs.ctypes.data, len(offs) - 1, 4, ctypes.byref(o))
+big = size(1 << 40, [0, 1, 2, 7], [0, 4])
+small = size(10, [0, 1, 2, 7], [0, 4])
+boot = size(10, [2, 2, 0, 7, 1, 7, 7, 0], [0, 8])
+distinct = size(10, [0, 1, 2, 7], [0, 4])
+two = size(10, [3, 3, 3, 1, 0, 9], [0, 3, 6])
+two_distinct = size(10, [3, 0, 1, 9], [0, 1, 4])
+print(big, small, boot, distinct, two, two_distinct)
+assert big == small > 0 and boot == distinct and two == two_distinct > 0
+assert size(10, [0, 10], [0, 2]) == 0 and size(10, [0, -1], [0, 2]) == 0
+'''
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr[-2000:])
