@@ -34,7 +34,7 @@ UNIT = "iters/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--workload", choices=["fit", "path", "diff", "refit"], default="fit",
                     help="fit: one fit at p=40000 (default); path: lambda path x bootstrap subsamples at p=4000; "
                          "diff: held-out derivative in log(lambda) at p=2000; refit: Eq. 3.8 refit at p=40000")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 2000 if args.workload == "diff" else 3
     return args

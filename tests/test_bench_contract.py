@@ -54,3 +54,21 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_exit_quietly():
     r = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_profile_summaries_quote_commands_bench_accepts():
+    """Every ncu summary under profiles/ names the command that produced it,
+    and each bench.py command it quotes parses with today's bench.py."""
+    import glob
+    import re
+    import shlex
+    mds = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert mds
+    for md in mds:
+        txt = open(md).read()
+        cmds = re.findall(r"python bench\.py([^`\n]*)", txt)
+        assert cmds or "ncu" in txt, md
+        assert "ncu " in txt and "--clock-control none" in txt, md
+        for c in cmds:
+            args = bench.parse(shlex.split(c.replace("\\", " ")))
+            assert args.impl == "ours", (md, c)
