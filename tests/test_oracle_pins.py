@@ -481,6 +481,36 @@ def pin_implicit_dloglam_diagonal():
     return bool(ok)
 
 
+def pin_hessian_kronecker():
+    """The Hessian of the smooth loss -log det Omega_D + 1/2 tr(Omega^T Omega S)
+    in the column-major vectorisation of Omega is S (x) I_p + sum_i omega_ii^-2
+    (e_i e_i^T (x) e_i e_i^T) (proof of Thm 4.1): it equals central differences
+    of the oracle's gradient.  Entries of different rows do not couple, and row
+    i's block is S + omega_ii^-2 e_i e_i^T, the matrix of the implicit solves."""
+    rng = np.random.Generator(np.random.PCG64(91))
+    n, p, h = 12, 5, 1e-5
+    X = rng.standard_normal((n, p))
+    S = X.T @ X / n
+    O = 0.2 * rng.standard_normal((p, p))
+    np.fill_diagonal(O, rng.uniform(0.6, 1.8, size=p))
+    I = np.eye(p)
+    H = np.kron(S, I) + sum(np.kron(np.outer(I[i], I[i]), np.outer(I[i], I[i])) / O[i, i] ** 2 for i in range(p))
+    fd = np.zeros((p * p, p * p))
+    for c in range(p * p):
+        E = np.zeros(p * p)
+        E[c] = h
+        Ep = E.reshape(p, p, order="F")
+        dg = R.smooth_loss_grad_omega(O + Ep, X) - R.smooth_loss_grad_omega(O - Ep, X)
+        fd[:, c] = dg.ravel(order="F") / (2 * h)
+    ok = np.max(np.abs(fd - H)) <= 1e-7 * np.max(np.abs(H))
+    for i in range(p):
+        for k in range(p):
+            blk = H[np.ix_([i + p * j for j in range(p)], [k + p * j for j in range(p)])]
+            want = S + np.outer(I[i], I[i]) / O[i, i] ** 2 if i == k else np.zeros((p, p))
+            ok &= np.max(np.abs(blk - want)) <= 1e-12
+    return bool(ok)
+
+
 def pin_reparameterisation():
     """T(Theta) = Theta_D^-1/2 Theta (Thm 3.1) inverts to Theta = Omega_D Omega,
     and the partial correlations from Omega = T(Theta) equal the textbook
@@ -501,7 +531,7 @@ PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_id
         pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point,
         pin_refit_restricted_mle, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
         pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients, pin_implicit_dloglam_fd,
-        pin_implicit_dloglam_diagonal, pin_reparameterisation]
+        pin_implicit_dloglam_diagonal, pin_hessian_kronecker, pin_reparameterisation]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -629,6 +659,8 @@ MUTANTS = {
                                G, lam, lam_d, row0=row0)),
     "fit_always_penalizes_diagonal": ("fit", lambda X, lam, _f=R.fit, **kw: _f(X, lam, **{**kw, "penalize_diag": True})),
     "diag_prox_lambda_sign_flipped": ("diag_prox", lambda y, tau, lam_d, _f=R.diag_prox: _f(y, tau, -lam_d)),
+    "smooth_grad_s_omega": ("smooth_loss_grad_omega", lambda Om, X: -np.diag(1.0 / np.diag(Om))
+                            + R.sample_covariance(X) @ Om),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
