@@ -23,6 +23,7 @@
 
 #include "api_util.h"
 #include "internal.h"
+#include "subsamples.h"
 #include "tc_gemm.h"
 
 namespace accord {
@@ -167,46 +168,6 @@ PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_
   L.lz_b = take(c, (size_t)B * k * 8);
   L.total = c;
   return L;
-}
-
-// Distinct rows of every subsample with their multiplicities (host
-// bookkeeping on the caller's index lists).
-struct Subsamples {
-  std::vector<int32_t> rows;
-  std::vector<double> scale;
-  std::vector<int64_t> off;
-  std::vector<double> n_obs;
-  int64_t kmax = 0;
-};
-
-int compress_subsamples(const int32_t* rows, const int64_t* row_offsets, int64_t n_sub, int64_t n, Subsamples& S) {
-  // Multiplicities come from a sorted copy of each subsample's indices, so the
-  // host memory grows with the subsample, never with n.
-  S.off.assign(1, 0);
-  std::vector<int32_t> sorted;
-  for (int64_t s = 0; s < n_sub; ++s) {
-    const int64_t a = row_offsets[s], b = row_offsets[s + 1];
-    if (b <= a) return kEinval;
-    sorted.assign(rows + a, rows + b);
-    for (int32_t r : sorted)
-      if (r < 0 || r >= n) return kEinval;
-    std::sort(sorted.begin(), sorted.end());
-    const int64_t first = (int64_t)S.rows.size();
-    std::vector<int64_t> count;
-    for (size_t i = 0; i < sorted.size();) {
-      size_t j = i + 1;
-      while (j < sorted.size() && sorted[j] == sorted[i]) ++j;
-      S.rows.push_back(sorted[i]);
-      count.push_back((int64_t)(j - i));
-      i = j;
-    }
-    const double ns = (double)(b - a), K = (double)count.size();
-    for (int64_t c : count) S.scale.push_back(std::sqrt(K * (double)c / ns));
-    S.off.push_back((int64_t)S.rows.size());
-    S.n_obs.push_back(ns);
-    S.kmax = std::max<int64_t>(S.kmax, (int64_t)S.rows.size() - first);
-  }
-  return kOk;
 }
 
 int check_path_args(const float* X, int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets,
