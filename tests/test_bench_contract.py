@@ -72,3 +72,38 @@ def test_profile_summaries_quote_commands_bench_accepts():
         for c in cmds:
             args = bench.parse(shlex.split(c.replace("\\", " ")))
             assert args.impl == "ours", (md, c)
+
+
+def test_clock_sampler_parses_clocks_and_throttle_reasons(monkeypatch, tmp_path):
+    """ClockSampler reads nvidia-smi's CSV: the median SM clock under load, the
+    maximum clock, and every throttle reason seen Active ("Not Active" is not
+    one).  Here a fake nvidia-smi on PATH prints the rows."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!/bin/sh\n"
+        "echo '0, 1900, 2070, 1200.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+        "echo '0, 1800, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+        "echo '0, 2000, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+        "echo '0, [N/A], 2070, 900.0, 0x0, Not Active, Active, Not Active, Not Active'\n"
+        "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    for _ in range(100):
+        if os.path.getsize(cs.path) > 0 and open(cs.path).read().count("\n") >= 4:
+            break
+        time.sleep(0.05)
+    got = cs.stop()
+    assert got["samples"] == 4
+    assert got["sm_mhz"] == 1900.0 and got["sm_max_mhz"] == 2070.0   # the N/A sample is skipped
+    assert got["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    cs = bench.ClockSampler(0)
+    cs.start()
+    assert cs.stop() is None
+    assert not os.path.exists(cs.path)          # no temp file left behind
