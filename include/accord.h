@@ -172,8 +172,9 @@ int accord_fit(const float* X, int64_t n, int64_t p, double lambda, const accord
 int accord_refit(const float* X, int64_t n, int64_t p, double lambda, double phi, const void* Omega_hat,
                  const accord_opts* opts, void* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
 
-/* Same as accord_fit for FP64 data; requires opts->precision == ACCORD_FP64
- * (else EUNSUPPORTED).  Omega is double. */
+/* Same as accord_fit (Algorithm 1 with Eq. 3.5) for FP64 data; requires
+ * opts->precision == ACCORD_FP64 (else EUNSUPPORTED).  Omega is double.
+ * Errors as accord_fit. */
 int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const accord_opts* opts,
                    double* Omega, void* workspace, size_t ws_bytes, accord_stats* out);
 
@@ -183,7 +184,10 @@ int accord_fit_f64(const double* X, int64_t n, int64_t p, double lambda, const a
  *            + lambda_d sum_i omega_ii, lambda_d = lambda or 0 per penalize_diag;
  *            +Inf when some omega_ii <= 0.
  * f_out, g_out are HOST doubles (either may be NULL).  Allocates its scratch
- * on opts->stream (stream-ordered) and frees it before returning. */
+ * on opts->stream (stream-ordered) and frees it before returning.
+ * Errors: EINVAL (NULL X or Omega, n < 1, p < 1, lambda < 0 or not finite,
+ * unknown precision), EDOMAIN (non-finite X), ENOMEM (scratch), ECUDA,
+ * EUNSUPPORTED (not sm_103). */
 int accord_loss(const float* X, int64_t n, int64_t p, const void* Omega, double lambda,
                 const accord_opts* opts, double* f_out, double* g_out);
 
@@ -192,7 +196,9 @@ int accord_loss(const float* X, int64_t n, int64_t p, const void* Omega, double 
  *   smooth = 1:  G_out = -Omega_D^{-1} + Omega S  (gradient of Eq. 3.1's sample loss;
  *                the first two terms of the KKT condition Eq. 3.3)
  * G_out: device p x p, same element type as Omega, row-major, may not alias Omega.
- * Allocates its scratch on opts->stream and frees it before returning. */
+ * Allocates its scratch on opts->stream and frees it before returning.
+ * Errors: EINVAL (NULL X, Omega or G_out, G_out == Omega, n < 1, p < 1,
+ * unknown precision), EDOMAIN (non-finite X), ENOMEM, ECUDA, EUNSUPPORTED. */
 int accord_grad(const float* X, int64_t n, int64_t p, const void* Omega, int smooth,
                 const accord_opts* opts, void* G_out);
 
@@ -243,8 +249,10 @@ const char* accord_last_error(void);
  *   Rho_out   = partial correlations rho_ij = -(1/2)(omega_ij / omega_jj + omega_ji / omega_ii),
  *               rho_ii = 1.
  * Either output may be NULL (not both); both are device p x p, same element
- * type, and must not alias Omega.  EDOMAIN when a diagonal entry is not
- * positive (the outputs are still written). */
+ * type, and must not alias Omega.  Errors: EINVAL (NULL Omega, both outputs
+ * NULL, p < 1 or p > 2097120 (65535 row tiles of 32), unknown precision),
+ * EDOMAIN when a diagonal entry is not positive (the outputs are still
+ * written), ENOMEM, ECUDA, EUNSUPPORTED. */
 int accord_postprocess(int64_t p, const void* Omega, const accord_opts* opts, void* Theta_out, void* Rho_out);
 
 /* Compressed sparse rows of an estimate (Sec 3.1: the estimated graph is the
@@ -265,11 +273,17 @@ int accord_to_csr(int64_t p, const void* Omega, const accord_opts* opts, int64_t
 
 /* ---- differentiation ------------------------------------------------------ */
 
-/* Adjoint of the smooth loss L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S)
- * in the data: GX_out = dL/dX = (1/n) X Omega^T Omega (n x p, device, element type per
- * precision: double for ACCORD_FP64, float for the mixed modes), formed as
- * Y^T = X Omega^T and (1/n) Y^T Omega.  dL/dOmega = -diag(1/omega_ii) + Omega S is
- * accord_grad with smooth = 1.  X: device n x p FP32; Omega: device p x p. */
+/* Adjoint in the data of the smooth loss, the unpenalised part of Eq. 3.2,
+ * L(Omega; X) = -sum_i log omega_ii + 1/2 tr(Omega^T Omega S): only g (Eq. 3.4)
+ * depends on X, so GX_out = dL/dX = (1/n) X Omega^T Omega (n x p, device,
+ * element type per precision: double for ACCORD_FP64, float for the mixed
+ * modes), formed as Y^T = X Omega^T and (1/n) Y^T Omega.  dL/dOmega =
+ * -diag(1/omega_ii) + Omega S is accord_grad with smooth = 1.  X: device n x p
+ * FP32; Omega: device p x p, element type per precision.  The call allocates
+ * its scratch on opts->stream and frees it before returning.
+ * Errors: EINVAL (NULL X, Omega or GX_out, n < 1, p < 1, unknown precision),
+ * EDOMAIN (non-finite X; non-finite Omega in FP64 mode), ENOMEM, ECUDA,
+ * EUNSUPPORTED. */
 int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const accord_opts* opts,
                   void* GX_out);
 
@@ -348,7 +362,10 @@ int accord_path(const float* X, int64_t n, int64_t p, const int32_t* rows, const
                 accord_path_entry* entries, uint32_t* support, void* omega_best, int32_t* best_index,
                 void* workspace, size_t ws_bytes, accord_stats* out);
 
-/* Workspace bytes of accord_path for these subsamples (0 on invalid arguments). */
+/* Workspace bytes of accord_path (Sec 3.4) for these subsamples and n_lambda
+ * penalties under opts (precision matters); 0 on invalid arguments (the checks
+ * of accord_path) or when the host bookkeeping cannot be allocated.  It
+ * depends on the subsamples only through their distinct-row counts. */
 size_t accord_path_workspace_bytes(int64_t n, int64_t p, const int32_t* rows, const int64_t* row_offsets,
                                    int64_t n_sub, int64_t n_lambda, const accord_opts* opts);
 
