@@ -243,7 +243,8 @@ const char* accord_last_error(void);
 
 /* ---- post-processing (Sec 3.1) ----------------------------------------------- */
 
-/* From an estimate Omega (device p x p, element type per opts->precision):
+/* The post-processing of Sec 3.1.  From an estimate Omega (device p x p,
+ * element type per opts->precision):
  *   Theta_out = T^-1(Omega) = Omega_D Omega, theta_ij = omega_ii omega_ij (the
  *               precision-matrix estimate), and/or
  *   Rho_out   = partial correlations rho_ij = -(1/2)(omega_ij / omega_jj + omega_ji / omega_ii),

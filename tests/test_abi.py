@@ -367,3 +367,20 @@ assert size(10, [0, 10], [0, 2]) == 0 and size(10, [0, -1], [0, 2]) == 0
     import sys
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr[-2000:])
+
+
+def test_header_documents_each_computing_entry_point():
+    """Each entry point that computes something cites the passage defining it
+    and states its error behaviour in the comment above its declaration."""
+    src = open(HEADER).read()
+    docs = {m.group(3): m.group(1) for m in re.finditer(
+        r"(/\*(?:(?!\*/).)*\*/)\s*((?:int|size_t)\s+(accord_\w+)\s*\([^;]*\);)", src, re.S)}
+    computing = ["accord_fit", "accord_refit", "accord_fit_f64", "accord_loss", "accord_grad", "accord_grad_x",
+                 "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_path",
+                 "accord_path_workspace_bytes", "accord_workspace_bytes", "accord_loss_f64_noalloc"]
+    cite = re.compile(r"Eq\. ?3\.\d|Sec \d|Algorithm \d|Thm \d|as accord_loss|as accord_fit")
+    errs = re.compile(r"Errors|EINVAL|ENOMEM|EUNSUPPORTED|Returns|returns|0 on invalid|0 for invalid")
+    for name in computing:
+        assert name in docs, name
+        assert cite.search(docs[name]), f"{name}: no passage cited"
+        assert errs.search(docs[name]), f"{name}: no error behaviour"
