@@ -135,8 +135,9 @@ typedef struct accord_stats {
 /* Fills *opts with the defaults listed above. */
 void accord_default_opts(accord_opts* opts);
 
-/* Device workspace, in bytes, that accord_fit needs for an n x p problem under
- * opts (precision and max_iter matter).  Returns 0 for invalid sizes.
+/* Device workspace, in bytes, that accord_fit (Algorithm 1) needs for an
+ * n x p problem under opts (precision and max_iter matter).  Returns 0 for
+ * invalid sizes.
  * It grows as about 12.3 p^2 bytes in BF16X3 mode and 16.5 p^2 in TF32X3 and
  * FP64 modes.  With the caller's Omega on the same GPU, a 284 GB GB300 holds
  * at n = 1000 a fit of p up to about 132000 (BF16X3), 118000 (TF32X3) or
