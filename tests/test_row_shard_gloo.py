@@ -13,6 +13,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -77,11 +78,11 @@ def sharded_fit(rank, world, X, lam, kkt_tol, max_iter, tau0=1.0, beta=0.5):
     return Om, taus, ntr, fs
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, p=90):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = workload("ar1", p=90, n=60)
+    w = workload("ar1", p=p, n=60)
     Om, taus, ntr, fs = sharded_fit(rank, world, w.X, w.lam, 1e-9, 2000)
     rows = [None] * world
     dist.all_gather_object(rows, Om)
@@ -91,19 +92,22 @@ def _worker(rank, world, port, q):
     dist.destroy_process_group()
 
 
-def test_row_sharded_fit_matches_single_process_oracle():
-    world = 2
+@pytest.mark.parametrize("world,p", [(2, 90), (3, 91)])
+def test_row_sharded_fit_matches_single_process_oracle(world, p):
+    """The shared line search on row blocks reproduces the single-process
+    oracle's steps, trial counts and objective values, with equal blocks
+    (2 ranks, p = 90) and ragged ones (3 ranks, p = 91: 30, 30, 31 rows)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, p)) for r in range(world)]
     for pr in procs:
         pr.start()
     Om, taus, ntr, fs = q.get(timeout=240)
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    w = workload("ar1", p=90, n=60)
+    w = workload("ar1", p=p, n=60)
     ref = R.fit(w.X, w.lam, kkt_tol=1e-9, max_iter=2000)
     assert ref.status == R.OK
     assert taus == ref.tau and ntr == ref.ntrials
