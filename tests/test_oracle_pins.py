@@ -278,6 +278,25 @@ def pin_refit_restricted_mle():
     return bool(ok and np.max(np.abs(r0.Omega - exact)) <= 1e-8)
 
 
+def pin_refit_diagonal_support():
+    """Eq. 3.8 on the diagonal support, at phi strictly between 0 and 1 and for
+    a non-diagonal S: the infinite weights keep every off-diagonal entry 0, so
+    row i reduces to -log w + 1/2 s_ii w^2 + phi lambda w, whose minimiser is
+    w = (-phi lambda + sqrt((phi lambda)^2 + 4 s_ii)) / (2 s_ii)."""
+    w = workload("ar1", p=40, n=30)
+    X = w.X.astype(np.float64)
+    s = np.diag(X.T @ X / X.shape[0])
+    sup = np.zeros((40, 40), dtype=bool)
+    ok = True
+    for phi in (0.3, 0.5, 0.8):
+        r = R.refit(X, w.lam, sup, phi, kkt_tol=1e-12, max_iter=20000)
+        a = phi * w.lam
+        want = (-a + np.sqrt(a * a + 4 * s)) / (2 * s)
+        ok &= r.status == R.OK
+        ok &= np.max(np.abs(r.Omega - np.diag(want))) <= 1e-10
+    return bool(ok)
+
+
 def pin_epbic_diagonal():
     """epBIC (Eq. 3.7) of the diagonal-S closed form: no off-diagonal nonzeros,
     so 2n(-sum log w_i + 1/2 sum s_i w_i^2)."""
@@ -382,8 +401,10 @@ def _diag_regime_lambda(S):
 def pin_path_diagonal_regime():
     """Above that lambda the estimate of every subsample is diagonal with the
     closed form computed from the subsample's own S; epBIC then has no
-    sparsity term, and the path picks the penalty with the smaller value of
-    2n(-sum log w_i + 1/2 sum s_ii w_i^2)."""
+    sparsity term, and the path picks the penalty with the smallest value of
+    2n(-sum log w_i + 1/2 sum s_ii w_i^2).  That value grows with lambda, so
+    the smallest penalty wins; it is solved first here, not last (penalties
+    are solved in the order given)."""
     X = _gauss(25, 8, 52)
     rows = [np.arange(25), np.random.Generator(np.random.PCG64(53)).integers(0, 25, size=20)]
     ok = True
@@ -392,7 +413,7 @@ def pin_path_diagonal_regime():
     for r in rows:
         Xs = X[r]
         lam_hi = max(lam_hi, _diag_regime_lambda(Xs.T @ Xs / len(r))[0])
-    lams = [2.0 * lam_hi, 1.2 * lam_hi]
+    lams = [1.2 * lam_hi, 2.0 * lam_hi, 1.5 * lam_hi]
     pr = R.lambda_path(X, rows, lams, kkt_tol=1e-12, max_iter=20000)
     for s, r in enumerate(rows):
         Xs = X[r]
@@ -403,7 +424,7 @@ def pin_path_diagonal_regime():
             w = (-lam + np.sqrt(lam * lam + 4 * d)) / (2 * d)
             ok &= np.max(np.abs(pr.fits[s][k].Omega - np.diag(w))) <= 1e-10
             sc.append(2 * len(r) * (-np.sum(np.log(w)) + 0.5 * np.sum(d * w * w)))
-        ok &= pr.best[s] == int(np.argmin(sc))
+        ok &= pr.best[s] == int(np.argmin(sc)) == 0
         ok &= np.allclose(pr.epbic[:, s], sc, rtol=1e-10)
     return bool(ok)
 
@@ -529,7 +550,7 @@ def pin_reparameterisation():
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_diagonal_penalty_both_ways, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
         pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point,
-        pin_refit_restricted_mle, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
+        pin_refit_restricted_mle, pin_refit_diagonal_support, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
         pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients, pin_implicit_dloglam_fd,
         pin_implicit_dloglam_diagonal, pin_hessian_kronecker, pin_reparameterisation]
 
@@ -661,10 +682,20 @@ MUTANTS = {
     "diag_prox_lambda_sign_flipped": ("diag_prox", lambda y, tau, lam_d, _f=R.diag_prox: _f(y, tau, -lam_d)),
     "smooth_grad_s_omega": ("smooth_loss_grad_omega", lambda Om, X: -np.diag(1.0 / np.diag(Om))
                             + R.sample_covariance(X) @ Om),
+    "epbic_gamma_without_4": ("epbic", lambda Om, X, gm, _f=R.epbic: _f(Om, X, gm / 4.0)),
+    "refit_phi_squared": ("refit", lambda X, lam, support, phi, _f=R.refit, **kw: _f(X, lam, support, phi * phi, **kw)),
+    "theta_hat_sqrt_diagonal": ("theta_hat", lambda Om: np.sqrt(np.diag(Om))[:, None] * Om),
+    "path_keeps_last_penalty": ("lambda_path", lambda X, rows, lams, _f=R.lambda_path, **kw:
+                                _path_last(_f(X, rows, lams, **kw))),
     "objective_drops_logdet": ("objective", lambda Om, X, lam, penalize_diag=True, lam_diag=None, _f=R.objective:
                                _f(Om, X, lam, penalize_diag=penalize_diag, lam_diag=lam_diag)
                                + float(np.sum(np.log(R.diag_entries(Om))))),
 }
+
+
+def _path_last(pr):
+    best = [len(pr.lambdas) - 1] * pr.epbic.shape[1]
+    return R.PathResult(pr.lambdas, pr.fits, pr.epbic, best, [pr.fits[s][b].Omega for s, b in enumerate(best)])
 
 
 def _path_argmax(pr):
