@@ -241,6 +241,29 @@ def pin_linear_rate():
     return bool(ok)
 
 
+def pin_sufficient_decrease():
+    """Every accepted step decreases f by at least ||Omega^(t+1) - Omega^t||_F^2
+    / (2 tau_t): with the quadratic bound of Algorithm 1's test holding at
+    Omega^(t+1), the prox step's optimality gives that decrease.  Steps never
+    fall below tau_min = min(tau_0, beta / L) (Thm 3.3, case ii), and with
+    beta = 1 every step is tau_0."""
+    w = workload("ar1", p=60, n=40)
+    X = w.X.astype(np.float64)
+    L = R.lipschitz(X)
+    ok = True
+    for kw in (dict(beta=0.5), dict(beta=0.5, tau0=3.0), dict(beta=1.0, tau0=1.0 / L)):
+        r = R.fit(X, w.lam, kkt_tol=1e-9, max_iter=5000, **kw)
+        ok &= r.status == R.OK
+        f, tau, dfro = np.array(r.f), np.array(r.tau), np.array(r.delta_fro)
+        drop = f[:-1] - f[1:]
+        ok &= bool(np.all(drop >= dfro ** 2 / (2 * tau) - 1e-12 * np.abs(f[:-1])))
+        tau0, beta = kw.get("tau0", 1.0), kw["beta"]
+        ok &= bool(np.all(tau >= min(tau0, beta / L) * (1 - 1e-15)))
+        if beta == 1.0:
+            ok &= bool(np.all(tau == tau0))
+    return bool(ok)
+
+
 def pin_line_search_identity():
     """g(O+) - g(O) - <Delta, grad g(O)> = ||Delta X^T||^2 / (2n) (g is quadratic),
     so the printed and difference forms of the test agree away from rounding."""
@@ -549,7 +572,7 @@ def pin_reparameterisation():
 
 PINS = [pin_prox_root, pin_soft_threshold, pin_gradient, pin_lipschitz, pin_f_identity, pin_objective_diagonal,
         pin_diagonal_S, pin_diagonal_penalty_both_ways, pin_identity_S, pin_low_dim_closed_form, pin_brute_force,
-        pin_kkt_descent_path, pin_linear_rate, pin_line_search_identity, pin_refit_fixed_point,
+        pin_kkt_descent_path, pin_linear_rate, pin_sufficient_decrease, pin_line_search_identity, pin_refit_fixed_point,
         pin_refit_restricted_mle, pin_refit_diagonal_support, pin_epbic_diagonal, pin_epbic_edges, pin_kkt_min_norm_subgradient,
         pin_path_warm_start, pin_path_diagonal_regime, pin_smooth_loss_gradients, pin_implicit_dloglam_fd,
         pin_implicit_dloglam_diagonal, pin_hessian_kronecker, pin_reparameterisation]
