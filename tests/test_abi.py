@@ -384,3 +384,19 @@ def test_header_documents_each_computing_entry_point():
         assert name in docs, name
         assert cite.search(docs[name]), f"{name}: no passage cited"
         assert errs.search(docs[name]), f"{name}: no error behaviour"
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, precision modes and trace columns of the binding equal
+    the header's #defines."""
+    from paper_2412_11554_gb300 import accord
+    defs = dict(re.findall(r"#define\s+(ACCORD_\w+)\s+(-?\d+)", open(HEADER).read()))
+    for name, val in (("OK", accord.OK), ("NOT_CONVERGED", accord.NOT_CONVERGED), ("EINVAL", accord.EINVAL),
+                      ("EDOMAIN", accord.EDOMAIN), ("ENONFINITE", accord.ENONFINITE),
+                      ("EBACKTRACK", accord.EBACKTRACK), ("ENOMEM", accord.ENOMEM), ("ECUDA", accord.ECUDA),
+                      ("EUNSUPPORTED", accord.EUNSUPPORTED), ("FP64", accord.FP64),
+                      ("MIXED_BF16X3", accord.MIXED_BF16X3), ("MIXED_TF32X3", accord.MIXED_TF32X3),
+                      ("TRACE_FIELDS", accord.TRACE_FIELDS)):
+        assert int(defs["ACCORD_" + name]) == val, name
+    for col in ("f", "kkt", "tau", "ntrials", "nnz", "delta", "g"):
+        assert int(defs["ACCORD_TRACE_" + col.upper()]) == accord.TRACE_COLUMNS.index(col), col
