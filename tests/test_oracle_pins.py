@@ -750,3 +750,26 @@ def test_planted_mistake_is_caught(monkeypatch, mutant):
         except Exception:
             return
     pytest.fail(f"mutant {mutant} passed every pin")
+
+
+def test_oracle_statuses():
+    """The oracle's exits, with the meaning the C header gives them: the
+    line search exhausted (the last accepted iterate is returned), non-finite
+    data, and max_iter accepted steps."""
+    w = workload("ar1", p=30, n=20)
+    X = w.X.astype(np.float64)
+    L = R.lipschitz(X)
+    # tau0 far above 1/L and too few reductions to reach it: no step is accepted
+    r = R.fit(X, w.lam, tau0=1e6, max_backtracks=2)
+    assert 1e6 * 0.25 > 1.0 / L
+    assert r.status == R.EBACKTRACK and r.iters == 0 and r.trials == 3
+    assert np.array_equal(r.Omega, np.eye(30))
+    # enough reductions: the same start converges
+    assert R.fit(X, w.lam, tau0=1e6, max_backtracks=60, kkt_tol=1e-6).status == R.OK
+    Xn = X.copy()
+    Xn[3, 4] = np.nan
+    with pytest.raises(np.linalg.LinAlgError):    # the eigensolver for L refuses NaN data
+        R.fit(Xn, w.lam)
+    assert R.fit(Xn, w.lam, L=L).status == R.ENONFINITE  # with L given, the iteration's own check
+    r = R.fit(X, w.lam, max_iter=2, kkt_tol=0.0)
+    assert r.status == R.NOT_CONVERGED and r.iters == 2 and len(r.f) == 3
