@@ -20,7 +20,9 @@
  *     never frees them and never keeps them after the call returns.
  *   - Work is queued on opts->stream (a cudaStream_t; NULL = legacy default
  *     stream).  Every call returns after synchronising that stream, so
- *     outputs are ready when it returns.
+ *     outputs are ready when it returns, with two exceptions that say so
+ *     below: accord_to_csr queues its fill after its one synchronisation, and
+ *     accord_loss_f64_noalloc does not synchronise at all.
  *   - Return value: ACCORD_OK (0), a positive soft status, or a negative error.
  *     No call aborts, throws or traps the GPU; device loops are bounded.
  *   - Only compute capability 10.3 (GB300, sm_103a) is supported; any other
