@@ -246,12 +246,14 @@ def pin_sufficient_decrease():
     / (2 tau_t): with the quadratic bound of Algorithm 1's test holding at
     Omega^(t+1), the prox step's optimality gives that decrease.  Steps never
     fall below tau_min = min(tau_0, beta / L) (Thm 3.3, case ii), and with
-    beta = 1 every step is tau_0."""
+    beta = 1 every step is tau_0.  With tau_warm each step starts from
+    min(tau_0, tau_(t-1) / beta) and only shrinks from there."""
     w = workload("ar1", p=60, n=40)
     X = w.X.astype(np.float64)
     L = R.lipschitz(X)
     ok = True
-    for kw in (dict(beta=0.5), dict(beta=0.5, tau0=3.0), dict(beta=1.0, tau0=1.0 / L)):
+    for kw in (dict(beta=0.5), dict(beta=0.5, tau0=3.0), dict(beta=1.0, tau0=1.0 / L),
+               dict(beta=0.5, tau0=3.0, tau_warm=True)):
         r = R.fit(X, w.lam, kkt_tol=1e-9, max_iter=5000, **kw)
         ok &= r.status == R.OK
         f, tau, dfro = np.array(r.f), np.array(r.tau), np.array(r.delta_fro)
@@ -261,6 +263,8 @@ def pin_sufficient_decrease():
         ok &= bool(np.all(tau >= min(tau0, beta / L) * (1 - 1e-15)))
         if beta == 1.0:
             ok &= bool(np.all(tau == tau0))
+        if kw.get("tau_warm"):
+            ok &= bool(np.all(tau[1:] <= np.minimum(tau0, tau[:-1] / beta) * (1 + 1e-15)))
     return bool(ok)
 
 
