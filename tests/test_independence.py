@@ -89,3 +89,19 @@ def test_bench_uses_the_oracle_only_for_the_cpu_baseline():
     assert found >= 1
     # the module itself does not import the oracle at load time
     assert all(not isinstance(parents.get(n), ast.Module) for m, n in _imported_modules(path, tree) if m == "oracle")
+
+
+def test_smoke_refuses_to_run_without_a_gpu():
+    """__graft_entry__.smoke() needs a CUDA device; on a host without one it
+    stops before any computation instead of falling back."""
+    import sys
+
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    sys.path.insert(0, ROOT)
+    import __graft_entry__ as g
+    assert callable(g.build) and callable(g.smoke)
+    with pytest.raises(AssertionError, match="CUDA device"):
+        g.smoke()
