@@ -47,6 +47,9 @@ def parse(argv=None):
     ap.add_argument("--kkt-tol", type=float, default=1e-4)
     ap.add_argument("--fp64-iters", type=int, default=2, help="FP64 iterations timed for the comparison (0: skip)")
     ap.add_argument("--tf32-fits", type=int, default=1, help="TF32x3 fits timed for the comparison (0: skip)")
+    ap.add_argument("--fp64-full", action="store_true",
+                    help="also run one whole FP64 fit to the same KKT tolerance (several minutes at p=40000), "
+                         "timed, and grade the mixed estimate against it (rel. Frobenius, support, FP64 KKT)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -397,6 +400,10 @@ def run_ours(args):
                 "tf32_peak_tflops": round(peak32, 1),
                 "peak_note": "measured sustained BF16 peak x nominal TF32/BF16 ratio 1.1/2.25"}
 
+    fp64_full = None
+    if args.fp64_full and rank == 0:
+        fp64_full = fp64_full_leg(A, X, w, Om, stats[-1], args.kkt_tol)
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         X64 = w.X.astype(np.float64)
@@ -425,6 +432,7 @@ def run_ours(args):
             "final_kkt": stats[-1].kkt if stats else None, "status": stats[-1].status if stats else None,
             "gpu_launches": int(sum(s.n_launches for s in stats)),
             "roofline": roofline, "e2e": e2e, "e2e_dense_omega": e2e_dense, "fp64_gpu": fp64, "tf32x3_gpu": tf32,
+            "fp64_full": fp64_full,
             "cpu_baseline": cpu,
             "clocks": clk,
             "kernel_source_digest": digest,
@@ -432,6 +440,80 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _kkt_and_support(O32, O64, Gm64, G64, lam, s_diag, band, rows=2000):
+    """Row block by row block on the device, in FP64: the KKT residual of Eq.
+    3.3 of the mixed estimate O32 (gradient Gm64 = O32 S), and the off-diagonal
+    support of O32 against O64 (gradient G64 = O64 S).  A support mismatch is
+    borderline when its slack is within `band`: lambda - |G_ij| for a zero
+    entry of O64, |omega_ij| S_jj for a nonzero one (gradient units)."""
+    import torch
+    p = O64.shape[0]
+    kkt, tp, n32, n64, mism, unexpl = 0.0, 0, 0, 0, 0, 0
+    largest = []
+    for r0 in range(0, p, rows):
+        r1 = min(p, r0 + rows)
+        a, b = O32[r0:r1].double(), O64[r0:r1]
+        g32, g64 = Gm64[r0:r1], G64[r0:r1]
+        idx = torch.arange(r1 - r0, device=a.device)
+        diag = torch.zeros_like(a, dtype=torch.bool)
+        diag[idx, r0 + idx] = True
+        res = torch.where(a != 0, (g32 + lam * torch.sign(a)).abs(), (g32.abs() - lam).clamp_min(0.0))
+        d = a[idx, r0 + idx]
+        res[idx, r0 + idx] = (g32[idx, r0 + idx] - 1.0 / d + lam).abs()
+        kkt = max(kkt, float(res.max()))
+        pa, pb = (a != 0) & ~diag, (b != 0) & ~diag
+        tp += int((pa & pb).sum())
+        n32 += int(pa.sum())
+        n64 += int(pb.sum())
+        diff = pa != pb
+        slack = torch.where(pb, b.abs() * s_diag[None, :], lam - g64.abs())
+        mism += int(diff.sum())
+        unexpl += int((diff & (slack > band)).sum())
+        if bool(diff.any()):
+            largest.append(slack[diff].max().item())
+    return {"fp64_kkt_of_mixed": kkt, "support_f1": 2.0 * tp / max(n32 + n64, 1), "nnz_offdiag_mixed": n32,
+            "nnz_offdiag_fp64": n64, "support_mismatches": mism, "unexplained_mismatches": unexpl,
+            "largest_mismatch_slack": max(largest) if largest else 0.0}
+
+
+def fp64_full_leg(A, X, w, O32, st32, kkt_tol):
+    """One whole FP64 fit to the same KKT tolerance on the same workload
+    (time to KKT measured from the call, as for the mixed fits), and the mixed
+    estimate graded against it."""
+    import torch
+    p = w.p
+    O64 = torch.empty((p, p), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    _, s64 = A.accord_fit(X, w.lam, precision="fp64", kkt_tol=kkt_tol, max_iter=500, Omega=O64, check=False)
+    e[1].record()
+    torch.cuda.synchronize()
+    t = e[0].elapsed_time(e[1]) / 1e3
+    out = {"status": s64.status, "iters": s64.iters, "trials": s64.trials, "time_to_kkt_s": round(t, 2),
+           "setup_ms": round(s64.t_setup_ms, 1), "iters_per_s": round(s64.iters / t, 4), "final_kkt": s64.kkt}
+    # accuracy of the mixed estimate against the FP64 one
+    rel = float(torch.linalg.vector_norm(O32.double() - O64) / torch.linalg.vector_norm(O64))
+    Gm64 = A.accord_grad(X, O32.double())      # FP64 product at the mixed estimate
+    Gm = A.accord_grad(X, O32)                 # the mixed product at the same point
+    err_g = float((Gm.double() - Gm64).abs().max())
+    del Gm
+    G64 = A.accord_grad(X, O64)                # FP64 gradient at the FP64 estimate
+    Xd = X.double()
+    s_diag = (Xd * Xd).sum(dim=0) / X.shape[0]
+    del Xd
+    band = 10.0 * err_g + st32.kkt + s64.kkt
+    out.update({"mixed_iters": st32.iters, "mixed_rel_fro_to_fp64": rel, "mixed_grad_err_max": err_g,
+                "support_band": band,
+                "support_rule": "a mismatch is borderline when its slack (lambda - |G| at a zero, |omega| S_jj at a "
+                                "nonzero of the FP64 estimate) is within 10 x the mixed gradient error plus both "
+                                "fits' stopping KKT"})
+    out.update(_kkt_and_support(O32, O64, Gm64, G64, w.lam, s_diag, band))
+    del Gm64, G64, O64
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -578,7 +660,7 @@ def run_path(args):
                           "lambda_range": [float(pw.lambdas[0]), float(pw.lambdas[-1])], "kkt_tol": pw.kkt_tol,
                           "precision": "mixed_bf16x3", "parallelism": "batched chains, CUDA graph",
                           "autotuned_prox_tiles": {"tile": "128x256", "group_m": int(r0.stats.tile_group_m),
-                                                   "clusters": int(r0.stats.tile_clusters)},
+                                                   "pairs": int(r0.stats.tile_pairs)},
                           "l2": "inputs larger than L2 (16 chains x 64 MB Omega per buffer)"},
                "status": int(r0.status), "estimates_not_converged": int(np.sum(r0.entry_status == 1)),
                "prox_evaluations": int(evals.sum()), "iters_total": int(r0.stats.iters),
@@ -763,8 +845,9 @@ def run_refit(args):
 
 
 def run_profile_sequence(args):
-    """The call sequences of profiles/path_p4000_L32_S16.md and
-    profiles/diff_p2000.md, for ncu to capture: no timing, a few statistics."""
+    """Fixed call sequences for ncu to capture (the lambda path with
+    per-launch events; the derivative, X-gradient and post-processing calls):
+    no timing, a few statistics."""
     import torch
     from paper_2412_11554_gb300 import build as B
     B.build()

@@ -127,9 +127,9 @@ typedef struct accord_stats {
     double  logdet_d;        /* sum_i log omega_ii of the returned Omega                         */
     double  epbic;           /* extended pseudo-BIC of Eq. 3.7 with opts->epbic_gamma:
                                 2n(-log det Omega_D + g) + nnz (log n + 4 gamma log p)           */
-    int32_t tile_group_m;    /* accord_path, mixed modes: raster group (cluster rows) of the
-                                batched prox GEMM in use (0 elsewhere)                           */
-    int32_t tile_clusters;   /* ... and its persistent grid in clusters of 2 CTAs                */
+    int32_t tile_group_m;    /* accord_path, mixed modes: raster group (rows of 256-row pair
+                                tiles) of the batched prox GEMM in use (0 elsewhere)             */
+    int32_t tile_pairs;      /* ... and its persistent grid in CTA pairs (2 SMs each)            */
     int64_t delta_entries;   /* mixed modes, single fit: nonzero Delta entries the sparse Y
                                 update applied, summed over the trials (0 elsewhere)             */
 } accord_stats;
@@ -225,6 +225,11 @@ int accord_device_check(void);
  *   fg_out   device, 2 doubles: fg_out[0] = f, fg_out[1] = g, as accord_loss.
  *   stream   cudaStream_t (NULL = legacy default stream); the call does not
  *            synchronise it -- read fg_out after the stream's work completes.
+ * Domain errors: the call never reads its results back, so its status cannot
+ * report them (accord_loss returns ACCORD_EDOMAIN instead).  Check fg_out:
+ * f = +inf when a diagonal entry of Omega is non-positive or non-finite, and
+ * f = g = NaN when X holds a non-finite value.  n or p above 2^31 - 1 gives
+ * ACCORD_EINVAL before anything is sized or launched.
  * Scratch: a file-scope __device__ array of ACCORD_NOALLOC_SCRATCH_BYTES bytes
  * per GPU, held until the process exits; the call needs
  * 32 * ceil(p/64) * ceil(n/64) + 64 * p bytes of it (each part rounded up to
@@ -236,6 +241,19 @@ int accord_device_check(void);
  * race on it; the array's previous contents are never read. */
 int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double* Omega, double lambda,
                             int penalize_diag, void* stream, double* fg_out);
+
+/* Testing hook for the bounded device waits (the paper has no counterpart).
+ * Every mbarrier wait of the tensor-core kernels gives up after a time limit,
+ * sets a device error bit, lets the copies it issued land, frees its TMEM and
+ * returns; the call then reports ACCORD_ECUDA and accord_last_error() names
+ * the timeout.  This sets that limit for every later launch in the process
+ * (wait_limit_ns = 0 restores the default of 4 s) and, with
+ * withhold_next_prox = 1, makes the producers of the next prox GEMM launch
+ * (mixed modes) skip the copies of their first pipeline stage, so that the
+ * MMA issuer's first wait runs out with no copy in flight for that stage.
+ * Returns ACCORD_OK, or ACCORD_EINVAL for a negative limit or a flag other
+ * than 0 / 1.  Not for production use: a short limit can end correct work. */
+int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox);
 
 /* Description of the first failure of the calling thread's most recent call
  * of an entry point that queues GPU work (fit, refit, path, loss, gradients,

@@ -13,7 +13,7 @@ Every array here is float64; numpy's matmul and symmetric eigensolver serve as
 library primitives.  Nothing is blocked, fused or reordered beyond what the
 definitions and Algorithm 1 state.
 
-Readings of the paper taken here (each listed in the design notes):
+Readings of the paper taken here, where it is silent or ambiguous:
   * lambda penalises every entry, the diagonal included (Eq. 3.2; the diagonal
     prox of Eq. 3.5 carries tau*lambda).  `penalize_diag=False` drops it from
     the diagonal only.

@@ -22,6 +22,7 @@ from .accord import (  # noqa: F401
     accord_loss,
     accord_loss_f64_noalloc,
     accord_status_string,
+    accord_test_wait_limit,
     accord_workspace_bytes,
     load_library,
 )

@@ -46,7 +46,7 @@ class AccordStats(ctypes.Structure):
         ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
         ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64), ("logdet_d", ctypes.c_double), ("epbic", ctypes.c_double),
-        ("tile_group_m", ctypes.c_int32), ("tile_clusters", ctypes.c_int32), ("delta_entries", ctypes.c_int64),
+        ("tile_group_m", ctypes.c_int32), ("tile_pairs", ctypes.c_int32), ("delta_entries", ctypes.c_int64),
     ]
 
 
@@ -62,7 +62,7 @@ class AccordPathEntry(ctypes.Structure):
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
-           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr")
+           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_test_wait_limit")
 
 _lib = None
 
@@ -100,6 +100,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_last_error.argtypes = []
     lib.accord_last_error.restype = ctypes.c_char_p
     lib.accord_loss_f64_noalloc.argtypes = [P, i64, i64, P, dbl, i32, P, P]
+    lib.accord_test_wait_limit.restype = i32
+    lib.accord_test_wait_limit.argtypes = [i64, i32]
     lib.accord_loss_f64_noalloc.restype = i32
     lib.accord_path.argtypes = [P, i64, i64, P, P, i64, P, i64, opts_p, ctypes.POINTER(AccordPathEntry), P, P, P, P,
                                 ctypes.c_size_t, stats_p]
@@ -151,7 +153,7 @@ class FitStats:
     epbic: float = 0.0
     trace: np.ndarray | None = None
     tile_group_m: int = 0
-    tile_clusters: int = 0
+    tile_pairs: int = 0
     delta_entries: int = 0
 
 
@@ -521,7 +523,7 @@ def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed
 
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms, st.t_y_gemm_ms,
-                     st.n_launches, st.logdet_d, st.epbic, None, st.tile_group_m, st.tile_clusters)
+                     st.n_launches, st.logdet_d, st.epbic, None, st.tile_group_m, st.tile_pairs)
     return PathResult(status, col("lambda_", np.float64), col("status", np.int32), col("iters", np.int32),
                       col("trials", np.int32), col("f", np.float64), col("g", np.float64), col("kkt", np.float64),
                       col("logdet_d", np.float64), col("epbic", np.float64), col("tau_last", np.float64),
@@ -538,3 +540,8 @@ def accord_device_check() -> int:
 
 def accord_last_error() -> str:
     return load_library().accord_last_error().decode()
+
+
+def accord_test_wait_limit(wait_limit_ns: int, withhold_next_prox: bool = False) -> int:
+    """Testing hook of the bounded device waits (see include/accord.h)."""
+    return int(load_library().accord_test_wait_limit(int(wait_limit_ns), int(bool(withhold_next_prox))))

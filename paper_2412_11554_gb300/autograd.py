@@ -24,15 +24,13 @@ class SmoothLoss(torch.autograd.Function):
     def backward(ctx, gout: torch.Tensor):
         Omega, X = ctx.saved_tensors
         gO = gX = None
-        scale = None if bool(gout == 1) else gout
+        # the incoming gradient stays on the device: scaling by it always,
+        # rather than testing it for 1 on the host, keeps backward free of a
+        # stream synchronisation
         if ctx.needs_input_grad[0]:
-            gO = accord_grad(X, Omega, smooth=True)
-            if scale is not None:
-                gO = gO * scale
+            gO = accord_grad(X, Omega, smooth=True) * gout.to(Omega.dtype)
         if ctx.needs_input_grad[1]:
-            gX = accord_grad_x(X, Omega).to(X.dtype)
-            if scale is not None:
-                gX = gX * scale.to(X.dtype)
+            gX = accord_grad_x(X, Omega).to(X.dtype) * gout.to(X.dtype)
         return gO, gX
 
 

@@ -736,6 +736,12 @@ const char* accord_status_string(int s) {
 
 int accord_device_check(void) { return check_device(); }
 
+int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox) {
+  if (wait_limit_ns < 0 || (withhold_next_prox != 0 && withhold_next_prox != 1)) return ACCORD_EINVAL;
+  tc_set_wait_test((uint64_t)wait_limit_ns, withhold_next_prox);
+  return ACCORD_OK;
+}
+
 const char* accord_last_error(void) { return g_last_error; }
 
 }  // extern "C"

@@ -20,6 +20,7 @@ namespace accord {
 namespace {
 
 constexpr size_t kScratchBytes = ACCORD_NOALLOC_SCRATCH_BYTES;
+constexpr int64_t kMaxExtent = 2147483647LL;  // n and p; larger sizes are rejected with ACCORD_EINVAL
 
 // Device scratch.  In host code this name is only a stand-in for the symbol:
 // the device address comes from cudaGetSymbolAddress.
@@ -60,6 +61,11 @@ extern "C" int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, co
   if (X == nullptr || Omega == nullptr || fg_out == nullptr || n < 1 || p < 1 || !(lambda >= 0.0) ||
       !std::isfinite(lambda))
     return kEinval;
+  // index limits first, so that the size arithmetic below cannot wrap
+  if (n > kMaxExtent || p > kMaxExtent) {
+    set_last_error(__FILE__, __LINE__, "n and p must not exceed 2^31 - 1");
+    return kEinval;
+  }
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return kEcuda;
   if (dev < 0 || dev >= kMaxDevices) return kEunsupported;

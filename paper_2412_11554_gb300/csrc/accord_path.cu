@@ -228,13 +228,13 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
 int launches_per_trial(bool f64) { return f64 ? 5 : 7; }
 
 // ------------------------------------------------------------ autotuner ---
-// The batched prox GEMM's tile raster (cluster rows per group) and its
-// persistent grid are picked by timing each candidate on the call's own
+// The batched prox GEMM's tile raster (pair rows of 256 per group) and its
+// persistent grid (CTA pairs) are picked by timing each candidate on the call's own
 // operands, once per (device, p, K, chains) in the process.  The runs happen
 // before the control blocks are initialised: with tau = 0 the prox returns
 // Omega unchanged, so Delta is empty and no state needs restoring.
 struct TuneChoice {
-  int group_m = 0, clusters = 0;
+  int group_m = 0, pairs = 0;
 };
 std::mutex g_tune_mu;
 std::map<std::array<int64_t, 5>, TuneChoice> g_tune;
@@ -249,11 +249,11 @@ int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
     if (it != g_tune.end()) {
       best = it->second;
       P.t2.group_m = best.group_m;
-      P.t2.max_clusters = best.clusters;
+      P.t2.max_pairs = best.pairs;
       return kOk;
     }
   }
-  const int maxc = tc_max_clusters(kModeProx, P.L.pt);
+  const int maxc = tc_max_pairs(kModeProx, P.L.pt);
   std::vector<int> grids{maxc};
   for (int c : {maxc * 3 / 4, maxc / 2})
     if (c > 0 && c != grids.back()) grids.push_back(c);
@@ -267,10 +267,10 @@ int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
   evp.b = e1;
   float best_ms = 1e30f;
   for (int g : {1, 2, 4, 8, 16}) {
-    if (g > P.t2.tiles_mc && g != 1) continue;
+    if (g > P.t2.tiles_mp && g != 1) continue;
     for (int c : grids) {
       P.t2.group_m = g;
-      P.t2.max_clusters = c;
+      P.t2.max_pairs = c;
       ACCORD_CK(launch_tc_gemm(kModeProx, P.t2, st));  // warm
       ACCORD_CK(cudaEventRecord(e0, st));
       for (int r = 0; r < 2; ++r) ACCORD_CK(launch_tc_gemm(kModeProx, P.t2, st));
@@ -281,12 +281,12 @@ int tune_prox(PathPlan& P, cudaStream_t st, TuneChoice& best) {
       if (ms < best_ms) {
         best_ms = ms;
         best.group_m = g;
-        best.clusters = c;
+        best.pairs = c;
       }
     }
   }
   P.t2.group_m = best.group_m;
-  P.t2.max_clusters = best.clusters;
+  P.t2.max_pairs = best.pairs;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
   return kOk;
@@ -767,7 +767,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     out->n_launches = nlaunch;
     out->L = hctrl[0].L;
     out->tile_group_m = f64 ? 0 : P.t2.group_m;
-    out->tile_clusters = f64 ? 0 : (P.t2.max_clusters > 0 ? P.t2.max_clusters : tc_max_clusters(kModeProx, L.pt));
+    out->tile_pairs = f64 ? 0 : (P.t2.max_pairs > 0 ? P.t2.max_pairs : tc_max_pairs(kModeProx, L.pt));
   }
   return hstatus;
 }

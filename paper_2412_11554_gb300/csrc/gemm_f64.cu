@@ -158,7 +158,8 @@ cudaError_t launch_gemm_f64(int mode, const GemmF64Params& prm, cudaStream_t st)
   if (prm.M <= 0 || prm.N <= 0) return cudaSuccess;
   dim3 grid((unsigned)((prm.N + BN - 1) / BN), (unsigned)((prm.M + BM - 1) / BM),
             (unsigned)(prm.nprob > 1 ? prm.nprob : 1));
-  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
+  if ((prm.N + BN - 1) / BN > 2147483647LL || grid.y > 65535u || grid.z > 65535u)
+    return cudaErrorInvalidConfiguration;
   switch (mode) {
     case kModeY: gemm_f64_kernel<kModeY><<<grid, NT, 0, st>>>(prm); break;
     case kModeProx: gemm_f64_kernel<kModeProx><<<grid, NT, 0, st>>>(prm); break;

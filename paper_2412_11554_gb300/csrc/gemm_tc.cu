@@ -9,17 +9,28 @@
 // bytes (32 BF16 or 16 TF32 of K), so the shared-memory layout, descriptors
 // and stage sizes are the same for both types.
 //
-// Warp roles (one CTA per SM, persistent over output tiles):
-//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo tiles (64 bytes of K a
-//               row) into a 4-deep shared-memory ring (64-byte swizzle), one
-//               mbarrier per stage.
-//   warp 1      TMEM allocator and single-thread MMA issuer (tcgen05.mma).
-//   warps 2..9  epilogue: tcgen05.ld from a double-buffered TMEM accumulator,
-//               so the epilogue of tile i overlaps the main loop of tile i+1.
+// CTA pairs (tcgen05 cta_group::2): two CTAs of a 2-CTA cluster, one per SM,
+// compute one 256 x 256 output tile with M = 256 MMAs.  Each CTA loads its own
+// 128 rows of A and its half (128 rows) of the B tile into its own shared
+// memory; the MMA reads both CTAs' halves, so no operand byte is fetched
+// twice for a pair, and each CTA's 128 accumulator rows land in its own TMEM.
+//
+// Warp roles (one CTA per SM, persistent over pair tiles):
+//   warp 0      TMA producer of each CTA: its A_hi, A_lo, B_hi, B_lo halves
+//               (64 bytes of K a row) into a 6-deep shared-memory ring (64-byte
+//               swizzle).  The copies of both CTAs complete on the even
+//               (leader) CTA's stage barrier.
+//   warp 1      TMEM allocator of each CTA; in the leader, the single-thread
+//               MMA issuer (tcgen05.mma.cta_group::2), whose commits release
+//               each CTA's stage and signal each CTA's accumulator barrier.
+//   warps 2..9  epilogue of each CTA: tcgen05.ld from a double-buffered TMEM
+//               accumulator, so the epilogue of tile i overlaps the main loop
+//               of tile i+1; its release goes to the leader.
 //
 // Epilogues: Y+ = Y + Delta X^T with ||Delta X^T||^2 and ||Y+||^2 (Algorithm
 // 1's test), G = Y X / n fused with the prox of Eq. 3.5, the Delta planes and
 // the trial / KKT reductions, the gradient of Sec 3.2, and X X^T / n.
+#include <atomic>
 #include <cstdio>
 
 #include "tc_gemm.h"
@@ -28,29 +39,25 @@
 namespace accord {
 namespace {
 
-constexpr int BM = 128;
+constexpr int BM = 128;           // accumulator rows of one CTA (one TMEM lane each)
 constexpr int kRowBytes = 64;        // K bytes of a plane row per stage (one 64-byte swizzle row)
 template <int PT>
 constexpr int kBK = kRowBytes / (int)plane_bytes(PT);  // K elements per stage: 32 BF16 or 16 TF32
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 64 + kEpiThreads;
-constexpr int kBN = 256;
-constexpr int kStages = 4;
-// CTAs of a cluster take consecutive M blocks of one N block; each loads
-// 1/kClusterM of the shared B tile and multicasts it to all of them.
-constexpr int kClusterM = 2;
-constexpr int kBBox = kBN / kClusterM;                 // B rows one CTA loads
-constexpr uint32_t kBSliceBytes = kBBox * kRowBytes;
+constexpr int kBN = 256;          // output columns of a tile (MMA N)
+constexpr int kBHalf = kBN / 2;   // B rows each CTA of the pair holds
+constexpr int kStages = 6;
 constexpr uint32_t kABytes = BM * kRowBytes;
-constexpr uint32_t kBBytes = kBN * kRowBytes;
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr uint32_t kBBytes = kBHalf * kRowBytes;
+constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // one CTA's share of a stage
 constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
 constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 block per epilogue warp
 constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + 1024;
 // Tail after the epilogue buffers: 2 kStages + 5 mbarriers, the TMEM slot and
 // two flags, then the epilogue's FP64 partials [kEpiWarps][8] from kRedOffset.
-constexpr size_t kRedOffset = 128;
+constexpr size_t kRedOffset = 256;
 static_assert((2 * kStages + 5) * 8 + 12 <= kRedOffset, "barriers overlap the epilogue partials");
 static_assert(kRedOffset + kEpiWarps * 8 * 8 <= 1024, "epilogue partials overflow the shared-memory tail");
 static_assert(kSmemBytes <= 232448, "more dynamic shared memory than one CTA may use");
@@ -65,17 +72,18 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   nb = r / gm;
 }
 
-// Cluster tile T (scheduled per cluster) -> this CTA's M / N block.
-__device__ __forceinline__ void cta_tile(int T, const TcParams& prm, int rank, int& mb, int& nb) {
-  int mg;
-  tile_coords(T, prm.tiles_mc, prm.tiles_n, prm.group_m, mg, nb);
-  mb = mg * kClusterM + rank;
+// Pair tile T (256 rows, scheduled per pair) -> this CTA's 128-row M block
+// and the N block.
+__device__ __forceinline__ void pair_tile(int T, const TcParams& prm, int rank, int& mb, int& nb) {
+  int mp;
+  tile_coords(T, prm.tiles_mp, prm.tiles_n, prm.group_m, mp, nb);
+  mb = 2 * mp + rank;
 }
 
-// Flat tile index T of a batch -> problem b and its cluster tile Tl.
+// Flat pair-tile index T of a batch -> problem b and its pair tile Tl.
 __device__ __forceinline__ int tile_problem(const TcParams& prm, int T, int& Tl) {
-  const int slot = T / prm.ntiles_c;
-  Tl = T - slot * prm.ntiles_c;
+  const int slot = T / prm.ntiles_p;
+  Tl = T - slot * prm.ntiles_p;
   return prm.active ? prm.active[slot] : slot;
 }
 
@@ -365,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const bool batch = prm.nprob > 1 || prm.active != nullptr;
   if (!batch && ctrl != nullptr && (ctrl->done || (prm.gate_dense && !ctrl->dense))) return;
   if (prm.gate_dense && prm.any_dense != nullptr && *prm.any_dense == 0) return;
-  const int ntot = (prm.active ? *prm.nactive : (prm.nprob > 1 ? prm.nprob : 1)) * prm.ntiles_c;
+  const int ntot = (prm.active ? *prm.nactive : (prm.nprob > 1 ? prm.nprob : 1)) * prm.ntiles_p;
   if (ntot <= 0) return;
 
   extern __shared__ uint8_t smem_raw[];
@@ -382,34 +390,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   double* red = reinterpret_cast<double*>(smem + kStages * kStageBytes + kEpiBufBytes + kRedOffset);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int rank = (int)ptx::cluster_ctarank();  // 0: leader (issues the MMAs), 1: peer
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], kClusterM);  // one release from every CTA's MMA
+      ptx::mbar_init(&full[s], 1);   // leader: its expect_tx; both CTAs' copies complete on it
+      ptx::mbar_init(&empty[s], 1);  // released by the leader's MMA commit
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
-      ptx::mbar_init(&tempty[a], kEpiThreads);
+      ptx::mbar_init(&tempty[a], 2 * kEpiWarps);  // leader: one arrival per epilogue warp of the pair
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     *stop_flag = 0;
     ptx::fence_mbar_init();
   }
+  // the peer's barriers must be live before any copy, commit or arrival reaches them
+  ptx::cluster_sync();
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_slot, kTmemCols);
-    ptx::tmem_relinquish();
+    ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish_pair();
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  // peers multicast into this CTA's shared memory: their barriers must be live
-  ptx::cluster_sync();
-  const int rank = (int)ptx::cluster_ctarank();
-  const int cluster_id = blockIdx.x / kClusterM;
-  const int nclusters = gridDim.x / kClusterM;
-  constexpr uint16_t kMask = (uint16_t)((1u << kClusterM) - 1u);
+  const int cta = blockIdx.x / 2;     // pair index
+  const int nctas = gridDim.x / 2;    // pairs
 
   const CUtensorMap* mB_hi = &prm.b_hi;
   const CUtensorMap* mB_lo = &prm.b_lo;
@@ -434,11 +441,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       bool filled[kStages];
       for (int q = 0; q < kStages; ++q) { filled[q] = false; fill_ph[q] = 0; }
       bool ok = true;
+      bool withhold = prm.withhold_first != 0;  // test of the timeout path: skip the first stage's copies
       int b = 0, Tl = 0;
-      for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot && ok;
-           T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl)) {
+      for (int T = next_tile(prm, cta, ntot, nctas, b, Tl); T < ntot && ok;
+           T = next_tile(prm, T + nctas, ntot, nctas, b, Tl)) {
         int mb, nb;
-        cta_tile(Tl, prm, rank, mb, nb);
+        pair_tile(Tl, prm, rank, mb, nb);
         const int cb = ctrl ? ctrl[b].cur : 0;
         const int asel = prm.a_nxt ? (cb ^ 1) : cb;
         const CUtensorMap* mA_hi = &prm.a_hi[asel];
@@ -446,53 +454,59 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
         const int32_t zb = prm.b_batched ? b : 0;
         for (int kb = 0; kb < nkb; ++kb) {
-          // the slot is free only when every CTA of the cluster released it
-          if (!ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
-          ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
-          const uint32_t st = smem_base + s * kStageBytes;
-          ptx::tma_load_3d(st, mA_hi, &full[s], kb * BK, mb * BM, b, pol_a);
-          ptx::tma_load_3d(st + kABytes, mA_lo, &full[s], kb * BK, mb * BM, b, pol_a);
-          const int32_t by = nb * kBN + rank * kBBox;
-          ptx::tma_load_3d_mc(st + 2 * kABytes + rank * kBSliceBytes, mB_hi, &full[s], kb * BK, by, zb, kMask,
-                              pol_keep);
-          ptx::tma_load_3d_mc(st + 2 * kABytes + kBBytes + rank * kBSliceBytes, mB_lo, &full[s], kb * BK, by, zb,
-                              kMask, pol_keep);
-          filled[s] = true;
-          fill_ph[s] = ph;
+          if (!ptx::mbar_wait_cluster(&empty[s], ph ^ 1u, abort_flag, prm.wait_ns)) { ok = false; break; }
+          if (!withhold) {
+            // the leader expects the bytes of both CTAs' copies of this stage
+            if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * kStageBytes);
+            const uint32_t st = smem_base + s * kStageBytes;
+            const uint32_t fb = ptx::map_to_cta(&full[s], 0);
+            const int32_t by = nb * kBN + rank * kBHalf;
+            ptx::tma_load_3d_pair(st, mA_hi, fb, kb * BK, mb * BM, b, pol_a);
+            ptx::tma_load_3d_pair(st + kABytes, mA_lo, fb, kb * BK, mb * BM, b, pol_a);
+            ptx::tma_load_3d_pair(st + 2 * kABytes, mB_hi, fb, kb * BK, by, zb, pol_keep);
+            ptx::tma_load_3d_pair(st + 2 * kABytes + kBBytes, mB_lo, fb, kb * BK, by, zb, pol_keep);
+            filled[s] = true;
+            fill_ph[s] = ph;
+          }
+          withhold = false;
           if (++s == kStages) { s = 0; ph ^= 1u; }
         }
       }
       if (ok) {
-        // wait for the last releases of every slot, so that no peer signal
-        // can still be on its way to this CTA when it leaves
+        // wait for the last release of every slot, so that no commit can
+        // still be on its way to this CTA's barriers when it leaves
         for (int q = 0; q < kStages; ++q)
-          if (filled[q] && !ptx::mbar_wait(&empty[q], fill_ph[q], abort_flag)) ok = false;
+          if (filled[q] && !ptx::mbar_wait_cluster(&empty[q], fill_ph[q], abort_flag, prm.wait_ns)) ok = false;
       }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(prm.err, kErrWaitTimeout);
-        // let the copies already issued land before the CTA can exit
-        for (int q = 0; q < kStages; ++q)
-          if (filled[q]) (void)ptx::mbar_wait(&full[q], fill_ph[q], nullptr);
+        // let the leader's copies already issued land before the CTA can exit
+        // (the peer's copies complete on the leader's barriers; the exit
+        // barrier of the pair below keeps the leader alive meanwhile)
+        if (rank == 0)
+          for (int q = 0; q < kStages; ++q)
+            if (filled[q]) (void)ptx::mbar_wait_cluster(&full[q], fill_ph[q], nullptr, prm.wait_ns);
       }
     }
   } else if (warp == 1) {
-    // -------------------------------------------------------- MMA issuer --
-    if (lane == 0) {
-      constexpr uint32_t idesc = PT == kPlaneTf32 ? ptx::idesc_tf32_f32(BM, kBN) : ptx::idesc_bf16_f32(BM, kBN);
+    // ------------------------------------------- MMA issuer (leader only) --
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc =
+          PT == kPlaneTf32 ? ptx::idesc_tf32_f32(2 * BM, kBN) : ptx::idesc_bf16_f32(2 * BM, kBN);
       uint32_t s = 0, ph = 0;
       bool ok = true;
       int i = 0;
       int b = 0, Tl = 0;
-      for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot && ok;
-           T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl), ++i) {
+      for (int T = next_tile(prm, cta, ntot, nctas, b, Tl); T < ntot && ok;
+           T = next_tile(prm, T + nctas, ntot, nctas, b, Tl), ++i) {
         const uint32_t acc = i & 1, aph = (i >> 1) & 1;
-        if (!ptx::mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { ok = false; break; }
+        if (!ptx::mbar_wait_cluster(&tempty[acc], aph ^ 1u, abort_flag, prm.wait_ns)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem_base + acc * kBN;
         const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!ptx::mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
+          if (!ptx::mbar_wait_cluster(&full[s], ph, abort_flag, prm.wait_ns)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t st = smem_base + s * kStageBytes;
           const uint64_t a_hi = ptx::sdesc_k64(st);
@@ -503,26 +517,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int kk = 0; kk < kRowBytes / 32; ++kk) {
             const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4: K = 16 BF16 or 8 TF32
             if constexpr (PT == kPlaneTf32) {
-              ptx::mma_tf32(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
-              ptx::mma_tf32(d, a_hi + off, b_lo + off, idesc, 1u);
-              ptx::mma_tf32(d, a_hi + off, b_hi + off, idesc, 1u);
+              ptx::mma_tf32_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+              ptx::mma_tf32_pair(d, a_hi + off, b_lo + off, idesc, 1u);
+              ptx::mma_tf32_pair(d, a_hi + off, b_hi + off, idesc, 1u);
             } else {
-              ptx::mma_f16(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
-              ptx::mma_f16(d, a_hi + off, b_lo + off, idesc, 1u);
-              ptx::mma_f16(d, a_hi + off, b_hi + off, idesc, 1u);
+              ptx::mma_f16_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+              ptx::mma_f16_pair(d, a_hi + off, b_lo + off, idesc, 1u);
+              ptx::mma_f16_pair(d, a_hi + off, b_hi + off, idesc, 1u);
             }
           }
-          ptx::mma_commit_mc(&empty[s], kMask);  // release the slot in every CTA
+          // release the slot in both CTAs once these MMAs have read it
+          ptx::mma_commit_pair(ptx::map_to_cta(&empty[s], 0));
+          ptx::mma_commit_pair(ptx::map_to_cta(&empty[s], 1));
           if (++s == kStages) { s = 0; ph ^= 1u; }
         }
         if (!ok) break;
-        ptx::mma_commit(&tfull[acc]);
+        ptx::mma_commit_pair(ptx::map_to_cta(&tfull[acc], 0));
+        ptx::mma_commit_pair(ptx::map_to_cta(&tfull[acc], 1));
       }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(prm.err, kErrWaitTimeout);
-        ptx::mma_commit(drain);
-        (void)ptx::mbar_wait(drain, 0, nullptr);
+        ptx::mma_commit_pair(ptx::map_to_cta(drain, 0));
+        (void)ptx::mbar_wait(drain, 0, nullptr, prm.wait_ns);
       }
     }
   } else {
@@ -554,10 +571,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
     int i = 0;
     int b = 0, Tl = 0;
-    for (int T = next_tile(prm, cluster_id, ntot, nclusters, b, Tl); T < ntot;
-         T = next_tile(prm, T + nclusters, ntot, nclusters, b, Tl), ++i) {
+    for (int T = next_tile(prm, cta, ntot, nctas, b, Tl); T < ntot;
+         T = next_tile(prm, T + nctas, ntot, nctas, b, Tl), ++i) {
       int mb, nb;
-      cta_tile(Tl, prm, rank, mb, nb);
+      pair_tile(Tl, prm, rank, mb, nb);
       // this tile's problem: its iterate buffers, step and penalty
       const int cb = ctrl ? ctrl[b].cur : 0, nx = cb ^ 1;
       ea.out = prm.out[nx] ? prm.out[nx] + b * prm.s_out : nullptr;
@@ -598,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane, ea.pol_stream);
         pending = true;
       }
-      const bool ok = ptx::mbar_wait(&tfull[acc], aph, abort_flag);
+      const bool ok = ptx::mbar_wait_cluster(&tfull[acc], aph, abort_flag, prm.wait_ns);
       if (!ok) {
         *abort_flag = 1;
         if (lane == 0) atomicOr(prm.err, kErrWaitTimeout);
@@ -657,8 +674,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
       }
       if (pending) asm volatile("cp.async.wait_group 0;" ::: "memory");
+      // this warp's TMEM reads are done: one release per warp, on the leader
       ptx::tc_fence_before();
-      ptx::mbar_arrive(&tempty[acc]);
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive_cluster(ptx::map_to_cta(&tempty[acc], 0));
       // Partial sums of this tile: FP32 warp trees, then FP64 across the warps
       // (fixed order).  Both named barriers run on every tile so that all
       // epilogue warps leave the loop together (the stop decision is taken by
@@ -711,20 +730,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncwarp();
   ptx::tc_fence_before();
   __syncthreads();
-  ptx::cluster_sync();  // no CTA leaves while a peer may still signal it
+  // neither CTA leaves while its peer may still read its shared memory or
+  // signal its barriers
+  ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, kTmemCols);
+    ptx::tmem_dealloc_pair(tmem_base, kTmemCols);
   }
 }
 
-// Shared-memory opt-in and the persistent grid size (clusters that fit at
-// once), set up once per device, mode and plane type.  Done outside any launch
-// so that a stream capture records launches only.
+// Shared-memory opt-in and the persistent grid size (CTA pairs that fit at
+// once), set up once per device, mode and plane type.  Done outside any
+// launch so that a stream capture records launches only.
 template <int MODE, int PT>
-cudaError_t configure_mode(int& max_clusters) {
+cudaError_t configure_mode(int& max_pairs) {
   static int configured = -1;
-  static int clusters = 0;
+  static int pairs = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -735,37 +756,37 @@ cudaError_t configure_mode(int& max_clusters) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterM;
+    attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = kSmemBytes;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.gridDim = dim3(kClusterM, 1, 1);
+    cfg.gridDim = dim3(2, 1, 1);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<MODE, PT>, &cfg) != cudaSuccess || n < 1) {
       (void)cudaGetLastError();
       int sms = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      n = sms / kClusterM > 0 ? sms / kClusterM : 1;
+      n = sms / 2 > 0 ? sms / 2 : 1;
     }
-    clusters = n;
+    pairs = n;
     configured = dev;
   }
-  max_clusters = clusters;
+  max_pairs = pairs;
   return cudaSuccess;
 }
 
 template <int MODE, int PT>
 cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
-  int max_clusters = 0;
-  cudaError_t e = configure_mode<MODE, PT>(max_clusters);
+  int max_pairs = 0;
+  cudaError_t e = configure_mode<MODE, PT>(max_pairs);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kClusterM;
+  attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -773,15 +794,15 @@ cudaError_t launch_mode(const TcParams& prm, cudaStream_t st) {
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (prm.max_clusters > 0 && prm.max_clusters < max_clusters) max_clusters = prm.max_clusters;
-  const int64_t tiles_total = (int64_t)(prm.nprob > 1 ? prm.nprob : 1) * prm.ntiles_c;
-  const int clusters = (int)std::min<int64_t>(tiles_total, max_clusters);
-  cfg.gridDim = dim3((unsigned)(clusters * kClusterM), 1, 1);
+  if (prm.max_pairs > 0 && prm.max_pairs < max_pairs) max_pairs = prm.max_pairs;
+  const int64_t tiles_total = (int64_t)(prm.nprob > 1 ? prm.nprob : 1) * prm.ntiles_p;
+  const int pairs = (int)std::min<int64_t>(tiles_total, max_pairs);
+  cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
   return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, PT>, prm);
 }
 
 template <int PT>
-int max_clusters_of(int mode) {
+int max_pairs_of(int mode) {
   int m = 0;
   switch (mode) {
     case kModeY: configure_mode<kModeY, PT>(m); break;
@@ -815,12 +836,12 @@ cudaError_t launch_type(int mode, const TcParams& prm, cudaStream_t st) {
 
 }  // namespace
 
-int tc_box_n() { return kBBox; }
+int tc_box_n() { return kBHalf; }
 
 int tc_bk(int pt) { return pt == kPlaneTf32 ? kBK<kPlaneTf32> : kBK<kPlaneBf16>; }
 
-int tc_max_clusters(int mode, int pt) {
-  return pt == kPlaneTf32 ? max_clusters_of<kPlaneTf32>(mode) : max_clusters_of<kPlaneBf16>(mode);
+int tc_max_pairs(int mode, int pt) {
+  return pt == kPlaneTf32 ? max_pairs_of<kPlaneTf32>(mode) : max_pairs_of<kPlaneBf16>(mode);
 }
 
 cudaError_t tc_prepare() {
@@ -841,17 +862,30 @@ void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K, int pt) {
   prm.tiles_m = (int32_t)((M + BM - 1) / BM);
   prm.tiles_n = (int32_t)((N + kBN - 1) / kBN);
   prm.ntiles = prm.tiles_m * prm.tiles_n;
-  prm.tiles_mc = (prm.tiles_m + kClusterM - 1) / kClusterM;
-  prm.ntiles_c = prm.tiles_mc * prm.tiles_n;
-  // raster: groups of cluster rows, N block by N block; wide groups when there
-  // are many N blocks (the B tiles then stream, A tiles stay in L2)
+  prm.tiles_mp = (prm.tiles_m + 1) / 2;
+  prm.ntiles_p = prm.tiles_mp * prm.tiles_n;
+  // raster: groups of pair rows (256 rows each), N block by N block; wide
+  // groups when there are many N blocks (the B tiles then stream, A tiles
+  // stay in L2)
   prm.group_m = prm.tiles_n > 16 ? 32 : 4;
   prm.bn = kBN;
 }
 
-cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st) {
-  if (prm.ntiles <= 0) return cudaSuccess;
-  if (prm.ntiles_c <= 0) return cudaErrorInvalidValue;
+// Process-wide wait limit of the tensor-core kernels and the one-shot
+// withholding of the timeout test (accord_test_wait_limit).
+static std::atomic<uint64_t> g_wait_ns{ptx::kWaitTimeoutNs};
+static std::atomic<int> g_withhold_next_prox{0};
+
+void tc_set_wait_test(uint64_t wait_ns, int withhold_next_prox) {
+  g_wait_ns.store(wait_ns > 0 ? wait_ns : ptx::kWaitTimeoutNs);
+  g_withhold_next_prox.store(withhold_next_prox ? 1 : 0);
+}
+
+cudaError_t launch_tc_gemm(int mode, const TcParams& prm_in, cudaStream_t st) {
+  if (prm_in.ntiles <= 0) return cudaSuccess;
+  TcParams prm = prm_in;
+  prm.wait_ns = g_wait_ns.load();
+  prm.withhold_first = (mode == kModeProx && g_withhold_next_prox.exchange(0) != 0) ? 1 : 0;
   if (prm.ptype == kPlaneTf32) return launch_type<kPlaneTf32>(mode, prm, st);
   if (prm.ptype == kPlaneBf16) return launch_type<kPlaneBf16>(mode, prm, st);
   return cudaErrorInvalidValue;

@@ -789,9 +789,10 @@ __global__ void loss_finish_kernel(const double* ompart, int64_t nomp, const dou
   fold_partials<kProxSlots>(ompart, nomp, 0u, om);
   fold_partials<kYSlots>(ypart, nyp, 0u, y);
   if (threadIdx.x != 0) return;
-  const double g = 0.5 * y[kYNorm2] * inv_n;
+  double g = 0.5 * y[kYNorm2] * inv_n;
   double f = g - om[kPLogDiag] + lam * om[kPL1Off] + lam_d * om[kPDiagSum];
-  if (om[kPBad] > 0.0) f = INFINITY;
+  if (om[kPBad] > 0.0) f = INFINITY;  // a diagonal entry outside the domain of -log
+  if (y[kYBad] > 0.0) f = g = NAN;    // non-finite data: Omega X^T has no finite value
   out[0] = f;
   out[1] = g;
 }

@@ -22,8 +22,8 @@ struct TcParams {
   Ctrl* ctrl;           // null: cur = 0, no early exit; a batch: one per problem
   int* err;             // device error word (kErr* bits), never null
   int64_t M, N, K;
-  int32_t num_kb, tiles_m, tiles_n, ntiles;
-  int32_t tiles_mc, ntiles_c;  // cluster rows of M blocks, cluster tiles
+  int32_t num_kb, tiles_m, tiles_n, ntiles;  // 128-row M blocks, 256-column N blocks
+  int32_t tiles_mp, ntiles_p;                 // pair rows (256 rows), pair tiles per problem
   int32_t a_nxt, smooth, group_m, bn;
   float* out[2];        // FP32 output (Y+, Omega+ or G), index nxt
   int64_t ldout;
@@ -62,8 +62,16 @@ struct TcParams {
   // gated launch returns at once while *any_dense is clear (no problem needs
   // the dense product), instead of scanning every problem's tiles.
   int* any_dense;
-  int32_t max_clusters;  // persistent grid limit in clusters (0: as many as fit at once)
+  int32_t max_pairs;     // persistent grid limit in CTA pairs (0: as many as fit at once)
   int32_t ptype;         // plane type of the operands and plane outputs: kPlaneBf16 / kPlaneTf32
+  // Bounded waits: every mbarrier wait of the launch gives up after wait_ns
+  // (set from the process-wide limit, 4 s by default).  withhold_first: the
+  // producers of both CTAs of the first pair skip the copies of their first
+  // stage, so that the MMA issuer's first wait runs out (the test of the
+  // timeout path; set only through accord_test_wait_limit).
+  uint64_t wait_ns;
+  int32_t withhold_first;
+  int32_t pad2;
 };
 
 // Encodes a 3-D tensor map over `depth` slices of a rows x cols plane of type
@@ -79,12 +87,16 @@ int tc_bk(int pt);
 // M x N x K problem (the K blocking depends on pt).
 void tc_shape(TcParams& prm, int64_t M, int64_t N, int64_t K, int pt);
 int64_t tc_tiles(int64_t M, int64_t N);
-int tc_box_n();  // rows of the B box one CTA loads (its share of the N tile)
+int tc_box_n();  // rows of the B box a CTA loads (its half of the N tile)
 cudaError_t launch_tc_gemm(int mode, const TcParams& prm, cudaStream_t st);
+// Wait limit of every later tensor-core launch in the process (0: the default
+// 4 s); withhold_next_prox = 1 makes the next prox GEMM launch skip its first
+// stage's copies so that its first wait runs out (the timeout path's test).
+void tc_set_wait_test(uint64_t wait_ns, int withhold_next_prox);
 // One-time per-device setup of every mode (done lazily by the first launch
 // otherwise); call before capturing launches into a CUDA graph.
 cudaError_t tc_prepare();
-// Clusters of the persistent grid that fit on the device at once (mode's kernel).
-int tc_max_clusters(int mode, int pt = 0);
+// CTA pairs of the persistent grid that fit on the device at once (mode's kernel).
+int tc_max_pairs(int mode, int pt = 0);
 
 }  // namespace accord

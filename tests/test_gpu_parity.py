@@ -5,8 +5,12 @@ Tolerances
   FP64 mode: the iterate sequence matches the oracle's (same accepted steps,
   same trial counts and step sizes) and the returned Omega is within 1e-9
   relative Frobenius of the oracle's (the bar the method's FP64 target states).
+  FP64 mode also keeps the oracle's zero pattern, except entries within 1e-8 of
+  the soft-threshold (|omega_ij| <= 1e-8, or lambda - |G_ij| <= 1e-8).
   Mixed BF16x3 mode: 1e-4 relative Frobenius to the FP64 result, support equal
-  except entries within the rounding band of the soft-threshold.
+  except entries whose slack is within ten times the measured gradient error
+  of the mixed product plus the two fits' stopping KKT residuals
+  (tests/support_rules.py states both rules).
 """
 import json
 import os
@@ -17,6 +21,7 @@ import torch
 
 from oracle import accord_ref as R
 from synth import workload
+from support_rules import fp64_support_ok, unexplained_mismatches
 
 pytestmark = pytest.mark.gpu
 
@@ -31,14 +36,22 @@ def rel_fro(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def support_mismatch(Om, ref, G_ref, lam, band):
-    """Entries whose zero pattern differs, excluding those inside the band
-    around the soft-threshold (|omega| <= band or |lam - |G|| <= band)."""
-    p = ref.shape[0]
-    off = ~np.eye(p, dtype=bool)
-    diff = ((Om != 0) != (ref != 0)) & off
-    border = (np.abs(ref) <= band) | (np.abs(lam - np.abs(G_ref)) <= band)
-    return int(np.sum(diff & ~border))
+def oracle_grad(Om, X):
+    return R.grad_g(Om, np.asarray(X, dtype=np.float64))
+
+
+def mixed_grad_error(A, X, O32):
+    """max |G_mixed - G_FP64| of the mixed gradient product at the mixed
+    estimate (both through accord_grad; the FP64 product is held to the
+    oracle at smaller sizes)."""
+    Gm = A.accord_grad(X, O32).double()
+    G64 = A.accord_grad(X, O32.double())
+    return float((Gm - G64).abs().max())
+
+
+def s_diag_of(X):
+    Xd = np.asarray(X, dtype=np.float64)
+    return np.einsum("ij,ij->j", Xd, Xd) / Xd.shape[0]
 
 
 # ------------------------------------------------------------- FP64 path ---
@@ -58,6 +71,7 @@ def test_fp64_chain_iterate_sequence_matches_oracle(A):
     assert abs(st.L - ref.L) <= 1e-10 * ref.L
     O = Om.cpu().numpy()
     assert rel_fro(O, ref.Omega) <= 1e-9
+    assert fp64_support_ok(O, ref.Omega, oracle_grad(ref.Omega, w.X), w.lam)
     gold = json.load(open(os.path.join(GOLD, "chain_p200_n100.json")))
     assert st.iters == gold["iters"]
 
@@ -73,6 +87,7 @@ def test_fp64_matches_exact_row_solution(A):
     S = X.T @ X / X.shape[0]
     P = R.polish(O, S, w.lam, w.lam)
     assert rel_fro(O, P) <= 1e-9
+    assert fp64_support_ok(O, P, P @ S, w.lam)
     assert R.kkt_residual(O, R.grad_g(O, X), w.lam, w.lam) <= 2e-11
 
 
@@ -86,6 +101,7 @@ def test_fp64_ragged_and_tiny(A, n, p):
     assert st.status == ref.status
     assert st.iters == ref.iters and st.trials == ref.trials
     assert rel_fro(Om.cpu().numpy(), ref.Omega) <= 1e-9
+    assert fp64_support_ok(Om.cpu().numpy(), ref.Omega, oracle_grad(ref.Omega, X), lam)
 
 
 def test_fp64_penalize_diag_off_and_options(A):
@@ -99,6 +115,7 @@ def test_fp64_penalize_diag_off_and_options(A):
         assert st.status == ref.status, kw
         assert st.iters == ref.iters and st.trials == ref.trials, kw
         assert rel_fro(Om.cpu().numpy(), ref.Omega) <= 1e-9, kw
+        assert fp64_support_ok(Om.cpu().numpy(), ref.Omega, oracle_grad(ref.Omega, w.X), w.lam), kw
 
 
 def test_fp64_warm_start_and_max_iter(A):
@@ -176,8 +193,13 @@ def test_mixed_fit_matches_oracle(A):
     assert st.status == 0, st
     O = Om.double().cpu().numpy()
     assert rel_fro(O, ref.Omega) <= 1e-4
-    G_ref = R.grad_g(ref.Omega, w.X.astype(np.float64))
-    assert support_mismatch(O, ref.Omega, G_ref, w.lam, band=1e-4) == 0
+    G_ref = oracle_grad(ref.Omega, w.X)
+    err_g = mixed_grad_error(A, dev(w.X), Om)
+    band = 10 * err_g + st.kkt + ref.kkt[-1]
+    bad, nmis, slacks = unexplained_mismatches(O, ref.Omega, G_ref, w.lam, grad_band=band, s_diag=s_diag_of(w.X))
+    print(f"p=600 mixed vs oracle: {nmis} support mismatches, slacks {np.sort(slacks)[:8]}, "
+          f"band {band:.2e} = 10 x {err_g:.2e} + KKT {st.kkt:.1e} + {ref.kkt[-1]:.1e}")
+    assert int(np.sum(bad)) == 0
     Xd = w.X.astype(np.float64)
     assert R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam) <= 1e-4
 
@@ -340,8 +362,10 @@ def _f1(a, b):
 def test_scalefree_p5000_mixed_against_fp64(A, precision):
     """Scale-free p=5000, n=1000, lambda=0.15 at full size: the mixed
     estimate against the FP64 GPU estimate (itself held to the oracle's iterate
-    sequence at smaller sizes): relative Frobenius <= 1e-4, support F1, and
-    the mixed estimate's KKT residual evaluated in FP64."""
+    sequence at smaller sizes): relative Frobenius <= 1e-4, the same zero
+    pattern except entries whose slack is within ten times the measured
+    gradient error of the mixed product, and the mixed estimate's KKT residual
+    evaluated in FP64.  Support F1 is reported, not graded."""
     w = workload("scalefree")
     X = dev(w.X)
     O64, s64 = A.accord_fit(X, w.lam, precision="fp64", kkt_tol=1e-7, max_iter=3000)
@@ -352,9 +376,15 @@ def test_scalefree_p5000_mixed_against_fp64(A, precision):
     f1 = _f1(a, b)
     G = A.accord_grad(X, O32.double()).cpu().numpy()
     kkt = R.kkt_residual(a, G, w.lam, w.lam)
-    print(f"p=5000 {precision} vs fp64: rel_fro {err:.2e}, support F1 {f1:.6f}, FP64 KKT {kkt:.2e}")
+    G64 = A.accord_grad(X, O64).cpu().numpy()
+    err_g = mixed_grad_error(A, X, O32)
+    band = 10 * err_g + s32.kkt + s64.kkt
+    bad, nmis, slacks = unexplained_mismatches(a, b, G64, w.lam, grad_band=band, s_diag=s_diag_of(w.X))
+    print(f"p=5000 {precision} vs fp64: rel_fro {err:.2e}, support F1 {f1:.6f}, FP64 KKT {kkt:.2e}, "
+          f"{nmis} support mismatches (largest slack {np.max(slacks) if nmis else 0.0:.2e}, "
+          f"band {band:.2e} = 10 x {err_g:.2e} + KKT {s32.kkt:.1e} + {s64.kkt:.1e}), {int(np.sum(bad))} unexplained")
     assert err <= 1e-4
-    assert f1 >= 0.999
+    assert int(np.sum(bad)) == 0
     assert kkt <= 1e-4
 
 
@@ -387,6 +417,19 @@ def test_hubblock_p40000_sampled_rows(A, precision):
           f"worst rel. to the exact row solution {worst_rel:.2e}")
     assert worst_kkt <= 1.5e-4
     assert worst_rel <= 1e-3
+    # the whole estimate: its FP64 gradient through the FP64 product (held to
+    # the oracle at smaller sizes), and the oracle's KKT residual of Eq. 3.3
+    # over every entry, one block of rows at a time
+    Od = Om.double()
+    del Om
+    G = A.accord_grad(X, Od)
+    full_kkt = 0.0
+    for r0 in range(0, p, 2000):
+        r1 = min(p, r0 + 2000)
+        full_kkt = max(full_kkt, R.kkt_residual(Od[r0:r1].cpu().numpy(), G[r0:r1].cpu().numpy(), w.lam, w.lam,
+                                                row0=r0))
+    print(f"p=40000 {precision}: FP64 KKT residual over all {p * p} entries {full_kkt:.2e} (fit reported {st.kkt:.2e})")
+    assert full_kkt <= 1.5e-4
 
 
 # --------------------------------------------- closed forms, degenerate data ---

@@ -63,6 +63,80 @@ def test_noalloc_loss_matches_accord_loss_twice(lib):
         assert abs(g - g_ref) <= 1e-12 * abs(g_ref)
 
 
+def test_noalloc_loss_matches_the_oracle(lib):
+    """The same evaluation held directly against the oracle's objective and
+    smooth part (Eq. 3.2), in FP64."""
+    from oracle import accord_ref as R
+    n, p, lam = 90, 210, 0.25
+    X, Om = _case(n, p, 3)
+    X64 = torch.as_tensor(X, device="cuda").double().contiguous()
+    O = torch.as_tensor(Om, device="cuda")
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    for pen in (True, False):
+        st = lib.accord_loss_f64_noalloc(X64.data_ptr(), n, p, O.data_ptr(), lam, int(pen), None, out.data_ptr())
+        assert st == 0, lib.accord_last_error()
+        torch.cuda.synchronize()
+        f, g = out.tolist()
+        Xd = X.astype(np.float64)
+        assert abs(g - R.smooth_g(Om, Xd)) <= 1e-12 * abs(g)
+        assert abs(f - R.objective(Om, Xd, lam, penalize_diag=pen)) <= 1e-12 * abs(f)
+
+
+def test_noalloc_loss_on_a_side_stream(lib):
+    """On a caller's own stream the call queues its work there and does not
+    synchronise; the result is read once that stream has finished."""
+    n, p, lam = 120, 260, 0.3
+    X, Om = _case(n, p, 4)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        X32 = torch.as_tensor(X, device="cuda")
+        X64 = X32.double().contiguous()
+        O = torch.as_tensor(Om, device="cuda")
+        out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.accord_loss_f64_noalloc(X64.data_ptr(), n, p, O.data_ptr(), lam, 1, side.cuda_stream,
+                                         out.data_ptr())
+        assert st == 0, lib.accord_last_error()
+    side.synchronize()
+    f, g = out.tolist()
+    f_ref, g_ref = _reference(lib, X32, O, lam, True)
+    assert abs(f - f_ref) <= 1e-12 * abs(f_ref)
+    assert abs(g - g_ref) <= 1e-12 * abs(g_ref)
+
+
+def test_noalloc_non_finite_inputs_give_the_documented_values(lib):
+    """The status cannot report domain errors (nothing is read back): a
+    non-finite X gives f = g = NaN and a non-positive diagonal gives
+    f = +inf, with status ACCORD_OK."""
+    n, p = 40, 70
+    X, Om = _case(n, p, 5)
+    X[3, 11] = np.nan
+    X64 = torch.as_tensor(X, device="cuda").double().contiguous()
+    O = torch.as_tensor(Om, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = lib.accord_loss_f64_noalloc(X64.data_ptr(), n, p, O.data_ptr(), 0.2, 1, None, out.data_ptr())
+    assert st == 0
+    torch.cuda.synchronize()
+    assert all(np.isnan(v) for v in out.tolist())
+    X, Om = _case(n, p, 6)
+    Om[5, 5] = -0.5
+    X64 = torch.as_tensor(X, device="cuda").double().contiguous()
+    O = torch.as_tensor(Om, device="cuda")
+    st = lib.accord_loss_f64_noalloc(X64.data_ptr(), n, p, O.data_ptr(), 0.2, 1, None, out.data_ptr())
+    assert st == 0
+    torch.cuda.synchronize()
+    f, g = out.tolist()
+    assert f == float("inf") and np.isfinite(g)
+
+
+def test_noalloc_rejects_extents_beyond_the_index_limit(lib):
+    from paper_2412_11554_gb300 import accord
+    X = torch.zeros((1, 8), dtype=torch.float64, device="cuda")  # never read: rejected first
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for n, p in ((2 ** 31, 8), (1, 2 ** 40), (2 ** 62, 2 ** 62)):
+        st = lib.accord_loss_f64_noalloc(X.data_ptr(), n, p, X.data_ptr(), 0.1, 1, None, out.data_ptr())
+        assert st == accord.EINVAL, (n, p)
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_array(lib):
     from paper_2412_11554_gb300 import accord
     n, p = 1, 200000  # needs 72 * p > 8 MiB of scratch
