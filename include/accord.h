@@ -140,10 +140,10 @@ void accord_default_opts(accord_opts* opts);
 /* Device workspace, in bytes, that accord_fit (Algorithm 1) needs for an
  * n x p problem under opts (precision and max_iter matter).  Returns 0 for
  * invalid sizes.
- * It grows as about 12.3 p^2 bytes in BF16X3 mode and 16.5 p^2 in TF32X3 and
- * FP64 modes.  With the caller's Omega on the same GPU, a 284 GB GB300 holds
- * at n = 1000 a fit of p up to about 132000 (BF16X3), 118000 (TF32X3) or
- * 108000 (FP64). */
+ * It grows as about 12.6 p^2 bytes in BF16X3 mode, 16.8 p^2 in TF32X3 mode
+ * and 16.4 p^2 in FP64 mode.  With the caller's Omega on the same GPU, a
+ * 284 GB GB300 holds at n = 1000 a fit of p up to about 131000 (BF16X3),
+ * 117000 (TF32X3) or 108000 (FP64). */
 size_t accord_workspace_bytes(int64_t n, int64_t p, const accord_opts* opts);
 
 /* ACCORD-FBS fit (Algorithm 1 with Eq. 3.5; stopping rule r(Omega^t) <= kkt_tol

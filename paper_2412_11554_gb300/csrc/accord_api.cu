@@ -43,6 +43,7 @@ struct Layout {
   size_t om[2] = {0, 0}, y[2] = {0, 0};
   size_t x64 = 0, xt64 = 0;                        // FP64 mode
   size_t om_hi = 0, om_lo = 0, y_hi[2] = {0, 0}, y_lo[2] = {0, 0};
+  size_t bm[2] = {0, 0};                           // occupancy bitmaps of the iterate buffers
   size_t x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0;  // mixed modes
   size_t gram = 0, lz_v = 0, lz_w = 0, lz_a = 0, lz_b = 0;
   size_t mask = 0;
@@ -90,6 +91,7 @@ Layout make_layout(int64_t n, int64_t p, int precision, int max_iter, int lanczo
     L.xt64 = take(c, (size_t)p * L.ldy * 8);
   } else {
     for (int b = 0; b < 2; ++b) L.y[b] = take(c, (size_t)p * L.ldy * 4);
+    for (int b = 0; b < 2; ++b) L.bm[b] = take(c, (size_t)bitmap_words(p) * 4);
     L.om_hi = take(c, (size_t)p * L.ldk * pe);
     L.om_lo = take(c, (size_t)p * L.ldk * pe);
     for (int b = 0; b < 2; ++b) {
@@ -297,6 +299,10 @@ int make_trial_plan(const Plan& P, TrialPlan& T, double lam, double lam_d) {
   t2.lam = (float)lam;
   t2.lam_d = (float)lam_d;
   t2.scale = (float)(1.0 / (double)L.n);
+  t2.bm[0] = at<uint32_t>(ws, L.bm[0]);
+  t2.bm[1] = at<uint32_t>(ws, L.bm[1]);
+  t2.ldbm = bitmap_ld(L.p);
+  t2.s_bm = 0;
 
   TcParams& t1 = T.t1;
   if (!encode_plane_map(&t1.a_hi[0], at<void>(ws, L.om_hi), L.pt, L.p, L.p, L.ldk, 128) ||
@@ -488,8 +494,20 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     }
   }
   int64_t nomp = 0, nyp = 0;
+  if (!f64) {
+    // buffer 1 starts as I with its bitmap: the prox epilogue writes a
+    // buffer only where the new iterate or the buffer's old content is
+    // nonzero, so both buffers and their bitmaps must agree from the start
+    ACCORD_CK(launch_set_identity(at<void>(ws, L.om[1]), 0, p, L.ldo, P.st));
+    ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[1]), p, P.st));
+    nlaunch += 2;
+  }
   if (o.init_from_omega) {
     ACCORD_CK(launch_copy_omega(Omega, p, at<void>(ws, L.om[0]), L.ldo, f64, p, P.st));
+    if (!f64) {
+      ACCORD_CK(launch_bitmap_from_dense(at<float>(ws, L.om[0]), p, L.ldo, at<uint32_t>(ws, L.bm[0]), P.st));
+      nlaunch += 1;
+    }
     ACCORD_CK(launch_omega_stats(at<void>(ws, L.om[0]), f64, p, L.ldo, at<double>(ws, L.part_om), &nomp, P.st));
     if (int e = setup_y(P, 0, 0)) return e;
     nyp = f64 ? gemm_f64_tiles(p, n) : tc_tiles(p, n);
@@ -497,6 +515,10 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   } else {
     // Omega^0 = I: its statistics are known and Y^0 = I X^T = X^T exactly
     ACCORD_CK(launch_set_identity(at<void>(ws, L.om[0]), f64, p, L.ldo, P.st));
+    if (!f64) {
+      ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[0]), p, P.st));
+      nlaunch += 1;
+    }
     ACCORD_CK(launch_identity_stats(at<double>(ws, L.part_om), p, P.st));
     nomp = 1;
     nlaunch += 2;

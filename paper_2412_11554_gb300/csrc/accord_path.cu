@@ -92,6 +92,7 @@ struct PathLayout {
   size_t kb_of = 0, g_rows = 0, g_scale = 0, g_off = 0;
   size_t part_prox = 0, part_y = 0;
   size_t om[2] = {0, 0}, y[2] = {0, 0};
+  size_t bm[2] = {0, 0};  // occupancy bitmaps of the iterate buffers (mixed modes), one per chain
   size_t x64 = 0, xt64 = 0;
   size_t y_hi[2] = {0, 0}, y_lo[2] = {0, 0}, x_hi = 0, x_lo = 0, xt_hi = 0, xt_lo = 0, dp_hi = 0, dp_lo = 0;
   size_t xt32 = 0, bkt_keys = 0, bkt_vals = 0, bkt_cnt = 0, part_sy = 0;
@@ -149,6 +150,7 @@ PathLayout make_path_layout(int64_t p, int64_t nchains, int64_t n_lambda, int64_
     L.x_lo = take(c, (size_t)B * K * L.ldo * pe);
     L.xt_hi = take(c, (size_t)B * p * K * pe);
     L.xt_lo = take(c, (size_t)B * p * K * pe);
+    for (int q = 0; q < 2; ++q) L.bm[q] = take(c, (size_t)B * bitmap_words(p) * 4);
     L.dp_hi = take(c, (size_t)B * p * L.ldo * pe);
     L.dp_lo = take(c, (size_t)B * p * L.ldo * pe);
     L.xt32 = take(c, (size_t)B * p * K * 4);
@@ -402,11 +404,21 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     ACCORD_CK(cudaGetLastError());
     nlaunch += 1;
   }
-  // Omega^0 = I and Y^0 = X^T for every chain
+  // Omega^0 = I and Y^0 = X^T for every chain.  In the mixed modes the
+  // second buffer starts as I too, and both carry their occupancy bitmaps: the
+  // prox epilogue writes a buffer only where the new iterate or the buffer's
+  // old content is nonzero.
   const size_t es = f64 ? 8 : 4;
-  for (int64_t c = 0; c < B; ++c)
+  for (int64_t c = 0; c < B; ++c) {
     ACCORD_CK(launch_set_identity(at<char>(ws, L.om[0]) + (size_t)c * p * L.ldo * es, f64, p, L.ldo, st));
-  nlaunch += B;
+    nlaunch += 1;
+    if (!f64) {
+      ACCORD_CK(launch_set_identity(at<char>(ws, L.om[1]) + (size_t)c * p * L.ldo * es, 0, p, L.ldo, st));
+      for (int q = 0; q < 2; ++q)
+        ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[q]) + c * bitmap_words(p), p, st));
+      nlaunch += 3;
+    }
+  }
   if (f64) {
     ACCORD_CK(cudaMemcpyAsync(at<double>(ws, L.y[0]), at<double>(ws, L.xt64), (size_t)B * p * K * 8,
                               cudaMemcpyDeviceToDevice, st));
@@ -563,6 +575,10 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     t2.nactive = pd.nactive;
     t2.kb_of = at<int32_t>(ws, L.kb_of);
     t2.s_out = p * L.ldo; t2.s_aux = p * L.ldo; t2.s_part = L.tiles_prox; t2.s_bkt = L.nbuckets;
+    t2.bm[0] = at<uint32_t>(ws, L.bm[0]);
+    t2.bm[1] = at<uint32_t>(ws, L.bm[1]);
+    t2.ldbm = bitmap_ld(p);
+    t2.s_bm = bitmap_words(p);
     t2.any_dense = at<int>(ws, L.any_dense);
     // a chain in dense Y mode gets its Delta planes from this epilogue
     t2.out_hi[0] = t2.out_hi[1] = at<void>(ws, L.dp_hi);

@@ -170,6 +170,44 @@ __device__ __forceinline__ void prefetch_block(float* buf, const float* __restri
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// 32 x 32 bit-matrix transpose across a warp: on entry lane r holds row r
+// (bit c = element (r, c)); on exit lane c holds column c (bit r = element
+// (r, c)).  Five butterfly stages swap the off-diagonal j x j bit blocks of
+// lanes lane and lane ^ j, for j = 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t transpose_bits(uint32_t x, int lane) {
+  uint32_t m = 0x0000FFFFu;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1, m ^= m << j) {
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t & m) << j));
+  }
+  return x;
+}
+
+// The 32 x 32 block src[row_base .. +31][col0 .. +31] into buf (row-major),
+// reading only its nonzero entries: rbits holds, in lane r, the occupancy
+// word of row r (bit c: column col0 + c nonzero).  The buffer is zeroed and
+// the nonzero entries are copied over it asynchronously; rows with no
+// nonzero entry cost nothing beyond the zeroing.
+__device__ __forceinline__ void prefetch_sparse_block(float* buf, const float* __restrict__ src, int64_t ld,
+                                                      int64_t row_base, int64_t col0, uint32_t rbits, int lane,
+                                                      uint64_t pol) {
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) reinterpret_cast<float4*>(buf)[k * 32 + lane] = z;
+  __syncwarp();
+  const uint32_t sbase = ptx::smem_u32(buf);
+  uint32_t rows = __ballot_sync(0xffffffffu, rbits != 0u);
+  while (rows != 0u) {
+    const int r = __ffs(rows) - 1;
+    rows &= rows - 1u;
+    const uint32_t m = __shfl_sync(0xffffffffu, rbits, r);
+    if ((m >> lane) & 1u)
+      ptx::cp_async4_hint(sbase + (uint32_t)((r * 32 + lane) * 4), src + (row_base + r) * ld + col0 + lane, pol);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // Column `lane` of a block written by prefetch_block (conflict-free reads).
 __device__ __forceinline__ void read_block_column(const float* buf, int lane, float (&pre)[32]) {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -239,10 +277,14 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
 // and the diagonal (row == colt); the unchecked form is the hot path.
+// oldcol: bit r set where the buffer receiving Omega+ holds a nonzero at
+// (row_base + r, colt); Omega+ is stored where it is nonzero or where that
+// stale value must be cleared.  Returns the occupancy of Omega+ in this
+// column (bit r: row_base + r nonzero).
 template <int PT, bool CHECK, bool MASK, bool SPARSE>
-__device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
-                                           int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
-                                           int lane) {
+__device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
+                                               int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
+                                               int lane, uint32_t oldcol) {
   float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
@@ -254,6 +296,7 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
   const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
   const int64_t mcol = (colt - lane) >> 5;  // mask word of this 32-column chunk
   uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
+  uint32_t newcol = 0u;  // bit r: Omega+ in row r of this column is nonzero
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     if (CHECK && row_base + r >= ea.M) continue;  // warp-uniform
@@ -289,7 +332,9 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
       chk = fmaf(g, 0.f, chk);
       d = w - om;
       sd = fmaf(d, d, sd);
-      ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
+      const bool nzw = w != 0.f;
+      newcol |= nzw ? (1u << r) : 0u;
+      if (nzw || ((oldcol >> r) & 1u)) ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
       if (!sparse) st_split_hint<PT>(ph + r * ldp, pl + r * ldp, d, ea.pol_stream);
     }
     v[r] = d;
@@ -338,6 +383,7 @@ __device__ __forceinline__ void prox_chunk(const EpiArgs& ea, const TcParams& pr
   sm.r4 += nnz;
   sm.kkt = fmaxf(sm.kkt, kk);
   if (chk != 0.f || !(sd == sd)) sm.bad += 1.f;
+  return newcol;
 }
 
 __device__ __forceinline__ void grad_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base, int64_t colt,
@@ -608,10 +654,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       Sums sm;
       float pre[32];
+      // Prox mode: occupancy words of this warp's four chunks (lane r: row
+      // row_base + r) of the current iterate (which entries of Omega exist)
+      // and of the buffer that receives Omega+ (which stale entries to clear).
+      uint32_t wc0 = 0u, wc1 = 0u, wc2 = 0u, wc3 = 0u, wo0 = 0u, wo1 = 0u, wo2 = 0u, wo3 = 0u;
+      uint32_t* bmn = nullptr;
+      const int64_t ch0 = col_base >> 5;
+      if (MODE == kModeProx && row_base < prm.M) {
+        const uint32_t* bmc = prm.bm[cb] + b * prm.s_bm + ch0 * prm.ldbm + row_base + lane;
+        bmn = prm.bm[nx] + b * prm.s_bm;
+        const uint32_t* bmo = bmn + ch0 * prm.ldbm + row_base + lane;
+        const int64_t nch = (prm.N + 31) >> 5;
+        if (ch0 < nch) { wc0 = __ldg(bmc); wo0 = bmo[0]; }
+        if (ch0 + 1 < nch) { wc1 = __ldg(bmc + prm.ldbm); wo1 = bmo[prm.ldbm]; }
+        if (ch0 + 2 < nch) { wc2 = __ldg(bmc + 2 * prm.ldbm); wo2 = bmo[2 * prm.ldbm]; }
+        if (ch0 + 3 < nch) { wc3 = __ldg(bmc + 3 * prm.ldbm); wo3 = bmo[3 * prm.ldbm]; }
+      }
       // the first chunk's operand does not depend on the MMA: start fetching it
       // before waiting for the accumulator
       bool pending = false;
-      if (kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
+      if (MODE == kModeProx) {
+        prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, wc0, lane, ea.pol_stream);
+        pending = true;
+      } else if (kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
         prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane, ea.pol_stream);
         pending = true;
       }
@@ -638,8 +703,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           float v[32];
           transpose32(tbuf, rr, lane, v);
           // the buffer is free again: fetch the next chunk's operand while this one computes
-          if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
-              col0 + 64 <= prm.N) {
+          const int k = c >> 5;
+          if (MODE == kModeProx) {
+            if (c + 32 < kColsPerWarp) {
+              const uint32_t wn = k == 0 ? wc1 : (k == 1 ? wc2 : wc3);
+              prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wn, lane, ea.pol_stream);
+              pending = true;
+            }
+          } else if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
+                     col0 + 64 <= prm.N) {
             prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, lane, ea.pol_stream);
             pending = true;
           }
@@ -651,21 +723,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           } else if (MODE == kModeProx) {
             // compile-time variants: full interior chunk, Delta to buckets, no refit mask is the hot one
             const bool fast = full && !diag;
+            const uint32_t oldcol = transpose_bits(k == 0 ? wo0 : (k == 1 ? wo1 : (k == 2 ? wo2 : wo3)), lane);
+            uint32_t newcol;
             if (ea.mask == nullptr) {
               if (ea.bkey != nullptr) {
-                if (fast) prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) newcol = prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+                else newcol = prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
               } else {
-                if (fast) prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) newcol = prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+                else newcol = prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
               }
             } else if (ea.bkey != nullptr) {
-              if (fast) prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) newcol = prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+              else newcol = prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
             } else {
-              if (fast) prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) newcol = prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+              else newcol = prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
             }
+            // the occupancy of Omega+ in this chunk, one word per row
+            bmn[(ch0 + k) * prm.ldbm + row_base + lane] = transpose_bits(newcol, lane);
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
           } else {

@@ -63,6 +63,14 @@ cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void
                                     void* XThi, void* XTlo, int64_t ldxt, int* bad_flag, int pt, cudaStream_t st);
 // Omega^0 = I in an internal buffer with leading dimension ld (elements).
 cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st);
+// Occupancy bitmaps of the mixed-mode iterate buffers (the prox epilogue's
+// sparse reads and writes of Omega): ceil(p / 32) column chunks of
+// bitmap_ld(p) words each; word [c * bitmap_ld(p) + i] has bit j - 32 c set
+// iff Omega[i][j] != 0.  Rows past p hold 0.
+int64_t bitmap_ld(int64_t p);
+int64_t bitmap_words(int64_t p);
+cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st);
+cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st);
 // Copy between a dense p x p user array (ld = p) and an internal buffer.
 cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
                               int64_t p, cudaStream_t st);

@@ -133,6 +133,36 @@ __global__ void set_identity_kernel(T* __restrict__ Om, int64_t p, int64_t ld) {
   }
 }
 
+// Occupancy bitmap of Omega = I: word (c, i) = c * ldbm + i holds the bit of
+// the diagonal entry (i, i) when column i falls in chunk c.
+__global__ void identity_bitmap_kernel(uint32_t* __restrict__ bm, int64_t p, int64_t ldbm, int64_t nwords) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nwords; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = k / ldbm, i = k - c * ldbm;
+    bm[k] = (i < p && (i >> 5) == c) ? (1u << (i & 31)) : 0u;
+  }
+}
+
+// Occupancy bitmap of a dense FP32 matrix: one warp per 32 x 32 block, one
+// ballot per row, and lane r stores the word of row r.
+__global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t p, int64_t ld, uint32_t* __restrict__ bm,
+                                         int64_t ldbm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nch = (p + 31) / 32, nblk = nch * nch;
+  const int64_t wpb = blockDim.x / 32;
+  for (int64_t blk = blockIdx.x * wpb + threadIdx.x / 32; blk < nblk; blk += (int64_t)gridDim.x * wpb) {
+    const int64_t rb = blk / nch, c = blk - rb * nch;
+    const int64_t col = c * 32 + lane;
+    uint32_t mine = 0u;
+    for (int r = 0; r < 32; ++r) {
+      const int64_t row = rb * 32 + r;
+      const bool nz = row < p && col < p && Om[row * ld + col] != 0.f;
+      const uint32_t w = __ballot_sync(0xffffffffu, nz);
+      if (lane == r) mine = w;
+    }
+    bm[c * ldbm + rb * 32 + lane] = mine;
+  }
+}
+
 template <class T>
 __global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
                                   int64_t ldd, int64_t p) {
@@ -830,6 +860,23 @@ cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cud
   const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
   if (is_f64) set_identity_kernel<double><<<g, 512, 0, st>>>((double*)Om, p, ld);
   else set_identity_kernel<float><<<g, 512, 0, st>>>((float*)Om, p, ld);
+  return cudaGetLastError();
+}
+
+int64_t bitmap_ld(int64_t p) { return (p + 31) / 32 * 32; }
+int64_t bitmap_words(int64_t p) { return (p + 31) / 32 * bitmap_ld(p); }
+
+cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st) {
+  const int64_t nw = bitmap_words(p);
+  identity_bitmap_kernel<<<grid_for(nw, 256), 256, 0, st>>>(bm, p, bitmap_ld(p), nw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st) {
+  const int64_t nch = (p + 31) / 32;
+  const int64_t blocks = (nch * nch + 7) / 8;
+  bitmap_from_dense_kernel<<<(unsigned)std::min<int64_t>(blocks, 152 * 32), 256, 0, st>>>(Om, p, ld, bm,
+                                                                                           bitmap_ld(p));
   return cudaGetLastError();
 }
 

@@ -64,6 +64,14 @@ struct TcParams {
   int* any_dense;
   int32_t max_pairs;     // persistent grid limit in CTA pairs (0: as many as fit at once)
   int32_t ptype;         // plane type of the operands and plane outputs: kPlaneBf16 / kPlaneTf32
+  // Occupancy bitmaps of the two iterate buffers (prox mode): word
+  // [c * ldbm + i] has bit j - 32 c set iff Omega[i][j] != 0 for the 32
+  // columns j of chunk c; rows past p read as 0.  The prox epilogue fetches
+  // only the nonzero entries of Omega, stores Omega+ only where it is nonzero
+  // or where the buffer it overwrites was nonzero, and writes the new
+  // bitmap.  A batch keeps one pair per problem, s_bm words apart.
+  uint32_t* bm[2];
+  int64_t ldbm, s_bm;
   // Bounded waits: every mbarrier wait of the launch gives up after wait_ns
   // (set from the process-wide limit, 4 s by default).  withhold_first: the
   // producers of both CTAs of the first pair skip the copies of their first

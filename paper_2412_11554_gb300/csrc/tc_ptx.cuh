@@ -141,6 +141,11 @@ __device__ __forceinline__ void cp_async16_hint(uint32_t dst, const void* src, u
                : "memory");
 }
 
+__device__ __forceinline__ void cp_async4_hint(uint32_t dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "l"(pol)
+               : "memory");
+}
+
 // ------------------------------------------------------------------ TMA ---
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
