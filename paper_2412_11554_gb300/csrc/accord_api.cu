@@ -405,7 +405,8 @@ int launch_trial(const Plan& P, const TrialPlan& T, Profiler& prof, int64_t& nla
   } else if (L.sparse) {
     // Y+ = Y + Delta X^T: sparse update, or the dense fallback when a bucket
     // overflowed (each kernel checks ctrl->dense and exits when not its turn)
-    ACCORD_CK(launch_delta_planes(P.ctrl, at<float>(P.ws, L.om[0]), at<float>(P.ws, L.om[1]), L.p, L.ldo,
+    ACCORD_CK(launch_delta_planes(P.ctrl, at<float>(P.ws, L.om[0]), at<float>(P.ws, L.om[1]),
+                                  at<uint32_t>(P.ws, L.bm[0]), at<uint32_t>(P.ws, L.bm[1]), L.p, L.ldo,
                                   at<void>(P.ws, L.om_hi), at<void>(P.ws, L.om_lo), L.ldk, L.pt, P.st));
     ACCORD_CK(launch_tc_gemm(kModeY, T.t1, P.st));
     ACCORD_CK(launch_sparse_y(T.sy, P.st));
@@ -494,14 +495,9 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     }
   }
   int64_t nomp = 0, nyp = 0;
-  if (!f64) {
-    // buffer 1 starts as I with its bitmap: the prox epilogue writes a
-    // buffer only where the new iterate or the buffer's old content is
-    // nonzero, so both buffers and their bitmaps must agree from the start
-    ACCORD_CK(launch_set_identity(at<void>(ws, L.om[1]), 0, p, L.ldo, P.st));
-    ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[1]), p, P.st));
-    nlaunch += 2;
-  }
+  // Mixed modes: a buffer's values count only where its occupancy bitmap has
+  // a bit, and every prox launch writes the whole bitmap of the buffer it
+  // fills, so only buffer 0 (the starting iterate) needs one here.
   if (o.init_from_omega) {
     ACCORD_CK(launch_copy_omega(Omega, p, at<void>(ws, L.om[0]), L.ldo, f64, p, P.st));
     if (!f64) {
@@ -629,8 +625,13 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
     hc.status = kEcuda;
   }
 
-  // copy the returned iterate to the caller
-  ACCORD_CK(launch_copy_omega(at<void>(ws, L.om[hc.cur]), L.ldo, Omega, p, f64, p, P.st));
+  // copy the returned iterate to the caller (mixed modes: zeros wherever its
+  // bitmap has no bit)
+  if (f64)
+    ACCORD_CK(launch_copy_omega(at<void>(ws, L.om[hc.cur]), L.ldo, Omega, p, f64, p, P.st));
+  else
+    ACCORD_CK(launch_copy_omega_masked(at<float>(ws, L.om[hc.cur]), L.ldo, at<uint32_t>(ws, L.bm[hc.cur]),
+                                       static_cast<float*>(Omega), p, p, P.st));
   nlaunch += 1;
   ACCORD_CK(cudaEventRecord(ev[2], P.st));
   if (o.trace && o.trace_cap > 0) {

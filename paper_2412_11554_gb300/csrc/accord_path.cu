@@ -214,9 +214,10 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
   } else {
     // sparse Y+ = Y + Delta X^T, or the dense product for a chain whose Delta
     // bucket overflowed (each kernel checks its chain's flag)
-    ACCORD_CK(launch_delta_planes(ctrl, at<float>(ws, L.om[0]), at<float>(ws, L.om[1]), L.p, L.ldo,
-                                  at<void>(ws, L.dp_hi), at<void>(ws, L.dp_lo), L.ldo, L.pt, st, B,
-                                  P.pd.active, P.pd.nactive, L.p * L.ldo, L.p * L.ldo, at<int>(ws, L.any_dense)));
+    ACCORD_CK(launch_delta_planes(ctrl, at<float>(ws, L.om[0]), at<float>(ws, L.om[1]), at<uint32_t>(ws, L.bm[0]),
+                                  at<uint32_t>(ws, L.bm[1]), L.p, L.ldo, at<void>(ws, L.dp_hi), at<void>(ws, L.dp_lo),
+                                  L.ldo, L.pt, st, B, P.pd.active, P.pd.nactive, L.p * L.ldo, L.p * L.ldo,
+                                  at<int>(ws, L.any_dense), bitmap_words(L.p)));
     ACCORD_CK(launch_tc_gemm(kModeY, P.t1, st));
     ACCORD_CK(launch_sparse_y(P.sy, st));
   }
@@ -404,19 +405,17 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     ACCORD_CK(cudaGetLastError());
     nlaunch += 1;
   }
-  // Omega^0 = I and Y^0 = X^T for every chain.  In the mixed modes the
-  // second buffer starts as I too, and both carry their occupancy bitmaps: the
-  // prox epilogue writes a buffer only where the new iterate or the buffer's
-  // old content is nonzero.
+  // Omega^0 = I and Y^0 = X^T for every chain.  In the mixed modes a buffer's
+  // values count only where its occupancy bitmap has a bit, and every prox
+  // launch writes the whole bitmap of the buffer it fills, so only buffer 0
+  // needs one here.
   const size_t es = f64 ? 8 : 4;
   for (int64_t c = 0; c < B; ++c) {
     ACCORD_CK(launch_set_identity(at<char>(ws, L.om[0]) + (size_t)c * p * L.ldo * es, f64, p, L.ldo, st));
     nlaunch += 1;
     if (!f64) {
-      ACCORD_CK(launch_set_identity(at<char>(ws, L.om[1]) + (size_t)c * p * L.ldo * es, 0, p, L.ldo, st));
-      for (int q = 0; q < 2; ++q)
-        ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[q]) + c * bitmap_words(p), p, st));
-      nlaunch += 3;
+      ACCORD_CK(launch_identity_bitmap(at<uint32_t>(ws, L.bm[0]) + c * bitmap_words(p), p, st));
+      nlaunch += 1;
     }
   }
   if (f64) {
@@ -673,7 +672,8 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     if (int r = launch_path_rest(P, s)) return r;
     if (emit)
       ACCORD_CK(launch_path_emit(pd, at<void>(ws, L.om[0]), at<void>(ws, L.om[1]), f64, p, L.ldo, p * L.ldo, support,
-                                 (p + 31) / 32, omega_best, s));
+                                 (p + 31) / 32, omega_best, s, f64 ? nullptr : at<uint32_t>(ws, L.bm[0]),
+                                 f64 ? nullptr : at<uint32_t>(ws, L.bm[1]), bitmap_words(p)));
     return kOk;
   };
   const bool use_graph = o.profile == 0;

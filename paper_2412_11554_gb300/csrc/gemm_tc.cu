@@ -48,13 +48,18 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kBN = 256;          // output columns of a tile (MMA N)
 constexpr int kBHalf = kBN / 2;   // B rows each CTA of the pair holds
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr uint32_t kABytes = BM * kRowBytes;
 constexpr uint32_t kBBytes = kBHalf * kRowBytes;
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // one CTA's share of a stage
 constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
 constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 block per epilogue warp
-constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + 1024;
+// Prox mode: occupancy words of two tiles per epilogue warp (the current one
+// and the next): the current iterate's words of the warp's four chunks, 32
+// words (rows) each.
+constexpr uint32_t kWordSlotWords = 4 * 32;
+constexpr uint32_t kWordBytes = kEpiWarps * 2 * kWordSlotWords * 4;
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + kWordBytes + 1024;
 // Tail after the epilogue buffers: 2 kStages + 5 mbarriers, the TMEM slot and
 // two flags, then the epilogue's FP64 partials [kEpiWarps][8] from kRedOffset.
 constexpr size_t kRedOffset = 256;
@@ -208,6 +213,23 @@ __device__ __forceinline__ void prefetch_sparse_block(float* buf, const float* _
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// Asynchronous copy of one tile's occupancy words into a word slot (prox
+// mode): row k is the current iterate's word of chunk ch0 + k; lane r of a
+// row is the word of matrix row row_base + r.  Chunks past nch, or a tile
+// whose rows lie past the matrix, read as zero words (no global read).  One
+// 16-byte copy a lane.
+__device__ __forceinline__ void load_words(uint32_t* slot, const uint32_t* bmc, int64_t ldbm, int64_t ch0, int64_t nch,
+                                           int64_t row_base, bool rows_in, int lane) {
+  const uint32_t sbase = ptx::smem_u32(slot);
+  const int k = lane >> 3, seg = lane & 7;
+  const bool in = rows_in && ch0 + k < nch;
+  const uint32_t* src = bmc + (in ? (ch0 + k) * ldbm + row_base + 4 * seg : 0);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sbase + (uint32_t)((k * 32 + 4 * seg) * 4)),
+               "l"(src), "r"(in ? 16 : 0)
+               : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // Column `lane` of a block written by prefetch_block (conflict-free reads).
 __device__ __forceinline__ void read_block_column(const float* buf, int lane, float (&pre)[32]) {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -277,15 +299,15 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
 // trial / KKT partial sums for column colt.  CHECK handles the matrix edge
 // and the diagonal (row == colt); the unchecked form is the hot path.
-// oldcol: bit r set where the buffer receiving Omega+ holds a nonzero at
-// (row_base + r, colt); Omega+ is stored where it is nonzero or where that
-// stale value must be cleared.  Returns the occupancy of Omega+ in this
-// column (bit r: row_base + r nonzero).
+// Omega+ is stored only where it is nonzero: the receiving buffer's values
+// count only where its occupancy bitmap (written from the return value) has
+// a bit.  Returns the occupancy of Omega+ in this column (bit r: row
+// row_base + r nonzero).
 template <int PT, bool CHECK, bool MASK, bool SPARSE>
 __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
                                                int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
-                                               int lane, uint32_t oldcol) {
-  float sd = 0.f, sl1 = 0.f, kk = 0.f, chk = 0.f, nnz = 0.f;
+                                               int lane) {
+  float sd = 0.f, sl1 = 0.f, kk = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
   const bool cok = !CHECK || colt < ea.N;
   constexpr bool sparse = SPARSE;  // Delta to the buckets (else to operand planes)
@@ -321,20 +343,20 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
             tlam_e = INFINITY;
           }
         }
+        // written so that a NaN gradient gives a NaN entry (caught below
+        // through ||Delta||^2) rather than a zero
         const float m = fabsf(a) - tlam_e;
-        w = m > 0.f ? copysignf(m, a) : 0.f;
+        w = m <= 0.f ? 0.f : copysignf(m, a);
         sl1 += fabsf(w);
-        nnz += (w != 0.f) ? 1.f : 0.f;
         const float kz = fabsf(g) - lam_e;                 // omega == 0: max(|G| - lambda, 0)
         const float knz = fabsf(g + copysignf(lam_e, om));  // omega != 0: |G + lambda sign(omega)|
         kk = fmaxf(kk, om != 0.f ? knz : kz);
       }
-      chk = fmaf(g, 0.f, chk);
       d = w - om;
       sd = fmaf(d, d, sd);
       const bool nzw = w != 0.f;
       newcol |= nzw ? (1u << r) : 0u;
-      if (nzw || ((oldcol >> r) & 1u)) ptx::st_f32_hint(po + r * ldo, w, ea.pol_stream);
+      ptx::st_f32_hint_if(po + r * ldo, w, ea.pol_stream, nzw);
       if (!sparse) st_split_hint<PT>(ph + r * ldp, pl + r * ldp, d, ea.pol_stream);
     }
     v[r] = d;
@@ -378,11 +400,19 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
       }
     }
   }
+  // off-diagonal nonzeros of Omega+ in this column: the occupancy bits,
+  // less the diagonal entry where this column meets it
+  int nnz = __popc(newcol);
+  if (CHECK) {
+    const int64_t dr = colt - row_base;
+    if (dr >= 0 && dr < 32 && ((newcol >> dr) & 1u)) nnz -= 1;
+  }
   sm.r0 += sd;
   sm.r1 += sl1;
-  sm.r4 += nnz;
+  sm.r4 += (float)nnz;
   sm.kkt = fmaxf(sm.kkt, kk);
-  if (chk != 0.f || !(sd == sd)) sm.bad += 1.f;
+  // a non-finite gradient or iterate entry makes ||Delta||^2 NaN or infinite
+  if (!(sd <= 3.4e38f)) sm.bad += 1.f;
   return newcol;
 }
 
@@ -425,7 +455,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* epi_buf = reinterpret_cast<float*>(smem + kStages * kStageBytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + kEpiBufBytes);
+  uint32_t* word_area = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes + kEpiBufBytes);
+  uint8_t* tail = smem + kStages * kStageBytes + kEpiBufBytes + kWordBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tail);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
   uint64_t* tempty = tfull + 2;
@@ -433,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* stop_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
-  double* red = reinterpret_cast<double*>(smem + kStages * kStageBytes + kEpiBufBytes + kRedOffset);
+  double* red = reinterpret_cast<double*>(tail + kRedOffset);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int rank = (int)ptx::cluster_ctarank();  // 0: leader (issues the MMAs), 1: peer
@@ -615,10 +647,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ea.mask = prm.mask;
     ea.mask_ld = prm.mask_ld;
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
+    constexpr bool kProx = MODE == kModeProx;
+    // Prox mode keeps one tile of lookahead: the next tile's occupancy words
+    // are copied during this tile's first chunk, and its first block of Omega
+    // during this tile's last, so that no tile starts on a memory round trip.
+    uint32_t* wslots = word_area + e * 2 * kWordSlotWords;
+    const int64_t nch = (prm.N + 31) >> 5;
+    int slot = 0;
+    bool pending = false;
     int i = 0;
     int b = 0, Tl = 0;
-    for (int T = next_tile(prm, cta, ntot, nctas, b, Tl); T < ntot;
-         T = next_tile(prm, T + nctas, ntot, nctas, b, Tl), ++i) {
+    int T = next_tile(prm, cta, ntot, nctas, b, Tl);
+    if (kProx && T < ntot) {
+      int mb0, nb0;
+      pair_tile(Tl, prm, rank, mb0, nb0);
+      const int cb0 = ctrl ? ctrl[b].cur : 0;
+      const int64_t rb0 = (int64_t)mb0 * BM + 32 * q, cbase0 = (int64_t)nb0 * kBN + h * kColsPerWarp;
+      load_words(wslots, prm.bm[cb0] + b * prm.s_bm, prm.ldbm, cbase0 >> 5, nch, rb0, rb0 < prm.M, lane);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp();
+      prefetch_sparse_block(tbuf, prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0, wslots[lane], lane,
+                            ea.pol_stream);
+      pending = true;
+    }
+    for (; T < ntot; ++i) {
+      int bN = 0, TlN = 0;
+      const int TN = next_tile(prm, T + nctas, ntot, nctas, bN, TlN);
       int mb, nb;
       pair_tile(Tl, prm, rank, mb, nb);
       // this tile's problem: its iterate buffers, step and penalty
@@ -654,29 +708,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       Sums sm;
       float pre[32];
-      // Prox mode: occupancy words of this warp's four chunks (lane r: row
-      // row_base + r) of the current iterate (which entries of Omega exist)
-      // and of the buffer that receives Omega+ (which stale entries to clear).
-      uint32_t wc0 = 0u, wc1 = 0u, wc2 = 0u, wc3 = 0u, wo0 = 0u, wo1 = 0u, wo2 = 0u, wo3 = 0u;
-      uint32_t* bmn = nullptr;
+      // Prox mode: this tile's occupancy words (slot `slot`, lane r: row
+      // row_base + r) of the current iterate (which entries of Omega exist);
+      // the next tile's go to the other slot.
+      const uint32_t* wcur = wslots + slot * kWordSlotWords;
+      uint32_t* wnext = wslots + (slot ^ 1) * kWordSlotWords;
+      uint32_t* bmn = kProx ? prm.bm[nx] + b * prm.s_bm : nullptr;
       const int64_t ch0 = col_base >> 5;
-      if (MODE == kModeProx && row_base < prm.M) {
-        const uint32_t* bmc = prm.bm[cb] + b * prm.s_bm + ch0 * prm.ldbm + row_base + lane;
-        bmn = prm.bm[nx] + b * prm.s_bm;
-        const uint32_t* bmo = bmn + ch0 * prm.ldbm + row_base + lane;
-        const int64_t nch = (prm.N + 31) >> 5;
-        if (ch0 < nch) { wc0 = __ldg(bmc); wo0 = bmo[0]; }
-        if (ch0 + 1 < nch) { wc1 = __ldg(bmc + prm.ldbm); wo1 = bmo[prm.ldbm]; }
-        if (ch0 + 2 < nch) { wc2 = __ldg(bmc + 2 * prm.ldbm); wo2 = bmo[2 * prm.ldbm]; }
-        if (ch0 + 3 < nch) { wc3 = __ldg(bmc + 3 * prm.ldbm); wo3 = bmo[3 * prm.ldbm]; }
+      int cbN = 0;
+      int64_t rbN = 0, cbaseN = 0;
+      if (kProx && TN < ntot) {
+        int mbN, nbN;
+        pair_tile(TlN, prm, rank, mbN, nbN);
+        cbN = ctrl ? ctrl[bN].cur : 0;
+        rbN = (int64_t)mbN * BM + 32 * q;
+        cbaseN = (int64_t)nbN * kBN + h * kColsPerWarp;
       }
       // the first chunk's operand does not depend on the MMA: start fetching it
-      // before waiting for the accumulator
-      bool pending = false;
-      if (MODE == kModeProx) {
-        prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, wc0, lane, ea.pol_stream);
-        pending = true;
-      } else if (kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
+      // before waiting for the accumulator (prox mode: fetched during the
+      // previous tile)
+      if (!kProx && kNeedAux && ea.aux != nullptr && aux_async && rows_full && col_base + 32 <= prm.N) {
         prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col_base, lane, ea.pol_stream);
         pending = true;
       }
@@ -697,6 +748,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             else load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
           }
           pending = false;
+          // the next tile's words, queued behind this tile's first block
+          if (kProx && c == 0 && TN < ntot)
+            load_words(wnext, prm.bm[cbN] + bN * prm.s_bm, prm.ldbm, cbaseN >> 5, nch, rbN, rbN < prm.M, lane);
           uint32_t rr[32];
           ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * kBN + h * kColsPerWarp + c, rr);
           ptx::tmem_ld_wait();
@@ -704,10 +758,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           transpose32(tbuf, rr, lane, v);
           // the buffer is free again: fetch the next chunk's operand while this one computes
           const int k = c >> 5;
-          if (MODE == kModeProx) {
+          if (kProx) {
             if (c + 32 < kColsPerWarp) {
-              const uint32_t wn = k == 0 ? wc1 : (k == 1 ? wc2 : wc3);
-              prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wn, lane, ea.pol_stream);
+              prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wcur[(k + 1) * 32 + lane], lane,
+                                    ea.pol_stream);
+              pending = true;
+            } else if (TN < ntot) {
+              // the next tile's first block (its words arrived during chunk 1's wait)
+              prefetch_sparse_block(tbuf, prm.aux[cbN] + bN * prm.s_aux, prm.ldaux, rbN, cbaseN, wnext[lane], lane,
+                                    ea.pol_stream);
               pending = true;
             }
           } else if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
@@ -723,22 +782,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           } else if (MODE == kModeProx) {
             // compile-time variants: full interior chunk, Delta to buckets, no refit mask is the hot one
             const bool fast = full && !diag;
-            const uint32_t oldcol = transpose_bits(k == 0 ? wo0 : (k == 1 ? wo1 : (k == 2 ? wo2 : wo3)), lane);
             uint32_t newcol;
             if (ea.mask == nullptr) {
               if (ea.bkey != nullptr) {
-                if (fast) newcol = prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
-                else newcol = prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+                if (fast) newcol = prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else newcol = prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
               } else {
-                if (fast) newcol = prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
-                else newcol = prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+                if (fast) newcol = prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                else newcol = prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
               }
             } else if (ea.bkey != nullptr) {
-              if (fast) newcol = prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
-              else newcol = prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+              if (fast) newcol = prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else newcol = prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
             } else {
-              if (fast) newcol = prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
-              else newcol = prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane, oldcol);
+              if (fast) newcol = prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              else newcol = prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
             }
             // the occupancy of Omega+ in this chunk, one word per row
             bmn[(ch0 + k) * prm.ldbm + row_base + lane] = transpose_bits(newcol, lane);
@@ -749,7 +807,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
         }
       }
-      if (pending) asm volatile("cp.async.wait_group 0;" ::: "memory");
+      if (!kProx && pending) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        pending = false;
+      }
       // this warp's TMEM reads are done: one release per warp, on the leader
       ptx::tc_fence_before();
       __syncwarp();
@@ -800,7 +861,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       epi_bar();
       if (*stop_flag) break;
+      T = TN;
+      b = bN;
+      Tl = TlN;
+      slot ^= 1;
     }
+    // no copy of this warp may still be in flight when the CTA leaves
+    if (pending) asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
 
   __syncwarp();

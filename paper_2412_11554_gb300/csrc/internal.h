@@ -70,6 +70,9 @@ cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cud
 int64_t bitmap_ld(int64_t p);
 int64_t bitmap_words(int64_t p);
 cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st);
+// Dense copy (ld ldd) of an FP32 iterate buffer that counts only where its bitmap has a bit.
+cudaError_t launch_copy_omega_masked(const float* src, int64_t lds, const uint32_t* bm, float* dst, int64_t ldd,
+                                     int64_t p, cudaStream_t st);
 cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st);
 // Copy between a dense p x p user array (ld = p) and an internal buffer.
 cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
@@ -165,9 +168,12 @@ cudaError_t launch_path_advance(const PathDev& pd, cudaStream_t st);
 // For each estimate recorded by the last advance: its support bits (if
 // support != null; record k * nchains + c, p rows of mask_ld words) and, when
 // its epBIC is the chain's best so far, a dense copy into omega_best + c p^2.
+// Mixed modes pass the buffers' occupancy bitmaps (bm0, bm1, s_bm words per
+// chain): a buffer's values count only where its bitmap has a bit.
 cudaError_t launch_path_emit(const PathDev& pd, const void* om0, const void* om1, int is_f64, int64_t p,
                              int64_t ldo, int64_t s_om, uint32_t* support, int64_t mask_ld, void* omega_best,
-                             cudaStream_t st);
+                             cudaStream_t st, const uint32_t* bm0 = nullptr, const uint32_t* bm1 = nullptr,
+                             int64_t s_bm = 0);
 
 // ------------------------------------------------------ sparse Y update ---
 // Rows of 32 share one bucket of Delta entries: key = (row - 32 b) << 25 | col,
@@ -198,10 +204,13 @@ cudaError_t sparse_y_prepare();  // one-time shared-memory opt-in (before a grap
 // Dense fallback: planes (type pt) of Delta = Omega[nxt] - Omega[cur] when ctrl->dense.
 // A batch runs grid y over problem slots (active list or 0 .. nprob-1) with
 // Omega at + b * s_om and the planes at + b * s_pl.
-cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                void* hi, void* lo, int64_t ldk, int pt, cudaStream_t st,
-                                int32_t nprob = 1, const int32_t* active = nullptr, const int32_t* nactive = nullptr,
-                                int64_t s_om = 0, int64_t s_pl = 0, const int* any_dense = nullptr);
+// The buffers count only where their occupancy bitmaps (bm0, bm1; s_bm words
+// apart in a batch) have a bit.
+cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, const uint32_t* bm0,
+                                const uint32_t* bm1, int64_t p, int64_t ld, void* hi, void* lo, int64_t ldk, int pt,
+                                cudaStream_t st, int32_t nprob = 1, const int32_t* active = nullptr,
+                                const int32_t* nactive = nullptr, int64_t s_om = 0, int64_t s_pl = 0,
+                                const int* any_dense = nullptr, int64_t s_bm = 0);
 // X^T in FP32 (p x ldxt).
 cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 

@@ -163,6 +163,20 @@ __global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t p
   }
 }
 
+// Dense copy of a mixed-mode iterate buffer: its value where its occupancy
+// bitmap has a bit, 0 elsewhere (the buffer's other entries are not read).
+__global__ void copy_omega_masked_kernel(const float* __restrict__ src, int64_t lds, const uint32_t* __restrict__ bm,
+                                         int64_t ldbm, float* __restrict__ dst, int64_t ldd, int64_t p) {
+  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+    const float* s = src + r * lds;
+    float* d = dst + r * ldd;
+    for (int64_t c = threadIdx.x; c < p; c += blockDim.x) {
+      const uint32_t w = __ldg(bm + (c >> 5) * ldbm + r);
+      d[c] = ((w >> (c & 31)) & 1u) ? s[c] : 0.f;
+    }
+  }
+}
+
 template <class T>
 __global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
                                   int64_t ldd, int64_t p) {
@@ -787,29 +801,41 @@ __global__ void path_advance_kernel(PathDev pd) {
 }
 
 template <class T>
+// bm0 / bm1 (mixed modes): the occupancy bitmaps of the two buffers, whose
+// values count only where a bit is set; null in FP64 mode (dense buffers).
 __global__ void path_emit_kernel(PathDev pd, const T* __restrict__ om0, const T* __restrict__ om1, int64_t p,
                                  int64_t ldo, int64_t s_om, uint32_t* __restrict__ support, int64_t mask_ld,
-                                 T* __restrict__ best) {
+                                 T* __restrict__ best, const uint32_t* __restrict__ bm0, const uint32_t* __restrict__ bm1,
+                                 int64_t ldbm, int64_t s_bm) {
   const int c = blockIdx.y;
   const Ctrl& C = pd.ctrl[c];
   if (C.emit == 0) return;
   const T* Om = (C.cur ? om1 : om0) + c * s_om;
+  const uint32_t* bm = bm0 != nullptr ? (C.cur ? bm1 : bm0) + c * s_bm : nullptr;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
   if (support != nullptr) {
     uint32_t* out = support + ((int64_t)C.emit_lam * pd.nchains + c) * p * mask_ld;
     for (int64_t i = tid; i < p * mask_ld; i += stride) {
       const int64_t r = i / mask_ld, w = i % mask_ld;
       uint32_t bits = 0u;
-      for (int q = 0; q < 32; ++q) {
-        const int64_t col = 32 * w + q;
-        if (col < p && (col == r || Om[r * ldo + col] != T(0))) bits |= 1u << q;
+      if (bm != nullptr) {
+        bits = bm[w * ldbm + r];  // the diagonal bit is always set (omega_ii > 0)
+      } else {
+        for (int q = 0; q < 32; ++q) {
+          const int64_t col = 32 * w + q;
+          if (col < p && (col == r || Om[r * ldo + col] != T(0))) bits |= 1u << q;
+        }
       }
       out[i] = bits;
     }
   }
   if ((C.emit & 2) && best != nullptr) {
     T* dst = best + c * p * p;
-    for (int64_t i = tid; i < p * p; i += stride) dst[i] = Om[(i / p) * ldo + i % p];
+    for (int64_t i = tid; i < p * p; i += stride) {
+      const int64_t r = i / p, col = i % p;
+      const bool nz = bm == nullptr || ((bm[(col >> 5) * ldbm + r] >> (col & 31)) & 1u);
+      dst[i] = nz ? Om[r * ldo + col] : T(0);
+    }
   }
 }
 
@@ -877,6 +903,13 @@ cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uin
   const int64_t blocks = (nch * nch + 7) / 8;
   bitmap_from_dense_kernel<<<(unsigned)std::min<int64_t>(blocks, 152 * 32), 256, 0, st>>>(Om, p, ld, bm,
                                                                                            bitmap_ld(p));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_omega_masked(const float* src, int64_t lds, const uint32_t* bm, float* dst, int64_t ldd,
+                                     int64_t p, cudaStream_t st) {
+  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
+  copy_omega_masked_kernel<<<g, 512, 0, st>>>(src, lds, bm, bitmap_ld(p), dst, ldd, p);
   return cudaGetLastError();
 }
 
@@ -1021,15 +1054,15 @@ cudaError_t launch_path_advance(const PathDev& pd, cudaStream_t st) {
 
 cudaError_t launch_path_emit(const PathDev& pd, const void* om0, const void* om1, int is_f64, int64_t p,
                              int64_t ldo, int64_t s_om, uint32_t* support, int64_t mask_ld, void* omega_best,
-                             cudaStream_t st) {
+                             cudaStream_t st, const uint32_t* bm0, const uint32_t* bm1, int64_t s_bm) {
   if (pd.nchains < 1 || pd.nchains > 65535) return cudaErrorInvalidValue;
   const dim3 g(64, (unsigned)pd.nchains);
   if (is_f64)
     path_emit_kernel<double><<<g, 256, 0, st>>>(pd, (const double*)om0, (const double*)om1, p, ldo, s_om, support,
-                                                mask_ld, (double*)omega_best);
+                                                mask_ld, (double*)omega_best, nullptr, nullptr, 0, 0);
   else
     path_emit_kernel<float><<<g, 256, 0, st>>>(pd, (const float*)om0, (const float*)om1, p, ldo, s_om, support,
-                                               mask_ld, (float*)omega_best);
+                                               mask_ld, (float*)omega_best, bm0, bm1, bitmap_ld(p), s_bm);
   return cudaGetLastError();
 }
 

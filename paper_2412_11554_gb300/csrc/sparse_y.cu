@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
 }
 
 // Dense fallback when a bucket overflowed: planes (type pt) of Delta = Omega+ - Omega.
-__global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
+__global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, const uint32_t* bm0,
+                                    const uint32_t* bm1, int64_t ldbm, int64_t s_bm, int64_t p, int64_t ld,
                                     void* hi, void* lo, int64_t ldk, int pt, const int32_t* active,
                                     const int32_t* nactive, int64_t s_om, int64_t s_pl, const int* any_dense) {
   if (any_dense != nullptr && *any_dense == 0) return;
@@ -186,10 +187,16 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
   if (ctrl->done || !ctrl->dense || ctrl->ymode) return;
   const float* Om = (ctrl->cur ? om1 : om0) + b * s_om;
   const float* Op = (ctrl->cur ? om0 : om1) + b * s_om;
+  const uint32_t* Bm = (ctrl->cur ? bm1 : bm0) + b * s_bm;
+  const uint32_t* Bp = (ctrl->cur ? bm0 : bm1) + b * s_bm;
   const int64_t total = p * p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / p, c = i % p;
-    store_split(hi, lo, b * s_pl + r * ldk + c, Op[r * ld + c] - Om[r * ld + c], pt);
+    const int64_t wi = (c >> 5) * ldbm + r;
+    const uint32_t bit = 1u << (c & 31);
+    const float op = (Bp[wi] & bit) ? Op[r * ld + c] : 0.f;
+    const float om = (Bm[wi] & bit) ? Om[r * ld + c] : 0.f;
+    store_split(hi, lo, b * s_pl + r * ldk + c, op - om, pt);
   }
 }
 
@@ -225,15 +232,15 @@ cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, int64_t p, int64_t ld,
-                                void* hi, void* lo, int64_t ldk, int pt, cudaStream_t st, int32_t nprob,
-                                const int32_t* active, const int32_t* nactive, int64_t s_om, int64_t s_pl,
-                                const int* any_dense) {
+cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, const uint32_t* bm0,
+                                const uint32_t* bm1, int64_t p, int64_t ld, void* hi, void* lo, int64_t ldk, int pt,
+                                cudaStream_t st, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                int64_t s_om, int64_t s_pl, const int* any_dense, int64_t s_bm) {
   const unsigned nb = (unsigned)(nprob > 1 ? nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
   const unsigned gx = nb > 1 ? 152u * 16u / nb + 1u : 152u * 16u;
-  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, p, ld, hi, lo, ldk, pt, active, nactive, s_om,
-                                                    s_pl, any_dense);
+  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, bm0, bm1, bitmap_ld(p), s_bm, p, ld, hi, lo, ldk,
+                                                    pt, active, nactive, s_om, s_pl, any_dense);
   return cudaGetLastError();
 }
 

@@ -66,10 +66,11 @@ struct TcParams {
   int32_t ptype;         // plane type of the operands and plane outputs: kPlaneBf16 / kPlaneTf32
   // Occupancy bitmaps of the two iterate buffers (prox mode): word
   // [c * ldbm + i] has bit j - 32 c set iff Omega[i][j] != 0 for the 32
-  // columns j of chunk c; rows past p read as 0.  The prox epilogue fetches
-  // only the nonzero entries of Omega, stores Omega+ only where it is nonzero
-  // or where the buffer it overwrites was nonzero, and writes the new
-  // bitmap.  A batch keeps one pair per problem, s_bm words apart.
+  // columns j of chunk c; rows past p read as 0.  A buffer's values count
+  // only where its bitmap has a bit (elsewhere the entry is 0, whatever the
+  // buffer holds).  The prox epilogue fetches only the nonzero entries of
+  // Omega, stores only the nonzero entries of Omega+, and writes the whole
+  // bitmap of Omega+.  A batch keeps one pair per problem, s_bm words apart.
   uint32_t* bm[2];
   int64_t ldbm, s_bm;
   // Bounded waits: every mbarrier wait of the launch gives up after wait_ns

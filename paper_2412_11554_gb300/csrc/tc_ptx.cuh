@@ -133,6 +133,14 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
 __device__ __forceinline__ void st_f32_hint(float* ptr, float v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(ptr), "f"(v), "l"(pol) : "memory");
 }
+// Store under a predicate inside the instruction, so that a conditional
+// store costs no branch.
+__device__ __forceinline__ void st_f32_hint_if(float* ptr, float v, uint64_t pol, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p st.global.L2::cache_hint.f32 [%0], %1, %2;\n}\n" ::"l"(ptr),
+      "f"(v), "l"(pol), "r"((uint32_t)pred)
+      : "memory");
+}
 __device__ __forceinline__ void st_b16_hint(void* ptr, uint16_t v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(pol) : "memory");
 }
