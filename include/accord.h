@@ -99,7 +99,8 @@ typedef struct accord_opts {
     double  lipschitz;       /* > 0: use this L = sigma_max(S); 0: estimate it by Lanczos on
                                 X X^T / n (default 0)                                            */
     double  lipschitz_tol;   /* relative change of the Ritz value that ends Lanczos; 0 (default)
-                                = 1e-14 in FP64 mode, 1e-8 in the mixed modes                    */
+                                = 1e-14 in FP64 mode (FP64 process), 1e-6 in the mixed modes
+                                (FP32 process: there L only sets the tau <= 1/L floor)           */
     double  epbic_gamma;     /* gamma of the extended pseudo-BIC, Eq. 3.7 (default 0.5)         */
     void*   stream;          /* cudaStream_t for all work (default NULL)                        */
     double* trace;           /* optional HOST array, trace_cap x ACCORD_TRACE_FIELDS doubles    */

@@ -545,15 +545,16 @@ int fit_impl(const float* X32, const double* X64in, int64_t n, int64_t p, double
   if (!(L_given > 0.0)) {
     if (int e = setup_gram(P)) return e;
     // 0 = automatic: FP64 mode matches a dense eigensolver to rounding; the
-    // the mixed modes need L only to set the tau <= 1/L floor
-    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-8);
-    ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st));
+    // mixed modes need L only to set the tau <= 1/L floor, and run the
+    // process in FP32 on a Gram that carries FP32 accumulation error anyway
+    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-6);
+    ACCORD_CK(launch_lanczos_init(P.ctrl, at<double>(ws, L.lz_v), n, P.st, 1, 0, f64 ? 0 : 1));
     nlaunch += 2;
     const int chunk = 8;
     for (int steps = 0; steps < L.lz_k + chunk; steps += chunk) {
       ACCORD_CK(launch_lanczos_steps(P.ctrl, at<double>(ws, L.gram), n, at<double>(ws, L.lz_v),
                                      at<double>(ws, L.lz_w), at<double>(ws, L.lz_a), at<double>(ws, L.lz_b), n,
-                                     L.lz_k, chunk, lz_tol, P.st));
+                                     L.lz_k, chunk, lz_tol, P.st, 1, 0, 0, 0, 0, f64 ? 0 : 1));
       nlaunch += 2 * chunk;
       if (int e = read_ctrl(P, &hc)) return e;
       if (hc.power_done) break;

@@ -455,14 +455,15 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     gg.s_a = gg.s_b = K * L.ldo;
     gg.s_out = K * K;
     ACCORD_CK(launch_gemm_f64(kModeGram, gg, st));
-    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-8);
-    ACCORD_CK(launch_lanczos_init(ctrl, at<double>(ws, L.lz_v), K, st, (int)B, (int64_t)(L.lz_k + 1) * K));
+    const double lz_tol = o.lipschitz_tol > 0.0 ? o.lipschitz_tol : (f64 ? 1e-14 : 1e-6);
+    ACCORD_CK(launch_lanczos_init(ctrl, at<double>(ws, L.lz_v), K, st, (int)B, (int64_t)(L.lz_k + 1) * K,
+                                  f64 ? 0 : 1));
     nlaunch += 2;
     const int chunk = 8;
     for (int steps = 0; steps < L.lz_k + chunk; steps += chunk) {
       ACCORD_CK(launch_lanczos_steps(ctrl, at<double>(ws, L.gram), K, at<double>(ws, L.lz_v), at<double>(ws, L.lz_w),
                                      at<double>(ws, L.lz_a), at<double>(ws, L.lz_b), K, L.lz_k, chunk, lz_tol, st,
-                                     (int)B, K * K, (int64_t)(L.lz_k + 1) * K, K, L.lz_k));
+                                     (int)B, K * K, (int64_t)(L.lz_k + 1) * K, K, L.lz_k, f64 ? 0 : 1));
       nlaunch += 2 * chunk;
       ACCORD_CK(cudaMemcpyAsync(hctrl.data(), ctrl, B * sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       ACCORD_CK(cudaStreamSynchronize(st));

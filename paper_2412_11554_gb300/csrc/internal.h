@@ -95,10 +95,13 @@ cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, in
 constexpr int kLanczosMax = 128;
 // A batch of nprob problems (one Ctrl each) takes its slices of K, V, w and
 // alpha / beta at the given strides (doubles).
-cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st, int nprob = 1, int64_t sV = 0);
-cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
-                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st,
-                                 int nprob = 1, int64_t sK = 0, int64_t sV = 0, int64_t sW = 0, int64_t sAB = 0);
+// f32 = 1 runs the process in FP32 (V, w, alpha, beta are float arrays; the
+// mixed modes), else in FP64 (double arrays).  K is FP64 in both.
+cudaError_t launch_lanczos_init(Ctrl* ctrl, void* V, int64_t n, cudaStream_t st, int nprob = 1, int64_t sV = 0,
+                                int f32 = 0);
+cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, void* V, void* w, void* alpha, void* beta,
+                                 int64_t n, int kmax, int nsteps, double tol, cudaStream_t st, int nprob = 1,
+                                 int64_t sK = 0, int64_t sV = 0, int64_t sW = 0, int64_t sAB = 0, int f32 = 0);
 
 // Control kernels of the Algorithm 1 loop.
 cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, const double* ypart,

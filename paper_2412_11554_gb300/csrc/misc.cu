@@ -244,16 +244,29 @@ __global__ void split_planes_kernel(const float* __restrict__ src, int64_t rows,
 
 // Lanczos kernels serve one problem or a batch: problem b (block x of init
 // and step, block y of matvec) uses ctrl[b] and its slices of K, V, w, alpha
-// and beta at the strides in LzStrides.
+// and beta at the strides in LzStrides.  They run in FP64 (FP64 mode, where
+// L must match a dense eigensolver to rounding) or in FP32 (mixed modes,
+// where the Gram itself carries FP32 accumulation error and L only sets the
+// tau <= 1/L floor): FP64 is a slow pipe on this part, and the Sturm
+// multisection's divisions dominate an FP64 step.
 struct LzStrides {
   int64_t K, V, w, ab;
 };
 
-__global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n, LzStrides s) {
+template <class T> struct LzEps;
+template <> struct LzEps<double> {
+  static constexpr double section = 4e-16, breakdown = 1e-13, tiny = 1e-300, huge = 1e300;
+};
+template <> struct LzEps<float> {
+  static constexpr float section = 2e-7f, breakdown = 1e-6f, tiny = 1e-30f, huge = 1e30f;
+};
+
+template <class T>
+__global__ void lanczos_init_kernel(Ctrl* ctrl, T* V, int64_t n, LzStrides s) {
   const int b = blockIdx.x;
   ctrl += b;
   V += b * s.V;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = 1.0 / sqrt((double)n);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = T(1) / sqrt(T(n));
   if (threadIdx.x == 0) {
     ctrl->power_done = 0;
     ctrl->pw_iter = 0;
@@ -262,54 +275,59 @@ __global__ void lanczos_init_kernel(Ctrl* ctrl, double* V, int64_t n, LzStrides 
   }
 }
 
-// w = K V[j], one warp per row.
+// w = K V[j], one warp per row (K is the FP64 Gram in both precisions).
+template <class T>
 __global__ void lanczos_matvec_kernel(const Ctrl* ctrl, const double* __restrict__ K, int64_t ldk,
-                                      const double* __restrict__ V, double* __restrict__ w, int64_t n, LzStrides st) {
+                                      const T* __restrict__ V, T* __restrict__ w, int64_t n, LzStrides st) {
   const int b = blockIdx.y;
   ctrl += b;
   K += b * st.K;
   V += b * st.V;
   w += b * st.w;
   if (ctrl->power_done) return;
-  const double* v = V + (int64_t)ctrl->pw_iter * n;
+  const T* v = V + (int64_t)ctrl->pw_iter * n;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= n) return;
-  double s = 0.0;
-  for (int64_t c = lane; c < n; c += 32) s = fma(K[row * ldk + c], v[c], s);
-  s = warp_sum(s);
+  T s = T(0);
+  for (int64_t c = lane; c < n; c += 32) s = fma(T(K[row * ldk + c]), v[c], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) w[row] = s;
 }
 
-__device__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
+template <class T>
+__device__ T block_sum(T v, T* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   __syncthreads();
   if (lane == 0) sh[warp] = v;
   __syncthreads();
-  double t = 0.0;
+  T t = T(0);
   for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += sh[q];
   return t;
 }
 
 // number of eigenvalues of the m x m tridiagonal (a, b) below x
-__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+template <class T>
+__device__ int sturm_count(const T* a, const T* b, int m, T x) {
   int c = 0;
-  double d = a[0] - x;
-  if (d < 0.0) ++c;
+  T d = a[0] - x;
+  if (d < T(0)) ++c;
   for (int i = 1; i < m; ++i) {
-    const double dd = (d == 0.0) ? 1e-300 : d;
+    const T dd = (d == T(0)) ? LzEps<T>::tiny : d;
     d = a[i] - x - b[i - 1] * b[i - 1] / dd;
-    if (d < 0.0) ++c;
+    if (d < T(0)) ++c;
   }
   return c;
 }
 
 // One Lanczos step on w = K v_j (block of kLanczosThreads threads).
 constexpr int kLanczosThreads = 1024;
-__global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctrl, double* V, double* w,
-                                                                       double* alpha, double* beta, int64_t n,
-                                                                       int kmax, double tol, LzStrides st) {
+template <class T>
+__global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctrl, T* V, T* w, T* alpha, T* beta,
+                                                                       int64_t n, int kmax, double tol, LzStrides st) {
   {
     const int b = blockIdx.x;
     ctrl += b;
@@ -319,39 +337,40 @@ __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctr
     beta += b * st.ab;
   }
   if (ctrl->power_done) return;
-  __shared__ double sh[kLanczosThreads / 32];
-  __shared__ double h[256];
-  __shared__ double lohi[2];
+  __shared__ T sh[kLanczosThreads / 32];
+  __shared__ T h[256];
+  __shared__ T lohi[2];
   const int j = ctrl->pw_iter;
-  const double* vj = V + (int64_t)j * n;
-  double a = 0.0;
+  const T* vj = V + (int64_t)j * n;
+  T a = T(0);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a = fma(vj[i], w[i], a);
   a = block_sum(a, sh);
-  const double bprev = j > 0 ? beta[j - 1] : 0.0;
+  const T bprev = j > 0 ? beta[j - 1] : T(0);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-    w[i] -= a * vj[i] + (j > 0 ? bprev * V[(int64_t)(j - 1) * n + i] : 0.0);
+    w[i] -= a * vj[i] + (j > 0 ? bprev * V[(int64_t)(j - 1) * n + i] : T(0));
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   for (int pass = 0; pass < 2; ++pass) {  // w -= V_{0..j} (V_{0..j}^T w), twice
     for (int q = warp; q <= j; q += nw) {
-      const double* vq = V + (int64_t)q * n;
-      double s = 0.0;
+      const T* vq = V + (int64_t)q * n;
+      T s = T(0);
       for (int64_t i = lane; i < n; i += 32) s = fma(vq[i], w[i], s);
-      s = warp_sum(s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) h[q] = s;
     }
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      double s = 0.0;
+      T s = T(0);
       for (int q = 0; q <= j; ++q) s = fma(h[q], V[(int64_t)q * n + i], s);
       w[i] -= s;
     }
     if (threadIdx.x == 0) a += h[j];
     __syncthreads();
   }
-  double bb = 0.0;
+  T bb = T(0);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) bb = fma(w[i], w[i], bb);
-  const double b = sqrt(block_sum(bb, sh));
+  const T b = sqrt(block_sum(bb, sh));
   if (threadIdx.x == 0) {
     alpha[j] = a;
     beta[j] = b;
@@ -360,9 +379,9 @@ __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctr
   // largest eigenvalue of T_{j+1} by multisection (warp 0: 32 probes a round)
   const int m = j + 1;
   if (warp == 0) {
-    double lo = 1e300, hi = -1e300;
+    T lo = LzEps<T>::huge, hi = -LzEps<T>::huge;
     for (int i = lane; i < m; i += 32) {
-      const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(beta[i]) : 0.0);
+      const T r = (i > 0 ? fabs(beta[i - 1]) : T(0)) + (i + 1 < m ? fabs(beta[i]) : T(0));
       lo = fmin(lo, alpha[i] - r);
       hi = fmax(hi, alpha[i] + r);
     }
@@ -371,13 +390,13 @@ __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctr
       lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
       hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    for (int round = 0; round < 16 && hi - lo > 4e-16 * fmax(fabs(hi), 1e-300); ++round) {
-      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    for (int round = 0; round < 16 && hi - lo > LzEps<T>::section * fmax(fabs(hi), LzEps<T>::tiny); ++round) {
+      const T x = lo + (hi - lo) * T(lane + 1) / T(33);
       const bool above = sturm_count(alpha, beta, m, x) == m;  // lambda_max < x
       const unsigned mask = __ballot_sync(0xffffffffu, above);
       const int first = mask ? __ffs(mask) - 1 : 32;  // lowest probe above lambda_max
-      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / 33.0;
-      const double nhi = first == 32 ? hi : lo + (hi - lo) * (double)(first + 1) / 33.0;
+      const T nlo = first == 0 ? lo : lo + (hi - lo) * T(first) / T(33);
+      const T nhi = first == 32 ? hi : lo + (hi - lo) * T(first + 1) / T(33);
       lo = nlo;
       hi = nhi;
     }
@@ -387,9 +406,9 @@ __global__ void __launch_bounds__(kLanczosThreads) lanczos_step_kernel(Ctrl* ctr
     }
   }
   __syncthreads();
-  const double theta = 0.5 * (lohi[0] + lohi[1]);
-  const bool stop = (b <= 1e-13 * fmax(fabs(theta), 1e-300)) || (m >= kmax) || (m >= n) ||
-                    (j >= 3 && fabs(theta - ctrl->pw_est) <= tol * theta);
+  const double theta = 0.5 * ((double)lohi[0] + (double)lohi[1]);
+  const bool stop = ((double)b <= (double)LzEps<T>::breakdown * fmax(fabs(theta), 1e-300)) || (m >= kmax) ||
+                    (m >= n) || (j >= 3 && fabs(theta - ctrl->pw_est) <= tol * theta);
   if (!stop)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)(j + 1) * n + i] = w[i] / b;
   __syncthreads();
@@ -936,21 +955,31 @@ cudaError_t launch_split_planes(const float* src, int64_t rows, int64_t cols, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_init(Ctrl* ctrl, double* V, int64_t n, cudaStream_t st, int nprob, int64_t sV) {
+cudaError_t launch_lanczos_init(Ctrl* ctrl, void* V, int64_t n, cudaStream_t st, int nprob, int64_t sV, int f32) {
   if (nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
-  lanczos_init_kernel<<<(unsigned)nprob, 256, 0, st>>>(ctrl, V, n, LzStrides{0, sV, 0, 0});
+  if (f32) lanczos_init_kernel<float><<<(unsigned)nprob, 256, 0, st>>>(ctrl, (float*)V, n, LzStrides{0, sV, 0, 0});
+  else lanczos_init_kernel<double><<<(unsigned)nprob, 256, 0, st>>>(ctrl, (double*)V, n, LzStrides{0, sV, 0, 0});
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, double* V, double* w, double* alpha,
-                                 double* beta, int64_t n, int kmax, int nsteps, double tol, cudaStream_t st,
-                                 int nprob, int64_t sK, int64_t sV, int64_t sW, int64_t sAB) {
+cudaError_t launch_lanczos_steps(Ctrl* ctrl, const double* K, int64_t ldk, void* V, void* w, void* alpha, void* beta,
+                                 int64_t n, int kmax, int nsteps, double tol, cudaStream_t st, int nprob, int64_t sK,
+                                 int64_t sV, int64_t sW, int64_t sAB, int f32) {
   if (kmax > 256 || nprob < 1 || nprob > 65535) return cudaErrorInvalidValue;
   const LzStrides s{sK, sV, sW, sAB};
   const dim3 g((unsigned)((n + 7) / 8), (unsigned)nprob);
   for (int q = 0; q < nsteps; ++q) {
-    lanczos_matvec_kernel<<<g, 256, 0, st>>>(ctrl, K, ldk, V, w, n, s);
-    lanczos_step_kernel<<<(unsigned)nprob, kLanczosThreads, 0, st>>>(ctrl, V, w, alpha, beta, n, kmax, tol, s);
+    if (f32) {
+      lanczos_matvec_kernel<float><<<g, 256, 0, st>>>(ctrl, K, ldk, (const float*)V, (float*)w, n, s);
+      lanczos_step_kernel<float><<<(unsigned)nprob, kLanczosThreads, 0, st>>>(ctrl, (float*)V, (float*)w,
+                                                                              (float*)alpha, (float*)beta, n, kmax,
+                                                                              tol, s);
+    } else {
+      lanczos_matvec_kernel<double><<<g, 256, 0, st>>>(ctrl, K, ldk, (const double*)V, (double*)w, n, s);
+      lanczos_step_kernel<double><<<(unsigned)nprob, kLanczosThreads, 0, st>>>(ctrl, (double*)V, (double*)w,
+                                                                               (double*)alpha, (double*)beta, n, kmax,
+                                                                               tol, s);
+    }
   }
   return cudaGetLastError();
 }

@@ -15,9 +15,11 @@ import bench  # noqa: E402
 
 def test_committed_traffic_matches_the_kernel_code():
     """profiles/traffic.json was captured from the prox kernel as it is now,
-    so bench.py reports its DRAM traffic instead of null."""
+    so bench.py reports its DRAM traffic instead of null.  A launch reads the
+    occupancy bitmap of Omega and writes that of Omega+ (p^2 / 8 bytes each)
+    at the least."""
     t = bench.profiled_traffic("tc_gemm_prox", bench.kernel_digest())
-    assert t is not None and t > 8 * 40000 ** 2  # at least Omega in and Omega+ out
+    assert t is not None and t > 40000 ** 2 / 4
 
 
 def test_digest_ignores_comments_and_blank_space():
