@@ -50,6 +50,8 @@ def parse(argv=None):
     ap.add_argument("--fp64-full", action="store_true",
                     help="also run one whole FP64 fit to the same KKT tolerance (several minutes at p=40000), "
                          "timed, and grade the mixed estimate against it (rel. Frobenius, support, FP64 KKT)")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="path: skip the baseline of the same fits made one accord_fit call at a time")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -267,6 +269,7 @@ def run_ours(args):
     ty = sum(s.t_y_gemm_ms for s in stats)
     npx = sum(s.n_prox_gemm for s in stats)
     ny = sum(s.n_y_gemm for s in stats)
+    nco = sum(s.coarse_prox for s in stats)
     flops = 2.0 * n * p * p
     pk, pk_src = peaks()
     peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
@@ -279,7 +282,9 @@ def run_ours(args):
                 "peak_source": f"bf16_tflops_sustained ({pk_src})",
                 "traffic": profiled_traffic(dominant, digest),
                 "algorithmic_flops_per_launch": flops,
-                "executed_frac": round(3 * achieved / peak, 4),
+                # executed: three split products a launch, one in the coarse launches
+                "executed_frac": round((3 * (npx - nco) + nco) / max(npx, 1) * achieved / peak, 4),
+                "coarse_launches_per_fit": nco / max(len(stats), 1),
                 "avg_launch_ms": {"tc_gemm_prox": round(tp / max(npx, 1), 3), "y_update": round(ty / max(ny, 1), 3)},
                 "gemm_share_of_step": round((tp + ty) / ms, 3)}
 
@@ -424,16 +429,19 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate, fp64 reductions)",
             "data": "synthetic (seeded hub-and-block precision, Gaussian X)",
             "config": {"workload": w.name, "p": p, "n": n, "lambda": w.lam, "kkt_tol": args.kkt_tol,
-                       "precision": "mixed_bf16x3", "tau0": 1.0, "beta": 0.5,
+                       "precision": "mixed_bf16x3", "coarse_kkt": 5e-3, "y_refresh": 32, "tau0": 1.0, "beta": 0.5,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2 (Omega {4 * p * p / 1e9:.1f} GB per buffer)"},
             "time_to_kkt_s": round(ms / max(args.steps, 1) / 1e3, 3),
             "fit_ms": {"median": round(fit_ms[len(fit_ms) // 2], 2), "best": round(fit_ms[0], 2)} if fit_ms else None,
             "iters_per_fit": mean_iters, "trials_per_fit": sum(s.trials for s in stats) / max(len(stats), 1),
+            "prox_launches_per_fit": sum(s.n_prox_gemm for s in stats) / max(len(stats), 1),
             "solve_iters_per_s": round(iters / (sum(s.t_solve_ms for s in stats) / 1e3), 3),
             "setup_ms": round(sum(s.t_setup_ms for s in stats) / max(len(stats), 1), 2),
             "final_kkt": stats[-1].kkt if stats else None, "status": stats[-1].status if stats else None,
             "gpu_launches": int(sum(s.n_launches for s in stats)),
+            "y_refresh": {"refreshes_per_fit": sum(s.y_refreshes for s in stats) / max(len(stats), 1),
+                          "max_drift": max((s.y_drift for s in stats), default=0.0)},
             "roofline": roofline, "e2e": e2e, "e2e_dense_omega": e2e_dense, "fp64_gpu": fp64, "tf32x3_gpu": tf32,
             "fp64_full": fp64_full,
             "cpu_baseline": cpu,
@@ -565,6 +573,41 @@ def oracle_trial_seconds(Xs, lam, rows):
     return oracle_sample(np.asarray(Xs, dtype=np.float64), lam, rows)
 
 
+def sequential_fits(A, X, pw, kw, stream):
+    """The path's 512 problems solved one accord_fit call at a time: along
+    each subsample's chain, every penalty warm-started from the previous
+    estimate, on the same data matrix the path uses (the distinct rows, row j
+    scaled by sqrt(K c_j / n_s): the subsample's S), one workspace for all."""
+    import torch
+    p = X.shape[1]
+    mats = []
+    for s in pw.subsamples:
+        u, c = np.unique(np.asarray(s), return_counts=True)
+        scale = np.sqrt(len(u) * c / float(len(s)))
+        idx = torch.as_tensor(u, device="cuda")
+        mats.append((X.index_select(0, idx) * torch.as_tensor(scale, dtype=torch.float32, device="cuda")[:, None])
+                    .contiguous())
+    kmax = max(m.shape[0] for m in mats)
+    ws = torch.empty(A.accord_workspace_bytes(kmax, p, **kw), dtype=torch.uint8, device="cuda")
+    O = torch.empty((p, p), dtype=torch.float32, device="cuda")
+    iters = trials = 0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for m in mats:
+        for k, lam in enumerate(pw.lambdas):
+            _, st = A.accord_fit(m, float(lam), Omega=O, init_from_omega=k > 0, workspace=ws, **kw)
+            iters += st.iters
+            trials += st.trials
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nfit = len(mats) * len(pw.lambdas)
+    return {"value": round(nfit / (ms / 1e3), 3), "unit": PATH_UNIT, "ms": round(ms, 1), "fits": nfit,
+            "iters_total": iters, "trials_total": trials,
+            "note": "one pass, the same problems and warm starts, one accord_fit call each"}
+
+
 def run_path(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -621,6 +664,16 @@ def run_path(args):
                 "tensor_tflops_algorithmic": round(flops_alg / prox_s / 1e12, 1),
                 "prox_share_of_path": round(rp.stats.t_prox_gemm_ms / max(rp.stats.t_solve_ms, 1e-9), 3)}
 
+    # launch cost of the captured trial graph: one replay after every chain
+    # has finished (each kernel returns at once), times the replays of a path
+    replays = int(r0.stats.n_prox_gemm) // 8
+    graph = {"idle_replay_ms": round(r0.stats.t_graph_idle_ms, 4), "replays": replays,
+             "launch_share_of_path": round(r0.stats.t_graph_idle_ms * replays / max(r0.stats.t_solve_ms, 1e-9), 4)}
+
+    seq = None
+    if not args.no_sequential and rank == 0:
+        seq = sequential_fits(A, X, pw, kw, stream)
+
     e2e = None
     if not args.no_e2e:
         Xh = torch.as_tensor(pw.X).pin_memory()
@@ -662,13 +715,15 @@ def run_path(args):
                           "subsample_rows": [len(s) for s in pw.subsamples], "distinct_rows": K.astype(int).tolist(),
                           "lambda_range": [float(pw.lambdas[0]), float(pw.lambdas[-1])], "kkt_tol": pw.kkt_tol,
                           "precision": "mixed_bf16x3", "parallelism": "batched chains, CUDA graph",
-                          "autotuned_prox_tiles": {"tile": "128x256", "group_m": int(r0.stats.tile_group_m),
+                          "autotuned_prox_tiles": {"tile": "256x256 per CTA pair", "group_m": int(r0.stats.tile_group_m),
                                                    "pairs": int(r0.stats.tile_pairs)},
                           "l2": "inputs larger than L2 (16 chains x 64 MB Omega per buffer)"},
                "status": int(r0.status), "estimates_not_converged": int(np.sum(r0.entry_status == 1)),
                "prox_evaluations": int(evals.sum()), "iters_total": int(r0.stats.iters),
                "setup_ms": round(r0.stats.t_setup_ms, 2), "solve_ms": round(r0.stats.t_solve_ms, 2),
                "gpu_launches": int(r0.stats.n_launches), "best_index": r0.best_index.tolist(),
+               "y_refresh": {"refreshes": int(r0.stats.y_refreshes), "max_drift": r0.stats.y_drift},
+               "graph": graph, "sequential_fits": seq,
                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(out))
 

@@ -105,13 +105,30 @@ typedef struct accord_opts {
     void*   stream;          /* cudaStream_t for all work (default NULL)                        */
     double* trace;           /* optional HOST array, trace_cap x ACCORD_TRACE_FIELDS doubles    */
     int64_t trace_cap;       /* rows available in trace (rows beyond are dropped)               */
+    int32_t y_refresh;       /* mixed modes: Y = Omega X^T is carried from step to step as
+                                Y + Delta X^T in FP32, which accumulates rounding; every
+                                y_refresh accepted steps (default 32), ahead of a step whose KKT
+                                test the last ratio of residuals predicts to pass, and before a
+                                KKT residual under kkt_tol may end a fit (that trial is then cut
+                                short), Y is formed afresh from the iterate.  0: never (the
+                                residual test then uses the carried Y).  Ignored in FP64 mode,
+                                where every trial forms Y+ = Omega+ X^T.                        */
+    int32_t reserved1;
+    double  coarse_kkt;      /* mixed modes: while the KKT residual is above this (default 5e-3),
+                                the prox GEMM forms G with the one product hi x hi instead of the
+                                three split products (G then carries the error of one BF16 or TF32
+                                product, about 1e-4 of |G| at n = 1000); the first residual under it
+                                switches to the three products for the rest of the fit (and a
+                                path's penalty), and no fit ends on a one-product residual.
+                                0: three products throughout.  Ignored in FP64 mode.           */
 } accord_opts;
 
 typedef struct accord_stats {
     int32_t iters;           /* accepted steps taken                                            */
-    int32_t trials;          /* prox evaluations (accepted + rejected)                           */
+    int32_t trials;          /* prox evaluations (accepted + rejected; a trial whose KKT test
+                                asked for a refresh of Y is not one)                             */
     int32_t status;          /* same value as the call's return                                  */
-    int32_t reserved0;
+    int32_t y_refreshes;     /* mixed modes: times Y was formed afresh (opts->y_refresh)         */
     double  f;               /* objective of the returned Omega (Eq. 3.2)                        */
     double  g;               /* its smooth part g = 1/2 tr(Omega^T Omega S)                      */
     double  kkt;             /* its KKT residual                                                 */
@@ -120,7 +137,8 @@ typedef struct accord_stats {
     int64_t nnz_offdiag;     /* off-diagonal nonzeros of the returned Omega                     */
     double  t_setup_ms;      /* device time: conversions, L estimate, Omega^0, Y^0              */
     double  t_solve_ms;      /* device time: the iteration loop and the copy-out                 */
-    int32_t n_prox_gemm;     /* prox GEMM launches that did work (trials + final KKT check)     */
+    int32_t n_prox_gemm;     /* prox GEMM launches that did work (trials, trials cut short by a
+                                refresh of Y, and the final KKT check)                           */
     int32_t n_y_gemm;        /* Y GEMM launches that did work (one per trial)                    */
     double  t_prox_gemm_ms;  /* their summed device time when opts->profile, else 0              */
     double  t_y_gemm_ms;
@@ -133,6 +151,16 @@ typedef struct accord_stats {
     int32_t tile_pairs;      /* ... and its persistent grid in CTA pairs (2 SMs each)            */
     int64_t delta_entries;   /* mixed modes, single fit: nonzero Delta entries the sparse Y
                                 update applied, summed over the trials (0 elsewhere)             */
+    double  y_drift;         /* mixed modes: the largest ||Y - Omega X^T||_F / ||Omega X^T||_F
+                                that a refresh of Y found (the rounding the carried Y had
+                                gathered since the one before); accord_path: the largest over
+                                every chain and penalty.  0 in FP64 mode.                        */
+    double  t_graph_idle_ms; /* accord_path: device time of one replay of its captured trial
+                                graph after every chain has finished, when each of its kernels
+                                returns at once: what launching a replay costs (0 elsewhere)     */
+    int32_t coarse_prox;     /* mixed modes: prox launches that formed G with one product
+                                (opts->coarse_kkt); accord_path: summed over the chains          */
+    int32_t reserved2;
 } accord_stats;
 
 /* Fills *opts with the defaults listed above. */
@@ -256,6 +284,49 @@ int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double*
  * than 0 / 1.  Not for production use: a short limit can end correct work. */
 int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox);
 
+/* Row blocks of one fit.  The objective of Eq. 3.2 separates over the rows
+ * of Omega (the row-wise form in the proof of Thm 3.2), as the paper's
+ * distributed solver uses when it spreads Omega over nodes by rows (Sec 3.3):
+ * a fit can be split into blocks of rows that keep X whole and share only
+ * the scalars of Algorithm 1.  Each block calls accord_fit_rows (on its own
+ * GPU, or its own stream); once per trial every block passes its sums to
+ * `exchange`, which must return the sums over all blocks of the partition,
+ * so that every block takes the same decisions and the blocks together
+ * follow the iterate sequence of one accord_fit.
+ *
+ *   exchange(sums, 9, maxes, 1, ctx): on entry this block's values; on
+ *            return, element by element, the sums (sums) and the maxima
+ *            (maxes) over all blocks.  sums: ||Delta||_F^2, sum log
+ *            omega+_ii, sum omega+_ii, sum |omega+_ij| off the diagonal,
+ *            off-diagonal nonzeros, non-finite count, ||Delta X^T||_F^2,
+ *            ||Y+||_F^2, non-finite count of Y+; maxes: the KKT residual of
+ *            Eq. 3.3.  It is called once before the first trial (the sums
+ *            of Omega^0 and Y^0 = Omega^0 X^T, the KKT maximum 0) and once
+ *            per trial, the same number of times in every block; a nonzero
+ *            return ends the fit with ACCORD_ECUDA.  It runs on the calling
+ *            thread, which waits for it.
+ *   X        device, n x p row-major FP32, the whole data matrix on every
+ *            block.
+ *   row0, rows  this block holds rows row0 .. row0 + rows - 1 of Omega;
+ *            row0 must be a multiple of 32 (the diagonal then crosses whole
+ *            32 x 32 blocks of the kernels), rows >= 1, row0 + rows <= p.
+ *   Omega_rows  device, rows x p row-major (FP32 in the mixed modes, FP64 in
+ *            FP64 mode): the block's rows of Omega-hat on return, its rows of
+ *            the starting iterate on entry when opts->init_from_omega.
+ *   opts, lambda, n, p: the same in every block (the stream and workspace
+ *            may differ).  The support-restricted refit is not offered here.
+ *   out      the stats of the whole fit: f, g, the KKT residual, nnz and the
+ *            counts are global and the same in every block.
+ * Returns as accord_fit; ACCORD_EINVAL for a bad row range or a null
+ * exchange.  One fit of the whole matrix is the case row0 = 0, rows = p. */
+typedef int (*accord_exchange_fn)(double* sums, int32_t nsums, double* maxes, int32_t nmaxes, void* ctx);
+int accord_fit_rows(const float* X, int64_t n, int64_t p, int64_t row0, int64_t rows, double lambda,
+                    const accord_opts* opts, accord_exchange_fn exchange, void* ctx, void* Omega_rows,
+                    void* workspace, size_t ws_bytes, accord_stats* out);
+/* Device workspace, in bytes, of accord_fit_rows for a block of `rows` rows
+ * (0 for invalid sizes). */
+size_t accord_fit_rows_workspace_bytes(int64_t n, int64_t p, int64_t rows, const accord_opts* opts);
+
 /* Description of the first failure of the calling thread's most recent call
  * of an entry point that queues GPU work (fit, refit, path, loss, gradients,
  * derivative, post-processing, CSR export; "" when it succeeded): the
@@ -324,9 +395,11 @@ int accord_grad_x(const float* X, int64_t n, int64_t p, const void* Omega, const
  *   dOmega    device or NULL: p x p dOmega-hat / dlog(lambda), element type per precision
  * FP64 mode forms S and the held-out products with FP64 GEMMs; the mixed modes
  * use their split-operand tensor-core products (FP32 accumulation, S written
- * in FP64, FP64 reductions).  The row systems are FP64 in all modes.
+ * in FP64, FP64 reductions).  The row systems are FP64 in all modes: one
+ * CTA a row in shared memory up to 128 active entries, larger ones in a
+ * second pass with the system in the workspace (up to 1024 entries).
  * Errors: EINVAL; EUNSUPPORTED when a row's active set has more
- * than 128 entries; EDOMAIN when a row system is not positive definite (an
+ * than 1024 entries; EDOMAIN when a row system is not positive definite (an
  * active set larger than the training rows can support) or Omega_hat has a
  * non-positive diagonal. */
 int accord_dloss_dloglam(const float* X_train, int64_t n, const float* X_val, int64_t n_val, int64_t p,
@@ -342,7 +415,7 @@ typedef struct {
                                 ends the chain (its later records carry the same status)   */
     int32_t iters;           /* accepted steps at this penalty                              */
     int32_t trials;          /* prox evaluations at this penalty                            */
-    int32_t reserved0;
+    int32_t y_refreshes;     /* mixed modes: refreshes of Y at this penalty                 */
     double  lambda;          /* the penalty                                                 */
     double  f, g, kkt;       /* objective (Eq. 3.2), smooth part, KKT residual (Eq. 3.3)    */
     double  logdet_d;        /* sum_i log omega_ii                                          */
@@ -350,6 +423,8 @@ typedef struct {
                                 opts->epbic_gamma (+inf after an error)                     */
     double  tau_last;        /* last accepted step                                          */
     int64_t nnz_offdiag;     /* ||Omega||_0 off the diagonal                                */
+    double  y_drift;         /* mixed modes: the largest relative drift of Y a refresh found
+                                at this penalty (accord_stats.y_drift)                      */
 } accord_path_entry;
 
 /* Tuning by epBIC over a penalty grid (Sec 3.4) on subsamples of one data set.

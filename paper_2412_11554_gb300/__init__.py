@@ -9,6 +9,8 @@ from .accord import (  # noqa: F401
     accord_default_opts,
     accord_device_check,
     accord_fit,
+    accord_fit_rows,
+    accord_fit_rows_workspace_bytes,
     accord_grad_x,
     accord_postprocess,
     accord_to_csr,
@@ -24,6 +26,7 @@ from .accord import (  # noqa: F401
     accord_status_string,
     accord_test_wait_limit,
     accord_workspace_bytes,
+    dist_exchange,
     load_library,
 )
 from .autograd import SmoothLoss, smooth_loss  # noqa: F401,E402

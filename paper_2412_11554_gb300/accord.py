@@ -35,34 +35,43 @@ class AccordOpts(ctypes.Structure):
         ("lipschitz", ctypes.c_double), ("lipschitz_tol", ctypes.c_double), ("epbic_gamma", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int64),
+        ("y_refresh", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("coarse_kkt", ctypes.c_double),
     ]
 
 
 class AccordStats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int32), ("trials", ctypes.c_int32), ("status", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("f", ctypes.c_double), ("g", ctypes.c_double), ("kkt", ctypes.c_double),
+        ("y_refreshes", ctypes.c_int32), ("f", ctypes.c_double), ("g", ctypes.c_double), ("kkt", ctypes.c_double),
         ("tau_last", ctypes.c_double), ("L", ctypes.c_double), ("nnz_offdiag", ctypes.c_int64),
         ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("n_prox_gemm", ctypes.c_int32),
         ("n_y_gemm", ctypes.c_int32), ("t_prox_gemm_ms", ctypes.c_double), ("t_y_gemm_ms", ctypes.c_double),
         ("n_launches", ctypes.c_int64), ("logdet_d", ctypes.c_double), ("epbic", ctypes.c_double),
         ("tile_group_m", ctypes.c_int32), ("tile_pairs", ctypes.c_int32), ("delta_entries", ctypes.c_int64),
+        ("y_drift", ctypes.c_double), ("t_graph_idle_ms", ctypes.c_double),
+        ("coarse_prox", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
 class AccordPathEntry(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("trials", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("lambda_", ctypes.c_double), ("f", ctypes.c_double),
+        ("y_refreshes", ctypes.c_int32), ("lambda_", ctypes.c_double), ("f", ctypes.c_double),
         ("g", ctypes.c_double), ("kkt", ctypes.c_double), ("logdet_d", ctypes.c_double),
         ("epbic", ctypes.c_double), ("tau_last", ctypes.c_double), ("nnz_offdiag", ctypes.c_int64),
+        ("y_drift", ctypes.c_double),
     ]
 
 
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
-           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_test_wait_limit")
+           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_test_wait_limit",
+           "accord_fit_rows", "accord_fit_rows_workspace_bytes")
+
+# exchange(sums, nsums, maxes, nmaxes, ctx) of accord_fit_rows
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_void_p)
 
 _lib = None
 
@@ -102,6 +111,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_loss_f64_noalloc.argtypes = [P, i64, i64, P, dbl, i32, P, P]
     lib.accord_test_wait_limit.restype = i32
     lib.accord_test_wait_limit.argtypes = [i64, i32]
+    lib.accord_fit_rows.argtypes = [P, i64, i64, i64, i64, dbl, opts_p, EXCHANGE_FN, P, P, P, ctypes.c_size_t, stats_p]
+    lib.accord_fit_rows.restype = i32
+    lib.accord_fit_rows_workspace_bytes.argtypes = [i64, i64, i64, opts_p]
+    lib.accord_fit_rows_workspace_bytes.restype = ctypes.c_size_t
     lib.accord_loss_f64_noalloc.restype = i32
     lib.accord_path.argtypes = [P, i64, i64, P, P, i64, P, i64, opts_p, ctypes.POINTER(AccordPathEntry), P, P, P, P,
                                 ctypes.c_size_t, stats_p]
@@ -155,6 +168,10 @@ class FitStats:
     tile_group_m: int = 0
     tile_pairs: int = 0
     delta_entries: int = 0
+    y_refreshes: int = 0
+    y_drift: float = 0.0
+    t_graph_idle_ms: float = 0.0
+    coarse_prox: int = 0
 
 
 def _stream_handle(stream) -> int | None:
@@ -290,12 +307,103 @@ def accord_fit(X: torch.Tensor, lam: float, *, precision: str = "mixed", Omega: 
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms,
                      st.t_y_gemm_ms, st.n_launches, st.logdet_d, st.epbic, None,
-                     delta_entries=st.delta_entries)
+                     delta_entries=st.delta_entries, y_refreshes=st.y_refreshes, y_drift=st.y_drift,
+                     coarse_prox=st.coarse_prox)
     if tr is not None:
         stats.trace = tr[: st.iters + 1].copy()
     if check and status < 0:
         raise AccordError(status, "accord_fit")
     return Omega, stats
+
+
+def accord_fit_rows(X: torch.Tensor, lam: float, row0: int, rows: int, exchange, *, precision: str = "mixed",
+                    Omega: torch.Tensor | None = None, init_from_omega: bool = False,
+                    workspace: torch.Tensor | None = None, trace: bool = False, stream=None, check: bool = True,
+                    **opts) -> tuple[torch.Tensor, FitStats]:
+    """Fit rows row0 .. row0 + rows - 1 of Omega-hat as one block of a fit
+    split by rows (include/accord.h, accord_fit_rows).  exchange(sums, maxes)
+    receives this block's 9 sums and 1 maximum as float64 numpy arrays and
+    must overwrite them, in place, with the sums and maxima over all blocks;
+    it is called once before the first trial and once per trial, the same
+    number of times in every block.  Returns the block's rows (rows x p) and
+    the stats of the whole fit."""
+    lib = load_library()
+    prec = PRECISIONS[precision]
+    _check_x(X, torch.float32)
+    n, p = X.shape
+    odt = _omega_dtype(prec)
+    ws_ptr, ws_bytes = _check_workspace(workspace)
+    if Omega is None:
+        if init_from_omega:
+            raise ValueError("init_from_omega needs Omega")
+        Omega = torch.empty((int(rows), p), dtype=odt, device=X.device)
+    else:
+        _check_tensor(Omega, "Omega", odt, (int(rows), p))
+    o = accord_default_opts(precision=prec, init_from_omega=int(init_from_omega), **opts)
+    o.stream = _stream_handle(stream)
+    tr = None
+    if trace:
+        tr = np.full((o.max_iter + 2, TRACE_FIELDS), np.nan)
+        o.trace = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.trace_cap = tr.shape[0]
+    failure = []
+
+    def _cb(sums_p, nsums, maxes_p, nmaxes, _ctx):
+        try:
+            sums = np.ctypeslib.as_array(sums_p, shape=(nsums,))
+            maxes = np.ctypeslib.as_array(maxes_p, shape=(nmaxes,))
+            exchange(sums, maxes)
+            return 0
+        except Exception as e:  # no Python exception may cross the C boundary
+            failure.append(e)
+            return 1
+
+    cb = EXCHANGE_FN(_cb)
+    st = AccordStats()
+    status = lib.accord_fit_rows(X.data_ptr(), n, p, int(row0), int(rows), float(lam), ctypes.byref(o), cb, None,
+                                 Omega.data_ptr(), ws_ptr, ws_bytes, ctypes.byref(st))
+    stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
+                     st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms,
+                     st.t_y_gemm_ms, st.n_launches, st.logdet_d, st.epbic, None,
+                     delta_entries=st.delta_entries, y_refreshes=st.y_refreshes, y_drift=st.y_drift,
+                     coarse_prox=st.coarse_prox)
+    if tr is not None:
+        stats.trace = tr[: st.iters + 1].copy()
+    if failure:
+        raise failure[0]
+    if check and status < 0:
+        raise AccordError(status, "accord_fit_rows")
+    return Omega, stats
+
+
+def accord_fit_rows_workspace_bytes(n: int, p: int, rows: int, **kw) -> int:
+    return int(load_library().accord_fit_rows_workspace_bytes(n, p, rows, ctypes.byref(accord_default_opts(**kw))))
+
+
+def dist_exchange(group=None):
+    """An exchange for accord_fit_rows between the ranks of a torch.distributed
+    process group whose backend takes host tensors (gloo), one row block per
+    rank.  Each call all-gathers every rank's 9 sums and 1 maximum; every rank
+    then adds the sums in rank order and takes the maxima, so all ranks hold
+    the same bits and take the same accept / stop decisions.  A collective
+    that fails (a rank that left, the group's timeout) raises here, and
+    accord_fit_rows then ends the fit and re-raises it."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+
+    def exchange(sums: np.ndarray, maxes: np.ndarray) -> None:
+        mine = torch.from_numpy(np.concatenate([sums, maxes]))
+        parts = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(parts, mine, group=group)
+        allv = torch.stack(parts).numpy()
+        ns = sums.shape[0]
+        tot = allv[0, :ns].copy()
+        for r in range(1, world):
+            tot += allv[r, :ns]
+        sums[:] = tot
+        maxes[:] = allv[:, ns:].max(axis=0)
+
+    return exchange
 
 
 def accord_loss(X: torch.Tensor, Omega: torch.Tensor, lam: float, *, precision: str | None = None,
@@ -470,6 +578,8 @@ class PathResult:
     omega_best: torch.Tensor | None          # (n_sub, p, p) estimates at best_index
     support: torch.Tensor | None             # (n_lambda, n_sub, p, ceil(p/32)) int32 bit words
     stats: FitStats
+    y_refreshes: np.ndarray | None = None    # mixed modes: refreshes of Y per (penalty, subsample)
+    y_drift: np.ndarray | None = None        # ... and the largest relative drift of Y they found
 
 
 def _subsample_arrays(subsamples) -> tuple[np.ndarray, np.ndarray]:
@@ -523,11 +633,14 @@ def accord_path(X: torch.Tensor, subsamples, lambdas, *, precision: str = "mixed
 
     stats = FitStats(st.iters, st.trials, st.status, st.f, st.g, st.kkt, st.tau_last, st.L, st.nnz_offdiag,
                      st.t_setup_ms, st.t_solve_ms, st.n_prox_gemm, st.n_y_gemm, st.t_prox_gemm_ms, st.t_y_gemm_ms,
-                     st.n_launches, st.logdet_d, st.epbic, None, st.tile_group_m, st.tile_pairs)
+                     st.n_launches, st.logdet_d, st.epbic, None, st.tile_group_m, st.tile_pairs,
+                     y_refreshes=st.y_refreshes, y_drift=st.y_drift, t_graph_idle_ms=st.t_graph_idle_ms,
+                     coarse_prox=st.coarse_prox)
     return PathResult(status, col("lambda_", np.float64), col("status", np.int32), col("iters", np.int32),
                       col("trials", np.int32), col("f", np.float64), col("g", np.float64), col("kkt", np.float64),
                       col("logdet_d", np.float64), col("epbic", np.float64), col("tau_last", np.float64),
-                      col("nnz_offdiag", np.int64), bidx[:ns].copy(), best, sup, stats)
+                      col("nnz_offdiag", np.int64), bidx[:ns].copy(), best, sup, stats,
+                      col("y_refreshes", np.int32), col("y_drift", np.float64))
 
 
 def accord_status_string(status: int) -> str:

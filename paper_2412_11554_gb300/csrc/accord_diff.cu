@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "api_util.h"
 #include "internal.h"
@@ -24,9 +25,12 @@
 namespace accord {
 namespace {
 
-constexpr int kMaxActive = 128;  // largest active set of a row
+constexpr int kMaxActive = 128;  // active sets up to this size are solved in shared memory
 constexpr int kRowThreads = 256;
 constexpr size_t kRowSmem = (size_t)kMaxActive * kMaxActive * 8 + kMaxActive * 8;
+constexpr int kBigActive = 1024;  // larger ones (up to this size) in a global-memory scratch
+constexpr int kBigBlocks = 4;     // blocks of the large-row pass, one scratch slot each
+constexpr int kBigThreads = 512;
 
 template <class T>
 __global__ void to_f64_kernel(const T* __restrict__ src, int64_t count, double* __restrict__ dst) {
@@ -34,67 +38,62 @@ __global__ void to_f64_kernel(const T* __restrict__ src, int64_t count, double* 
     dst[i] = (double)src[i];
 }
 
-template <class TO>
-__global__ void __launch_bounds__(kRowThreads) implicit_row_kernel(const double* __restrict__ S,
-                                                                   const double* __restrict__ Om,
-                                                                   const double* __restrict__ Gv, int64_t p,
-                                                                   double lam, int pen_diag,
-                                                                   double* __restrict__ contrib, TO* __restrict__ dOm,
-                                                                   int* err) {
-  extern __shared__ double smem[];
-  double* H = smem;                         // kMaxActive x kMaxActive (row-major, lower part used)
-  double* v = H + kMaxActive * kMaxActive;  // right-hand side, then the solution
-  __shared__ int idx[kMaxActive];
-  __shared__ int wcnt[kRowThreads / 32];
-  __shared__ double red[kRowThreads / 32];
-  __shared__ int m_sh, pos_sh, bad_sh;
-  constexpr int K = kMaxActive;
-  const int64_t i = blockIdx.x;
-  const double* orow = Om + i * p;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// The active set of row i (its nonzero columns, the diagonal included) in
+// increasing column order into idx[0 .. cap); returns its size, which may
+// exceed cap (then only the first cap columns are stored), and sets *pos to
+// the diagonal's place (-1 if it lies past cap).  All threads of the block
+// call it; wcnt holds one int per warp.
+__device__ int active_set(const double* __restrict__ orow, int64_t i, int64_t p, int* idx, int cap, int* wcnt,
+                          int* m_sh, int* pos_sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) {
-    m_sh = 0;
-    pos_sh = -1;
-    bad_sh = 0;
+    *m_sh = 0;
+    *pos_sh = -1;
   }
   __syncthreads();
-  // active set of row i in increasing column order
-  for (int64_t base = 0; base < p; base += kRowThreads) {
+  for (int64_t base = 0; base < p; base += blockDim.x) {
     const int64_t j = base + tid;
     const bool nz = j < p && (j == i || orow[j] != 0.0);
     const unsigned bal = __ballot_sync(0xffffffffu, nz);
     if (lane == 0) wcnt[warp] = __popc(bal);
     __syncthreads();
-    int off = m_sh;
+    int off = *m_sh;
     for (int w = 0; w < warp; ++w) off += wcnt[w];
     off += __popc(bal & ((1u << lane) - 1u));
-    if (nz && off < K) {
+    if (nz && off < cap) {
       idx[off] = (int)j;
-      if (j == i) pos_sh = off;
+      if (j == i) *pos_sh = off;
     }
     __syncthreads();
     if (tid == 0) {
-      int t = m_sh;
-      for (int w = 0; w < kRowThreads / 32; ++w) t += wcnt[w];
-      m_sh = t;
+      int t = *m_sh;
+      for (int w = 0; w < nw; ++w) t += wcnt[w];
+      *m_sh = t;
     }
     __syncthreads();
   }
-  const int m = m_sh, pos = pos_sh;
-  if (m > K || pos < 0) {
-    if (tid == 0) {
-      atomicOr(err, 1);
-      contrib[i] = NAN;
-    }
-    return;
-  }
-  for (int t = tid; t < m * m; t += kRowThreads) {
+  return *m_sh;
+}
+
+// Row i's system (S_AA + omega_ii^-2 e_i e_i^T) x = v on its active set A =
+// idx[0 .. m) (the diagonal at pos), factored by Cholesky in H (leading
+// dimension ldh, shared or global memory) and solved in v; then this row's
+// share of the derivative into contrib[i] and, if dOm, its row of
+// dOmega / dlog(lambda) = -lambda x.  All threads of the block call it.
+template <class TO>
+__device__ void solve_row(const double* __restrict__ S, const double* __restrict__ orow, const double* __restrict__ Gv,
+                          int64_t p, double lam, int pen_diag, int64_t i, const int* idx, int m, int pos, double* H,
+                          int ldh, double* v, double* red, int* bad_sh, double* __restrict__ contrib,
+                          TO* __restrict__ dOm, int* err) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  if (tid == 0) *bad_sh = 0;
+  for (int t = tid; t < m * m; t += nt) {
     const int a = t / m, b = t % m;
     double h = S[(int64_t)idx[a] * p + idx[b]];
     if (a == pos && b == pos) h += 1.0 / (orow[i] * orow[i]);
-    H[a * K + b] = h;
+    H[(int64_t)a * ldh + b] = h;
   }
-  for (int a = tid; a < m; a += kRowThreads) {
+  for (int a = tid; a < m; a += nt) {
     const double w = orow[idx[a]];
     v[a] = (a == pos) ? (pen_diag ? 1.0 : 0.0) : (w > 0.0 ? 1.0 : -1.0);
   }
@@ -102,54 +101,117 @@ __global__ void __launch_bounds__(kRowThreads) implicit_row_kernel(const double*
   // Cholesky factor H = L L^T in place (lower triangle)
   for (int k = 0; k < m; ++k) {
     if (tid == 0) {
-      const double d = H[k * K + k];
+      const double d = H[(int64_t)k * ldh + k];
       if (!(d > 0.0)) {
-        bad_sh = 1;
-        H[k * K + k] = 1.0;
+        *bad_sh = 1;
+        H[(int64_t)k * ldh + k] = 1.0;
       } else {
-        H[k * K + k] = sqrt(d);
+        H[(int64_t)k * ldh + k] = sqrt(d);
       }
     }
     __syncthreads();
-    const double lkk = H[k * K + k];
-    for (int r = k + 1 + tid; r < m; r += kRowThreads) H[r * K + k] /= lkk;
+    const double lkk = H[(int64_t)k * ldh + k];
+    for (int r = k + 1 + tid; r < m; r += nt) H[(int64_t)r * ldh + k] /= lkk;
     __syncthreads();
     const int t = m - k - 1;
-    for (int q = tid; q < t * t; q += kRowThreads) {
+    for (int q = tid; q < t * t; q += nt) {
       const int r = k + 1 + q / t, c = k + 1 + q % t;
-      if (c <= r) H[r * K + c] -= H[r * K + k] * H[c * K + k];
+      if (c <= r) H[(int64_t)r * ldh + c] -= H[(int64_t)r * ldh + k] * H[(int64_t)c * ldh + k];
     }
     __syncthreads();
   }
   // L y = v, then L^T x = y
   for (int k = 0; k < m; ++k) {
-    if (tid == 0) v[k] /= H[k * K + k];
+    if (tid == 0) v[k] /= H[(int64_t)k * ldh + k];
     __syncthreads();
-    for (int r = k + 1 + tid; r < m; r += kRowThreads) v[r] -= H[r * K + k] * v[k];
+    for (int r = k + 1 + tid; r < m; r += nt) v[r] -= H[(int64_t)r * ldh + k] * v[k];
     __syncthreads();
   }
   for (int k = m - 1; k >= 0; --k) {
-    if (tid == 0) v[k] /= H[k * K + k];
+    if (tid == 0) v[k] /= H[(int64_t)k * ldh + k];
     __syncthreads();
-    for (int r = tid; r < k; r += kRowThreads) v[r] -= H[k * K + r] * v[k];
+    for (int r = tid; r < k; r += nt) v[r] -= H[(int64_t)k * ldh + r] * v[k];
     __syncthreads();
   }
   // d omega_iA / d log(lambda) = -lambda x; this row's share of the derivative
   double s = 0.0;
-  for (int a = tid; a < m; a += kRowThreads) s += Gv[i * p + idx[a]] * (-lam * v[a]);
+  for (int a = tid; a < m; a += nt) s += Gv[i * p + idx[a]] * (-lam * v[a]);
   s = warp_sum(s);
   if (lane == 0) red[warp] = s;
   __syncthreads();
   if (tid == 0) {
     double tsum = 0.0;
-    for (int w = 0; w < kRowThreads / 32; ++w) tsum += red[w];
-    contrib[i] = bad_sh ? NAN : tsum;
-    if (bad_sh) atomicOr(err, 2);
+    for (int w = 0; w < (nt >> 5); ++w) tsum += red[w];
+    contrib[i] = *bad_sh ? NAN : tsum;
+    if (*bad_sh) atomicOr(err, 2);
   }
   if (dOm != nullptr) {
-    for (int64_t j = tid; j < p; j += kRowThreads) dOm[i * p + j] = TO(0);
+    for (int64_t j = tid; j < p; j += nt) dOm[i * p + j] = TO(0);
     __syncthreads();
-    for (int a = tid; a < m; a += kRowThreads) dOm[i * p + idx[a]] = (TO)(-lam * v[a]);
+    for (int a = tid; a < m; a += nt) dOm[i * p + idx[a]] = (TO)(-lam * v[a]);
+  }
+  __syncthreads();
+}
+
+// One CTA per row; a row whose active set exceeds kMaxActive is listed in
+// big_rows for implicit_big_kernel instead.
+template <class TO>
+__global__ void __launch_bounds__(kRowThreads) implicit_row_kernel(const double* __restrict__ S,
+                                                                   const double* __restrict__ Om,
+                                                                   const double* __restrict__ Gv, int64_t p,
+                                                                   double lam, int pen_diag,
+                                                                   double* __restrict__ contrib, TO* __restrict__ dOm,
+                                                                   int* err, int* big_rows, int* n_big) {
+  extern __shared__ double smem[];
+  double* H = smem;                         // kMaxActive x kMaxActive (row-major, lower part used)
+  double* v = H + kMaxActive * kMaxActive;  // right-hand side, then the solution
+  __shared__ int idx[kMaxActive];
+  __shared__ int wcnt[kRowThreads / 32];
+  __shared__ double red[kRowThreads / 32];
+  __shared__ int m_sh, pos_sh, bad_sh;
+  const int64_t i = blockIdx.x;
+  const double* orow = Om + i * p;
+  const int m = active_set(orow, i, p, idx, kMaxActive, wcnt, &m_sh, &pos_sh);
+  if (m > kMaxActive) {
+    if (threadIdx.x == 0) big_rows[atomicAdd(n_big, 1)] = (int)i;
+    return;
+  }
+  const int pos = pos_sh;
+  solve_row<TO>(S, orow, Gv, p, lam, pen_diag, i, idx, m, pos, H, kMaxActive, v, red, &bad_sh, contrib, dOm, err);
+}
+
+// The listed rows, kBigBlocks CTAs each taking every kBigBlocks-th one, with
+// the system in the CTA's slot of a global scratch (max_m x max_m FP64,
+// L2-resident at these sizes).  A row over max_m entries sets error bit 1.
+template <class TO>
+__global__ void __launch_bounds__(kBigThreads) implicit_big_kernel(const double* __restrict__ S,
+                                                                   const double* __restrict__ Om,
+                                                                   const double* __restrict__ Gv, int64_t p,
+                                                                   double lam, int pen_diag,
+                                                                   double* __restrict__ contrib, TO* __restrict__ dOm,
+                                                                   int* err, const int* big_rows, const int* n_big,
+                                                                   double* scratch, int* scratch_idx, int max_m) {
+  __shared__ int wcnt[kBigThreads / 32];
+  __shared__ double red[kBigThreads / 32];
+  __shared__ int m_sh, pos_sh, bad_sh;
+  double* H = scratch + (int64_t)blockIdx.x * ((int64_t)max_m * max_m + max_m);
+  double* v = H + (int64_t)max_m * max_m;
+  int* idx = scratch_idx + (int64_t)blockIdx.x * max_m;
+  const int nb = *n_big;
+  for (int r = blockIdx.x; r < nb; r += gridDim.x) {
+    const int64_t i = big_rows[r];
+    const double* orow = Om + i * p;
+    const int m = active_set(orow, i, p, idx, max_m, wcnt, &m_sh, &pos_sh);
+    const int pos = pos_sh;
+    if (m > max_m || pos < 0) {
+      if (threadIdx.x == 0) {
+        atomicOr(err, 1);
+        contrib[i] = NAN;
+      }
+      __syncthreads();
+      continue;
+    }
+    solve_row<TO>(S, orow, Gv, p, lam, pen_diag, i, idx, m, pos, H, max_m, v, red, &bad_sh, contrib, dOm, err);
   }
 }
 
@@ -302,7 +364,7 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   const int64_t ldk = round_up(p, 8), ldn = round_up(n, 8);
   size_t c = 0;
   // error words: [0] non-finite training rows, [1] row-system bits (1: an
-  // active set over 128 entries, 2: not positive definite), [2] non-finite
+  // active set over 1024 entries, 2: not positive definite), [2] non-finite
   // held-out rows, [3] device error bits of the GEMMs
   // results: res[0] = dloss, res[1..2] = f, g of the held-out loss
   const size_t err_off = take(c, 64), res_off = take(c, 64), contrib_off = take(c, (size_t)p * 8);
@@ -310,6 +372,12 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   const size_t om_off = take(c, (size_t)p * p * 8);
   const size_t x_off = take(c, (size_t)n * ldk * 8), xt_off = take(c, (size_t)p * ldn * 8);
   const size_t g32_off = take(c, f64 ? 0 : (size_t)p * p * 4);  // mixed modes: FP32 held-out gradient
+  // rows whose active set exceeds kMaxActive: their list and the large-row
+  // pass's scratch (kBigBlocks systems of up to max_m entries)
+  const int max_m = (int)(p < kBigActive ? p : kBigActive);
+  const size_t big_off = take(c, (size_t)p * 4 + 64);
+  const size_t bigs_off = take(c, (size_t)kBigBlocks * ((size_t)max_m * max_m + max_m) * 8);
+  const size_t bigi_off = take(c, (size_t)kBigBlocks * max_m * 4);
   Guard g;
   if (cudaMallocAsync(&g.ptr, c, st) != cudaSuccess) return kEnomem;
   g.st = st;
@@ -317,6 +385,9 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
   int* err = at<int>(ws, err_off);
   double* Om64 = at<double>(ws, om_off);
   ACCORD_CK(cudaMemsetAsync(err, 0, 64, st));
+  int* big_rows = at<int>(ws, big_off);
+  int* n_big = big_rows + p;
+  ACCORD_CK(cudaMemsetAsync(n_big, 0, sizeof(int), st));
   if (f64) ACCORD_CK(cudaMemcpyAsync(Om64, Omega_hat, (size_t)p * p * 8, cudaMemcpyDeviceToDevice, st));
   else to_f64_kernel<float><<<blocks_for(p * p), 256, 0, st>>>(static_cast<const float*>(Omega_hat), p * p, Om64);
   ACCORD_CK(cudaGetLastError());
@@ -373,9 +444,11 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
     ACCORD_CK(cudaGetLastError());
   }
   // per-row implicit solves
+  static std::mutex mu;
   static int configured = -1;
   int dev = 0;
   ACCORD_CK(cudaGetDevice(&dev));
+  std::unique_lock<std::mutex> lock(mu);
   if (configured != dev) {
     ACCORD_CK(cudaFuncSetAttribute(implicit_row_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kRowSmem));
@@ -383,16 +456,28 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
                                    (int)kRowSmem));
     configured = dev;
   }
+  lock.unlock();
   if (p > 2147483647LL) return kEinval;
   const int pen = o.penalize_diag ? 1 : 0;
-  if (f64)
+  double* bigs = at<double>(ws, bigs_off);
+  int* bigi = at<int>(ws, bigi_off);
+  if (f64) {
     implicit_row_kernel<double><<<(unsigned)p, kRowThreads, kRowSmem, st>>>(
         at<double>(ws, S_off), Om64, at<double>(ws, Gv_off), p, lambda, pen, at<double>(ws, contrib_off),
-        static_cast<double*>(dOmega), err + 1);
-  else
+        static_cast<double*>(dOmega), err + 1, big_rows, n_big);
+    ACCORD_CK(cudaGetLastError());
+    implicit_big_kernel<double><<<kBigBlocks, kBigThreads, 0, st>>>(
+        at<double>(ws, S_off), Om64, at<double>(ws, Gv_off), p, lambda, pen, at<double>(ws, contrib_off),
+        static_cast<double*>(dOmega), err + 1, big_rows, n_big, bigs, bigi, max_m);
+  } else {
     implicit_row_kernel<float><<<(unsigned)p, kRowThreads, kRowSmem, st>>>(
         at<double>(ws, S_off), Om64, at<double>(ws, Gv_off), p, lambda, pen, at<double>(ws, contrib_off),
-        static_cast<float*>(dOmega), err + 1);
+        static_cast<float*>(dOmega), err + 1, big_rows, n_big);
+    ACCORD_CK(cudaGetLastError());
+    implicit_big_kernel<float><<<kBigBlocks, kBigThreads, 0, st>>>(
+        at<double>(ws, S_off), Om64, at<double>(ws, Gv_off), p, lambda, pen, at<double>(ws, contrib_off),
+        static_cast<float*>(dOmega), err + 1, big_rows, n_big, bigs, bigi, max_m);
+  }
   ACCORD_CK(cudaGetLastError());
   sum_kernel<<<1, 512, 0, st>>>(at<double>(ws, contrib_off), p, res);
   ACCORD_CK(cudaGetLastError());
@@ -408,7 +493,7 @@ int dloss_impl(const float* Xt, int64_t n, const float* Xv, int64_t n_val, int64
     return kEcuda;
   }
   if (h[1] & 1) {
-    set_last_error(__FILE__, __LINE__, "a row's active set exceeds 128 entries");
+    set_last_error(__FILE__, __LINE__, "a row's active set exceeds 1024 entries");
     return kEunsupported;
   }
   if (h[1] & 2) {

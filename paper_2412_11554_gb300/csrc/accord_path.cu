@@ -192,11 +192,19 @@ struct PathPlan {
   GemmF64Params g2{}, g1{};
   TcParams t2{}, t1{};
   SparseYParams sy{};
+  YRefreshParams rf{};
+  bool refresh = false;  // mixed modes with sp.y_refresh > 0
 };
 
 // One trial of every running chain: the batched prox GEMM, then the rest of
 // Algorithm 1's trial and the path bookkeeping.
 int launch_path_prox(const PathPlan& P, cudaStream_t st) {
+  if (P.refresh) {
+    // Y formed afresh for the chains whose last decision asked for it
+    ACCORD_CK(launch_y_refresh(P.rf, st));
+    ACCORD_CK(launch_y_refresh_fold(P.pd.ctrl, (int32_t)P.L.nchains, P.pd.active, P.pd.nactive,
+                                    at<double>(P.ws, P.L.part_sy), P.L.nbuckets, P.L.nbuckets * kYSlots, 1, st));
+  }
   if (P.L.f64) ACCORD_CK(launch_gemm_f64(kModeProx, P.g2, st));
   else ACCORD_CK(launch_tc_gemm(kModeProx, P.t2, st));
   return kOk;
@@ -228,7 +236,7 @@ int launch_path_rest(const PathPlan& P, cudaStream_t st) {
   return kOk;
 }
 
-int launches_per_trial(bool f64) { return f64 ? 5 : 7; }
+int launches_per_trial(bool f64, bool refresh) { return f64 ? 5 : (refresh ? 10 : 7); }
 
 // ------------------------------------------------------------ autotuner ---
 // The batched prox GEMM's tile raster (pair rows of 256 per group) and its
@@ -502,6 +510,9 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
   sp.tau_warm = o.tau_warm;
   sp.fixed_step = o.beta >= 1.0 ? 1 : 0;
   sp.trace_cap = 0;
+  sp.y_refresh = f64 ? 0 : o.y_refresh;
+  sp.coarse_kkt = f64 ? 0.0 : o.coarse_kkt;
+  pd.coarse = sp.coarse_kkt > 0.0 ? 1 : 0;
   if (f64) {
     GemmF64Params& g2 = P.g2;  // G = Y X / n, prox, Omega[cur] -> Omega[nxt]
     g2.ctrl = ctrl;
@@ -555,6 +566,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
         !encode_plane_map(&t2.b_lo, at<void>(ws, L.xt_lo), L.pt, p, K, K, tc_box_n(), B, p * K))
       return kEcuda;
     t2.ctrl = ctrl;
+    t2.coarse_ok = sp.coarse_kkt > 0.0 ? 1 : 0;
     t2.err = &ctrl[0].dev_error;
     tc_shape(t2, p, p, K, L.pt);
     t2.out[0] = at<float>(ws, L.om[0]);
@@ -640,6 +652,33 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     sy.nprob = (int32_t)B;
     sy.s_y = p * K; sy.s_yk = p * K; sy.s_xt = p * K; sy.s_bkt = L.nbuckets;
     sy.ptype = L.pt;
+    YRefreshParams& rf = P.rf;
+    rf.ctrl = ctrl;
+    for (int q = 0; q < 2; ++q) {
+      rf.om[q] = at<float>(ws, L.om[q]);
+      rf.bm[q] = at<uint32_t>(ws, L.bm[q]);
+      rf.y[q] = at<float>(ws, L.y[q]);
+      rf.y_hi[q] = at<void>(ws, L.y_hi[q]);
+      rf.y_lo[q] = at<void>(ws, L.y_lo[q]);
+    }
+    rf.xt = at<float>(ws, L.xt32);
+    rf.rows = p;
+    rf.p = p;
+    rf.n = K;
+    rf.ldo = L.ldo;
+    rf.ldbm = bitmap_ld(p);
+    rf.ldy = K;
+    rf.ldyk = K;
+    rf.ldx = K;
+    rf.part = at<double>(ws, L.part_sy);
+    rf.ptype = L.pt;
+    rf.nprob = (int32_t)B;
+    rf.active = pd.active;
+    rf.nactive = pd.nactive;
+    rf.s_om = p * L.ldo; rf.s_bm = bitmap_words(p); rf.s_y = p * K; rf.s_yk = p * K; rf.s_xt = p * K;
+    rf.s_part = L.nbuckets * kYSlots;
+    rf.dense_nnz = 0.1 * (double)p * (double)p;
+    P.refresh = P.sp.y_refresh > 0;
   }
   TuneChoice tune;
   if (!f64 && o.autotune) {
@@ -709,7 +748,7 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     cudaGraphDestroy(graph);
     ACCORD_CK(ie);
   }
-  const int per_trial = launches_per_trial(f64) + (emit ? 1 : 0);
+  const int per_trial = launches_per_trial(f64, P.refresh) + (emit ? 1 : 0);
 
   // every penalty ends by max_iter steps of at most max_backtracks + 1 trials
   const int64_t max_graphs =
@@ -740,6 +779,25 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     if (cudaEventElapsedTime(&ms, marks.v[i], marks.v[i + 1]) == cudaSuccess) prox_ms += ms;
   }
   ACCORD_CK(cudaEventRecord(ev[2], st));
+  // the launch cost of a replay: the same graph once more, now that every
+  // chain has finished and each of its kernels returns at once
+  double idle_ms = 0.0;
+  if (use_graph && hstatus == kOk) {
+    cudaEvent_t i0 = nullptr, i1 = nullptr;
+    ACCORD_CK(cudaEventCreate(&i0));
+    cudaError_t ie = cudaEventCreate(&i1);
+    if (ie == cudaSuccess) ie = cudaEventRecord(i0, st);
+    if (ie == cudaSuccess) ie = cudaGraphLaunch(egd.g, st);
+    if (ie == cudaSuccess) ie = cudaEventRecord(i1, st);
+    if (ie == cudaSuccess) ie = cudaEventSynchronize(i1);
+    float ms = 0.f;
+    if (ie == cudaSuccess) ie = cudaEventElapsedTime(&ms, i0, i1);
+    cudaEventDestroy(i0);
+    if (i1) cudaEventDestroy(i1);
+    ACCORD_CK(ie);
+    idle_ms = ms;
+    nlaunch += (int64_t)per_trial * kTrialsPerGraph;
+  }
 
   // ------------------------------------------------------- results -------
   static_assert(sizeof(PathRec) == sizeof(accord_path_entry), "path record layout");
@@ -779,6 +837,18 @@ int path_impl(const float* X, int64_t n, int64_t p, const int32_t* rows, const i
     }
     out->iters = (int32_t)it;
     out->trials = (int32_t)tr;
+    int64_t nrf = 0;
+    double drift = 0.0;
+    for (int64_t i = 0; i < n_lambda * B; ++i) {
+      nrf += entries[i].y_refreshes;
+      drift = std::max(drift, entries[i].y_drift);
+    }
+    out->y_refreshes = (int32_t)nrf;
+    int64_t nco = 0;
+    for (int64_t c = 0; c < B; ++c) nco += hctrl[c].n_coarse;
+    out->coarse_prox = (int32_t)nco;
+    out->y_drift = drift;
+    out->t_graph_idle_ms = idle_ms;
     out->n_prox_gemm = (int32_t)(graphs * kTrialsPerGraph);
     out->t_prox_gemm_ms = prox_ms;
     out->n_launches = nlaunch;

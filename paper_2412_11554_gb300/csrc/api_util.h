@@ -95,6 +95,8 @@ int check_opts(const accord_opts& o) {
   if (!(o.lipschitz_tol >= 0.0)) return kEinval;
   if (!(o.epbic_gamma >= 0.0)) return kEinval;
   if (o.trace_cap < 0) return kEinval;
+  if (o.y_refresh < 0) return kEinval;
+  if (!(o.coarse_kkt >= 0.0) || !std::isfinite(o.coarse_kkt)) return kEinval;
   return kOk;
 }
 

@@ -74,14 +74,29 @@ struct Ctrl {
   int32_t trials_tot; // lambda path: prox evaluations over the whole chain
   int32_t ymode;      // batch: 1 = the prox epilogue writes dense Delta planes (Delta too dense for
                       // the buckets), 0 = it fills the sparse buckets
-  int32_t pad1;
+  // mixed modes: Y = Omega X^T is carried forward by Y+ = Y + Delta X^T in
+  // FP32, which accumulates rounding; it is formed afresh from Omega^t every
+  // SolveParams::y_refresh accepted steps and before a KKT residual under
+  // the tolerance may end the fit
+  int32_t refresh;        // 1: Y of Omega^t is formed afresh before the next trial
+  int32_t since_refresh;  // accepted steps since Y was last formed from Omega
+  int32_t n_refresh;      // refreshes so far
+  int32_t cut_trials;     // trials cut short because their KKT test asked for a refresh
+  double y_drift;         // largest ||Y - Omega X^T||_F / ||Omega X^T||_F found by a refresh
+  double kkt_prev;        // KKT residual of the iterate before Omega^t (INFINITY if none)
+  // mixed modes: 1 while the prox GEMM forms G with the one product hi x hi
+  // (SolveParams::coarse_kkt); the first KKT residual under that threshold
+  // switches to the three split products for the rest of the fit
+  int32_t coarse;
+  int32_t n_coarse;       // prox launches that ran with the one product
 };
 
 // One estimate of a lambda path (same layout as accord_path_entry).
 struct PathRec {
-  int32_t status, iters, trials, reserved0;
+  int32_t status, iters, trials, y_refreshes;
   double lambda, f, g, kkt, logdet_d, epbic, tau_last;
   int64_t nnz_offdiag;
+  double y_drift;
 };
 
 struct SolveParams {
@@ -89,6 +104,9 @@ struct SolveParams {
   double inv_n;
   int32_t max_iter, max_backtracks, tau_warm, fixed_step;
   int64_t trace_cap;
+  int32_t y_refresh;  // mixed modes: accepted steps between refreshes of Y (0: none)
+  int32_t pad0;
+  double coarse_kkt;  // mixed modes: one-product gradients while the KKT residual is above this (0: never)
 };
 
 constexpr int kTraceFields = 8;

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
       } else if (MODE == kModeProx) {
         // v = [Omega S]_ij; A = Omega - tau G; Eq. 3.5.
         const double om = aux[row * prm.ldaux + col];
-        const bool dg = (row == col);
+        const bool dg = (row + prm.row_off == col);
         const double a = om - tau * v;
         double lam_e = lam;  // Eq. 3.8 refit: infinite weight off the support
         if (prm.mask != nullptr && !dg && !((prm.mask[row * prm.mask_ld + (col >> 5)] >> (col & 31)) & 1u))
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmF64Params prm) {
         if (!isfinite(w) || !isfinite(v)) r.s[kPBad] += 1.0;
       } else if (MODE == kModeGrad) {
         double gv = v;
-        if (prm.smooth && row == col) gv -= 1.0 / aux[row * prm.ldaux + col];
+        if (prm.smooth && row + prm.row_off == col) gv -= 1.0 / aux[row * prm.ldaux + col];
         out[row * prm.ldout + col] = gv;
       } else {  // kModeGram
         out[row * prm.ldout + col] = v;

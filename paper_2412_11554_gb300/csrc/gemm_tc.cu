@@ -32,6 +32,7 @@
 // the trial / KKT reductions, the gradient of Sec 3.2, and X X^T / n.
 #include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "tc_gemm.h"
 #include "tc_ptx.cuh"
@@ -100,6 +101,14 @@ __device__ __forceinline__ bool skip_problem(const TcParams& prm, int b) {
   if (prm.ctrl == nullptr) return false;
   const Ctrl& c = prm.ctrl[b];
   return c.done || (prm.gate_dense && !c.dense && !c.ymode);
+}
+
+// Prox mode, a problem whose control block asks for the coarse gradient:
+// G from the one product hi x hi (the lo planes are neither loaded nor
+// multiplied).  The producer and the MMA issuer read the same flag, which
+// does not change while the kernel runs.
+__device__ __forceinline__ bool coarse_tile(const TcParams& prm, int b) {
+  return prm.coarse_ok && prm.ctrl != nullptr && prm.ctrl[b].coarse != 0;
 }
 
 // First flat tile >= T (stepping by `stride`) that is not skipped; ntot if none.
@@ -189,28 +198,56 @@ __device__ __forceinline__ uint32_t transpose_bits(uint32_t x, int lane) {
   return x;
 }
 
-// The 32 x 32 block src[row_base .. +31][col0 .. +31] into buf (row-major),
-// reading only its nonzero entries: rbits holds, in lane r, the occupancy
-// word of row r (bit c: column col0 + c nonzero).  The buffer is zeroed and
-// the nonzero entries are copied over it asynchronously; rows with no
-// nonzero entry cost nothing beyond the zeroing.
-__device__ __forceinline__ void prefetch_sparse_block(float* buf, const float* __restrict__ src, int64_t ld,
-                                                      int64_t row_base, int64_t col0, uint32_t rbits, int lane,
-                                                      uint64_t pol) {
-  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) reinterpret_cast<float4*>(buf)[k * 32 + lane] = z;
-  __syncwarp();
-  const uint32_t sbase = ptx::smem_u32(buf);
+// Rows with at most this many nonempty rows in a 32 x 32 block are fetched
+// entry by entry, denser blocks row by row.
+constexpr int kGatherRows = 8;
+
+// The nonzero entries of the 32 x 32 block src[row_base .. +31][col0 .. +31]
+// into buf, row-major with each row's 16-byte slots XOR-swizzled by row
+// (columns 4s .. 4s + 3 of row r at slot s ^ (r & 7)), so that the copies and
+// the column reads below are free of bank conflicts.  rbits holds, in lane r,
+// the occupancy word of row r (bit c: column col0 + c nonzero).  A block with
+// few nonempty rows is gathered one row per instruction, lane c copying entry
+// c when its bit is set (only the sectors that hold nonzeros are read); a
+// denser one is copied by lane r as its row's eight 16-byte segments (eight
+// instructions whatever the block holds).  Entries whose bit is clear are not
+// defined in buf; read_block_masked reads them as 0.  Nothing past column
+// ld - 1 is read.
+__device__ __forceinline__ void prefetch_rows(float* buf, const float* __restrict__ src, int64_t ld,
+                                              int64_t row_base, int64_t col0, uint32_t rbits, int lane,
+                                              uint64_t pol) {
+  const uint32_t sbuf = ptx::smem_u32(buf);
   uint32_t rows = __ballot_sync(0xffffffffu, rbits != 0u);
-  while (rows != 0u) {
-    const int r = __ffs(rows) - 1;
-    rows &= rows - 1u;
-    const uint32_t m = __shfl_sync(0xffffffffu, rbits, r);
-    if ((m >> lane) & 1u)
-      ptx::cp_async4_hint(sbase + (uint32_t)((r * 32 + lane) * 4), src + (row_base + r) * ld + col0 + lane, pol);
+  if (__popc(rows) <= kGatherRows) {
+    while (rows != 0u) {
+      const int r = __ffs(rows) - 1;
+      rows &= rows - 1u;
+      const uint32_t m = __shfl_sync(0xffffffffu, rbits, r);
+      if ((m >> lane) & 1u)
+        ptx::cp_async4_hint(sbuf + (uint32_t)((r * 32 + ((((lane >> 2) ^ (r & 7))) << 2) + (lane & 3)) * 4),
+                            src + (row_base + r) * ld + col0 + lane, pol);
+    }
+  } else if (rbits != 0u) {
+    const uint32_t sbase = sbuf + (uint32_t)lane * 128u;
+    const float* g = src + (row_base + lane) * ld + col0;
+#pragma unroll
+    for (int seg = 0; seg < 8; ++seg)
+      if (col0 + 4 * seg + 4 <= ld) ptx::cp_async16_hint(sbase + (uint32_t)((seg ^ (lane & 7)) << 4), g + 4 * seg, pol);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Column `lane` of a block written by prefetch_rows: entry r where bit r of
+// colbits is set (colbits: the block's occupancy in this column), else 0.
+__device__ __forceinline__ void read_block_masked(const float* buf, int lane, uint32_t colbits, float (&pre)[32]) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const float x = buf[r * 32 + ((((lane >> 2) ^ (r & 7))) << 2) + (lane & 3)];
+    pre[r] = ((colbits >> r) & 1u) ? x : 0.f;
+  }
+  __syncwarp();
 }
 
 // Asynchronous copy of one tile's occupancy words into a word slot (prox
@@ -328,7 +365,7 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
       const float om = pre[r];
       const float a = fmaf(-tau, g, om);
       float w;
-      if (CHECK && row_base + r == colt) {
+      if (CHECK && row_base + r + prm.row_off == colt) {
         w = diag_prox(a, tau, ea.lam_d);
         sm.r2 += log((double)w);
         sm.r3 += (double)w;
@@ -404,7 +441,7 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
   // less the diagonal entry where this column meets it
   int nnz = __popc(newcol);
   if (CHECK) {
-    const int64_t dr = colt - row_base;
+    const int64_t dr = colt - row_base - prm.row_off;
     if (dr >= 0 && dr < 32 && ((newcol >> dr) & 1u)) nnz -= 1;
   }
   sm.r0 += sd;
@@ -424,7 +461,7 @@ __device__ __forceinline__ void grad_chunk(const EpiArgs& ea, const TcParams& pr
     const int64_t row = row_base + r;
     if (check && !(cok && row < ea.M)) continue;
     float g = v[r] * ea.scale;
-    if (prm.smooth && check && row == colt) g -= 1.f / ea.aux[row * prm.ldaux + row];
+    if (prm.smooth && check && row + prm.row_off == colt) g -= 1.f / ea.aux[row * prm.ldaux + colt];
     ea.out[row * prm.ldout + colt] = g;
   }
 }
@@ -531,18 +568,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const CUtensorMap* mA_lo = &prm.a_lo[asel];
         const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
         const int32_t zb = prm.b_batched ? b : 0;
+        const bool one = coarse_tile(prm, b);
         for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait_cluster(&empty[s], ph ^ 1u, abort_flag, prm.wait_ns)) { ok = false; break; }
           if (!withhold) {
             // the leader expects the bytes of both CTAs' copies of this stage
-            if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * kStageBytes);
+            if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], one ? 2 * (kABytes + kBBytes) : 2 * kStageBytes);
             const uint32_t st = smem_base + s * kStageBytes;
             const uint32_t fb = ptx::map_to_cta(&full[s], 0);
             const int32_t by = nb * kBN + rank * kBHalf;
             ptx::tma_load_3d_pair(st, mA_hi, fb, kb * BK, mb * BM, b, pol_a);
-            ptx::tma_load_3d_pair(st + kABytes, mA_lo, fb, kb * BK, mb * BM, b, pol_a);
+            if (!one) ptx::tma_load_3d_pair(st + kABytes, mA_lo, fb, kb * BK, mb * BM, b, pol_a);
             ptx::tma_load_3d_pair(st + 2 * kABytes, mB_hi, fb, kb * BK, by, zb, pol_keep);
-            ptx::tma_load_3d_pair(st + 2 * kABytes + kBBytes, mB_lo, fb, kb * BK, by, zb, pol_keep);
+            if (!one) ptx::tma_load_3d_pair(st + 2 * kABytes + kBBytes, mB_lo, fb, kb * BK, by, zb, pol_keep);
             filled[s] = true;
             fill_ph[s] = ph;
           }
@@ -583,6 +621,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         ptx::tc_fence_after();
         const uint32_t d = tmem_base + acc * kBN;
         const int nkb = prm.kb_of ? prm.kb_of[b] : prm.num_kb;
+        const bool one = coarse_tile(prm, b);
         for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait_cluster(&full[s], ph, abort_flag, prm.wait_ns)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -591,17 +630,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint64_t a_lo = ptx::sdesc_k64(st + kABytes);
           const uint64_t b_hi = ptx::sdesc_k64(st + 2 * kABytes);
           const uint64_t b_lo = ptx::sdesc_k64(st + 2 * kABytes + kBBytes);
+          if (one) {
 #pragma unroll
-          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-            const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4: K = 16 BF16 or 8 TF32
-            if constexpr (PT == kPlaneTf32) {
-              ptx::mma_tf32_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
-              ptx::mma_tf32_pair(d, a_hi + off, b_lo + off, idesc, 1u);
-              ptx::mma_tf32_pair(d, a_hi + off, b_hi + off, idesc, 1u);
-            } else {
-              ptx::mma_f16_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
-              ptx::mma_f16_pair(d, a_hi + off, b_lo + off, idesc, 1u);
-              ptx::mma_f16_pair(d, a_hi + off, b_hi + off, idesc, 1u);
+            for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+              const uint64_t off = (uint64_t)(kk * 2);
+              if constexpr (PT == kPlaneTf32) ptx::mma_tf32_pair(d, a_hi + off, b_hi + off, idesc, (kb | kk) != 0);
+              else ptx::mma_f16_pair(d, a_hi + off, b_hi + off, idesc, (kb | kk) != 0);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+              const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4: K = 16 BF16 or 8 TF32
+              if constexpr (PT == kPlaneTf32) {
+                ptx::mma_tf32_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+                ptx::mma_tf32_pair(d, a_hi + off, b_lo + off, idesc, 1u);
+                ptx::mma_tf32_pair(d, a_hi + off, b_hi + off, idesc, 1u);
+              } else {
+                ptx::mma_f16_pair(d, a_lo + off, b_hi + off, idesc, (kb | kk) != 0);
+                ptx::mma_f16_pair(d, a_hi + off, b_lo + off, idesc, 1u);
+                ptx::mma_f16_pair(d, a_hi + off, b_hi + off, idesc, 1u);
+              }
             }
           }
           // release the slot in both CTAs once these MMAs have read it
@@ -666,8 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       load_words(wslots, prm.bm[cb0] + b * prm.s_bm, prm.ldbm, cbase0 >> 5, nch, rb0, rb0 < prm.M, lane);
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncwarp();
-      prefetch_sparse_block(tbuf, prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0, wslots[lane], lane,
-                            ea.pol_stream);
+      prefetch_rows(tbuf, prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0, wslots[lane], lane, ea.pol_stream);
       pending = true;
     }
     for (; T < ntot; ++i) {
@@ -743,7 +790,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int64_t col0 = col_base + c;
           const int64_t colt = col0 + lane;
           const bool full = rows_full && col0 + 32 <= prm.N;
-          if (kNeedAux && ea.aux != nullptr) {
+          if (kProx) {
+            read_block_masked(tbuf, lane, transpose_bits(wcur[(c >> 5) * 32 + lane], lane), pre);
+          } else if (kNeedAux && ea.aux != nullptr) {
             if (pending) read_block_column(tbuf, lane, pre);
             else load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
           }
@@ -760,13 +809,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int k = c >> 5;
           if (kProx) {
             if (c + 32 < kColsPerWarp) {
-              prefetch_sparse_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wcur[(k + 1) * 32 + lane], lane,
-                                    ea.pol_stream);
+              prefetch_rows(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wcur[(k + 1) * 32 + lane], lane,
+                            ea.pol_stream);
               pending = true;
             } else if (TN < ntot) {
               // the next tile's first block (its words arrived during chunk 1's wait)
-              prefetch_sparse_block(tbuf, prm.aux[cbN] + bN * prm.s_aux, prm.ldaux, rbN, cbaseN, wnext[lane], lane,
-                                    ea.pol_stream);
+              prefetch_rows(tbuf, prm.aux[cbN] + bN * prm.s_aux, prm.ldaux, rbN, cbaseN, wnext[lane], lane,
+                            ea.pol_stream);
               pending = true;
             }
           } else if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
@@ -775,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             pending = true;
           }
           if (row_base >= prm.M || col0 >= prm.N) continue;  // warp-uniform
-          const bool diag = (row_base == col0);
+          const bool diag = (row_base + prm.row_off == col0);
           if (MODE == kModeY) {
             if (full) y_chunk<PT, false>(ea, prm, row_base, colt, v, pre, sm);
             else y_chunk<PT, true>(ea, prm, row_base, colt, v, pre, sm);
@@ -832,7 +881,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         double d2 = sm.r2, d3 = sm.r3;
         // diagonal entries exist only where the tile's row and column ranges meet
-        const int64_t r_lo = (int64_t)mb * BM, c_lo = (int64_t)nb * kBN;
+        const int64_t r_lo = (int64_t)mb * BM + prm.row_off, c_lo = (int64_t)nb * kBN;
         if (MODE == kModeProx && r_lo < c_lo + kBN && c_lo < r_lo + BM) {
           d2 = warp_sum(d2);
           d3 = warp_sum(d3);
@@ -884,14 +933,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 
 // Shared-memory opt-in and the persistent grid size (CTA pairs that fit at
 // once), set up once per device, mode and plane type.  Done outside any
-// launch so that a stream capture records launches only.
+// launch so that a stream capture records launches only.  Host threads that
+// fit row blocks side by side call this at once: the lock orders the two
+// statics.
 template <int MODE, int PT>
 cudaError_t configure_mode(int& max_pairs) {
+  static std::mutex mu;
   static int configured = -1;
   static int pairs = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
   if (configured != dev) {
     e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes);

@@ -49,6 +49,9 @@ struct GemmF64Params {
   const int32_t* active;    // device list of problems, or null (0 .. nprob-1)
   const int32_t* nactive;   // device length of `active`
   int64_t s_a, s_b, s_out, s_aux, s_part;  // strides: elements (s_part: tiles)
+  // Row block of Omega (prox / grad modes): output row r is row r + row_off
+  // of the full matrix, so its diagonal entry sits in column r + row_off.
+  int64_t row_off;
 };
 
 int64_t gemm_f64_tiles(int64_t M, int64_t N);
@@ -61,27 +64,34 @@ cudaError_t launch_convert_x_f64(const float* X32, const double* X64in, int64_t 
 // Operand planes (type pt, kPlaneBf16 or kPlaneTf32) of X and X^T.
 cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void* Xhi, void* Xlo, int64_t ldx,
                                     void* XThi, void* XTlo, int64_t ldxt, int* bad_flag, int pt, cudaStream_t st);
-// Omega^0 = I in an internal buffer with leading dimension ld (elements).
-cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st);
+// Omega^0 = I in an internal buffer with leading dimension ld (elements); a
+// row block (rows >= 0) holds rows row0 .. row0 + rows of it.
+cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st, int64_t rows = -1,
+                                int64_t row0 = 0);
 // Occupancy bitmaps of the mixed-mode iterate buffers (the prox epilogue's
 // sparse reads and writes of Omega): ceil(p / 32) column chunks of
 // bitmap_ld(p) words each; word [c * bitmap_ld(p) + i] has bit j - 32 c set
 // iff Omega[i][j] != 0.  Rows past p hold 0.
-int64_t bitmap_ld(int64_t p);
+// A row block of `rows` rows keeps ceil(p / 32) chunks of bitmap_ld(rows) words.
+int64_t bitmap_ld(int64_t rows);
+int64_t bitmap_words(int64_t rows, int64_t cols);
 int64_t bitmap_words(int64_t p);
-cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st);
+// rows >= 0: a row block holding rows row0 .. row0 + rows of the p x p matrix.
+cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st, int64_t rows = -1, int64_t row0 = 0);
 // Dense copy (ld ldd) of an FP32 iterate buffer that counts only where its bitmap has a bit.
 cudaError_t launch_copy_omega_masked(const float* src, int64_t lds, const uint32_t* bm, float* dst, int64_t ldd,
-                                     int64_t p, cudaStream_t st);
-cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st);
-// Copy between a dense p x p user array (ld = p) and an internal buffer.
+                                     int64_t p, cudaStream_t st, int64_t rows = -1);
+cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st,
+                                     int64_t rows = -1);
+// Copy between a dense p x p user array (ld = p) and an internal buffer
+// (rows >= 0: the first `rows` rows only).
 cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
-                              int64_t p, cudaStream_t st);
+                              int64_t p, cudaStream_t st, int64_t rows = -1);
 // Per-row-block statistics of Omega into kProxSlots partials (log-diag,
 // diag sum, off-diagonal l1, nnz, bad count); returns the number of rows of
 // partials written through *nparts.
 cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld, double* part,
-                               int64_t* nparts, cudaStream_t st);
+                               int64_t* nparts, cudaStream_t st, int64_t rows = -1, int64_t row0 = 0);
 // Support bitmask of the Eq. 3.8 refit: bit (i, j) of word [i][j / 32] is set
 // where Om_ij != 0 or i == j.  Om is p x p with leading dimension ld.
 cudaError_t launch_support_mask(const void* Om, int is_f64, int64_t p, int64_t ld, uint32_t* mask, int64_t mask_ld,
@@ -120,6 +130,16 @@ cudaError_t launch_identity_stats(double* part, int64_t p, cudaStream_t st);
 cudaError_t launch_decide(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                           double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
                           cudaStream_t st, unsigned long long* delta_entries = nullptr);
+// Row blocks of one fit: fold this block's trial sums into out[0 .. 11]
+// (kProxSlots prox sums, then the kYSlots sums of the Y update that ran;
+// empties the buckets), and, once the caller has exchanged them over all
+// blocks, take Algorithm 1's decisions on the global sums.
+cudaError_t launch_fold_block(Ctrl* ctrl, const double* prox_part, int64_t ntiles_prox, double* fold_scratch,
+                              const double* y_part, int64_t ntiles_y, int* bucket_counts, int nbuckets,
+                              const double* part_sparse, unsigned long long* delta_entries, double* out,
+                              cudaStream_t st);
+cudaError_t launch_decide_global(Ctrl* ctrl, const double* sums, const SolveParams& sp, double* trace,
+                                 cudaStream_t st);
 // Loss helper: reduce Omega stats and Y partials into out[0] = f, out[1] = g.
 cudaError_t launch_loss_finish(const double* ompart, int64_t nomp, const double* ypart, int64_t nyp,
                                double lam, double lam_d, double inv_n, double* out, cudaStream_t st);
@@ -143,7 +163,8 @@ struct PathDev {
   const double* lambdas;   // device, in solve order
   const double* n_obs;     // device, rows of each chain's subsample (the n of Eq. 3.7)
   double gamma, log_p;
-  int32_t penalize_diag, pad;
+  int32_t penalize_diag;
+  int32_t coarse;          // every penalty starts with one-product gradients (SolveParams::coarse_kkt > 0)
   PathRec* rec;            // device, n_lambda x nchains, record [k * nchains + c]
   double* best_epbic;      // device, per chain (initialised to +inf)
   int32_t* best_idx;       // device, per chain
@@ -201,6 +222,39 @@ struct SparseYParams {
   int32_t nprob;
   int64_t s_y, s_yk, s_xt, s_bkt;  // strides: Y (elements), planes, X^T, buckets
 };
+// Y of the current iterate formed afresh from Omega^t (mixed modes): for a
+// problem whose ctrl->refresh is set, Y[cur] and its operand planes become
+// Omega[cur] X^T (FP32, the nonzeros of Omega's occupancy bitmap in
+// ascending column order); part gets one row of kYSlots per 32-row group
+// (kYDiff2: ||Y_old - Y_new||^2, kYNorm2: ||Y_new||^2, kYBad).  A batch runs
+// grid y over problem slots with data at + b * stride.
+struct YRefreshParams {
+  const Ctrl* ctrl;
+  const float* om[2];      // Omega buffers (rows x ldo FP32), index cur
+  const uint32_t* bm[2];   // their occupancy bitmaps (chunk-major, ldbm words a chunk)
+  float* y[2];             // Y (rows x ldy FP32)
+  void* y_hi[2];           // planes of Y (rows x ldyk, type ptype)
+  void* y_lo[2];
+  const float* xt;         // X^T, p x ldx FP32
+  int64_t rows, p, n, ldo, ldbm, ldy, ldyk, ldx;
+  double* part;
+  int32_t ptype, nprob;
+  const int32_t* active;
+  const int32_t* nactive;
+  int64_t s_om, s_bm, s_y, s_yk, s_xt, s_part;  // per-problem strides (elements / words / doubles)
+  double dense_nnz;        // off-diagonal nonzeros of Omega from which the blocked (dense) form runs
+};
+// Two kernels per call: the one-warp-a-row walk over Omega's nonzeros, and a
+// blocked product for a problem with at least dense_nnz nonzeros; each
+// problem takes exactly one of them.
+cudaError_t launch_y_refresh(const YRefreshParams& prm, cudaStream_t st);
+// Folds the refresh partials (ngroups rows of kYSlots per problem, s_part
+// doubles apart): y_drift = max(y_drift, sqrt(||Y_old - Y_new||^2 /
+// ||Y_new||^2)); with update_g, g and f of the iterate from ||Y_new||^2; then
+// clears refresh and since_refresh.  One block per problem slot.
+cudaError_t launch_y_refresh_fold(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                  const double* part, int64_t ngroups, int64_t s_part, int update_g,
+                                  cudaStream_t st);
 size_t sparse_y_smem_bytes(int cap);
 cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st);
 cudaError_t sparse_y_prepare();  // one-time shared-memory opt-in (before a graph capture)
@@ -213,7 +267,7 @@ cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float*
                                 const uint32_t* bm1, int64_t p, int64_t ld, void* hi, void* lo, int64_t ldk, int pt,
                                 cudaStream_t st, int32_t nprob = 1, const int32_t* active = nullptr,
                                 const int32_t* nactive = nullptr, int64_t s_om = 0, int64_t s_pl = 0,
-                                const int* any_dense = nullptr, int64_t s_bm = 0);
+                                const int* any_dense = nullptr, int64_t s_bm = 0, int64_t rows = -1);
 // X^T in FP32 (p x ldxt).
 cudaError_t launch_transpose_x_f32(const float* X, int64_t n, int64_t p, float* XT, int64_t ldxt, cudaStream_t st);
 

@@ -126,28 +126,30 @@ __global__ void transpose_x_f32_kernel(const float* __restrict__ X, int64_t n, i
 // Row-parallel: a block takes rows r, r + gridDim.x, ..., its threads sweep
 // the row's columns contiguously (no index division per element).
 template <class T>
-__global__ void set_identity_kernel(T* __restrict__ Om, int64_t p, int64_t ld) {
-  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+__global__ void set_identity_kernel(T* __restrict__ Om, int64_t rows, int64_t ld, int64_t row0) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     T* row = Om + r * ld;
-    for (int64_t c = threadIdx.x; c < ld; c += blockDim.x) row[c] = (r == c) ? T(1) : T(0);
+    for (int64_t c = threadIdx.x; c < ld; c += blockDim.x) row[c] = (r + row0 == c) ? T(1) : T(0);
   }
 }
 
-// Occupancy bitmap of Omega = I: word (c, i) = c * ldbm + i holds the bit of
-// the diagonal entry (i, i) when column i falls in chunk c.
-__global__ void identity_bitmap_kernel(uint32_t* __restrict__ bm, int64_t p, int64_t ldbm, int64_t nwords) {
+// Occupancy bitmap of Omega = I (rows row0 .. row0 + rows of it): word
+// (c, i) = c * ldbm + i holds the bit of the diagonal entry (i, i + row0)
+// when column i + row0 falls in chunk c.
+__global__ void identity_bitmap_kernel(uint32_t* __restrict__ bm, int64_t rows, int64_t row0, int64_t ldbm,
+                                       int64_t nwords) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nwords; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = k / ldbm, i = k - c * ldbm;
-    bm[k] = (i < p && (i >> 5) == c) ? (1u << (i & 31)) : 0u;
+    const int64_t c = k / ldbm, i = k - c * ldbm, j = i + row0;
+    bm[k] = (i < rows && (j >> 5) == c) ? (1u << (j & 31)) : 0u;
   }
 }
 
-// Occupancy bitmap of a dense FP32 matrix: one warp per 32 x 32 block, one
-// ballot per row, and lane r stores the word of row r.
-__global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t p, int64_t ld, uint32_t* __restrict__ bm,
-                                         int64_t ldbm) {
+// Occupancy bitmap of a dense FP32 rows x cols matrix: one warp per 32 x 32
+// block, one ballot per row, and lane r stores the word of row r.
+__global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t rows, int64_t cols, int64_t ld,
+                                         uint32_t* __restrict__ bm, int64_t ldbm) {
   const int lane = threadIdx.x & 31;
-  const int64_t nch = (p + 31) / 32, nblk = nch * nch;
+  const int64_t nch = (cols + 31) / 32, nrb = (rows + 31) / 32, nblk = nch * nrb;
   const int64_t wpb = blockDim.x / 32;
   for (int64_t blk = blockIdx.x * wpb + threadIdx.x / 32; blk < nblk; blk += (int64_t)gridDim.x * wpb) {
     const int64_t rb = blk / nch, c = blk - rb * nch;
@@ -155,7 +157,7 @@ __global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t p
     uint32_t mine = 0u;
     for (int r = 0; r < 32; ++r) {
       const int64_t row = rb * 32 + r;
-      const bool nz = row < p && col < p && Om[row * ld + col] != 0.f;
+      const bool nz = row < rows && col < cols && Om[row * ld + col] != 0.f;
       const uint32_t w = __ballot_sync(0xffffffffu, nz);
       if (lane == r) mine = w;
     }
@@ -166,8 +168,8 @@ __global__ void bitmap_from_dense_kernel(const float* __restrict__ Om, int64_t p
 // Dense copy of a mixed-mode iterate buffer: its value where its occupancy
 // bitmap has a bit, 0 elsewhere (the buffer's other entries are not read).
 __global__ void copy_omega_masked_kernel(const float* __restrict__ src, int64_t lds, const uint32_t* __restrict__ bm,
-                                         int64_t ldbm, float* __restrict__ dst, int64_t ldd, int64_t p) {
-  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+                                         int64_t ldbm, float* __restrict__ dst, int64_t ldd, int64_t rows, int64_t p) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const float* s = src + r * lds;
     float* d = dst + r * ldd;
     for (int64_t c = threadIdx.x; c < p; c += blockDim.x) {
@@ -179,8 +181,8 @@ __global__ void copy_omega_masked_kernel(const float* __restrict__ src, int64_t 
 
 template <class T>
 __global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
-                                  int64_t ldd, int64_t p) {
-  for (int64_t r = blockIdx.x; r < p; r += gridDim.x) {
+                                  int64_t ldd, int64_t rows, int64_t p) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const T* s = src + r * lds;
     T* d = dst + r * ldd;
     for (int64_t c = threadIdx.x; c < p; c += blockDim.x) d[c] = s[c];
@@ -191,13 +193,13 @@ __global__ void copy_omega_kernel(const T* __restrict__ src, int64_t lds, T* __r
 // count (non-finite entry, or omega_ii <= 0).
 template <class T>
 __global__ void omega_stats_kernel(const T* __restrict__ Om, int64_t p, int64_t ld,
-                                   double* __restrict__ part) {
-  const int64_t r = blockIdx.x;
+                                   double* __restrict__ part, int64_t row0) {
+  const int64_t r = blockIdx.x, rd = r + row0;  // rd: this row's diagonal column
   double l1 = 0.0, nnz = 0.0, bad = 0.0;
   for (int64_t c = threadIdx.x; c < p; c += blockDim.x) {
     const double v = (double)Om[r * ld + c];
     if (!isfinite(v)) bad += 1.0;
-    if (c != r) {
+    if (c != rd) {
       l1 += fabs(v);
       nnz += (v != 0.0) ? 1.0 : 0.0;
     }
@@ -212,7 +214,7 @@ __global__ void omega_stats_kernel(const T* __restrict__ Om, int64_t p, int64_t 
   if (threadIdx.x == 0) {
     double a = 0, b = 0, c = 0;
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
-    const double d = (double)Om[r * ld + r];
+    const double d = (double)Om[r * ld + rd];
     if (!(d > 0.0)) c += 1.0;
     double* o = part + r * kProxSlots;
     o[kPDelta2] = 0.0;
@@ -501,6 +503,14 @@ __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp,
   c.trials = 0;
   c.cur = 0;
   c.done = 0;
+  c.refresh = 0;
+  c.since_refresh = 0;
+  c.n_refresh = 0;
+  c.cut_trials = 0;
+  c.y_drift = 0.0;
+  c.kkt_prev = INFINITY;
+  c.coarse = sp.coarse_kkt > 0.0 ? 1 : 0;
+  c.n_coarse = 0;
   c.status = kNotConverged;
   c.lam = sp.lam;
   c.lam_d = sp.lam_d;
@@ -533,10 +543,25 @@ __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp,
 // step the KKT residual of Omega^t decides convergence (it needs G(Omega^t),
 // which this GEMM has just formed); otherwise record the trial's sums.
 __device__ void post_prox_update(Ctrl& c, const double (&s)[kProxSlots], const SolveParams& sp, double* trace) {
+  const bool coarse = c.coarse != 0;
+  if (coarse) c.n_coarse += 1;
   if (c.k == 0) {
+    c.kkt_prev = c.kkt;
     c.kkt = s[kPKkt];
     trace_put(trace, sp.trace_cap, c.t, 1, c.kkt);
-    if (c.kkt <= sp.kkt_tol) {
+    // a residual from the one-product gradient never ends the fit: under the
+    // threshold (or the tolerance), or once it stops falling (the one
+    // product's own error floor), the next launches form G with the three
+    // split products
+    if (coarse && (c.kkt <= sp.coarse_kkt || c.kkt <= sp.kkt_tol || !(c.kkt < c.kkt_prev))) c.coarse = 0;
+    if (!coarse && c.kkt <= sp.kkt_tol) {
+      if (sp.y_refresh > 0 && c.since_refresh > 0) {
+        // the residual came from a Y carried forward by updates: form Y
+        // afresh from Omega^t and test again, cutting this trial short
+        c.refresh = 1;
+        c.cut_trials += 1;
+        return;
+      }
       c.done = 1;
       c.status = kOk;
       return;
@@ -570,6 +595,7 @@ __device__ void post_prox_update(Ctrl& c, const double (&s)[kProxSlots], const S
 // g is quadratic), or the tau <= 1/L floor; accept or backtrack.
 __device__ void decide_update(Ctrl& c, const double (&s)[kYSlots], const SolveParams& sp, double* trace) {
   c.dense = 0;
+  if (c.refresh) return;  // a trial cut short for a refresh of Y decides nothing
   c.trials += 1;
   if (s[kYBad] > 0.0) {
     c.done = 1;
@@ -599,6 +625,14 @@ __device__ void decide_update(Ctrl& c, const double (&s)[kYSlots], const SolvePa
     c.tau_prev = c.tau;
     c.k = 0;
     c.tau = sp.tau_warm ? fmin(c.tau0, c.tau / sp.beta) : c.tau0;
+    c.since_refresh += 1;
+    if (sp.y_refresh > 0) {
+      // due, or ahead of a step whose KKT test is expected to pass (the last
+      // ratio of residuals carried one step on): a refresh then saves the
+      // trial that a passing test on a carried Y would have to cut short
+      const double rate = (isfinite(c.kkt_prev) && c.kkt_prev > c.kkt) ? c.kkt / c.kkt_prev : 1.0;
+      if (c.since_refresh >= sp.y_refresh || c.kkt * rate <= sp.kkt_tol) c.refresh = 1;
+    }
   } else {
     c.k += 1;
     if (c.k > sp.max_backtracks) {
@@ -618,6 +652,54 @@ __global__ void post_prox_kernel(Ctrl* ctrl, const double* part, int64_t ntiles,
   if (threadIdx.x == 0) post_prox_update(*ctrl, s, sp, trace);
 }
 
+// ----------------------------------------------- row blocks of one fit --
+// The objective separates over the rows of Omega (the row-wise form in the
+// proof of Thm 3.2), so a fit can be split into blocks of rows that share
+// only Algorithm 1's scalars.  A block folds its own trial sums here (out:
+// the kProxSlots prox sums, then the kYSlots sums of whichever Y update ran)
+// for the caller's exchange over all blocks; decide_global_kernel then takes
+// the decisions of post_prox_update and decide_update on the sums over all
+// blocks, so every block takes the same ones.
+__global__ void fold_block_kernel(const Ctrl* ctrl, const double* prox_part, int64_t nprox, const double* y_part,
+                                  int64_t ny, int* bucket_counts, int nbuckets, const double* part_sparse,
+                                  unsigned long long* delta_entries, double* out) {
+  if (ctrl->done) return;
+  double s[kProxSlots], y[kYSlots];
+  fold_partials<kProxSlots>(prox_part, nprox, 1u << kPKkt, s);
+  const bool sparse_ran = part_sparse != nullptr && !ctrl->dense;
+  fold_partials<kYSlots>(sparse_ran ? part_sparse : y_part, sparse_ran ? nbuckets : ny, 0u, y);
+  unsigned long long cnt = 0;
+  for (int i = threadIdx.x; bucket_counts != nullptr && i < nbuckets; i += blockDim.x) {
+    if (sparse_ran) cnt += (unsigned long long)bucket_counts[i];
+    bucket_counts[i] = 0;
+  }
+  if (delta_entries != nullptr && sparse_ran) {
+    __shared__ unsigned long long red[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+      *delta_entries += t;
+    }
+  }
+  if (threadIdx.x < kProxSlots) out[threadIdx.x] = s[threadIdx.x];
+  if (threadIdx.x < kYSlots) out[kProxSlots + threadIdx.x] = y[threadIdx.x];
+}
+
+__global__ void decide_global_kernel(Ctrl* ctrl, const double* g, SolveParams sp, double* trace) {
+  if (threadIdx.x != 0 || ctrl->done) return;
+  double s[kProxSlots], y[kYSlots];
+#pragma unroll
+  for (int q = 0; q < kProxSlots; ++q) s[q] = g[q];
+#pragma unroll
+  for (int q = 0; q < kYSlots; ++q) y[q] = g[kProxSlots + q];
+  post_prox_update(*ctrl, s, sp, trace);
+  if (!ctrl->done) decide_update(*ctrl, y, sp, trace);
+}
+
 __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, SolveParams sp,
                               double* trace, int* bucket_counts, int nbuckets, const double* part_sparse,
                               unsigned long long* delta_entries) {
@@ -630,7 +712,7 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
   // Delta entries the sparse update applied in this trial (none overflowed
   // when it ran), then empty buckets for the next trial's prox epilogue
   unsigned long long cnt = 0;
-  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) {
+  for (int i = threadIdx.x; bucket_counts != nullptr && i < nbuckets; i += blockDim.x) {
     if (sparse_ran) cnt += (unsigned long long)bucket_counts[i];
     bucket_counts[i] = 0;
   }
@@ -647,6 +729,39 @@ __global__ void decide_kernel(Ctrl* ctrl, const double* part, int64_t ntiles, So
     }
   }
   if (threadIdx.x == 0) decide_update(*ctrl, s, sp, trace);
+}
+
+// After y_refresh_kernel: the drift it found and, for a whole fit, g and f
+// of the iterate from the Y formed afresh (a row block leaves them: its
+// ||Y||^2 covers its own rows only).  Then the trial that follows tests the
+// KKT residual on the new Y.
+__global__ void y_refresh_fold_kernel(Ctrl* ctrl, const int32_t* active, const int32_t* nactive, const double* part,
+                                      int64_t ngroups, int64_t s_part, int update_g) {
+  int b = blockIdx.x;
+  if (active != nullptr) {
+    if (b >= *nactive) return;
+    b = active[b];
+  }
+  Ctrl& c = ctrl[b];
+  if (c.done || !c.refresh) return;
+  double s[kYSlots];
+  fold_partials<kYSlots>(part + b * s_part, ngroups, 0u, s);
+  if (threadIdx.x != 0) return;
+  const double y2 = s[kYNorm2];
+  const double drift = y2 > 0.0 ? sqrt(s[kYDiff2] / y2) : (s[kYDiff2] > 0.0 ? INFINITY : 0.0);
+  c.y_drift = fmax(c.y_drift, drift);
+  if (s[kYBad] > 0.0) {
+    c.done = 1;
+    c.status = kEnonfinite;
+    return;
+  }
+  if (update_g) {
+    c.g = 0.5 * y2 * c.inv_n;
+    c.f = c.g - c.logdiag + c.lam * c.l1off + c.lam_d * c.diagsum;
+  }
+  c.refresh = 0;
+  c.since_refresh = 0;
+  c.n_refresh += 1;
 }
 
 // ------------------------------------------------------- batched control --
@@ -673,7 +788,8 @@ __global__ void decide_batch_kernel(Ctrl* ctrl, const int32_t* active, const int
   Ctrl& c = ctrl[b];
   // every problem of the trial starts the next one with empty Delta buckets,
   // including one whose fit ended in this trial (its prox already filled them)
-  for (int i = threadIdx.x; i < nbuckets; i += blockDim.x) bucket_counts[(int64_t)b * nbuckets + i] = 0;
+  for (int i = threadIdx.x; bucket_counts != nullptr && i < nbuckets; i += blockDim.x)
+    bucket_counts[(int64_t)b * nbuckets + i] = 0;
   if (c.done) {
     if (threadIdx.x == 0) c.dense = 0;
     return;
@@ -721,6 +837,14 @@ __global__ void batch_ctrl_init_kernel(PathDev pd, const T* __restrict__ yt0, in
     yb += sh[1][w];
   }
   Ctrl& C = pd.ctrl[c];
+  C.refresh = 0;
+  C.since_refresh = 0;
+  C.n_refresh = 0;
+  C.cut_trials = 0;
+  C.y_drift = 0.0;
+  C.kkt_prev = INFINITY;
+  C.coarse = sp.coarse_kkt > 0.0 ? 1 : 0;
+  C.n_coarse = 0;
   C.L = L_given > 0.0 ? L_given : C.pw_est;
   C.inv_L = C.L > 0.0 ? 1.0 / C.L : INFINITY;
   C.tau0 = sp.tau0 > 0.0 ? sp.tau0 : C.inv_L;
@@ -758,7 +882,8 @@ __global__ void path_advance_kernel(PathDev pd) {
     r.status = C.status;
     r.iters = C.t;
     r.trials = C.trials;
-    r.reserved0 = 0;
+    r.y_refreshes = C.n_refresh;
+    r.y_drift = C.y_drift;
     r.lambda = pd.lambdas[k];
     r.f = C.f;
     r.g = C.g;
@@ -792,6 +917,11 @@ __global__ void path_advance_kernel(PathDev pd) {
       C.kkt = INFINITY;
       C.status = kNotConverged;
       C.done = 0;
+      C.n_refresh = 0;
+      C.cut_trials = 0;
+      C.y_drift = 0.0;
+      C.kkt_prev = INFINITY;
+      C.coarse = pd.coarse;
     } else {
       // the chain ends here; an error also ends the penalties after it
       for (int q = k + 1; q < pd.n_lambda; ++q) {
@@ -901,51 +1031,59 @@ cudaError_t launch_convert_x_planes(const float* X32, int64_t n, int64_t p, void
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st) {
-  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
-  if (is_f64) set_identity_kernel<double><<<g, 512, 0, st>>>((double*)Om, p, ld);
-  else set_identity_kernel<float><<<g, 512, 0, st>>>((float*)Om, p, ld);
+cudaError_t launch_set_identity(void* Om, int is_f64, int64_t p, int64_t ld, cudaStream_t st, int64_t rows,
+                                int64_t row0) {
+  if (rows < 0) rows = p;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 16));
+  if (is_f64) set_identity_kernel<double><<<g, 512, 0, st>>>((double*)Om, rows, ld, row0);
+  else set_identity_kernel<float><<<g, 512, 0, st>>>((float*)Om, rows, ld, row0);
   return cudaGetLastError();
 }
 
-int64_t bitmap_ld(int64_t p) { return (p + 31) / 32 * 32; }
-int64_t bitmap_words(int64_t p) { return (p + 31) / 32 * bitmap_ld(p); }
+int64_t bitmap_ld(int64_t rows) { return (rows + 31) / 32 * 32; }
+int64_t bitmap_words(int64_t rows, int64_t cols) { return (cols + 31) / 32 * bitmap_ld(rows); }
+int64_t bitmap_words(int64_t p) { return bitmap_words(p, p); }
 
-cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st) {
-  const int64_t nw = bitmap_words(p);
-  identity_bitmap_kernel<<<grid_for(nw, 256), 256, 0, st>>>(bm, p, bitmap_ld(p), nw);
+cudaError_t launch_identity_bitmap(uint32_t* bm, int64_t p, cudaStream_t st, int64_t rows, int64_t row0) {
+  if (rows < 0) rows = p;
+  const int64_t nw = bitmap_words(rows, p);
+  identity_bitmap_kernel<<<grid_for(nw, 256), 256, 0, st>>>(bm, rows, row0, bitmap_ld(rows), nw);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st) {
-  const int64_t nch = (p + 31) / 32;
-  const int64_t blocks = (nch * nch + 7) / 8;
-  bitmap_from_dense_kernel<<<(unsigned)std::min<int64_t>(blocks, 152 * 32), 256, 0, st>>>(Om, p, ld, bm,
-                                                                                           bitmap_ld(p));
+cudaError_t launch_bitmap_from_dense(const float* Om, int64_t p, int64_t ld, uint32_t* bm, cudaStream_t st,
+                                     int64_t rows) {
+  if (rows < 0) rows = p;
+  const int64_t blocks = ((p + 31) / 32 * ((rows + 31) / 32) + 7) / 8;
+  bitmap_from_dense_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 32)), 256, 0, st>>>(
+      Om, rows, p, ld, bm, bitmap_ld(rows));
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_omega_masked(const float* src, int64_t lds, const uint32_t* bm, float* dst, int64_t ldd,
-                                     int64_t p, cudaStream_t st) {
-  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
-  copy_omega_masked_kernel<<<g, 512, 0, st>>>(src, lds, bm, bitmap_ld(p), dst, ldd, p);
+                                     int64_t p, cudaStream_t st, int64_t rows) {
+  if (rows < 0) rows = p;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 16));
+  copy_omega_masked_kernel<<<g, 512, 0, st>>>(src, lds, bm, bitmap_ld(rows), dst, ldd, rows, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_omega(const void* src, int64_t lds, void* dst, int64_t ldd, int is_f64,
-                              int64_t p, cudaStream_t st) {
-  const unsigned g = (unsigned)std::min<int64_t>(p, 152 * 16);
-  if (is_f64) copy_omega_kernel<double><<<g, 512, 0, st>>>((const double*)src, lds, (double*)dst, ldd, p);
-  else copy_omega_kernel<float><<<g, 512, 0, st>>>((const float*)src, lds, (float*)dst, ldd, p);
+                              int64_t p, cudaStream_t st, int64_t rows) {
+  if (rows < 0) rows = p;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 16));
+  if (is_f64) copy_omega_kernel<double><<<g, 512, 0, st>>>((const double*)src, lds, (double*)dst, ldd, rows, p);
+  else copy_omega_kernel<float><<<g, 512, 0, st>>>((const float*)src, lds, (float*)dst, ldd, rows, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_omega_stats(const void* Om, int is_f64, int64_t p, int64_t ld, double* part,
-                               int64_t* nparts, cudaStream_t st) {
-  if (p > 2147483647LL) return cudaErrorInvalidValue;
-  if (is_f64) omega_stats_kernel<double><<<(unsigned)p, 256, 0, st>>>((const double*)Om, p, ld, part);
-  else omega_stats_kernel<float><<<(unsigned)p, 256, 0, st>>>((const float*)Om, p, ld, part);
-  *nparts = p;
+                               int64_t* nparts, cudaStream_t st, int64_t rows, int64_t row0) {
+  if (rows < 0) rows = p;
+  if (rows > 2147483647LL || rows < 1) return cudaErrorInvalidValue;
+  if (is_f64) omega_stats_kernel<double><<<(unsigned)rows, 256, 0, st>>>((const double*)Om, p, ld, part, row0);
+  else omega_stats_kernel<float><<<(unsigned)rows, 256, 0, st>>>((const float*)Om, p, ld, part, row0);
+  *nparts = rows;
   return cudaGetLastError();
 }
 
@@ -991,6 +1129,15 @@ cudaError_t launch_ctrl_init(Ctrl* ctrl, const double* ompart, int64_t nomp, con
   return cudaGetLastError();
 }
 
+cudaError_t launch_y_refresh_fold(Ctrl* ctrl, int32_t nprob, const int32_t* active, const int32_t* nactive,
+                                  const double* part, int64_t ngroups, int64_t s_part, int update_g,
+                                  cudaStream_t st) {
+  if (nprob < 1 || nprob > 65535) return cudaErrorInvalidConfiguration;
+  y_refresh_fold_kernel<<<(unsigned)nprob, kRedThreads, 0, st>>>(ctrl, active, nactive, part, ngroups, s_part,
+                                                                 update_g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, const SolveParams& sp,
                              double* trace, double* fold_scratch, cudaStream_t st) {
   if (fold_scratch != nullptr && ntiles > 4 * kFoldChunks) {
@@ -1002,6 +1149,30 @@ cudaError_t launch_post_prox(Ctrl* ctrl, const double* part, int64_t ntiles, con
   } else {
     post_prox_kernel<<<1, kRedThreads, 0, st>>>(ctrl, part, ntiles, sp, trace);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_block(Ctrl* ctrl, const double* prox_part, int64_t ntiles_prox, double* fold_scratch,
+                              const double* y_part, int64_t ntiles_y, int* bucket_counts, int nbuckets,
+                              const double* part_sparse, unsigned long long* delta_entries, double* out,
+                              cudaStream_t st) {
+  const double* pp = prox_part;
+  int64_t np = ntiles_prox;
+  if (fold_scratch != nullptr && ntiles_prox > 4 * kFoldChunks) {
+    const int64_t chunk = (ntiles_prox + kFoldChunks - 1) / kFoldChunks;
+    fold_stage1_kernel<kProxSlots><<<kFoldChunks, kRedThreads, 0, st>>>(ctrl, prox_part, ntiles_prox, chunk,
+                                                                         1u << kPKkt, fold_scratch);
+    pp = fold_scratch;
+    np = kFoldChunks;
+  }
+  fold_block_kernel<<<1, kRedThreads, 0, st>>>(ctrl, pp, np, y_part, ntiles_y, bucket_counts, nbuckets, part_sparse,
+                                               delta_entries, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide_global(Ctrl* ctrl, const double* sums, const SolveParams& sp, double* trace,
+                                 cudaStream_t st) {
+  decide_global_kernel<<<1, 32, 0, st>>>(ctrl, sums, sp, trace);
   return cudaGetLastError();
 }
 

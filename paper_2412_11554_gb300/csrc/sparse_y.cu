@@ -13,6 +13,8 @@
 // of Y+ (BF16 or TF32: the A operand of the next gradient GEMM) and the
 // per-block partial sums
 // ||Delta X^T||^2 and ||Y+||^2 for the line search of Algorithm 1.
+#include <mutex>
+
 #include "internal.h"
 
 namespace accord {
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
     b = prm.active[b];
   }
   const Ctrl* ctrl = prm.ctrl + b;
-  if (ctrl->done || ctrl->dense || ctrl->ymode) return;
+  if (ctrl->done || ctrl->dense || ctrl->ymode || ctrl->refresh) return;
   extern __shared__ uint8_t smem_raw[];
   const int mb = blockIdx.x;  // bucket = 32-row group
   const int cur = ctrl->cur, nxt = cur ^ 1;
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) sparse_y_kernel(SparseYParams prm) {
 
 // Dense fallback when a bucket overflowed: planes (type pt) of Delta = Omega+ - Omega.
 __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const float* om1, const uint32_t* bm0,
-                                    const uint32_t* bm1, int64_t ldbm, int64_t s_bm, int64_t p, int64_t ld,
+                                    const uint32_t* bm1, int64_t ldbm, int64_t s_bm, int64_t rows, int64_t p, int64_t ld,
                                     void* hi, void* lo, int64_t ldk, int pt, const int32_t* active,
                                     const int32_t* nactive, int64_t s_om, int64_t s_pl, const int* any_dense) {
   if (any_dense != nullptr && *any_dense == 0) return;
@@ -189,7 +191,7 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
   const float* Op = (ctrl->cur ? om0 : om1) + b * s_om;
   const uint32_t* Bm = (ctrl->cur ? bm1 : bm0) + b * s_bm;
   const uint32_t* Bp = (ctrl->cur ? bm0 : bm1) + b * s_bm;
-  const int64_t total = p * p;
+  const int64_t total = rows * p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / p, c = i % p;
     const int64_t wi = (c >> 5) * ldbm + r;
@@ -200,15 +202,236 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
   }
 }
 
+// Y of the current iterate formed afresh (mixed modes).  The sparse and
+// dense updates carry Y = Omega X^T forward as Y + Delta X^T in FP32, so
+// rounding accumulates over the steps of a fit (and over the penalties of a
+// path chain); every few steps, and before a KKT residual under the tolerance
+// may end the fit, this kernel recomputes
+//
+//     Y[i, :] = sum_{j : omega_ij != 0} omega_ij X^T[j, :]               (FP32)
+//
+// from the nonzeros of Omega^t (its occupancy bitmap), in ascending j, in
+// place of Y[cur] and its hi/lo operand planes.  One warp a row, the row's
+// output columns in registers (32 a lane, 1024 a pass); the bitmap words of a
+// row are read 32 chunks at a time and each nonzero is broadcast to the warp.
+// Per 32-row group it writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the
+// drift statistic and g.
+constexpr int kRfThreads = 256;
+constexpr int kRfColsPerLane = 32;
+constexpr int kRdMaxThreads = 512;
+
+// A dense iterate makes the one-warp-a-row walk gather one X^T row per entry
+// of Omega; from this many nonzeros on (YRefreshParams::dense_nnz, a few
+// percent of the entries) the refresh runs as a blocked product instead.
+__device__ __forceinline__ bool refresh_is_dense(const YRefreshParams& prm, const Ctrl& c) {
+  return c.nnz >= prm.dense_nnz;
+}
+
+template <int PT>
+__global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams prm) {
+  using E = typename Plane<PT>::E;
+  int b = blockIdx.y;
+  if (prm.active != nullptr) {
+    if (b >= *prm.nactive) return;
+    b = prm.active[b];
+  }
+  const Ctrl* ctrl = prm.ctrl + b;
+  if (ctrl->done || !ctrl->refresh || refresh_is_dense(prm, *ctrl)) return;
+  const int cur = ctrl->cur;
+  const float* __restrict__ Om = prm.om[cur] + b * prm.s_om;
+  const uint32_t* __restrict__ Bm = prm.bm[cur] + b * prm.s_bm;
+  float* __restrict__ Y = prm.y[cur] + b * prm.s_y;
+  E* __restrict__ Yh = static_cast<E*>(prm.y_hi[cur]) + b * prm.s_yk;
+  E* __restrict__ Yl = static_cast<E*>(prm.y_lo[cur]) + b * prm.s_yk;
+  const float* __restrict__ XT = prm.xt + b * prm.s_xt;
+  const int mb = blockIdx.x;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+  const int64_t nchunks = (prm.p + 31) / 32;
+  constexpr int kPass = 32 * kRfColsPerLane;
+  float s_d = 0.f, s_n = 0.f, chk = 0.f;
+  for (int rl = warp; rl < kBucketRows; rl += nwarps) {
+    const int64_t row = (int64_t)mb * kBucketRows + rl;
+    if (row >= prm.rows) break;
+    const float* om_row = Om + row * prm.ldo;
+    for (int64_t c0 = 0; c0 < prm.n; c0 += kPass) {
+      float acc[kRfColsPerLane];
+#pragma unroll
+      for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
+      const bool full = c0 + kPass <= prm.n;
+      for (int64_t g = 0; g < nchunks; g += 32) {
+        const uint32_t word = (g + lane < nchunks) ? Bm[(g + lane) * prm.ldbm + row] : 0u;
+        uint32_t live = __ballot_sync(0xffffffffu, word != 0u);
+        while (live != 0u) {
+          const int src = __ffs(live) - 1;
+          live &= live - 1u;
+          uint32_t bits = __shfl_sync(0xffffffffu, word, src);
+          while (bits != 0u) {
+            const int bit = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int64_t j = (g + src) * 32 + bit;
+            const float v = om_row[j];
+            const float* xr = XT + j * prm.ldx + c0 + lane;
+            if (full) {
+#pragma unroll
+              for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = fmaf(v, __ldg(xr + 32 * u), acc[u]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < kRfColsPerLane; ++u)
+                if (c0 + lane + 32 * u < prm.n) acc[u] = fmaf(v, __ldg(xr + 32 * u), acc[u]);
+            }
+          }
+        }
+      }
+      float* yr = Y + row * prm.ldy;
+      E* hr = Yh + row * prm.ldyk;
+      E* lr = Yl + row * prm.ldyk;
+#pragma unroll
+      for (int u = 0; u < kRfColsPerLane; ++u) {
+        const int64_t c = c0 + lane + 32 * u;
+        if (c < prm.n) {
+          const float yn = acc[u];
+          const float d = yn - yr[c];
+          s_d = fmaf(d, d, s_d);
+          s_n = fmaf(yn, yn, s_n);
+          chk = fmaf(yn, 0.f, chk);
+          yr[c] = yn;
+          E h, l;
+          Plane<PT>::split(yn, h, l);
+          hr[c] = h;
+          lr[c] = l;
+        }
+      }
+    }
+  }
+  __shared__ double red[kRfThreads / 32][3];
+  s_d = warp_sum_f(s_d);
+  s_n = warp_sum_f(s_n);
+  const float bad = __ballot_sync(0xffffffffu, chk != 0.f) ? 1.f : 0.f;
+  if (lane == 0) {
+    red[warp][0] = (double)s_d;
+    red[warp][1] = (double)s_n;
+    red[warp][2] = (double)bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < kYSlots) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    if (q < 3)
+      for (int w = 0; w < nwarps; ++w) v += red[w][q];
+    prm.part[b * prm.s_part + (int64_t)mb * kYSlots + q] = v;
+  }
+}
+
+// The refresh for a dense iterate: one CTA per 32-row group, thread t owning
+// output column c0 + t with the 32 rows' accumulators in registers.  Each
+// 32-column chunk of Omega (zeros where its bitmap has no bit) is staged in
+// shared memory, XOR-swizzled in 4-float granules, and every thread reads
+// its X^T entry of each of the chunk's columns once for all 32 rows.  The
+// sums run in ascending column order with zero terms adding exactly 0, so
+// the result is bit for bit that of y_refresh_kernel.
+template <int PT>
+__global__ void __launch_bounds__(kRdMaxThreads) y_refresh_dense_kernel(YRefreshParams prm) {
+  using E = typename Plane<PT>::E;
+  int b = blockIdx.y;
+  if (prm.active != nullptr) {
+    if (b >= *prm.nactive) return;
+    b = prm.active[b];
+  }
+  const Ctrl* ctrl = prm.ctrl + b;
+  if (ctrl->done || !ctrl->refresh || !refresh_is_dense(prm, *ctrl)) return;
+  const int cur = ctrl->cur;
+  const float* __restrict__ Om = prm.om[cur] + b * prm.s_om;
+  const uint32_t* __restrict__ Bm = prm.bm[cur] + b * prm.s_bm;
+  float* __restrict__ Y = prm.y[cur] + b * prm.s_y;
+  E* __restrict__ Yh = static_cast<E*>(prm.y_hi[cur]) + b * prm.s_yk;
+  E* __restrict__ Yl = static_cast<E*>(prm.y_lo[cur]) + b * prm.s_yk;
+  const float* __restrict__ XT = prm.xt + b * prm.s_xt;
+  __shared__ __align__(16) float W[32 * 32];  // W[j][r]: Omega[r0 + r][32 c + j]
+  __shared__ double red[kRdMaxThreads / 32][3];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int64_t nchunks = (prm.p + 31) / 32;
+  float s_d = 0.f, s_n = 0.f, chk = 0.f;
+  for (int64_t c0 = 0; c0 < prm.n; c0 += nt) {
+    const int64_t col = c0 + tid;
+    const bool cok = col < prm.n;
+    float acc[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+    for (int64_t c = 0; c < nchunks; ++c) {
+      __syncthreads();  // the last chunk's reads of W are done
+      for (int t = tid; t < 1024; t += nt) {
+        const int r = t >> 5, j = t & 31;
+        const int64_t row = r0 + r, cj = c * 32 + j;
+        float v = 0.f;
+        if (row < prm.rows && cj < prm.p && ((Bm[c * prm.ldbm + row] >> j) & 1u)) v = Om[row * prm.ldo + cj];
+        W[j * 32 + ((((r >> 2) ^ (j & 7))) << 2) + (r & 3)] = v;
+      }
+      __syncthreads();
+      if (cok) {
+        const int jn = (int)(prm.p - c * 32 < 32 ? prm.p - c * 32 : 32);
+        for (int j = 0; j < jn; ++j) {
+          const float x = __ldg(XT + (c * 32 + j) * prm.ldx + col);
+          const float4* wj = reinterpret_cast<const float4*>(W + j * 32);
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const float4 w4 = wj[g ^ (j & 7)];
+            acc[4 * g + 0] = fmaf(w4.x, x, acc[4 * g + 0]);
+            acc[4 * g + 1] = fmaf(w4.y, x, acc[4 * g + 1]);
+            acc[4 * g + 2] = fmaf(w4.z, x, acc[4 * g + 2]);
+            acc[4 * g + 3] = fmaf(w4.w, x, acc[4 * g + 3]);
+          }
+        }
+      }
+    }
+    if (cok) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const int64_t row = r0 + r;
+        if (row < prm.rows) {
+          float* yp = Y + row * prm.ldy + col;
+          const float yn = acc[r];
+          const float d = yn - *yp;
+          s_d = fmaf(d, d, s_d);
+          s_n = fmaf(yn, yn, s_n);
+          chk = fmaf(yn, 0.f, chk);
+          *yp = yn;
+          E h, l;
+          Plane<PT>::split(yn, h, l);
+          Yh[row * prm.ldyk + col] = h;
+          Yl[row * prm.ldyk + col] = l;
+        }
+      }
+    }
+  }
+  s_d = warp_sum_f(s_d);
+  s_n = warp_sum_f(s_n);
+  const float bad = __ballot_sync(0xffffffffu, chk != 0.f) ? 1.f : 0.f;
+  if (lane == 0) {
+    red[warp][0] = (double)s_d;
+    red[warp][1] = (double)s_n;
+    red[warp][2] = (double)bad;
+  }
+  __syncthreads();
+  if (tid < kYSlots) {
+    double v = 0.0;
+    if (tid < 3)
+      for (int w = 0; w < (nt >> 5); ++w) v += red[w][tid];
+    prm.part[b * prm.s_part + (int64_t)blockIdx.x * kYSlots + tid] = v;
+  }
+}
+
 }  // namespace
 
 size_t sparse_y_smem_bytes(int cap) { return (size_t)cap * (sizeof(uint32_t) + sizeof(float)); }
 
 cudaError_t sparse_y_prepare() {
+  static std::mutex mu;
   static int configured = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
   if (configured != dev) {
     e = cudaFuncSetAttribute(sparse_y_kernel<kPlaneBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
@@ -232,15 +455,35 @@ cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_y_refresh(const YRefreshParams& prm, cudaStream_t st) {
+  const unsigned nb = (unsigned)(prm.nprob > 1 ? prm.nprob : 1);
+  if (nb > 65535u) return cudaErrorInvalidConfiguration;
+  const int64_t groups = (prm.rows + kBucketRows - 1) / kBucketRows;
+  if (groups < 1 || groups > 2147483647LL) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)groups, nb);
+  // both forms are launched; each problem's nonzero count picks the one that works
+  const int64_t nd = (prm.n + 31) / 32 * 32;
+  const unsigned td = (unsigned)(nd < kRdMaxThreads ? nd : kRdMaxThreads);
+  if (prm.ptype == kPlaneTf32) {
+    y_refresh_kernel<kPlaneTf32><<<grid, kRfThreads, 0, st>>>(prm);
+    y_refresh_dense_kernel<kPlaneTf32><<<grid, td, 0, st>>>(prm);
+  } else {
+    y_refresh_kernel<kPlaneBf16><<<grid, kRfThreads, 0, st>>>(prm);
+    y_refresh_dense_kernel<kPlaneBf16><<<grid, td, 0, st>>>(prm);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_delta_planes(const Ctrl* ctrl, const float* om0, const float* om1, const uint32_t* bm0,
                                 const uint32_t* bm1, int64_t p, int64_t ld, void* hi, void* lo, int64_t ldk, int pt,
                                 cudaStream_t st, int32_t nprob, const int32_t* active, const int32_t* nactive,
-                                int64_t s_om, int64_t s_pl, const int* any_dense, int64_t s_bm) {
+                                int64_t s_om, int64_t s_pl, const int* any_dense, int64_t s_bm, int64_t rows) {
   const unsigned nb = (unsigned)(nprob > 1 ? nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
+  if (rows < 0) rows = p;
   const unsigned gx = nb > 1 ? 152u * 16u / nb + 1u : 152u * 16u;
-  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, bm0, bm1, bitmap_ld(p), s_bm, p, ld, hi, lo, ldk,
-                                                    pt, active, nactive, s_om, s_pl, any_dense);
+  delta_planes_kernel<<<dim3(gx, nb), 256, 0, st>>>(ctrl, om0, om1, bm0, bm1, bitmap_ld(rows), s_bm, rows, p, ld, hi,
+                                                    lo, ldk, pt, active, nactive, s_om, s_pl, any_dense);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct TcParams {
   // gated launch returns at once while *any_dense is clear (no problem needs
   // the dense product), instead of scanning every problem's tiles.
   int* any_dense;
+  int32_t coarse_ok;     // prox mode: form G with one product while ctrl[b].coarse is set
   int32_t max_pairs;     // persistent grid limit in CTA pairs (0: as many as fit at once)
   int32_t ptype;         // plane type of the operands and plane outputs: kPlaneBf16 / kPlaneTf32
   // Occupancy bitmaps of the two iterate buffers (prox mode): word
@@ -73,6 +74,10 @@ struct TcParams {
   // bitmap of Omega+.  A batch keeps one pair per problem, s_bm words apart.
   uint32_t* bm[2];
   int64_t ldbm, s_bm;
+  // Row block of Omega (prox / grad modes): output row r is row r + row_off
+  // of the full matrix, so its diagonal entry sits in column r + row_off
+  // (a multiple of 32, so that the diagonal crosses whole 32 x 32 blocks).
+  int64_t row_off;
   // Bounded waits: every mbarrier wait of the launch gives up after wait_ns
   // (set from the process-wide limit, 4 s by default).  withhold_first: the
   // producers of both CTAs of the first pair skip the copies of their first

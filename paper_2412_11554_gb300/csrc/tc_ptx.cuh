@@ -149,6 +149,7 @@ __device__ __forceinline__ void cp_async16_hint(uint32_t dst, const void* src, u
                : "memory");
 }
 
+// 4-byte copy (cp.async.ca: the .cg form takes 16 bytes only)
 __device__ __forceinline__ void cp_async4_hint(uint32_t dst, const void* src, uint64_t pol) {
   asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "l"(pol)
                : "memory");

@@ -95,6 +95,40 @@ def test_implicit_derivative_matches_oracle(A):
     assert abs(d0 - d0_ref) <= 1e-10 * max(1.0, abs(d0_ref))
 
 
+def test_implicit_derivative_large_active_sets(A):
+    """Rows whose active set exceeds the 128 entries of the shared-memory
+    solve go to the second pass, whose systems sit in the workspace: a nearly
+    dense estimate (p = 300, n = 600, lambda = 0.01) against the oracle in FP64
+    mode and, on the same estimate in FP32, the mixed mode against FP64.  An
+    active set over 1024 entries is refused with EUNSUPPORTED."""
+    from paper_2412_11554_gb300 import accord
+    rng = np.random.Generator(np.random.PCG64(77))
+    X = rng.standard_normal((600, 300)).astype(np.float32)
+    Xv = rng.standard_normal((100, 300)).astype(np.float32)
+    lam = 0.01
+    r = R.fit(X, lam, kkt_tol=1e-10, max_iter=20000)
+    assert r.status == R.OK
+    m = (r.Omega != 0).sum(axis=1)
+    assert m.max() > 128 and m.min() <= 300
+    d_ref, dO_ref = R.implicit_dloglam(r.Omega, X, Xv, lam)
+    d, lv, dO = A.accord_dloss_dloglam(dev(X), dev(Xv), dev(r.Omega, torch.float64), lam, want_domega=True)
+    assert abs(d - d_ref) <= 1e-9 * max(1.0, abs(d_ref)), (d, d_ref)
+    assert np.max(np.abs(dO.cpu().numpy() - dO_ref)) <= 1e-9 * max(1.0, np.max(np.abs(dO_ref)))
+    O32 = dev(r.Omega, torch.float32)
+    d32, _, _ = A.accord_dloss_dloglam(dev(X), dev(Xv), O32, lam)
+    d64, _, _ = A.accord_dloss_dloglam(dev(X), dev(Xv), O32.double(), lam)
+    assert abs(d32 - d64) <= 1e-3 * abs(d64), (d32, d64)
+    # 1100 active entries in every row
+    p = 1100
+    Ob = np.full((p, p), 1e-3)
+    np.fill_diagonal(Ob, 1.0)
+    Xb = rng.standard_normal((40, p)).astype(np.float32)
+    with pytest.raises(accord.AccordError) as e:
+        A.accord_dloss_dloglam(dev(Xb), dev(Xb), dev(Ob, torch.float64), 0.1)
+    assert e.value.status == accord.EUNSUPPORTED
+    assert "1024" in accord.accord_last_error()
+
+
 def test_mixed_derivative_matches_fp64_on_same_estimate(A):
     """The mixed mode (tensor-core S and held-out products) against the FP64
     mode on the same FP32 estimate (p = 2000)."""

@@ -204,6 +204,37 @@ def test_mixed_fit_matches_oracle(A):
     assert R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam) <= 1e-4
 
 
+def test_precision_schedule(A):
+    """While the KKT residual is above opts.coarse_kkt (default 5e-3) the prox
+    GEMM forms G with the one product hi x hi; the first residual under it
+    switches to the three split products, and no fit ends on a one-product
+    residual.  The schedule and three products throughout reach the oracle's
+    estimate alike; so does a threshold below the tolerance (the switch then
+    comes when the one-product residual stops falling), and one above every
+    residual (three products from the second launch)."""
+    w = workload("scalefree", p=600, n=400)
+    ref = R.fit(w.X, w.lam, kkt_tol=1e-7, max_iter=3000)
+    X = dev(w.X)
+    Xd = w.X.astype(np.float64)
+    runs = {}
+    for ck in (5e-3, 0.0, 1e-9, 1e3):
+        Om, st = A.accord_fit(X, w.lam, precision="mixed", kkt_tol=2e-5, max_iter=3000, coarse_kkt=ck)
+        assert st.status == 0, (ck, st)
+        O = Om.double().cpu().numpy()
+        assert rel_fro(O, ref.Omega) <= 1e-4, ck
+        assert R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam) <= 1e-4, ck
+        runs[ck] = st
+    print({ck: (st.iters, st.trials, st.coarse_prox) for ck, st in runs.items()})
+    assert runs[0.0].coarse_prox == 0
+    assert runs[1e3].coarse_prox == 1
+    assert 1 <= runs[5e-3].coarse_prox < runs[5e-3].n_prox_gemm
+    assert 1 <= runs[1e-9].coarse_prox < runs[1e-9].n_prox_gemm
+    # TF32 planes take the same schedule
+    Ot, stt = A.accord_fit(X, w.lam, precision="tf32x3", kkt_tol=1e-6, max_iter=3000)
+    assert stt.status == 0 and stt.coarse_prox >= 1
+    assert rel_fro(Ot.double().cpu().numpy(), ref.Omega) <= 1e-5
+
+
 def test_mixed_fit_ragged_sizes(A):
     for kind, p, n in (("hubblock", 400, 130), ("er", 77, 45)):
         w = workload(kind, p=p, n=n)

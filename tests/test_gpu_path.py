@@ -143,6 +143,14 @@ def test_full_size_path_properties(A):
     # every estimate converges inside the iteration limit (the slowest needs
     # about 1500 steps, at the smallest penalty)
     assert out.status == 0 and np.all(out.entry_status == 0), out.entry_status
+    # the chain with the most steps carries Y longest: the drift every refresh
+    # of Y found along it (and along every other chain) stays under 1e-6
+    steps = out.iters.sum(axis=0)
+    longest = int(np.argmax(steps))
+    print(f"longest chain: {steps[longest]} steps, {out.y_refreshes[:, longest].sum()} refreshes, "
+          f"max drift {out.y_drift[:, longest].max():.2e}; all chains {out.y_drift.max():.2e}")
+    assert out.y_drift[:, longest].max() <= 1e-6 and out.y_drift.max() <= 1e-6
+    assert out.y_refreshes[:, longest].sum() >= steps[longest] // 32
     X = np.asarray(pw.X, dtype=np.float64)
     p = X.shape[1]
     sup = out.support

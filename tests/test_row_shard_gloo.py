@@ -232,3 +232,180 @@ def _dropout_worker(rank, world, port, q):
     q.close()
     q.join_thread()
     os._exit(0)
+
+
+# ------------------------------------------------ the library's host entry ---
+# accord_fit_rows (include/accord.h) over gloo ranks: the binding and its
+# exchange helper (dist_exchange) run as shipped; the device side of the call is
+# played on the host by the oracle, following the library's calling protocol
+# (one exchange of the starting iterate's sums, then one per trial with the
+# current iterate's KKT residual as the maximum), so the test needs no GPU.
+
+SUMS = 9  # ||Delta||^2, sum log w+_ii, sum w+_ii, sum |w+_ij| (i != j), nnz, bad, ||Delta X^T||^2, ||Y+||^2, bad Y
+
+
+class OracleRowsLib:
+    """The two entry points accord_fit_rows needs, with the oracle's FP64
+    arithmetic on one block of rows in place of the kernels."""
+
+    def __init__(self):
+        self.exchanges = 0
+
+    def accord_default_opts(self, o_ref):
+        o = o_ref._obj
+        o.tau0, o.beta, o.max_iter, o.max_backtracks, o.kkt_tol, o.penalize_diag = 1.0, 0.5, 3000, 60, 1e-4, 1
+
+    def accord_fit_rows(self, Xp, n, p, row0, rows, lam, o_ref, cb, ctx, Omp, ws, ws_bytes, st_ref):
+        import ctypes
+        o, st = o_ref._obj, st_ref._obj
+        X = np.ctypeslib.as_array((ctypes.c_float * (n * p)).from_address(Xp)).reshape(n, p).astype(np.float64)
+        out = np.ctypeslib.as_array((ctypes.c_double * (rows * p)).from_address(Omp)).reshape(rows, p)
+        lam_d = lam if o.penalize_diag else 0.0
+        diag = (np.arange(rows), row0 + np.arange(rows))
+        sums, maxes = (ctypes.c_double * SUMS)(), (ctypes.c_double * 1)()
+
+        def block_sums(Om, Y, D, dY):
+            d = Om[diag]
+            off = Om.copy()
+            off[diag] = 0.0
+            return [float(np.sum(D * D)), float(np.sum(np.log(d))), float(d.sum()), float(np.abs(off).sum()),
+                    float(np.count_nonzero(off)), 0.0, float(np.sum(dY * dY)), float(np.sum(Y * Y)), 0.0]
+
+        def exchange(vals, kkt):
+            sums[:] = vals
+            maxes[0] = kkt
+            if cb(sums, SUMS, maxes, 1, ctx) != 0:
+                return None
+            self.exchanges += 1
+            return list(sums), maxes[0]
+
+        def objective(s):
+            return s[7] / (2.0 * n) - s[1] + lam * s[3] + lam_d * s[2]
+
+        L = R.lipschitz(X)
+        Om = np.zeros((rows, p))
+        Om[diag] = 1.0
+        Y = Om @ X.T
+        ex = exchange(block_sums(Om, Y, 0.0, 0.0), 0.0)
+        if ex is None:
+            return -6
+        f, nnz = objective(ex[0]), ex[0][4]
+        it = trials = 0
+        status = 1
+        while True:
+            G = Y @ X / n
+            kkt_loc = R.kkt_residual(Om, G, lam, lam_d, row0=row0)
+            tau, accepted = o.tau0, False
+            for k in range(o.max_backtracks + 1):
+                Op, Yp, _, _, _, _ = R.fbs_trial(Om, Y, G, X, tau, lam, lam_d, row0=row0)
+                ex = exchange(block_sums(Op, Yp, Op - Om, Yp - Y), kkt_loc)
+                if ex is None:
+                    return -6
+                s, kkt = ex
+                if k == 0 and (kkt <= o.kkt_tol or it >= o.max_iter):
+                    status = 0 if kkt <= o.kkt_tol else 1
+                    break
+                trials += 1
+                if s[6] / n <= s[0] / tau or tau <= 1.0 / L:
+                    accepted = True
+                    break
+                tau *= o.beta
+            if not accepted:
+                break
+            Om, Y = Op, Yp
+            f, nnz = objective(s), s[4]
+            it += 1
+        out[:] = Om
+        st.iters, st.trials, st.status, st.f, st.kkt, st.nnz_offdiag, st.L = it, trials, status, f, kkt, int(nnz), L
+        return status
+
+
+def _host_check(t, name, dtype, shape=None, ndim=None):
+    dts = dtype if isinstance(dtype, tuple) else (dtype,)
+    assert t.dtype in dts and (shape is None or tuple(t.shape) == tuple(shape)), name
+
+
+class _HostStream:
+    cuda_stream = 0
+
+
+def _binding_worker(rank, world, port, q, p, bounds, fail_rank):
+    import datetime
+
+    from paper_2412_11554_gb300 import accord
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    fake = OracleRowsLib()
+    accord.load_library = lambda path=None: fake
+    accord._check_tensor = _host_check
+    w = workload("ar1", p=p, n=60)
+    X = torch.as_tensor(w.X, dtype=torch.float32)
+    r0, r1 = bounds[rank]
+    exchange = accord.dist_exchange()
+    if rank == fail_rank:
+        calls = [0]
+
+        def exchange(sums, maxes, inner=exchange):
+            calls[0] += 1
+            if calls[0] == 5:
+                raise RuntimeError("exchange lost")
+            inner(sums, maxes)
+    try:
+        Om, st = accord.accord_fit_rows(X, w.lam, r0, r1 - r0, exchange, precision="fp64", kkt_tol=1e-9,
+                                        stream=_HostStream())
+        q.put((rank, "ok", Om.numpy(), (st.iters, st.trials, st.status, st.f, st.nnz_offdiag), fake.exchanges))
+    except Exception as e:  # the fit ended on this rank: report why
+        q.put((rank, "raised", type(e).__name__ + ": " + str(e), None, fake.exchanges))
+    q.close()
+    q.join_thread()
+    os._exit(0)  # a rank whose peer failed may hold a broken group; leave without a collective
+
+
+def _run_binding(world, p, bounds, fail_rank=-1):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_binding_worker, args=(r, world, port, q, p, bounds, fail_rank))
+             for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = {}
+    for _ in range(world):
+        r = q.get(timeout=240)
+        res[r[0]] = r[1:]
+    for pr in procs:
+        pr.join(timeout=60)
+    return res
+
+
+@pytest.mark.parametrize("world,p,bounds", [(2, 90, [(0, 64), (64, 90)]),
+                                            (3, 96, [(0, 32), (32, 64), (64, 96)])])
+def test_binding_exchange_over_gloo_reproduces_the_single_fit(world, p, bounds):
+    """accord_fit_rows on gloo ranks, one row block each (row0 a multiple of
+    32, a ragged last block for p = 90), with dist_exchange as the exchange:
+    every rank reports the global stats of the oracle's single fit, after the
+    same number of exchanges, and the gathered rows equal its estimate."""
+    res = _run_binding(world, p, bounds)
+    ref = R.fit(workload("ar1", p=p, n=60).X, workload("ar1", p=p, n=60).lam, kkt_tol=1e-9, max_iter=3000)
+    assert ref.status == R.OK
+    assert all(v[0] == "ok" for v in res.values()), res
+    Om = np.vstack([res[r][1] for r in range(world)])
+    assert len({res[r][3] for r in range(world)}) == 1  # exchanges
+    for r in range(world):
+        iters, trials, status, f, nnz = res[r][2]
+        assert status == 0 and iters == ref.iters and trials == ref.trials
+        assert abs(f - ref.f[-1]) <= 1e-12 * abs(ref.f[-1])
+        assert nnz == ref.nnz[-1]
+    assert np.linalg.norm(Om - ref.Omega) <= 1e-11 * np.linalg.norm(ref.Omega)
+
+
+def test_binding_exchange_failure_ends_every_rank():
+    """One rank's exchange raises on its fifth call: that rank's
+    accord_fit_rows re-raises it, and the other rank's next all-gather fails
+    on the group's timeout, which its accord_fit_rows raises in turn, instead
+    of hanging."""
+    res = _run_binding(2, 90, [(0, 64), (64, 90)], fail_rank=1)
+    assert res[1][0] == "raised" and "exchange lost" in res[1][1]
+    assert res[0][0] == "raised"
+    assert res[1][3] == 4 and res[0][3] == 4  # four exchanges completed on both ranks
