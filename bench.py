@@ -45,6 +45,8 @@ def parse(argv=None):
     ap.add_argument("--p", type=int, default=40000)
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--kkt-tol", type=float, default=1e-4)
+    ap.add_argument("--coarse-kkt", type=float, default=5e-3,
+                    help="one-product gradients while the KKT residual is above this (0: three products throughout)")
     ap.add_argument("--fp64-iters", type=int, default=2, help="FP64 iterations timed for the comparison (0: skip)")
     ap.add_argument("--tf32-fits", type=int, default=1, help="TF32x3 fits timed for the comparison (0: skip)")
     ap.add_argument("--fp64-full", action="store_true",
@@ -224,7 +226,8 @@ def run_ours(args):
     ws = torch.empty(A.accord_workspace_bytes(n, p, precision="mixed", max_iter=500), dtype=torch.uint8,
                      device="cuda")
     Om = torch.empty((p, p), dtype=torch.float32, device="cuda")
-    fit_kw = dict(precision="mixed", kkt_tol=args.kkt_tol, max_iter=500, workspace=ws, Omega=Om)
+    fit_kw = dict(precision="mixed", kkt_tol=args.kkt_tol, max_iter=500, workspace=ws, Omega=Om,
+                  coarse_kkt=args.coarse_kkt)
 
     def barrier():
         if world > 1:
@@ -429,7 +432,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate, fp64 reductions)",
             "data": "synthetic (seeded hub-and-block precision, Gaussian X)",
             "config": {"workload": w.name, "p": p, "n": n, "lambda": w.lam, "kkt_tol": args.kkt_tol,
-                       "precision": "mixed_bf16x3", "coarse_kkt": 5e-3, "y_refresh": 32, "tau0": 1.0, "beta": 0.5,
+                       "precision": "mixed_bf16x3", "coarse_kkt": args.coarse_kkt, "y_refresh": 32, "tau0": 1.0,
+                       "beta": 0.5,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2 (Omega {4 * p * p / 1e9:.1f} GB per buffer)"},
             "time_to_kkt_s": round(ms / max(args.steps, 1) / 1e3, 3),

@@ -356,6 +356,8 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
   const int64_t mcol = (colt - lane) >> 5;  // mask word of this 32-column chunk
   uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
   uint32_t newcol = 0u;  // bit r: Omega+ in row r of this column is nonzero
+  float wdiag = 1.f;     // this column's diagonal entry of Omega+, if the chunk holds it
+  bool has_diag = false;
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     if (CHECK && row_base + r >= ea.M) continue;  // warp-uniform
@@ -367,8 +369,8 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
       float w;
       if (CHECK && row_base + r + prm.row_off == colt) {
         w = diag_prox(a, tau, ea.lam_d);
-        sm.r2 += log((double)w);
-        sm.r3 += (double)w;
+        wdiag = w;
+        has_diag = true;
         kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
       } else {
         float lam_e = lam, tlam_e = tlam;
@@ -398,6 +400,12 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
     }
     v[r] = d;
     nzmask |= (d != 0.f) ? (1u << r) : 0u;
+  }
+  // a column meets the diagonal in at most one row: its FP64 log and sum run
+  // once per lane, side by side, instead of once per row in turn
+  if (CHECK && has_diag) {
+    sm.r2 += log((double)wdiag);
+    sm.r3 += (double)wdiag;
   }
   // Delta is mostly zero: each lane appends only its own nonzero entries.
   // One atomic reserves the whole warp's entries (a warp prefix sum gives

@@ -212,19 +212,37 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
 //
 // from the nonzeros of Omega^t (its occupancy bitmap), in ascending j, in
 // place of Y[cur] and its hi/lo operand planes.  One warp a row, the row's
-// output columns in registers (32 a lane, 1024 a pass); the bitmap words of a
-// row are read 32 chunks at a time and each nonzero is broadcast to the warp.
-// Per 32-row group it writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the
-// drift statistic and g.
+// output columns in registers (16 a lane, 512 a pass); the bitmap words of a
+// row are read 32 chunks at a time, and the nonzeros are taken four at a
+// time, so that four X^T rows are in flight per lane.  Per 32-row group it
+// writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the drift statistic and g.
 constexpr int kRfThreads = 256;
-constexpr int kRfColsPerLane = 32;
+constexpr int kRfColsPerLane = 16;
 constexpr int kRdMaxThreads = 512;
 
 // A dense iterate makes the one-warp-a-row walk gather one X^T row per entry
-// of Omega; from this many nonzeros on (YRefreshParams::dense_nnz, a few
-// percent of the entries) the refresh runs as a blocked product instead.
+// of Omega; from this many nonzeros on (YRefreshParams::dense_nnz, a tenth
+// of the entries) the refresh runs as a blocked product instead.
 __device__ __forceinline__ bool refresh_is_dense(const YRefreshParams& prm, const Ctrl& c) {
   return c.nnz >= prm.dense_nnz;
+}
+
+// acc += v_k X^T[j_k, c0 + lane + 32 u] for the K entries k in order (K <= 4);
+// columns at or past n are neither read nor used.
+template <int K>
+__device__ __forceinline__ void rf_apply(float (&acc)[kRfColsPerLane], const float* __restrict__ XT, int64_t ldx,
+                                         int64_t c0, int64_t n, int lane, const int64_t (&j)[4], const float (&v)[4]) {
+  float x[K][kRfColsPerLane];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float* xr = XT + j[k] * ldx + c0 + lane;
+#pragma unroll
+    for (int u = 0; u < kRfColsPerLane; ++u) x[k][u] = (c0 + lane + 32 * u < n) ? __ldg(xr + 32 * u) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kRfColsPerLane; ++u)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[u] = fmaf(v[k], x[k][u], acc[u]);
 }
 
 template <int PT>
@@ -257,7 +275,9 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
       float acc[kRfColsPerLane];
 #pragma unroll
       for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
-      const bool full = c0 + kPass <= prm.n;
+      int64_t j[4] = {0, 0, 0, 0};
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      int np = 0;  // entries waiting in j / v (warp-uniform)
       for (int64_t g = 0; g < nchunks; g += 32) {
         const uint32_t word = (g + lane < nchunks) ? Bm[(g + lane) * prm.ldbm + row] : 0u;
         uint32_t live = __ballot_sync(0xffffffffu, word != 0u);
@@ -268,20 +288,22 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
           while (bits != 0u) {
             const int bit = __ffs(bits) - 1;
             bits &= bits - 1u;
-            const int64_t j = (g + src) * 32 + bit;
-            const float v = om_row[j];
-            const float* xr = XT + j * prm.ldx + c0 + lane;
-            if (full) {
-#pragma unroll
-              for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = fmaf(v, __ldg(xr + 32 * u), acc[u]);
-            } else {
-#pragma unroll
-              for (int u = 0; u < kRfColsPerLane; ++u)
-                if (c0 + lane + 32 * u < prm.n) acc[u] = fmaf(v, __ldg(xr + 32 * u), acc[u]);
+            const int64_t jj = (g + src) * 32 + bit;
+            const float vv = om_row[jj];
+            if (np == 0) { j[0] = jj; v[0] = vv; }
+            else if (np == 1) { j[1] = jj; v[1] = vv; }
+            else if (np == 2) { j[2] = jj; v[2] = vv; }
+            else { j[3] = jj; v[3] = vv; }
+            if (++np == 4) {
+              rf_apply<4>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
+              np = 0;
             }
           }
         }
       }
+      if (np == 3) rf_apply<3>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
+      else if (np == 2) rf_apply<2>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
+      else if (np == 1) rf_apply<1>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
       float* yr = Y + row * prm.ldy;
       E* hr = Yh + row * prm.ldyk;
       E* lr = Yl + row * prm.ldyk;
@@ -315,10 +337,10 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
   __syncthreads();
   if (threadIdx.x < kYSlots) {
     const int q = threadIdx.x;
-    double v = 0.0;
+    double vs = 0.0;
     if (q < 3)
-      for (int w = 0; w < nwarps; ++w) v += red[w][q];
-    prm.part[b * prm.s_part + (int64_t)mb * kYSlots + q] = v;
+      for (int w = 0; w < nwarps; ++w) vs += red[w][q];
+    prm.part[b * prm.s_part + (int64_t)mb * kYSlots + q] = vs;
   }
 }
 
