@@ -184,19 +184,6 @@ __device__ __forceinline__ void prefetch_block(float* buf, const float* __restri
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// 32 x 32 bit-matrix transpose across a warp: on entry lane r holds row r
-// (bit c = element (r, c)); on exit lane c holds column c (bit r = element
-// (r, c)).  Five butterfly stages swap the off-diagonal j x j bit blocks of
-// lanes lane and lane ^ j, for j = 16, 8, 4, 2, 1.
-__device__ __forceinline__ uint32_t transpose_bits(uint32_t x, int lane) {
-  uint32_t m = 0x0000FFFFu;
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1, m ^= m << j) {
-    const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
-    x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t & m) << j));
-  }
-  return x;
-}
 
 // Rows with at most this many nonempty rows in a 32 x 32 block are fetched
 // entry by entry, denser blocks row by row.
@@ -237,18 +224,6 @@ __device__ __forceinline__ void prefetch_rows(float* buf, const float* __restric
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Column `lane` of a block written by prefetch_rows: entry r where bit r of
-// colbits is set (colbits: the block's occupancy in this column), else 0.
-__device__ __forceinline__ void read_block_masked(const float* buf, int lane, uint32_t colbits, float (&pre)[32]) {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const float x = buf[r * 32 + ((((lane >> 2) ^ (r & 7))) << 2) + (lane & 3)];
-    pre[r] = ((colbits >> r) & 1u) ? x : 0.f;
-  }
-  __syncwarp();
-}
 
 // Asynchronous copy of one tile's occupancy words into a word slot (prox
 // mode): row k is the current iterate's word of chunk ch0 + k; lane r of a
@@ -333,84 +308,132 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
   if (chk != 0.f) sm.bad += 1.f;
 }
 
-// G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta planes, and the
-// trial / KKT partial sums for column colt.  CHECK handles the matrix edge
-// and the diagonal (row == colt); the unchecked form is the hot path.
-// Omega+ is stored only where it is nonzero: the receiving buffer's values
-// count only where its occupancy bitmap (written from the return value) has
-// a bit.  Returns the occupancy of Omega+ in this column (bit r: row
-// row_base + r nonzero).
+// Row `lane` of a block written by prefetch_rows, as eight 16-byte reads
+// (conflict-free: each quarter-warp reads eight distinct slots): entry c
+// where bit c of word is set (word: this row's occupancy word), else 0.
+__device__ __forceinline__ void read_row_masked(const float* buf, int lane, uint32_t word, float (&pre)[32]) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  const float4* row = reinterpret_cast<const float4*>(buf + lane * 32);
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    const float4 x = row[g ^ (lane & 7)];
+    pre[4 * g + 0] = ((word >> (4 * g + 0)) & 1u) ? x.x : 0.f;
+    pre[4 * g + 1] = ((word >> (4 * g + 1)) & 1u) ? x.y : 0.f;
+    pre[4 * g + 2] = ((word >> (4 * g + 2)) & 1u) ? x.z : 0.f;
+    pre[4 * g + 3] = ((word >> (4 * g + 3)) & 1u) ? x.w : 0.f;
+  }
+  __syncwarp();
+}
+
+// G = acc / n, Eq. 3.5 on A = Omega - tau G, Omega+ and Delta (to the
+// buckets, or to operand planes), and the trial / KKT partial sums for one
+// 32 x 32 chunk, in TMEM order: lane `lane` owns row row_base + lane, and
+// v[c], pre[c] are its columns col0 + c.  CHECK handles the matrix edge and
+// the diagonal; the unchecked form is the hot path.  Omega+ is stored only
+// where it is nonzero (the receiving buffer's values count only where its
+// bitmap has a bit), as 16-byte stores in a whole chunk.  Returns this row's
+// occupancy word of Omega+ (bit c: column col0 + c nonzero), with no
+// transpose of the accumulator or of the words.
 template <int PT, bool CHECK, bool MASK, bool SPARSE>
-__device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
-                                               int64_t colt, float (&v)[32], const float (&pre)[32], Sums& sm,
-                                               int lane) {
+__device__ __forceinline__ uint32_t prox_row_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base,
+                                                   int64_t col0, float (&v)[32], float (&pre)[32], Sums& sm,
+                                                   int lane) {
   float sd = 0.f, sl1 = 0.f, kk = 0.f;
   const float tau = ea.tau, tlam = ea.tau * ea.lam, lam = ea.lam, scale = ea.scale;
-  const bool cok = !CHECK || colt < ea.N;
-  constexpr bool sparse = SPARSE;  // Delta to the buckets (else to operand planes)
+  const int64_t row = row_base + lane;
+  const bool rok = !CHECK || row < ea.M;
+  constexpr bool sparse = SPARSE;
   using E = typename Plane<PT>::E;
-  float* po = ea.out + row_base * prm.ldout + colt;
-  E* ph = sparse ? nullptr : static_cast<E*>(ea.out_hi) + row_base * prm.ldplane + colt;
-  E* pl = sparse ? nullptr : static_cast<E*>(ea.out_lo) + row_base * prm.ldplane + colt;
-  const uint32_t ldo = (uint32_t)prm.ldout, ldp = (uint32_t)prm.ldplane;
-  const int64_t mcol = (colt - lane) >> 5;  // mask word of this 32-column chunk
-  uint32_t nzmask = 0u;  // bit r: Delta in row r of this column is nonzero
-  uint32_t newcol = 0u;  // bit r: Omega+ in row r of this column is nonzero
-  float wdiag = 1.f;     // this column's diagonal entry of Omega+, if the chunk holds it
+  float* po = ea.out + row * prm.ldout + col0;
+  E* ph = sparse ? nullptr : static_cast<E*>(ea.out_hi) + row * prm.ldplane + col0;
+  E* pl = sparse ? nullptr : static_cast<E*>(ea.out_lo) + row * prm.ldplane + col0;
+  const int64_t dcol = row + prm.row_off - col0;  // this row's diagonal column in the chunk
+  uint32_t mw = 0xffffffffu;
+  if (MASK && rok) mw = __ldg(ea.mask + row * ea.mask_ld + (col0 >> 5));
+  uint32_t nzmask = 0u, newrow = 0u;
+  float wdiag = 1.f;
   bool has_diag = false;
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    if (CHECK && row_base + r >= ea.M) continue;  // warp-uniform
+  for (int c = 0; c < 32; ++c) {
     float d = 0.f;
-    if (cok) {
-      const float g = v[r] * scale;
-      const float om = pre[r];
+    if (!CHECK || (rok && col0 + c < ea.N)) {
+      const float g = v[c] * scale;
+      const float om = pre[c];
       const float a = fmaf(-tau, g, om);
       float w;
-      if (CHECK && row_base + r + prm.row_off == colt) {
+      if (CHECK && dcol == c) {
         w = diag_prox(a, tau, ea.lam_d);
         wdiag = w;
         has_diag = true;
         kk = fmaxf(kk, kkt_entry(om, g, true, lam, ea.lam_d));
       } else {
         float lam_e = lam, tlam_e = tlam;
-        if (MASK) {
-          // one broadcast load a row: the word covers this chunk's 32 columns
-          const uint32_t mw = __ldg(ea.mask + (row_base + r) * ea.mask_ld + mcol);
-          if (!((mw >> lane) & 1u)) {
-            lam_e = INFINITY;
-            tlam_e = INFINITY;
-          }
+        if (MASK && !((mw >> c) & 1u)) {
+          lam_e = INFINITY;
+          tlam_e = INFINITY;
         }
-        // written so that a NaN gradient gives a NaN entry (caught below
-        // through ||Delta||^2) rather than a zero
         const float m = fabsf(a) - tlam_e;
         w = m <= 0.f ? 0.f : copysignf(m, a);
         sl1 += fabsf(w);
-        const float kz = fabsf(g) - lam_e;                 // omega == 0: max(|G| - lambda, 0)
-        const float knz = fabsf(g + copysignf(lam_e, om));  // omega != 0: |G + lambda sign(omega)|
+        const float kz = fabsf(g) - lam_e;
+        const float knz = fabsf(g + copysignf(lam_e, om));
         kk = fmaxf(kk, om != 0.f ? knz : kz);
       }
       d = w - om;
       sd = fmaf(d, d, sd);
       const bool nzw = w != 0.f;
-      newcol |= nzw ? (1u << r) : 0u;
-      ptx::st_f32_hint_if(po + r * ldo, w, ea.pol_stream, nzw);
-      if (!sparse) st_split_hint<PT>(ph + r * ldp, pl + r * ldp, d, ea.pol_stream);
+      newrow |= nzw ? (1u << c) : 0u;
+      if (CHECK) {
+        ptx::st_f32_hint_if(po + c, w, ea.pol_stream, nzw);
+        if (!sparse) st_split_hint<PT>(ph + c, pl + c, d, ea.pol_stream);
+      } else {
+        pre[c] = w;
+      }
     }
-    v[r] = d;
-    nzmask |= (d != 0.f) ? (1u << r) : 0u;
+    v[c] = d;
+    nzmask |= (d != 0.f) ? (1u << c) : 0u;
   }
-  // a column meets the diagonal in at most one row: its FP64 log and sum run
-  // once per lane, side by side, instead of once per row in turn
+  if (!CHECK) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      ptx::st_v4_hint_if(po + 4 * g, __float_as_uint(pre[4 * g]), __float_as_uint(pre[4 * g + 1]),
+                         __float_as_uint(pre[4 * g + 2]), __float_as_uint(pre[4 * g + 3]), ea.pol_stream,
+                         ((newrow >> (4 * g)) & 0xFu) != 0u);
+    if (!sparse) {
+      if constexpr (PT == kPlaneTf32) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          float hi[4], lo[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) split_tf32(v[4 * g + t], hi[t], lo[t]);
+          ptx::st_v4_hint_if(ph + 4 * g, __float_as_uint(hi[0]), __float_as_uint(hi[1]), __float_as_uint(hi[2]),
+                             __float_as_uint(hi[3]), ea.pol_stream, true);
+          ptx::st_v4_hint_if(pl + 4 * g, __float_as_uint(lo[0]), __float_as_uint(lo[1]), __float_as_uint(lo[2]),
+                             __float_as_uint(lo[3]), ea.pol_stream, true);
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v[8 * g + 2 * t], h0, l0);
+            split_bf16(v[8 * g + 2 * t + 1], h1, l1);
+            hw[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          ptx::st_v4_hint_if(ph + 8 * g, hw[0], hw[1], hw[2], hw[3], ea.pol_stream, true);
+          ptx::st_v4_hint_if(pl + 8 * g, lw[0], lw[1], lw[2], lw[3], ea.pol_stream, true);
+        }
+      }
+    }
+  }
   if (CHECK && has_diag) {
     sm.r2 += log((double)wdiag);
     sm.r3 += (double)wdiag;
   }
-  // Delta is mostly zero: each lane appends only its own nonzero entries.
-  // One atomic reserves the whole warp's entries (a warp prefix sum gives
-  // each lane its slots), so a dense Delta does not serialise on the
-  // bucket counter.
   if (sparse) {
     const int cnt = __popc(nzmask);
     int incl = cnt;
@@ -427,15 +450,15 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
       int pos = base + incl - cnt;
       uint32_t m = nzmask;
       while (m != 0u) {
-        const int r = __ffs(m) - 1;
+        const int c = __ffs(m) - 1;
         m &= m - 1u;
-        float dr = 0.f;
+        float dc = 0.f;
 #pragma unroll
         for (int u = 0; u < 32; ++u)
-          if (u == r) dr = v[u];
+          if (u == c) dc = v[u];
         if (pos < ea.cap) {
-          ea.bkey[pos] = ((uint32_t)r << 25) | (uint32_t)colt;
-          ea.bval[pos] = dr;
+          ea.bkey[pos] = ((uint32_t)lane << 25) | (uint32_t)(col0 + c);
+          ea.bval[pos] = dc;
         }
         ++pos;
       }
@@ -445,20 +468,14 @@ __device__ __forceinline__ uint32_t prox_chunk(const EpiArgs& ea, const TcParams
       }
     }
   }
-  // off-diagonal nonzeros of Omega+ in this column: the occupancy bits,
-  // less the diagonal entry where this column meets it
-  int nnz = __popc(newcol);
-  if (CHECK) {
-    const int64_t dr = colt - row_base - prm.row_off;
-    if (dr >= 0 && dr < 32 && ((newcol >> dr) & 1u)) nnz -= 1;
-  }
+  int nnz = __popc(newrow);
+  if (CHECK && dcol >= 0 && dcol < 32 && ((newrow >> dcol) & 1u)) nnz -= 1;
   sm.r0 += sd;
   sm.r1 += sl1;
   sm.r4 += (float)nnz;
   sm.kkt = fmaxf(sm.kkt, kk);
-  // a non-finite gradient or iterate entry makes ||Delta||^2 NaN or infinite
   if (!(sd <= 3.4e38f)) sm.bad += 1.f;
-  return newcol;
+  return newrow;
 }
 
 __device__ __forceinline__ void grad_chunk(const EpiArgs& ea, const TcParams& prm, int64_t row_base, int64_t colt,
@@ -799,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int64_t colt = col0 + lane;
           const bool full = rows_full && col0 + 32 <= prm.N;
           if (kProx) {
-            read_block_masked(tbuf, lane, transpose_bits(wcur[(c >> 5) * 32 + lane], lane), pre);
+            read_row_masked(tbuf, lane, wcur[(c >> 5) * 32 + lane], pre);
           } else if (kNeedAux && ea.aux != nullptr) {
             if (pending) read_block_column(tbuf, lane, pre);
             else load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
@@ -812,7 +829,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * kBN + h * kColsPerWarp + c, rr);
           ptx::tmem_ld_wait();
           float v[32];
-          transpose32(tbuf, rr, lane, v);
+          if (kProx) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) v[u] = __uint_as_float(rr[u]);
+          } else {
+            transpose32(tbuf, rr, lane, v);
+          }
           // the buffer is free again: fetch the next chunk's operand while this one computes
           const int k = c >> 5;
           if (kProx) {
@@ -839,24 +861,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           } else if (MODE == kModeProx) {
             // compile-time variants: full interior chunk, Delta to buckets, no refit mask is the hot one
             const bool fast = full && !diag;
-            uint32_t newcol;
+            uint32_t newrow;
             if (ea.mask == nullptr) {
               if (ea.bkey != nullptr) {
-                if (fast) newcol = prox_chunk<PT, false, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else newcol = prox_chunk<PT, true, false, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) newrow = prox_row_chunk<PT, false, false, true>(ea, prm, row_base, col0, v, pre, sm, lane);
+                else newrow = prox_row_chunk<PT, true, false, true>(ea, prm, row_base, col0, v, pre, sm, lane);
               } else {
-                if (fast) newcol = prox_chunk<PT, false, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-                else newcol = prox_chunk<PT, true, false, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+                if (fast) newrow = prox_row_chunk<PT, false, false, false>(ea, prm, row_base, col0, v, pre, sm, lane);
+                else newrow = prox_row_chunk<PT, true, false, false>(ea, prm, row_base, col0, v, pre, sm, lane);
               }
             } else if (ea.bkey != nullptr) {
-              if (fast) newcol = prox_chunk<PT, false, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else newcol = prox_chunk<PT, true, true, true>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) newrow = prox_row_chunk<PT, false, true, true>(ea, prm, row_base, col0, v, pre, sm, lane);
+              else newrow = prox_row_chunk<PT, true, true, true>(ea, prm, row_base, col0, v, pre, sm, lane);
             } else {
-              if (fast) newcol = prox_chunk<PT, false, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
-              else newcol = prox_chunk<PT, true, true, false>(ea, prm, row_base, colt, v, pre, sm, lane);
+              if (fast) newrow = prox_row_chunk<PT, false, true, false>(ea, prm, row_base, col0, v, pre, sm, lane);
+              else newrow = prox_row_chunk<PT, true, true, false>(ea, prm, row_base, col0, v, pre, sm, lane);
             }
-            // the occupancy of Omega+ in this chunk, one word per row
-            bmn[(ch0 + k) * prm.ldbm + row_base + lane] = transpose_bits(newcol, lane);
+            // the occupancy of Omega+ in this chunk: this lane's row word
+            bmn[(ch0 + k) * prm.ldbm + row_base + lane] = newrow;
           } else if (MODE == kModeGrad) {
             grad_chunk(ea, prm, row_base, colt, diag || !full, v);
           } else {

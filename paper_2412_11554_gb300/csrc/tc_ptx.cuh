@@ -141,6 +141,14 @@ __device__ __forceinline__ void st_f32_hint_if(float* ptr, float v, uint64_t pol
       "f"(v), "l"(pol), "r"((uint32_t)pred)
       : "memory");
 }
+// 16-byte store under a predicate (ptr 16-byte aligned)
+__device__ __forceinline__ void st_v4_hint_if(void* ptr, uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint64_t pol,
+                                              bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %6, 0;\n\t@p st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;\n}\n" ::"l"(ptr),
+      "r"(a), "r"(b), "r"(c), "r"(d), "l"(pol), "r"((uint32_t)pred)
+      : "memory");
+}
 __device__ __forceinline__ void st_b16_hint(void* ptr, uint16_t v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(pol) : "memory");
 }
