@@ -60,12 +60,14 @@ constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 bl
 // words (rows) each.
 constexpr uint32_t kWordSlotWords = 4 * 32;
 constexpr uint32_t kWordBytes = kEpiWarps * 2 * kWordSlotWords * 4;
-constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + kWordBytes + 1024;
-// Tail after the epilogue buffers: 2 kStages + 5 mbarriers, the TMEM slot and
-// two flags, then the epilogue's FP64 partials [kEpiWarps][8] from kRedOffset.
+constexpr size_t kTailBytes = 2048;
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kEpiBufBytes + kWordBytes + kTailBytes;
+// Tail after the epilogue buffers: 2 kStages + 5 mbarriers, the TMEM slot, two
+// flags and two tile counters, then the epilogue's FP64 partials
+// [2][kEpiWarps][8] (by tile parity) from kRedOffset.
 constexpr size_t kRedOffset = 256;
-static_assert((2 * kStages + 5) * 8 + 12 <= kRedOffset, "barriers overlap the epilogue partials");
-static_assert(kRedOffset + kEpiWarps * 8 * 8 <= 1024, "epilogue partials overflow the shared-memory tail");
+static_assert((2 * kStages + 5) * 8 + 20 <= kRedOffset, "barriers overlap the epilogue partials");
+static_assert(kRedOffset + 2 * kEpiWarps * 8 * 8 <= kTailBytes, "epilogue partials overflow the shared-memory tail");
 static_assert(kSmemBytes <= 232448, "more dynamic shared memory than one CTA may use");
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& mb, int& nb) {
@@ -119,8 +121,6 @@ __device__ __forceinline__ int next_tile(const TcParams& prm, int T, int ntot, i
   }
   return ntot;
 }
-
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
 
 struct EpiArgs {
   float tau, lam, lam_d, scale;
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* stop_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  int* tile_count = reinterpret_cast<int*>(tmem_slot + 3);  // [2], by tile parity
   double* red = reinterpret_cast<double*>(tail + kRedOffset);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -542,7 +542,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
-    *stop_flag = 0;
+    tile_count[0] = 0;
+    tile_count[1] = 0;
     ptx::fence_mbar_init();
   }
   // the peer's barriers must be live before any copy, commit or arrival reaches them
@@ -890,15 +891,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         pending = false;
       }
-      // this warp's TMEM reads are done: one release per warp, on the leader
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive_cluster(ptx::map_to_cta(&tempty[acc], 0));
       // Partial sums of this tile: FP32 warp trees, then FP64 across the warps
-      // (fixed order).  Both named barriers run on every tile so that all
-      // epilogue warps leave the loop together (the stop decision is taken by
-      // one thread between them).
+      // in a fixed order, by whichever warp finishes the tile last (a counter
+      // per tile parity; no warp waits for another).  The TMEM release comes
+      // after, so no warp can reach tile i + 2, and reuse this parity's
+      // partials and counter, before the fold of tile i is done.
       constexpr int W = (MODE == kModeY) ? kYSlots : kProxSlots;
+      double* red_t = red + (i & 1) * kEpiWarps * 8;
       if (MODE == kModeY || MODE == kModeProx) {
         float f0 = sm.r0, f1 = sm.r1, f4 = sm.r4, fb = sm.bad, fk = sm.kkt;
 #pragma unroll
@@ -917,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           d3 = warp_sum(d3);
         }
         if (lane == 0) {
-          double* rw = red + e * 8;
+          double* rw = red_t + e * 8;
           if (MODE == kModeY) {
             rw[kYDiff2] = (double)f0; rw[kYNorm2] = (double)f1; rw[kYBad] = (double)fb; rw[3] = 0.0;
           } else {
@@ -926,20 +925,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
         }
       }
-      epi_bar();
-      if (e == 0) {
-        if ((MODE == kModeY || MODE == kModeProx) && part_b != nullptr && lane < W && mb < prm.tiles_m) {
-          double x = red[lane];
-          for (int w = 1; w < kEpiWarps; ++w)
-            x = (MODE == kModeProx && lane == kPKkt) ? fmax(x, red[w * 8 + lane]) : x + red[w * 8 + lane];
-          const int bad_slot = (MODE == kModeProx) ? (int)kPBad : (int)kYBad;
-          if (*abort_flag && lane == bad_slot) x += 1.0;
-          part_b[((int64_t)mb * prm.tiles_n + nb) * W + lane] = x;
+      if (MODE == kModeY || MODE == kModeProx) {
+        int done = 0;
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();  // this warp's partials before its count
+          done = atomicAdd(&tile_count[i & 1], 1) + 1;
         }
-        if (lane == 0) *stop_flag = *abort_flag;
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done == kEpiWarps) {
+          __threadfence_block();  // every warp's partials after the last count
+          if (part_b != nullptr && lane < W && mb < prm.tiles_m) {
+            const volatile double* rv = red_t;
+            double x = rv[lane];
+            for (int w = 1; w < kEpiWarps; ++w)
+              x = (MODE == kModeProx && lane == kPKkt) ? fmax(x, rv[w * 8 + lane]) : x + rv[w * 8 + lane];
+            const int bad_slot = (MODE == kModeProx) ? (int)kPBad : (int)kYBad;
+            if (*abort_flag && lane == bad_slot) x += 1.0;
+            part_b[((int64_t)mb * prm.tiles_n + nb) * W + lane] = x;
+          }
+          __syncwarp();
+          if (lane == 0) tile_count[i & 1] = 0;
+        }
       }
-      epi_bar();
-      if (*stop_flag) break;
+      // this warp's TMEM reads (and its share of the fold) are done: one
+      // release per warp, on the leader
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive_cluster(ptx::map_to_cta(&tempty[acc], 0));
+      if (*abort_flag) break;
       T = TN;
       b = bN;
       Tl = TlN;
