@@ -108,8 +108,9 @@ typedef struct accord_opts {
     int32_t y_refresh;       /* mixed modes: Y = Omega X^T is carried from step to step as
                                 Y + Delta X^T in FP32, which accumulates rounding; every
                                 y_refresh accepted steps (default 32), ahead of a step whose KKT
-                                test the last ratio of residuals predicts to pass, and before a
-                                KKT residual under kkt_tol may end a fit (that trial is then cut
+                                test the last ratio of residuals predicts to pass (once per fit
+                                or path penalty if the prediction misses), and before a KKT
+                                residual under kkt_tol may end a fit (that trial is then cut
                                 short), Y is formed afresh from the iterate.  0: never (the
                                 residual test then uses the carried Y).  Ignored in FP64 mode,
                                 where every trial forms Y+ = Omega+ X^T.                        */

@@ -89,6 +89,8 @@ struct Ctrl {
   // switches to the three split products for the rest of the fit
   int32_t coarse;
   int32_t n_coarse;       // prox launches that ran with the one product
+  int32_t predicted;      // the pending or last refresh was taken ahead of a predicted passing KKT test
+  int32_t no_predict;     // such a prediction missed: until the fit (or penalty) ends, refresh only when due
 };
 
 // One estimate of a lambda path (same layout as accord_path_entry).

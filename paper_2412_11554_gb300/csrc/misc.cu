@@ -511,6 +511,8 @@ __global__ void ctrl_init_kernel(Ctrl* ctrl, const double* ompart, int64_t nomp,
   c.kkt_prev = INFINITY;
   c.coarse = sp.coarse_kkt > 0.0 ? 1 : 0;
   c.n_coarse = 0;
+  c.predicted = 0;
+  c.no_predict = 0;
   c.status = kNotConverged;
   c.lam = sp.lam;
   c.lam_d = sp.lam_d;
@@ -549,6 +551,9 @@ __device__ void post_prox_update(Ctrl& c, const double (&s)[kProxSlots], const S
     c.kkt_prev = c.kkt;
     c.kkt = s[kPKkt];
     trace_put(trace, sp.trace_cap, c.t, 1, c.kkt);
+    // a refresh taken for a predicted pass that did not come: predict no more
+    if (c.predicted && c.since_refresh == 0 && !(c.kkt <= sp.kkt_tol)) c.no_predict = 1;
+    c.predicted = 0;
     // a residual from the one-product gradient never ends the fit: under the
     // threshold (or the tolerance), or once it stops falling (the one
     // product's own error floor), the next launches form G with the three
@@ -631,7 +636,10 @@ __device__ void decide_update(Ctrl& c, const double (&s)[kYSlots], const SolvePa
       // ratio of residuals carried one step on): a refresh then saves the
       // trial that a passing test on a carried Y would have to cut short
       const double rate = (isfinite(c.kkt_prev) && c.kkt_prev > c.kkt) ? c.kkt / c.kkt_prev : 1.0;
-      if (c.since_refresh >= sp.y_refresh || c.kkt * rate <= sp.kkt_tol) c.refresh = 1;
+      const bool due = c.since_refresh >= sp.y_refresh;
+      const bool predict = !c.no_predict && c.kkt * rate <= sp.kkt_tol;
+      if (due || predict) c.refresh = 1;
+      c.predicted = (!due && predict) ? 1 : 0;
     }
   } else {
     c.k += 1;
@@ -845,6 +853,8 @@ __global__ void batch_ctrl_init_kernel(PathDev pd, const T* __restrict__ yt0, in
   C.kkt_prev = INFINITY;
   C.coarse = sp.coarse_kkt > 0.0 ? 1 : 0;
   C.n_coarse = 0;
+  C.predicted = 0;
+  C.no_predict = 0;
   C.L = L_given > 0.0 ? L_given : C.pw_est;
   C.inv_L = C.L > 0.0 ? 1.0 / C.L : INFINITY;
   C.tau0 = sp.tau0 > 0.0 ? sp.tau0 : C.inv_L;
@@ -922,6 +932,8 @@ __global__ void path_advance_kernel(PathDev pd) {
       C.y_drift = 0.0;
       C.kkt_prev = INFINITY;
       C.coarse = pd.coarse;
+      C.predicted = 0;
+      C.no_predict = 0;
     } else {
       // the chain ends here; an error also ends the penalties after it
       for (int q = k + 1; q < pd.n_lambda; ++q) {
