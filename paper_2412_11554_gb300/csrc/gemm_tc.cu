@@ -54,7 +54,9 @@ constexpr uint32_t kABytes = BM * kRowBytes;
 constexpr uint32_t kBBytes = kBHalf * kRowBytes;
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // one CTA's share of a stage
 constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
-constexpr uint32_t kEpiBufBytes = kEpiWarps * 32 * 32 * 4;  // one 32x32 FP32 block per epilogue warp
+// two 32x32 FP32 blocks per epilogue warp (prox mode stages the iterate two
+// chunks ahead; the other modes use the first as their transpose buffer)
+constexpr uint32_t kEpiBufBytes = kEpiWarps * 2 * 32 * 32 * 4;
 // Prox mode: occupancy words of two tiles per epilogue warp (the current one
 // and the next): the current iterate's words of the warp's four chunks, 32
 // words (rows) each.
@@ -231,7 +233,7 @@ __device__ __forceinline__ void prefetch_rows(float* buf, const float* __restric
 // whose rows lie past the matrix, read as zero words (no global read).  One
 // 16-byte copy a lane.
 __device__ __forceinline__ void load_words(uint32_t* slot, const uint32_t* bmc, int64_t ldbm, int64_t ch0, int64_t nch,
-                                           int64_t row_base, bool rows_in, int lane) {
+                                           int64_t row_base, bool rows_in, int lane, bool commit = true) {
   const uint32_t sbase = ptx::smem_u32(slot);
   const int k = lane >> 3, seg = lane & 7;
   const bool in = rows_in && ch0 + k < nch;
@@ -239,7 +241,7 @@ __device__ __forceinline__ void load_words(uint32_t* slot, const uint32_t* bmc, 
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sbase + (uint32_t)((k * 32 + 4 * seg) * 4)),
                "l"(src), "r"(in ? 16 : 0)
                : "memory");
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (commit) asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Column `lane` of a block written by prefetch_block (conflict-free reads).
@@ -312,7 +314,7 @@ __device__ __forceinline__ void y_chunk(const EpiArgs& ea, const TcParams& prm, 
 // (conflict-free: each quarter-warp reads eight distinct slots): entry c
 // where bit c of word is set (word: this row's occupancy word), else 0.
 __device__ __forceinline__ void read_row_masked(const float* buf, int lane, uint32_t word, float (&pre)[32]) {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  asm volatile("cp.async.wait_group 1;" ::: "memory");  // the newest group (the next chunk) may still fly
   __syncwarp();
   const float4* row = reinterpret_cast<const float4*>(buf + lane * 32);
 #pragma unroll
@@ -704,7 +706,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const int q = warp & 3;
     const int h = e >> 2;
     constexpr int kColsPerWarp = kBN / (kEpiWarps / 4);
-    float* tbuf = epi_buf + e * 1024;
+    float* tbuf = epi_buf + e * 2048;
+    float* const pbuf[2] = {tbuf, tbuf + 1024};  // prox mode: chunk k's block in pbuf[k & 1]
     EpiArgs ea;
     ea.lam = prm.lam;
     ea.lam_d = prm.lam_d;
@@ -723,8 +726,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr bool kNeedAux = (MODE == kModeProx || MODE == kModeY);
     constexpr bool kProx = MODE == kModeProx;
     // Prox mode keeps one tile of lookahead: the next tile's occupancy words
-    // are copied during this tile's first chunk, and its first block of Omega
-    // during this tile's last, so that no tile starts on a memory round trip.
+    // are copied during this tile's first chunk, and the iterate's blocks are
+    // staged two chunks ahead (the next tile's first two during this tile's
+    // last two), so that no chunk starts on a memory round trip.  One
+    // cp.async group per chunk (empty when there is nothing to fetch), so
+    // that waiting for all but the newest group finds chunk k's block.
     uint32_t* wslots = word_area + e * 2 * kWordSlotWords;
     const int64_t nch = (prm.N + 31) >> 5;
     int slot = 0;
@@ -740,7 +746,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       load_words(wslots, prm.bm[cb0] + b * prm.s_bm, prm.ldbm, cbase0 >> 5, nch, rb0, rb0 < prm.M, lane);
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncwarp();
-      prefetch_rows(tbuf, prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0, wslots[lane], lane, ea.pol_stream);
+      prefetch_rows(pbuf[0], prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0, wslots[lane], lane, ea.pol_stream);
+      prefetch_rows(pbuf[1], prm.aux[cb0] + b * prm.s_aux, prm.ldaux, rb0, cbase0 + 32, wslots[32 + lane], lane,
+                    ea.pol_stream);
       pending = true;
     }
     for (; T < ntot; ++i) {
@@ -816,16 +824,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int64_t col0 = col_base + c;
           const int64_t colt = col0 + lane;
           const bool full = rows_full && col0 + 32 <= prm.N;
+          const int k = c >> 5;
           if (kProx) {
-            read_row_masked(tbuf, lane, wcur[(c >> 5) * 32 + lane], pre);
+            read_row_masked(pbuf[k & 1], lane, wcur[k * 32 + lane], pre);
+            // the next tile's words join the group of chunk k + 2's block
+            if (k == 0 && TN < ntot)
+              load_words(wnext, prm.bm[cbN] + bN * prm.s_bm, prm.ldbm, cbaseN >> 5, nch, rbN, rbN < prm.M, lane,
+                         false);
+            // the buffer just read takes the block two chunks ahead: this
+            // tile's, or (chunks 2 and 3) the next tile's first two, whose
+            // words arrived with chunk 2's block
+            if (c + 64 < kColsPerWarp) {
+              prefetch_rows(pbuf[k & 1], ea.aux, prm.ldaux, row_base, col0 + 64, wcur[(k + 2) * 32 + lane], lane,
+                            ea.pol_stream);
+            } else if (TN < ntot) {
+              const int kn = k + 2 - kColsPerWarp / 32;
+              prefetch_rows(pbuf[k & 1], prm.aux[cbN] + bN * prm.s_aux, prm.ldaux, rbN, cbaseN + 32 * kn,
+                            wnext[kn * 32 + lane], lane, ea.pol_stream);
+            } else {
+              asm volatile("cp.async.commit_group;" ::: "memory");
+            }
           } else if (kNeedAux && ea.aux != nullptr) {
             if (pending) read_block_column(tbuf, lane, pre);
             else load_column(ea.aux, prm.ldaux, row_base, colt, full, ea, pre);
+            pending = false;
           }
-          pending = false;
-          // the next tile's words, queued behind this tile's first block
-          if (kProx && c == 0 && TN < ntot)
-            load_words(wnext, prm.bm[cbN] + bN * prm.s_bm, prm.ldbm, cbaseN >> 5, nch, rbN, rbN < prm.M, lane);
           uint32_t rr[32];
           ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * q) << 16) + acc * kBN + h * kColsPerWarp + c, rr);
           ptx::tmem_ld_wait();
@@ -837,19 +860,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             transpose32(tbuf, rr, lane, v);
           }
           // the buffer is free again: fetch the next chunk's operand while this one computes
-          const int k = c >> 5;
-          if (kProx) {
-            if (c + 32 < kColsPerWarp) {
-              prefetch_rows(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, wcur[(k + 1) * 32 + lane], lane,
-                            ea.pol_stream);
-              pending = true;
-            } else if (TN < ntot) {
-              // the next tile's first block (its words arrived during chunk 1's wait)
-              prefetch_rows(tbuf, prm.aux[cbN] + bN * prm.s_aux, prm.ldaux, rbN, cbaseN, wnext[lane], lane,
-                            ea.pol_stream);
-              pending = true;
-            }
-          } else if (kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
+          if (!kProx && kNeedAux && ea.aux != nullptr && aux_async && c + 32 < kColsPerWarp && rows_full &&
                      col0 + 64 <= prm.N) {
             prefetch_block(tbuf, ea.aux, prm.ldaux, row_base, col0 + 32, lane, ea.pol_stream);
             pending = true;
