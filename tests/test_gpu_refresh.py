@@ -55,6 +55,23 @@ def test_refresh_bounds_the_drift_of_y(A):
     assert R.kkt_residual(O, R.grad_g(O, Xd), w.lam, w.lam) <= tol + 2 * err_g
 
 
+def test_refresh_walks_many_chunk_groups(A):
+    """p = 2400 has 75 32-column chunks a row, so the sparse refresh reads a
+    row's occupancy words in three groups (32, 32 and 11 chunks).  f of the
+    returned estimate, taken from the last Y formed afresh, is the oracle's
+    objective at it; a word read twice or missed would be far off.  The
+    drift stays at the level of one update's error (the early trials of this
+    fit overflow the Delta buckets and take the dense split-BF16 update,
+    ~2e-6 of Y; see the full-size path test)."""
+    w = workload("hubblock", p=2400, n=300)
+    Om, st = A.accord_fit(dev(w.X), w.lam, precision="mixed", kkt_tol=2e-5, max_iter=5000, y_refresh=4)
+    assert st.status == 0 and st.y_refreshes >= 2, st
+    assert st.y_drift <= 1e-5, st.y_drift
+    O = Om.double().cpu().numpy()
+    f_ref = R.objective(O, np.asarray(w.X, dtype=np.float64), w.lam)
+    assert abs(st.f - f_ref) <= 1e-6 * abs(f_ref), (st.f, f_ref)
+
+
 def test_refresh_interval_and_off(A):
     """y_refresh = 0 carries Y through the whole fit (no refresh, no drift
     measured); y_refresh = 1 forms it afresh before every step; a huge interval
