@@ -278,8 +278,12 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
       int64_t j[4] = {0, 0, 0, 0};
       float v[4] = {0.f, 0.f, 0.f, 0.f};
       int np = 0;  // entries waiting in j / v (warp-uniform)
+      uint32_t next_word = (lane < nchunks) ? Bm[(int64_t)lane * prm.ldbm + row] : 0u;
       for (int64_t g = 0; g < nchunks; g += 32) {
-        const uint32_t word = (g + lane < nchunks) ? Bm[(g + lane) * prm.ldbm + row] : 0u;
+        // this group's words; the next group's are read before this one's
+        // nonzeros are worked
+        const uint32_t word = next_word;
+        next_word = (g + 32 + lane < nchunks) ? Bm[(g + 32 + lane) * prm.ldbm + row] : 0u;
         uint32_t live = __ballot_sync(0xffffffffu, word != 0u);
         while (live != 0u) {
           const int src = __ffs(live) - 1;
