@@ -285,6 +285,20 @@ int accord_loss_f64_noalloc(const double* X, int64_t n, int64_t p, const double*
  * than 0 / 1.  Not for production use: a short limit can end correct work. */
 int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox);
 
+/* Testing hook for the refresh of Y = Omega X^T in the mixed modes (the paper
+ * has no counterpart; Y is re-formed from the iterate so that the FP32
+ * rounding of the carried Y + Delta X^T does not build up).  The refresh has
+ * two forms that give the same bits: a walk over the nonzeros of each row of
+ * Omega, which lists up to 512 of a row's nonzero columns at a time in shared
+ * memory and works a longer row in segments, and a blocked product used from
+ * p^2 / 10 nonzeros on.  For every later launch in the process,
+ *   list_cap: 0 for the walk's full list of 512, or 32 .. 512 to list fewer
+ *             nonzeros at a time (more segments per row);
+ *   form:     0 to choose by the nonzero count, 1 the walk, 2 the blocked form.
+ * Returns ACCORD_OK, or ACCORD_EINVAL for values outside those ranges.  The
+ * results do not depend on either setting, only the time does. */
+int accord_test_refresh(int32_t list_cap, int32_t form);
+
 /* Row blocks of one fit.  The objective of Eq. 3.2 separates over the rows
  * of Omega (the row-wise form in the proof of Thm 3.2), as the paper's
  * distributed solver uses when it spreads Omega over nodes by rows (Sec 3.3):

@@ -66,7 +66,7 @@ class AccordPathEntry(ctypes.Structure):
 EXPORTS = ("accord_default_opts", "accord_workspace_bytes", "accord_fit", "accord_fit_f64", "accord_refit", "accord_loss",
            "accord_grad", "accord_status_string", "accord_device_check", "accord_last_error",
            "accord_loss_f64_noalloc", "accord_path", "accord_path_workspace_bytes", "accord_grad_x",
-           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_test_wait_limit",
+           "accord_dloss_dloglam", "accord_postprocess", "accord_to_csr", "accord_test_wait_limit", "accord_test_refresh",
            "accord_fit_rows", "accord_fit_rows_workspace_bytes")
 
 # exchange(sums, nsums, maxes, nmaxes, ctx) of accord_fit_rows
@@ -111,6 +111,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.accord_loss_f64_noalloc.argtypes = [P, i64, i64, P, dbl, i32, P, P]
     lib.accord_test_wait_limit.restype = i32
     lib.accord_test_wait_limit.argtypes = [i64, i32]
+    lib.accord_test_refresh.restype = i32
+    lib.accord_test_refresh.argtypes = [i32, i32]
     lib.accord_fit_rows.argtypes = [P, i64, i64, i64, i64, dbl, opts_p, EXCHANGE_FN, P, P, P, ctypes.c_size_t, stats_p]
     lib.accord_fit_rows.restype = i32
     lib.accord_fit_rows_workspace_bytes.argtypes = [i64, i64, i64, opts_p]
@@ -658,3 +660,10 @@ def accord_last_error() -> str:
 def accord_test_wait_limit(wait_limit_ns: int, withhold_next_prox: bool = False) -> int:
     """Testing hook of the bounded device waits (see include/accord.h)."""
     return int(load_library().accord_test_wait_limit(int(wait_limit_ns), int(bool(withhold_next_prox))))
+
+
+def accord_test_refresh(list_cap: int = 0, form: int = 0) -> int:
+    """Testing hook of the refresh of Y (see include/accord.h): the walk's
+    list capacity (0: full) and the form (0: by nonzero count, 1: walk,
+    2: blocked)."""
+    return int(load_library().accord_test_refresh(int(list_cap), int(form)))

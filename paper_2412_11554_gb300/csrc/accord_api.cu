@@ -935,6 +935,12 @@ int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox) {
   return ACCORD_OK;
 }
 
+int accord_test_refresh(int32_t list_cap, int32_t form) {
+  if ((list_cap != 0 && (list_cap < 32 || list_cap > 512)) || form < 0 || form > 2) return ACCORD_EINVAL;
+  y_refresh_set_test(list_cap, form);
+  return ACCORD_OK;
+}
+
 const char* accord_last_error(void) { return g_last_error; }
 
 }  // extern "C"

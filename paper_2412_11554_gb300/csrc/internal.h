@@ -243,11 +243,17 @@ struct YRefreshParams {
   const int32_t* nactive;
   int64_t s_om, s_bm, s_y, s_yk, s_xt, s_part;  // per-problem strides (elements / words / doubles)
   double dense_nnz;        // off-diagonal nonzeros of Omega from which the blocked (dense) form runs
+  // set by launch_y_refresh from the testing hook: nonzeros of a row listed
+  // at once by the walk (0: its full list), and the form (0: by dense_nnz,
+  // 1: the walk, 2: the blocked product)
+  int32_t list_cap, form;
 };
 // Two kernels per call: the one-warp-a-row walk over Omega's nonzeros, and a
 // blocked product for a problem with at least dense_nnz nonzeros; each
 // problem takes exactly one of them.
 cudaError_t launch_y_refresh(const YRefreshParams& prm, cudaStream_t st);
+// Testing hook (accord_test_refresh): list_cap and form for later launches.
+void y_refresh_set_test(int list_cap, int form);
 // Folds the refresh partials (ngroups rows of kYSlots per problem, s_part
 // doubles apart): y_drift = max(y_drift, sqrt(||Y_old - Y_new||^2 /
 // ||Y_new||^2)); with update_g, g and f of the iterate from ||Y_new||^2; then

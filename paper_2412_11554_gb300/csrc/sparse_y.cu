@@ -13,6 +13,7 @@
 // of Y+ (BF16 or TF32: the A operand of the next gradient GEMM) and the
 // per-block partial sums
 // ||Delta X^T||^2 and ||Y+||^2 for the line search of Algorithm 1.
+#include <atomic>
 #include <mutex>
 
 #include "internal.h"
@@ -211,31 +212,115 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
 //     Y[i, :] = sum_{j : omega_ij != 0} omega_ij X^T[j, :]               (FP32)
 //
 // from the nonzeros of Omega^t (its occupancy bitmap), in ascending j, in
-// place of Y[cur] and its hi/lo operand planes.  One warp a row, the row's
-// output columns in registers (16 a lane, 512 a pass); the bitmap words of a
-// row are read 32 chunks at a time, and the nonzeros are taken four at a
-// time, so that four X^T rows are in flight per lane.  Per 32-row group it
-// writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the drift statistic and g.
+// place of Y[cur] and its hi/lo operand planes.  One warp a row.  The warp
+// first lists the row's nonzero columns in shared memory: each lane reads one
+// occupancy word of a 32-word group, eight groups in flight, and a warp scan
+// of the words' bit counts places every word's columns in ascending order;
+// then the lanes read the values omega_ij of the listed columns.  The
+// gathers take the list four entries at a time (four X^T rows in flight per
+// lane) into the row's output columns held in registers (16 a lane, 512 a
+// pass).  A row with more nonzeros than the list holds is worked in segments
+// of whole words, in order; a row that fits is listed once for all passes.
+// Per 32-row group it writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the
+// drift statistic and g.
 constexpr int kRfThreads = 256;
+constexpr int kRfWarps = kRfThreads / 32;
 constexpr int kRfColsPerLane = 16;
+constexpr int kRfListCap = 512;  // nonzeros of a row listed at once
+constexpr int kRfGroups = 8;     // 32-word groups of a row read together
 constexpr int kRdMaxThreads = 512;
 
 // A dense iterate makes the one-warp-a-row walk gather one X^T row per entry
 // of Omega; from this many nonzeros on (YRefreshParams::dense_nnz, a tenth
-// of the entries) the refresh runs as a blocked product instead.
+// of the entries) the refresh runs as a blocked product instead.  A testing
+// hook may fix the form (form 1: the walk, 2: the blocked product).
 __device__ __forceinline__ bool refresh_is_dense(const YRefreshParams& prm, const Ctrl& c) {
+  if (prm.form == 1) return false;
+  if (prm.form == 2) return true;
   return c.nnz >= prm.dense_nnz;
+}
+
+// Lists the columns of the row's nonzeros from occupancy word w0 on, in
+// ascending order, into col[0 .. len).  Stops before the first word whose
+// bits do not all fit in cap entries and returns that word; returns nchunks
+// when the row's words ran out.  bmr[c * ldbm] is the row's word of chunk c;
+// bits of columns at or past p are not listed.  Warp-uniform; cap >= 32, so
+// a segment always takes at least one word.
+__device__ __forceinline__ int64_t rf_list(const uint32_t* __restrict__ bmr, int64_t ldbm, int64_t p,
+                                           int64_t nchunks, int64_t w0, int cap, uint32_t* col, int& len,
+                                           int lane) {
+  const uint32_t last_mask = (p & 31) ? (1u << (p & 31)) - 1u : 0xFFFFFFFFu;
+  len = 0;
+  for (int64_t w = w0; w < nchunks; w += 32 * kRfGroups) {
+    uint32_t wd[kRfGroups];
+#pragma unroll
+    for (int g = 0; g < kRfGroups; ++g) {
+      const int64_t c = w + 32 * g + lane;
+      wd[g] = c < nchunks ? bmr[c * ldbm] : 0u;
+      if (c == nchunks - 1) wd[g] &= last_mask;
+    }
+#pragma unroll
+    for (int g = 0; g < kRfGroups; ++g) {
+      const int pc = __popc(wd[g]);
+      int incl = pc;  // inclusive scan of the bit counts over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const bool fits = len + incl <= cap;  // true for a prefix of the lanes
+      const uint32_t over = __ballot_sync(0xffffffffu, !fits);
+      if (fits) {
+        uint32_t bits = wd[g];
+        int pos = len + incl - pc;
+        const uint32_t base = (uint32_t)((w + 32 * g + lane) * 32);
+        while (bits != 0u) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          col[pos++] = base + (uint32_t)b;
+        }
+      }
+      if (over != 0u) {
+        const int f = __ffs(over) - 1;
+        len += __shfl_sync(0xffffffffu, incl - pc, f);
+        return w + 32 * g + f;
+      }
+      len += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  return nchunks;
+}
+
+// val[k] = omega[row, col[k]] for the listed entries, four loads a lane in
+// flight; the warp's list writes are visible on entry (__syncwarp).
+__device__ __forceinline__ void rf_values(const float* __restrict__ om_row, const uint32_t* col, float* val, int len,
+                                          int lane) {
+  for (int k0 = 0; k0 < len; k0 += 128) {
+    float t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + 32 * q + lane;
+      t[q] = k < len ? __ldg(om_row + col[k]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + 32 * q + lane;
+      if (k < len) val[k] = t[q];
+    }
+  }
 }
 
 // acc += v_k X^T[j_k, c0 + lane + 32 u] for the K entries k in order (K <= 4);
 // columns at or past n are neither read nor used.
 template <int K>
 __device__ __forceinline__ void rf_apply(float (&acc)[kRfColsPerLane], const float* __restrict__ XT, int64_t ldx,
-                                         int64_t c0, int64_t n, int lane, const int64_t (&j)[4], const float (&v)[4]) {
+                                         int64_t c0, int64_t n, int lane, const uint32_t* col, const float* val) {
   float x[K][kRfColsPerLane];
+  float v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float* xr = XT + j[k] * ldx + c0 + lane;
+    v[k] = val[k];
+    const float* xr = XT + (int64_t)col[k] * ldx + c0 + lane;
 #pragma unroll
     for (int u = 0; u < kRfColsPerLane; ++u) x[k][u] = (c0 + lane + 32 * u < n) ? __ldg(xr + 32 * u) : 0.f;
   }
@@ -245,9 +330,24 @@ __device__ __forceinline__ void rf_apply(float (&acc)[kRfColsPerLane], const flo
     for (int k = 0; k < K; ++k) acc[u] = fmaf(v[k], x[k][u], acc[u]);
 }
 
+// acc += the listed entries' terms, in list order
+__device__ __forceinline__ void rf_gather(float (&acc)[kRfColsPerLane], const float* __restrict__ XT, int64_t ldx,
+                                          int64_t c0, int64_t n, int lane, const uint32_t* col, const float* val,
+                                          int len) {
+  int k = 0;
+  for (; k + 4 <= len; k += 4) rf_apply<4>(acc, XT, ldx, c0, n, lane, col + k, val + k);
+  const int r = len - k;
+  if (r == 3) rf_apply<3>(acc, XT, ldx, c0, n, lane, col + k, val + k);
+  else if (r == 2) rf_apply<2>(acc, XT, ldx, c0, n, lane, col + k, val + k);
+  else if (r == 1) rf_apply<1>(acc, XT, ldx, c0, n, lane, col + k, val + k);
+}
+
 template <int PT>
 __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams prm) {
   using E = typename Plane<PT>::E;
+  __shared__ uint32_t s_col[kRfWarps][kRfListCap];
+  __shared__ float s_val[kRfWarps][kRfListCap];
+  __shared__ double red[kRfWarps][3];
   int b = blockIdx.y;
   if (prm.active != nullptr) {
     if (b >= *prm.nactive) return;
@@ -263,51 +363,39 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
   E* __restrict__ Yl = static_cast<E*>(prm.y_lo[cur]) + b * prm.s_yk;
   const float* __restrict__ XT = prm.xt + b * prm.s_xt;
   const int mb = blockIdx.x;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t nchunks = (prm.p + 31) / 32;
+  const int cap = (prm.list_cap >= 32 && prm.list_cap <= kRfListCap) ? prm.list_cap : kRfListCap;
   constexpr int kPass = 32 * kRfColsPerLane;
+  uint32_t* lcol = s_col[warp];
+  float* lval = s_val[warp];
   float s_d = 0.f, s_n = 0.f, chk = 0.f;
-  for (int rl = warp; rl < kBucketRows; rl += nwarps) {
+  for (int rl = warp; rl < kBucketRows; rl += kRfWarps) {
     const int64_t row = (int64_t)mb * kBucketRows + rl;
     if (row >= prm.rows) break;
+    const uint32_t* bmr = Bm + row;
     const float* om_row = Om + row * prm.ldo;
+    int len = 0;
+    __syncwarp();  // the previous row's list has been read
+    int64_t wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
+    __syncwarp();
+    rf_values(om_row, lcol, lval, len, lane);
+    __syncwarp();
+    const bool whole = wn >= nchunks;  // the list holds the whole row
     for (int64_t c0 = 0; c0 < prm.n; c0 += kPass) {
       float acc[kRfColsPerLane];
 #pragma unroll
       for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
-      int64_t j[4] = {0, 0, 0, 0};
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      int np = 0;  // entries waiting in j / v (warp-uniform)
-      uint32_t next_word = (lane < nchunks) ? Bm[(int64_t)lane * prm.ldbm + row] : 0u;
-      for (int64_t g = 0; g < nchunks; g += 32) {
-        // this group's words; the next group's are read before this one's
-        // nonzeros are worked
-        const uint32_t word = next_word;
-        next_word = (g + 32 + lane < nchunks) ? Bm[(g + 32 + lane) * prm.ldbm + row] : 0u;
-        uint32_t live = __ballot_sync(0xffffffffu, word != 0u);
-        while (live != 0u) {
-          const int src = __ffs(live) - 1;
-          live &= live - 1u;
-          uint32_t bits = __shfl_sync(0xffffffffu, word, src);
-          while (bits != 0u) {
-            const int bit = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const int64_t jj = (g + src) * 32 + bit;
-            const float vv = om_row[jj];
-            if (np == 0) { j[0] = jj; v[0] = vv; }
-            else if (np == 1) { j[1] = jj; v[1] = vv; }
-            else if (np == 2) { j[2] = jj; v[2] = vv; }
-            else { j[3] = jj; v[3] = vv; }
-            if (++np == 4) {
-              rf_apply<4>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
-              np = 0;
-            }
-          }
-        }
+      for (;;) {
+        rf_gather(acc, XT, prm.ldx, c0, prm.n, lane, lcol, lval, len);
+        if (wn >= nchunks) break;
+        // the next segment of the row, from the first word not listed
+        __syncwarp();
+        wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, wn, cap, lcol, len, lane);
+        __syncwarp();
+        rf_values(om_row, lcol, lval, len, lane);
+        __syncwarp();
       }
-      if (np == 3) rf_apply<3>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
-      else if (np == 2) rf_apply<2>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
-      else if (np == 1) rf_apply<1>(acc, XT, prm.ldx, c0, prm.n, lane, j, v);
       float* yr = Y + row * prm.ldy;
       E* hr = Yh + row * prm.ldyk;
       E* lr = Yl + row * prm.ldyk;
@@ -327,9 +415,16 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
           lr[c] = l;
         }
       }
+      if (!whole && c0 + kPass < prm.n) {
+        // a row worked in segments is listed again from its first word
+        __syncwarp();
+        wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
+        __syncwarp();
+        rf_values(om_row, lcol, lval, len, lane);
+        __syncwarp();
+      }
     }
   }
-  __shared__ double red[kRfThreads / 32][3];
   s_d = warp_sum_f(s_d);
   s_n = warp_sum_f(s_n);
   const float bad = __ballot_sync(0xffffffffu, chk != 0.f) ? 1.f : 0.f;
@@ -343,7 +438,7 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
     const int q = threadIdx.x;
     double vs = 0.0;
     if (q < 3)
-      for (int w = 0; w < nwarps; ++w) vs += red[w][q];
+      for (int w = 0; w < kRfWarps; ++w) vs += red[w][q];
     prm.part[b * prm.s_part + (int64_t)mb * kYSlots + q] = vs;
   }
 }
@@ -481,7 +576,18 @@ cudaError_t launch_sparse_y(const SparseYParams& prm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_y_refresh(const YRefreshParams& prm, cudaStream_t st) {
+static std::atomic<int> g_rf_list_cap{0};
+static std::atomic<int> g_rf_form{0};
+
+void y_refresh_set_test(int list_cap, int form) {
+  g_rf_list_cap.store(list_cap);
+  g_rf_form.store(form);
+}
+
+cudaError_t launch_y_refresh(const YRefreshParams& prm_in, cudaStream_t st) {
+  YRefreshParams prm = prm_in;
+  prm.list_cap = g_rf_list_cap.load();
+  prm.form = g_rf_form.load();
   const unsigned nb = (unsigned)(prm.nprob > 1 ? prm.nprob : 1);
   if (nb > 65535u) return cudaErrorInvalidConfiguration;
   const int64_t groups = (prm.rows + kBucketRows - 1) / kBucketRows;

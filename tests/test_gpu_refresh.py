@@ -134,3 +134,50 @@ def test_path_chain_drift(A):
     kb = int(out.best_index[longest])
     O = out.omega_best[longest].double().cpu().numpy()
     assert R.kkt_residual(O, R.grad_g(O, Xd[subs[longest]]), lams[kb], lams[kb]) <= 1e-4
+
+
+def test_refresh_forms_give_the_same_bits(A):
+    """The walk over a row's nonzeros and the blocked product form the same
+    Y bit for bit (ascending column order; a zero term adds exactly 0).  At
+    lambda = 0.05 every row of this iterate has 100 to 200 nonzeros, so the
+    walk with a list of at most 32 entries works each row in several
+    segments, and n = 700 takes two passes of output columns (512 + 188), the
+    second listing the row again.  The three fits must return the same
+    estimate in the same steps; the walk's two list sizes also give the same
+    sums (f, drift), the blocked form the same f up to the order of its FP32
+    partial sums, and f is the oracle's objective at the estimate."""
+    from paper_2412_11554_gb300 import accord
+    w = workload("hubblock", p=1000, n=700)
+    X = dev(w.X)
+    lam = 0.05
+    runs = {}
+    try:
+        for key in ((0, 1), (32, 1), (0, 2)):
+            assert accord.accord_test_refresh(*key) == 0
+            runs[key] = A.accord_fit(X, lam, precision="mixed", kkt_tol=2e-5, max_iter=5000, y_refresh=4)
+    finally:
+        assert accord.accord_test_refresh(0, 0) == 0
+    (Ow, sw), (Os, ss), (Ob, sb) = runs[(0, 1)], runs[(32, 1)], runs[(0, 2)]
+    print(f"iters {sw.iters} refreshes {sw.y_refreshes} nnz_offdiag {sw.nnz_offdiag} "
+          f"drift walk {sw.y_drift:.3e} blocked {sb.y_drift:.3e}")
+    for s in (sw, ss, sb):
+        assert s.status == 0 and s.y_refreshes >= 4, s
+    assert sw.nnz_offdiag >= 64 * 1000
+    assert torch.equal(Ow, Os) and (sw.iters, sw.trials) == (ss.iters, ss.trials)
+    assert sw.f == ss.f and sw.y_drift == ss.y_drift
+    assert torch.equal(Ow, Ob) and (sw.iters, sw.trials) == (sb.iters, sb.trials)
+    # ||Y||^2 (hence g and f) is summed in FP32 partials, over a row's columns
+    # in the walk and over the group's rows in the blocked form
+    assert abs(sw.f - sb.f) <= 1e-6 * abs(sw.f)
+    assert sw.y_drift <= 1e-5 and sb.y_drift <= 1e-5
+    f_ref = R.objective(Ow.double().cpu().numpy(), np.asarray(w.X, dtype=np.float64), lam)
+    assert abs(sw.f - f_ref) <= 1e-6 * abs(f_ref), (sw.f, f_ref)
+
+
+def test_refresh_hook_rejects_bad_arguments(A):
+    from paper_2412_11554_gb300 import accord
+    assert accord.accord_test_refresh(31, 0) == accord.EINVAL
+    assert accord.accord_test_refresh(513, 0) == accord.EINVAL
+    assert accord.accord_test_refresh(0, 3) == accord.EINVAL
+    assert accord.accord_test_refresh(0, -1) == accord.EINVAL
+    assert accord.accord_test_refresh(0, 0) == 0
