@@ -288,12 +288,13 @@ int accord_test_wait_limit(int64_t wait_limit_ns, int32_t withhold_next_prox);
 /* Testing hook for the refresh of Y = Omega X^T in the mixed modes (the paper
  * has no counterpart; Y is re-formed from the iterate so that the FP32
  * rounding of the carried Y + Delta X^T does not build up).  The refresh has
- * two forms that give the same bits: a walk over the nonzeros of each row of
- * Omega, which lists up to 512 of a row's nonzero columns at a time in shared
- * memory and works a longer row in segments, and a blocked product used from
- * p^2 / 10 nonzeros on.  For every later launch in the process,
- *   list_cap: 0 for the walk's full list of 512, or 32 .. 512 to list fewer
- *             nonzeros at a time (more segments per row);
+ * two forms that give the same bits: a walk over the nonzeros of Omega, and a
+ * blocked product used from p^2 / 10 nonzeros on.  The walk lists the
+ * nonzero columns of a group of 32 rows together when they number at most
+ * 4096, and otherwise row by row, up to 512 of a row at a time, working a
+ * longer row in segments.  For every later launch in the process,
+ *   list_cap: 0 for that choice, or 32 .. 512 to walk every group row by row
+ *             with at most that many of a row's nonzeros listed at a time;
  *   form:     0 to choose by the nonzero count, 1 the walk, 2 the blocked form.
  * Returns ACCORD_OK, or ACCORD_EINVAL for values outside those ranges.  The
  * results do not depend on either setting, only the time does. */

@@ -212,22 +212,27 @@ __global__ void delta_planes_kernel(const Ctrl* ctrl, const float* om0, const fl
 //     Y[i, :] = sum_{j : omega_ij != 0} omega_ij X^T[j, :]               (FP32)
 //
 // from the nonzeros of Omega^t (its occupancy bitmap), in ascending j, in
-// place of Y[cur] and its hi/lo operand planes.  One warp a row.  The warp
-// first lists the row's nonzero columns in shared memory: each lane reads one
-// occupancy word of a 32-word group, eight groups in flight, and a warp scan
-// of the words' bit counts places every word's columns in ascending order;
-// then the lanes read the values omega_ij of the listed columns.  The
-// gathers take the list four entries at a time (four X^T rows in flight per
-// lane) into the row's output columns held in registers (16 a lane, 512 a
-// pass).  A row with more nonzeros than the list holds is worked in segments
-// of whole words, in order; a row that fits is listed once for all passes.
-// Per 32-row group it writes ||Y_old - Y_new||^2 and ||Y_new||^2 for the
-// drift statistic and g.
+// place of Y[cur] and its hi/lo operand planes.  One CTA per 32-row group.
+// Its warps first list the group's nonzero columns in shared memory, row by
+// row in ascending order: each warp takes a slice of the chunks, and a warp
+// load fetches the group's 32 words of a chunk (lane = row, consecutive
+// words); the rows' bit counts give each row's start and each slice's start
+// within it, and a second read of the words places the columns.  All threads
+// then read the values omega_ij of the listed columns.  Then one warp a row:
+// the gathers take the row's list four entries at a time (four X^T rows in
+// flight per lane) into its output columns held in registers (16 a lane, 512
+// a pass).  A group with more nonzeros than the list holds is worked row by
+// row instead: the warp lists its row's columns from the row's words (32
+// chunks a warp load, eight loads in flight), 512 at a time, and a longer
+// row in segments of whole words, in order.  Per 32-row group it writes
+// ||Y_old - Y_new||^2 and ||Y_new||^2 for the drift statistic and g.
 constexpr int kRfThreads = 256;
 constexpr int kRfWarps = kRfThreads / 32;
 constexpr int kRfColsPerLane = 16;
-constexpr int kRfListCap = 512;  // nonzeros of a row listed at once
-constexpr int kRfGroups = 8;     // 32-word groups of a row read together
+constexpr int kRfGroupCap = 4096;                   // nonzeros of a 32-row group listed together
+constexpr int kRfListCap = kRfGroupCap / kRfWarps;  // nonzeros of a row listed at once by the row walk
+constexpr int kRfGroups = 8;                        // 32-word groups of a row read together by the row walk
+constexpr int kRfBatch = 16;                        // chunks of the group's words in flight per warp
 constexpr int kRdMaxThreads = 512;
 
 // A dense iterate makes the one-warp-a-row walk gather one X^T row per entry
@@ -342,11 +347,51 @@ __device__ __forceinline__ void rf_gather(float (&acc)[kRfColsPerLane], const fl
   else if (r == 1) rf_apply<1>(acc, XT, ldx, c0, n, lane, col + k, val + k);
 }
 
+// Y[row, c0 + lane + 32 u] = acc[u] with its planes, for the columns below n,
+// and the drift and norm sums of the group's partial row.
+template <int PT>
+__device__ __forceinline__ void rf_store(const float (&acc)[kRfColsPerLane], float* __restrict__ yr,
+                                         typename Plane<PT>::E* __restrict__ hr, typename Plane<PT>::E* __restrict__ lr,
+                                         int64_t c0, int64_t n, int lane, float& s_d, float& s_n, float& chk) {
+  using E = typename Plane<PT>::E;
+#pragma unroll
+  for (int u = 0; u < kRfColsPerLane; ++u) {
+    const int64_t c = c0 + lane + 32 * u;
+    if (c < n) {
+      const float yn = acc[u];
+      const float d = yn - yr[c];
+      s_d = fmaf(d, d, s_d);
+      s_n = fmaf(yn, yn, s_n);
+      chk = fmaf(yn, 0.f, chk);
+      yr[c] = yn;
+      E h, l;
+      Plane<PT>::split(yn, h, l);
+      hr[c] = h;
+      lr[c] = l;
+    }
+  }
+}
+
+// The words of chunks c .. c + kRfBatch (below ce) of one row, lane = row of
+// the group: one 128-byte load per chunk for the warp.
+__device__ __forceinline__ void rf_group_words(const uint32_t* __restrict__ Bm, int64_t ldbm, int64_t row, bool rok,
+                                               int64_t c, int64_t ce, int64_t nchunks, uint32_t last_mask,
+                                               uint32_t (&wd)[kRfBatch]) {
+#pragma unroll
+  for (int q = 0; q < kRfBatch; ++q) {
+    const int64_t cc = c + q;
+    wd[q] = (rok && cc < ce) ? Bm[cc * ldbm + row] : 0u;
+    if (cc == nchunks - 1) wd[q] &= last_mask;
+  }
+}
+
 template <int PT>
 __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams prm) {
   using E = typename Plane<PT>::E;
-  __shared__ uint32_t s_col[kRfWarps][kRfListCap];
-  __shared__ float s_val[kRfWarps][kRfListCap];
+  __shared__ uint32_t s_col[kRfGroupCap];
+  __shared__ float s_val[kRfGroupCap];
+  __shared__ int s_cnt[kRfWarps][32];
+  __shared__ int s_start[33];
   __shared__ double red[kRfWarps][3];
   int b = blockIdx.y;
   if (prm.active != nullptr) {
@@ -365,63 +410,132 @@ __global__ void __launch_bounds__(kRfThreads, 2) y_refresh_kernel(YRefreshParams
   const int mb = blockIdx.x;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t nchunks = (prm.p + 31) / 32;
-  const int cap = (prm.list_cap >= 32 && prm.list_cap <= kRfListCap) ? prm.list_cap : kRfListCap;
+  const int64_t r0 = (int64_t)mb * kBucketRows;
+  const uint32_t last_mask = (prm.p & 31) ? (1u << (prm.p & 31)) - 1u : 0xFFFFFFFFu;
   constexpr int kPass = 32 * kRfColsPerLane;
-  uint32_t* lcol = s_col[warp];
-  float* lval = s_val[warp];
   float s_d = 0.f, s_n = 0.f, chk = 0.f;
-  for (int rl = warp; rl < kBucketRows; rl += kRfWarps) {
-    const int64_t row = (int64_t)mb * kBucketRows + rl;
-    if (row >= prm.rows) break;
-    const uint32_t* bmr = Bm + row;
-    const float* om_row = Om + row * prm.ldo;
-    int len = 0;
-    __syncwarp();  // the previous row's list has been read
-    int64_t wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
-    __syncwarp();
-    rf_values(om_row, lcol, lval, len, lane);
-    __syncwarp();
-    const bool whole = wn >= nchunks;  // the list holds the whole row
-    for (int64_t c0 = 0; c0 < prm.n; c0 += kPass) {
-      float acc[kRfColsPerLane];
+
+  // The group's nonzeros, counted per row (lane) in this warp's slice of the
+  // chunks; then each row's start in the group list and each slice's start
+  // within the row.
+  const int64_t slice = (nchunks + kRfWarps - 1) / kRfWarps;
+  const int64_t cb = min(nchunks, (int64_t)warp * slice), ce = min(nchunks, cb + slice);
+  const int64_t grow = r0 + lane;
+  const bool rok = grow < prm.rows;
+  int cnt = 0;
+  for (int64_t c = cb; c < ce; c += kRfBatch) {
+    uint32_t wd[kRfBatch];
+    rf_group_words(Bm, prm.ldbm, grow, rok, c, ce, nchunks, last_mask, wd);
 #pragma unroll
-      for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
-      for (;;) {
-        rf_gather(acc, XT, prm.ldx, c0, prm.n, lane, lcol, lval, len);
-        if (wn >= nchunks) break;
-        // the next segment of the row, from the first word not listed
-        __syncwarp();
-        wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, wn, cap, lcol, len, lane);
-        __syncwarp();
-        rf_values(om_row, lcol, lval, len, lane);
-        __syncwarp();
-      }
-      float* yr = Y + row * prm.ldy;
-      E* hr = Yh + row * prm.ldyk;
-      E* lr = Yl + row * prm.ldyk;
+    for (int q = 0; q < kRfBatch; ++q) cnt += __popc(wd[q]);
+  }
+  s_cnt[warp][lane] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    int run = 0;
+    for (int w = 0; w < kRfWarps; ++w) {
+      const int t = s_cnt[w][lane];
+      s_cnt[w][lane] = run;
+      run += t;
+    }
+    int incl = run;
 #pragma unroll
-      for (int u = 0; u < kRfColsPerLane; ++u) {
-        const int64_t c = c0 + lane + 32 * u;
-        if (c < prm.n) {
-          const float yn = acc[u];
-          const float d = yn - yr[c];
-          s_d = fmaf(d, d, s_d);
-          s_n = fmaf(yn, yn, s_n);
-          chk = fmaf(yn, 0.f, chk);
-          yr[c] = yn;
-          E h, l;
-          Plane<PT>::split(yn, h, l);
-          hr[c] = h;
-          lr[c] = l;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    s_start[lane] = incl - run;
+    if (lane == 31) s_start[32] = incl;
+  }
+  __syncthreads();
+  const int total = s_start[32];
+
+  if (total <= kRfGroupCap && prm.list_cap == 0) {
+    // The group list: each row's columns in ascending order (the slices are
+    // in chunk order, the words in a slice too, the bits of a word too).
+    int pos = s_start[lane] + s_cnt[warp][lane];
+    for (int64_t c = cb; c < ce; c += kRfBatch) {
+      uint32_t wd[kRfBatch];
+      rf_group_words(Bm, prm.ldbm, grow, rok, c, ce, nchunks, last_mask, wd);
+#pragma unroll
+      for (int q = 0; q < kRfBatch; ++q) {
+        uint32_t bits = wd[q];
+        const uint32_t base = (uint32_t)((c + q) * 32);
+        while (bits != 0u) {
+          const int bit = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          s_col[pos++] = base + (uint32_t)bit;
         }
       }
-      if (!whole && c0 + kPass < prm.n) {
-        // a row worked in segments is listed again from its first word
-        __syncwarp();
-        wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
-        __syncwarp();
-        rf_values(om_row, lcol, lval, len, lane);
-        __syncwarp();
+    }
+    __syncthreads();
+    // the values: entry k belongs to the row r with s_start[r] <= k < s_start[r + 1]
+    for (int k = threadIdx.x; k < total; k += kRfThreads) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_start[mid] <= k) lo = mid;
+        else hi = mid;
+      }
+      s_val[k] = __ldg(Om + (r0 + lo) * prm.ldo + s_col[k]);
+    }
+    __syncthreads();
+    for (int rl = warp; rl < kBucketRows; rl += kRfWarps) {
+      const int64_t row = r0 + rl;
+      if (row >= prm.rows) break;
+      const int k0 = s_start[rl], len = s_start[rl + 1] - k0;
+      for (int64_t c0 = 0; c0 < prm.n; c0 += kPass) {
+        float acc[kRfColsPerLane];
+#pragma unroll
+        for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
+        rf_gather(acc, XT, prm.ldx, c0, prm.n, lane, s_col + k0, s_val + k0, len);
+        rf_store<PT>(acc, Y + row * prm.ldy, Yh + row * prm.ldyk, Yl + row * prm.ldyk, c0, prm.n, lane, s_d, s_n,
+                     chk);
+      }
+    }
+  } else {
+    // Too many for the group list (or the testing hook asks for it): one
+    // warp a row, each with a list of its own in the warp's share of the
+    // buffers, worked in segments of whole words when the row does not fit.
+    const int cap = (prm.list_cap >= 32 && prm.list_cap <= kRfListCap) ? prm.list_cap : kRfListCap;
+    uint32_t* lcol = s_col + warp * kRfListCap;
+    float* lval = s_val + warp * kRfListCap;
+    for (int rl = warp; rl < kBucketRows; rl += kRfWarps) {
+      const int64_t row = r0 + rl;
+      if (row >= prm.rows) break;
+      const uint32_t* bmr = Bm + row;
+      const float* om_row = Om + row * prm.ldo;
+      int len = 0;
+      __syncwarp();  // the previous row's list has been read
+      int64_t wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
+      __syncwarp();
+      rf_values(om_row, lcol, lval, len, lane);
+      __syncwarp();
+      const bool whole = wn >= nchunks;  // the list holds the whole row
+      for (int64_t c0 = 0; c0 < prm.n; c0 += kPass) {
+        float acc[kRfColsPerLane];
+#pragma unroll
+        for (int u = 0; u < kRfColsPerLane; ++u) acc[u] = 0.f;
+        for (;;) {
+          rf_gather(acc, XT, prm.ldx, c0, prm.n, lane, lcol, lval, len);
+          if (wn >= nchunks) break;
+          // the next segment of the row, from the first word not listed
+          __syncwarp();
+          wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, wn, cap, lcol, len, lane);
+          __syncwarp();
+          rf_values(om_row, lcol, lval, len, lane);
+          __syncwarp();
+        }
+        rf_store<PT>(acc, Y + row * prm.ldy, Yh + row * prm.ldyk, Yl + row * prm.ldyk, c0, prm.n, lane, s_d, s_n,
+                     chk);
+        if (!whole && c0 + kPass < prm.n) {
+          // a row worked in segments is listed again from its first word
+          __syncwarp();
+          wn = rf_list(bmr, prm.ldbm, prm.p, nchunks, 0, cap, lcol, len, lane);
+          __syncwarp();
+          rf_values(om_row, lcol, lval, len, lane);
+          __syncwarp();
+        }
       }
     }
   }
