@@ -243,14 +243,15 @@ struct YRefreshParams {
   const int32_t* nactive;
   int64_t s_om, s_bm, s_y, s_yk, s_xt, s_part;  // per-problem strides (elements / words / doubles)
   double dense_nnz;        // off-diagonal nonzeros of Omega from which the blocked (dense) form runs
-  // set by launch_y_refresh from the testing hook: nonzeros of a row listed
-  // at once by the walk (0: its full list), and the form (0: by dense_nnz,
-  // 1: the walk, 2: the blocked product)
+  // set by launch_y_refresh from the testing hook: 0 to list a 32-row
+  // group's nonzeros together when they fit, else the nonzeros of a row the
+  // row-by-row walk lists at once; and the form (0: by dense_nnz, 1: the
+  // walk, 2: the blocked product)
   int32_t list_cap, form;
 };
-// Two kernels per call: the one-warp-a-row walk over Omega's nonzeros, and a
-// blocked product for a problem with at least dense_nnz nonzeros; each
-// problem takes exactly one of them.
+// Two kernels per call: the walk over Omega's nonzeros (listed per 32-row
+// group, then gathered one warp a row), and a blocked product for a problem
+// with at least dense_nnz nonzeros; each problem takes exactly one of them.
 cudaError_t launch_y_refresh(const YRefreshParams& prm, cudaStream_t st);
 // Testing hook (accord_test_refresh): list_cap and form for later launches.
 void y_refresh_set_test(int list_cap, int form);

@@ -235,10 +235,10 @@ constexpr int kRfGroups = 8;                        // 32-word groups of a row r
 constexpr int kRfBatch = 16;                        // chunks of the group's words in flight per warp
 constexpr int kRdMaxThreads = 512;
 
-// A dense iterate makes the one-warp-a-row walk gather one X^T row per entry
-// of Omega; from this many nonzeros on (YRefreshParams::dense_nnz, a tenth
-// of the entries) the refresh runs as a blocked product instead.  A testing
-// hook may fix the form (form 1: the walk, 2: the blocked product).
+// A dense iterate makes the walk gather one X^T row per entry of Omega;
+// from this many nonzeros on (YRefreshParams::dense_nnz, a tenth of the
+// entries) the refresh runs as a blocked product instead.  A testing hook
+// may fix the form (form 1: the walk, 2: the blocked product).
 __device__ __forceinline__ bool refresh_is_dense(const YRefreshParams& prm, const Ctrl& c) {
   if (prm.form == 1) return false;
   if (prm.form == 2) return true;
