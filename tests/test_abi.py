@@ -401,3 +401,20 @@ def test_binding_constants_match_the_header():
         assert int(defs["ACCORD_" + name]) == val, name
     for col in ("f", "kkt", "tau", "ntrials", "nnz", "delta", "g"):
         assert int(defs["ACCORD_TRACE_" + col.upper()]) == accord.TRACE_COLUMNS.index(col), col
+
+
+def test_testing_hooks_check_their_arguments_on_the_host(lib):
+    """The two testing hooks only set process-wide values for later launches:
+    out-of-range values are rejected and the defaults restored, all without a
+    device."""
+    from paper_2412_11554_gb300 import accord
+    try:
+        assert lib.accord_test_wait_limit(-1, 0) == accord.EINVAL
+        assert lib.accord_test_wait_limit(0, 2) == accord.EINVAL
+        for cap, form in ((31, 0), (513, 0), (0, -1), (0, 3), (-5, 1)):
+            assert lib.accord_test_refresh(cap, form) == accord.EINVAL, (cap, form)
+        for cap, form in ((32, 1), (512, 2), (0, 1)):
+            assert lib.accord_test_refresh(cap, form) == accord.OK, (cap, form)
+    finally:
+        assert lib.accord_test_refresh(0, 0) == accord.OK
+        assert lib.accord_test_wait_limit(0, 0) == accord.OK
