@@ -49,6 +49,8 @@ def parse(argv=None):
                     help="one-product gradients while the KKT residual is above this (0: three products throughout)")
     ap.add_argument("--fp64-iters", type=int, default=2, help="FP64 iterations timed for the comparison (0: skip)")
     ap.add_argument("--tf32-fits", type=int, default=1, help="TF32x3 fits timed for the comparison (0: skip)")
+    ap.add_argument("--refresh-cost-fits", type=int, default=3,
+                    help="fits each with and without the refresh of Y, to report what the refresh costs (0: skip)")
     ap.add_argument("--fp64-full", action="store_true",
                     help="also run one whole FP64 fit to the same KKT tolerance (several minutes at p=40000), "
                          "timed, and grade the mixed estimate against it (rel. Frobenius, support, FP64 KKT)")
@@ -415,6 +417,23 @@ def run_ours(args):
                 "tf32_peak_tflops": round(peak32, 1),
                 "peak_note": "measured sustained BF16 peak x nominal TF32/BF16 ratio 1.1/2.25"}
 
+    # ----- what the refresh of Y costs a fit: the same fits without it -----
+    refresh_cost = None
+    if args.refresh_cost_fits > 0:
+        def time_fit(fn):
+            e4 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            e4[0].record(stream)
+            res = fn()
+            e4[1].record(stream)
+            torch.cuda.synchronize()
+            return e4[0].elapsed_time(e4[1]), res
+
+        try:
+            refresh_cost = refresh_cost_leg(A, X, w.lam, fit_kw, args.refresh_cost_fits, time_fit)
+        except Exception as exc:  # an informational leg: it never takes the bench line down with it
+            refresh_cost = {"error": f"{type(exc).__name__}: {exc}"}
+
     fp64_full = None
     if args.fp64_full and rank == 0:
         fp64_full = fp64_full_leg(A, X, w, Om, stats[-1], args.kkt_tol)
@@ -449,7 +468,7 @@ def run_ours(args):
             "final_kkt": stats[-1].kkt if stats else None, "status": stats[-1].status if stats else None,
             "gpu_launches": int(sum(s.n_launches for s in stats)),
             "y_refresh": {"refreshes_per_fit": sum(s.y_refreshes for s in stats) / max(len(stats), 1),
-                          "max_drift": max((s.y_drift for s in stats), default=0.0)},
+                          "max_drift": max((s.y_drift for s in stats), default=0.0), "cost": refresh_cost},
             "roofline": roofline, "e2e": e2e, "e2e_dense_omega": e2e_dense, "fp64_gpu": fp64, "tf32x3_gpu": tf32,
             "fp64_full": fp64_full,
             "cpu_baseline": cpu,
@@ -459,6 +478,29 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def refresh_cost_leg(A, X, lam, fit_kw, k, time_fit):
+    """What the refresh of Y costs a fit. The default refreshes every 32
+    accepted steps, before a predicted passing KKT test, and before a stop;
+    y_refresh = 0 carries Y through the whole fit instead. The two run in
+    alternation, k fits each, timed by time_fit(fn) -> (ms, fn()). Reports the
+    median times, their difference, and each fit's iterations and prox
+    launches: a refresh can repeat a passing KKT test on the fresh Y."""
+    times = {32: [], 0: []}
+    last = {}
+    for _ in range(k):
+        for yr in (0, 32):  # the default last: the caller's Omega buffer ends with its estimate
+            ms, (_, st) = time_fit(lambda yr=yr: A.accord_fit(X, lam, y_refresh=yr, **fit_kw))
+            times[yr].append(ms)
+            last[yr] = st
+    med = {yr: sorted(t)[len(t) // 2] for yr, t in times.items()}
+    with_, without = last[32], last[0]
+    return {"fits_each": k, "fit_ms_with": round(med[32], 2), "fit_ms_without": round(med[0], 2),
+            "cost_ms_per_fit": round(med[32] - med[0], 2), "refreshes_per_fit": with_.y_refreshes,
+            "iters_with": with_.iters, "iters_without": without.iters,
+            "prox_launches_with": with_.n_prox_gemm, "prox_launches_without": without.n_prox_gemm,
+            "final_kkt_without": without.kkt}
 
 
 def _kkt_and_support(O32, O64, Gm64, G64, lam, s_diag, band, rows=2000):

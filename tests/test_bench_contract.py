@@ -109,3 +109,33 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     cs.start()
     assert cs.stop() is None
     assert not os.path.exists(cs.path)          # no temp file left behind
+
+
+def test_refresh_cost_leg_alternates_and_reports_the_difference():
+    """The refresh-cost leg alternates fits without and with the refresh of Y,
+    ends on the default (so the caller's Omega buffer holds its estimate), and
+    reports the median times and their difference."""
+    calls = []
+
+    class Stats:
+        def __init__(self, yr):
+            self.y_refreshes, self.iters, self.n_prox_gemm, self.kkt = (2, 41, 46, 9e-5) if yr else (0, 41, 45, 8e-5)
+
+    class FakeLib:
+        @staticmethod
+        def accord_fit(X, lam, y_refresh, **kw):
+            assert kw == {"precision": "mixed"} and lam == 0.1
+            calls.append(y_refresh)
+            return None, Stats(y_refresh)
+
+    ms = {0: iter([300.0, 302.0, 301.0]), 32: iter([311.0, 309.0, 310.0])}
+
+    def time_fit(fn):
+        res = fn()
+        return next(ms[calls[-1]]), res
+
+    out = bench.refresh_cost_leg(FakeLib, "X", 0.1, {"precision": "mixed"}, 3, time_fit)
+    assert calls == [0, 32] * 3
+    assert out["fit_ms_with"] == 310.0 and out["fit_ms_without"] == 301.0 and out["cost_ms_per_fit"] == 9.0
+    assert (out["refreshes_per_fit"], out["prox_launches_with"], out["prox_launches_without"]) == (2, 46, 45)
+    assert out["fits_each"] == 3 and out["final_kkt_without"] == 8e-5
